@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Benchmark: env-steps/s of the fused persistent Fossen step on domain-randomised fleets.
+
+One benchmark step is one episode over the whole hot path: domain randomisation with the FP64
+mass-matrix inverse, reset, loading the episode's throttle schedule, 1,000 RK4 sub-steps
+(persistent kernel, 50 sub-steps per launch, replayed from one CUDA graph) and the state
+read-back.  Prints one JSON line.
+
+  python bench.py [--gpus N --steps K --warmup W]     # this library (default)
+  python bench.py --impl reference ...                 # the FP64 CPU oracle on the host cores
+
+Under torchrun (N > 1) every rank steps its own fleet (env ids offset by rank: weak scaling, no
+collective in the data path); the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "env-steps/s at 64K envs (fused vs per-step, same GPU); p50/p99 serve latency"
+
+# Algorithmic FP32 work per env and sub-step of the diagonal-mass step (FMA = 2 flops), counted
+# from the arithmetic of Eq. 1 + RK4 as the kernel performs it: 4 right-hand sides (6 thrusters:
+# 288 flops each; 8 thrusters: 318) + RK4 stage updates and combination (248 / 280) + quaternion
+# renormalisation (15).
+FLOPS_PER_ENV_STEP = {6: 4 * 288 + 248 + 15, 8: 4 * 318 + 280 + 15}
+# Algorithmic HBM bytes per env of one launch: state read + written ((13 + n_thr) floats each),
+# the 34 parameter floats of the diagonal-mass step, and one command vector per segment.
+STATE_BYTES = {6: 19 * 4, 8: 21 * 4}
+PARAM_BYTES = 34 * 4
+CMD_BYTES = {6: 6 * 4, 8: 8 * 4}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n-envs", type=int, default=65536)
+    ap.add_argument("--horizon", type=int, default=1000)
+    ap.add_argument("--k", type=int, default=50, help="sub-steps per persistent launch")
+    ap.add_argument("--epb", type=int, default=128, help="envs per block")
+    ap.add_argument("--hold", type=int, default=10)
+    ap.add_argument("--no-per-step", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_alu_peak_tflops(sm_mhz, n_sm=152):
+    # 4 sub-partitions x 32 FP32 lanes per SM, one FMA (2 flops) per lane per cycle.
+    return n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.path = None
+        self.dev = device_index
+
+    def start(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 8:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------- CPU baseline
+
+def cpu_baseline(n_envs, horizon, hold, target_s=12.0):
+    """The FP64 oracle as it stands, on the host cores, over a bounded sample of the same
+    workload (randomised BlueROV2 fleet with current, same command process)."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2410_14117_gb300 import inputs as I
+
+    vs = I.fleet_vehicles()
+    nominal = np.stack([I.round_f32(v.params) for v in vs])
+    geo = np.stack([I.round_f32(v.geo()) for v in vs])
+
+    def run(ns, steps):
+        types = np.zeros(ns, dtype=np.int32)
+        par = I.round_f32(O.randomize(1234, nominal, types, float(np.float32(0.8)),
+                                      float(np.float32(1.2)), float(np.float32(0.2))))
+        s0 = I.initial_states(21, ns)
+        cmd = I.commands(5678, max(1, math.ceil(steps / hold)), ns, 6).astype(np.float64)
+        t = time.perf_counter()
+        O.rollout(par, geo, types, s0, cmd, hold, steps, h=0.01)
+        return time.perf_counter() - t
+
+    ns = min(n_envs, 4096)
+    probe = run(ns, 20)
+    rate = ns * 20 / probe
+    steps = int(max(20, min(horizon, target_s * rate / ns)))
+    dt = run(ns, steps)
+    return {"value": ns * steps / dt, "unit": "env-steps/s", "cores": O.max_threads(),
+            "kind": "oracle",
+            "sample": f"{ns} envs x {steps} sub-steps of the same randomised BlueROV2 workload "
+                      f"(FP64 oracle, OpenMP over envs), {dt:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores, same metric and workload."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2410_14117_gb300 import inputs as I
+
+    vs = I.fleet_vehicles()
+    nominal = np.stack([I.round_f32(v.params) for v in vs])
+    geo = np.stack([I.round_f32(v.geo()) for v in vs])
+    ns = min(args.n_envs, 2048)
+    types = np.zeros(ns, dtype=np.int32)
+    par = I.round_f32(O.randomize(1234, nominal, types, float(np.float32(0.8)),
+                                  float(np.float32(1.2)), float(np.float32(0.2))))
+    s0 = I.initial_states(21, ns)
+    # size one step to ~0.5 s of host work
+    t = time.perf_counter()
+    O.rollout(par, geo, types, s0, I.commands(5678, 2, ns, 6).astype(np.float64), args.hold, 20)
+    rate = ns * 20 / (time.perf_counter() - t)
+    steps = int(max(10, min(args.horizon, 0.5 * rate / ns)))
+    cmd = I.commands(5678, math.ceil(steps / args.hold), ns, 6).astype(np.float64)
+    for _ in range(args.warmup):
+        O.rollout(par, geo, types, s0, cmd, args.hold, steps)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        O.rollout(par, geo, types, s0, cmd, args.hold, steps)
+        times.append(time.perf_counter() - t)
+    total = sum(times)
+    value = ns * steps * args.steps / total
+    sample = (f"{ns} envs x {steps} sub-steps per step of the 65,536-env randomised BlueROV2 "
+              f"workload (FP64 oracle, OpenMP over envs)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "env-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args),
+            "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": O.max_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args):
+    return {"workload": f"{args.n_envs:,} domain-randomised BlueROV2 envs (params U[0.8,1.2]"
+                        f"x nominal, NED current N(0,0.2)), {args.horizon:,} RK4 sub-steps of "
+                        f"0.01 s per episode, commands U[-1,1] held {args.hold} sub-steps; "
+                        f"persistent k={args.k} under one CUDA graph",
+            "n_envs": args.n_envs, "horizon": args.horizon, "steps_per_launch": args.k,
+            "envs_per_block": args.epb,
+            "l2": "flushed between timed steps (256 MB write, outside the events)"}
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2410_14117_gb300 import inputs as I
+    from paper_2410_14117_gb300.sim import Sim
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    n, horizon, hold, k = args.n_envs, args.horizon, args.hold, args.k
+    vs = I.fleet_vehicles()
+    sim = Sim(n, np.zeros(n, dtype=np.int32), vs)
+    sim.set_env_id_offset(rank * n)
+    sim.set_launch(args.epb, k, True)
+    n_seg = math.ceil(horizon / hold)
+    acts_np = I.commands(5678 + rank, n_seg, n, 6)
+    acts_host = torch.from_numpy(acts_np).pin_memory()
+    acts_dev = acts_host.to(dev)
+    out_dev = torch.empty((n, 21), dtype=torch.float32, device=dev)
+    out_host = torch.empty((n, 21), dtype=torch.float32).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    launches_per_episode = math.ceil(horizon / k)
+
+    def episode(seed, a, out):
+        sim.randomize(seed, 0.8, 1.2, 0.2, 0.3)
+        sim.reset()
+        sim.set_actions(a, hold)
+        sim.step(horizon)
+        sim.get_state(out)
+
+    for w in range(max(args.warmup, 3)):
+        episode(1000 + w, acts_dev, out_dev)
+    torch.cuda.synchronize()
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    barrier = (lambda: torch.distributed.barrier()) if world > 1 else (lambda: None)
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(args.steps):
+        flush.zero_()
+        e0, e1, e2 = ev[i]
+        e0.record(stream)
+        sim.randomize(2000 + i, 0.8, 1.2, 0.2, 0.3)
+        sim.reset()
+        sim.set_actions(acts_dev, hold)
+        e1.record(stream)
+        sim.step(horizon)
+        e2.record(stream)
+        sim.get_state(out_dev)
+        ev[i].append(torch.cuda.Event(enable_timing=True))
+        ev[i][3].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
+    graph_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * n * horizon * args.steps / (total_ms / 1e3)
+
+    peaks, peak_kind = load_peaks()
+    launch_s = statistics.mean(graph_ms) / 1e3 / launches_per_episode
+    flops = FLOPS_PER_ENV_STEP[6] * n * k
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = fp32_alu_peak_tflops(sm_max)
+    achieved = flops / launch_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": None,
+                "kernel": "k_fleet (persistent, 6 thrusters, diagonal mass)",
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 flops x {sm_max:.0f} MHz "
+                               f"({peak_kind} max SM clock)",
+                "flops_per_env_step": FLOPS_PER_ENV_STEP[6],
+                "launch_ms": launch_s * 1e3}
+
+    line = {"metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": workload_config(args), "roofline": roofline,
+            "clocks": clk,
+            "gpu_launches": args.steps * (launches_per_episode + 3)}
+
+    # ---- end to end through the public API with host buffers
+    if not args.no_e2e:
+        ke = min(args.steps, 10)
+        episode(1, acts_host, out_host)
+        torch.cuda.synchronize()
+        barrier()
+        t = time.perf_counter()
+        for i in range(ke):
+            episode(3000 + i, acts_host, out_host)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t
+        if world > 1:
+            tt = torch.tensor([el], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            el = float(tt.item())
+        line["e2e"] = {"value": world * n * horizon * ke / el, "unit": "env-steps/s",
+                       "h2d_bytes_per_step": acts_np.nbytes,
+                       "d2h_bytes_per_step": n * 21 * 4,
+                       "note": "throttle schedule H2D from pinned host and final state D2H "
+                               "inside the timed region; wall clock"}
+
+    # ---- the plain per-step form on the same GPU (one launch per sub-step)
+    if not args.no_per_step:
+        sim.set_actions(acts_dev, hold)
+        sim.set_launch(args.epb, 1, False)
+        sim.randomize(7, 0.8, 1.2, 0.2, 0.3)
+        sim.reset()
+        for _ in range(50):
+            sim.step(1)
+        reps = 2
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            sim.set_actions(acts_dev, hold)
+            for _ in range(horizon):
+                sim.step(1)
+        b.record(stream)
+        torch.cuda.synchronize()
+        host_ms = a.elapsed_time(b) / reps
+        sim.set_launch(args.epb, 1, True)
+        sim.set_actions(acts_dev, hold)
+        sim.step(horizon)  # capture
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            sim.set_actions(acts_dev, hold)
+            sim.step(horizon)
+        b.record(stream)
+        torch.cuda.synchronize()
+        graph_ms_ps = a.elapsed_time(b) / reps
+        per_launch_s = graph_ms_ps / 1e3 / horizon
+        bytes_per_launch = n * (2 * STATE_BYTES[6] + PARAM_BYTES + CMD_BYTES[6])
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        ach = bytes_per_launch / per_launch_s / 1e9
+        fused_ms_episode = statistics.mean(graph_ms)
+        line["per_step"] = {
+            "host_launched": n * horizon / (host_ms / 1e3),
+            "graph": n * horizon / (graph_ms_ps / 1e3),
+            "fused_sub_steps_only": n * horizon / (fused_ms_episode / 1e3),
+            "fused_over_host_launched": host_ms / fused_ms_episode,
+            "fused_over_graph": graph_ms_ps / fused_ms_episode,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                         "frac": ach / hbm, "bytes_per_env_step": bytes_per_launch // n,
+                         "launch_us": per_launch_s * 1e6,
+                         "peak_source": f"{peak_kind} hbm_gbs"}}
+        sim.set_launch(args.epb, k, True)
+
+    if world == 1 and rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(n, horizon, hold)
+
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

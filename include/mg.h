@@ -1,0 +1,204 @@
+/*
+ * mg.h — C ABI of the GB300 Fossen fleet stepper (libmg.so).
+ *
+ * The library advances many independent underwater vehicles ("envs") by the extended Fossen
+ * equation of §METHOD (Eq. 1):
+ *
+ *   tau = M_RB nu' + C_RB(nu) nu + g_RB(eta) + M_A nu' + C_A(nu_r) nu_r + D(nu_r) nu_r + g_A(eta)
+ *
+ * with eta the pose in NED, nu = (u,v,w,p,q,r) the body-frame velocity, nu_r the velocity
+ * relative to an ocean current constant in NED, tau the thruster wrench from per-thruster
+ * throttle actions (Eq. 3) with a first-order motor lag.  Each sub-step (§METHOD, "multiple
+ * sub-simulation steps within a single simulation step") is one classical RK4 step of size dt
+ * with the command held over the step; the attitude quaternion is renormalised after it.
+ *
+ * Conventions shared by every call:
+ *   - Body frame x forward, y starboard, z down; quaternion q = (w,x,y,z), Hamilton, body -> NED.
+ *   - A pointer argument marked "host or device" may be either; the library asks the CUDA
+ *     runtime which.  Device pointers are read or written asynchronously on the sim's stream
+ *     (mg_set_stream); a host pointer makes the call synchronous (it returns once the data has
+ *     been copied).  The caller owns every pointer it passes and may free it once the call has
+ *     returned (device inputs: once the stream has passed the call).
+ *   - The library owns every device buffer it allocates; mg_destroy frees them.
+ *   - Every call returns an mg_status.  Nothing throws across the ABI.  On failure
+ *     mg_last_error() gives a thread-local message.  Argument errors are found on the host and
+ *     change nothing.
+ *   - All floating-point state and parameters are FP32 on the device.  The 6x6 mass matrix is
+ *     inverted in FP64 when parameters change (mg_randomize, mg_set_params).
+ */
+#ifndef MG_H
+#define MG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MG_NPARAM 35   /* per-env parameter record, layout below */
+#define MG_NSTATE 21   /* per-env state record: p(3) q(4) nu(6) n(8) */
+#define MG_NTRAJ 13    /* per-env trajectory record: p(3) q(4) nu(6) */
+#define MG_MAX_THR 8   /* thrusters per vehicle type */
+#define MG_MAX_TYPES 8 /* vehicle types per sim */
+
+/* Parameter record (MG_NPARAM floats per env, "[n][MG_NPARAM]" below):
+ *   0 m | 1..3 Ixx Iyy Izz about the centre of gravity | 4..9 added mass M_A (diagonal)
+ *   10..15 linear damping (diagonal) | 16..21 quadratic damping (diagonal) | 22 W | 23 B
+ *   24..26 r_g | 27..29 r_b | 30 k_T (thrust = k_T n|n| N) | 31 tau_m (motor lag, s)
+ *   32..34 ocean current, NED, m/s */
+#define MG_P_M 0
+#define MG_P_IG 1
+#define MG_P_MA 4
+#define MG_P_DL 10
+#define MG_P_DQ 16
+#define MG_P_W 22
+#define MG_P_B 23
+#define MG_P_RG 24
+#define MG_P_RB 27
+#define MG_P_KT 30
+#define MG_P_TAU 31
+#define MG_P_VC 32
+
+typedef struct mg_sim mg_sim; /* opaque; owns all of a fleet's device buffers */
+
+typedef enum {
+  MG_OK = 0,
+  MG_EINVAL = 1,      /* bad argument; nothing changed */
+  MG_ENOMEM = 2,      /* device allocation failed */
+  MG_ECUDA = 3,       /* a CUDA runtime call failed; see mg_last_error() */
+  MG_ENONFINITE = 4,  /* some env's state became NaN/Inf (mg_sync) */
+  MG_ENOTSPD = 5,     /* some env's mass matrix M_RB + M_A is not positive definite */
+  MG_ETIMEOUT = 6,    /* a bounded wait gave up */
+  MG_ESTATE = 7       /* call not valid in the sim's current state */
+} mg_status;
+
+/* Nominal parameters and thruster geometry of one vehicle type (§METHOD: BlueROV2 and
+ * BlueROV2 Heavy).  Vectors are in the body frame above.  d[i] is a unit direction. */
+typedef struct {
+  float m, Ixx, Iyy, Izz;
+  float MA[6], Dl[6], Dq[6];
+  float W, B;
+  float rg[3], rb[3];
+  float kT, tau_m;
+  int32_t n_thr; /* 1..MG_MAX_THR */
+  float r[MG_MAX_THR][3], d[MG_MAX_THR][3];
+} mg_vehicle_params;
+
+/* Domain-randomisation ranges (§METHOD "physical parameter domain randomization"): each of the
+ * 27 scalars m, Ixx, Iyy, Izz, M_A(6), Dl(6), Dq(6), W, B, r_b.z, k_T, tau_m is scaled by
+ * U[lo, hi]; the NED current is N(0, current_sigma) per axis; mg_reset draws the initial body
+ * velocity N(0, nu0_sigma) per component.  flags must be 0. */
+typedef struct {
+  float lo, hi;
+  float current_sigma;
+  float nu0_sigma;
+  uint32_t flags;
+} mg_ranges;
+
+/* Model switch: drop the added-mass inertia of the current, M_A [omega x v_c^b; 0], which
+ * follows from nu_r' = nu' + [omega x v_c^b; 0] for a current constant in NED. */
+#define MG_MODEL_NO_CURRENT_ACCEL 1u
+
+/* Create a fleet of n_envs vehicles (§METHOD: "parallel execution of multiple environment
+ * instances").  vehicle_types: host [n_envs], values in [0, n_types).  params: host
+ * [n_types].  Each env starts with its type's nominal parameters, no current, zero state with
+ * identity attitude, zero actions.  Envs of one type that are adjacent in the index order are
+ * processed together; interleaving types costs throughput, not correctness.  The device is the
+ * caller's current CUDA device.  Errors: MG_EINVAL (n_envs < 1, n_types out of [1,
+ * MG_MAX_TYPES], a type id out of range, n_thr out of [1, MG_MAX_THR]), MG_ENOMEM, MG_ECUDA. */
+mg_status mg_create(int64_t n_envs, const int32_t *vehicle_types,
+                    const mg_vehicle_params *params, int32_t n_types, mg_sim **out);
+
+/* Free the sim and all its device buffers (synchronises its stream first). NULL is a no-op. */
+mg_status mg_destroy(mg_sim *sim);
+
+/* Stream every later call runs on (a cudaStream_t; NULL = the legacy default stream). */
+mg_status mg_set_stream(mg_sim *sim, void *cuda_stream);
+
+/* Offset added to env indices wherever they key a counter-based draw (randomisation, reset,
+ * procedural commands), so that disjoint shards of one logical fleet draw what the whole fleet
+ * would.  Default 0. */
+mg_status mg_set_env_id_offset(mg_sim *sim, int64_t offset);
+
+/* MG_MODEL_* bits.  Default 0 (full model). */
+mg_status mg_set_model_flags(mg_sim *sim, uint32_t flags);
+
+/* Sub-step size dt in seconds (default 0.01).  MG_EINVAL unless 0 < dt <= 1. */
+mg_status mg_set_timestep(mg_sim *sim, float dt);
+
+/* Launch shape: envs_per_block in [32, 256] (one thread per env), steps_per_launch >= 1 (RK4
+ * steps a kernel keeps state in registers for; 1 gives the plain per-step form), use_graph
+ * != 0 to replay mg_step's launch sequence from a cached CUDA graph.  Defaults 128, 50, 1. */
+mg_status mg_set_launch(mg_sim *sim, int32_t envs_per_block, int32_t steps_per_launch,
+                        int32_t use_graph);
+
+/* Domain randomisation (§METHOD; §EXPERIMENTS "supports domain randomization"): per env, draws
+ * from Philox4x32-10 keyed by (seed, env id + offset), then builds M = M_RB + M_A in FP64 and
+ * inverts it by Cholesky.  Also records (seed, nu0_sigma) for mg_reset and zeroes every env's
+ * episode counter.  Synchronous.  Errors: MG_EINVAL (ranges NULL, lo > hi, lo <= 0, negative
+ * sigma, flags != 0), MG_ENOTSPD (parameters are stored but some mass matrix has a pivot <= 0),
+ * MG_ECUDA. */
+mg_status mg_randomize(mg_sim *sim, uint64_t seed, const mg_ranges *ranges);
+
+/* Set every env's parameters from a [n][MG_NPARAM] record (host or device); inverts the mass
+ * matrices as mg_randomize does.  Synchronous.  Errors: MG_EINVAL, MG_ENOTSPD, MG_ECUDA. */
+mg_status mg_set_params(mg_sim *sim, const float *in);
+
+/* Copy every env's parameters into out [n][MG_NPARAM] (host or device). */
+mg_status mg_get_params(mg_sim *sim, float *out);
+
+/* Throttle actions (Eq. 3: one throttle setting per thruster).  a: host or device
+ * [n_seg][n_envs][MG_MAX_THR], entries past a vehicle's thruster count ignored.  The library
+ * copies it.  Sub-step j counted from this call (across later mg_step calls) uses segment
+ * min(j / hold_steps, n_seg - 1).  n_seg = 0 (a may be NULL) sets all commands to zero.
+ * Errors: MG_EINVAL (n_seg < 0, hold_steps < 1), MG_ENOMEM, MG_ECUDA. */
+mg_status mg_set_actions(mg_sim *sim, const float *a, int32_t n_seg, int32_t hold_steps);
+
+/* Procedural actions: throttle c_i = 2u - 1 with u from Philox4x32-10 keyed by (cmd_seed, env
+ * id + offset, segment j / hold_steps), no end.  Replaces any action buffer.  Resets the action
+ * cursor like mg_set_actions. */
+mg_status mg_set_procedural_actions(mg_sim *sim, uint64_t cmd_seed, int32_t hold_steps);
+
+/* Advance every env k >= 1 sub-steps (Eq. 1 integrated by RK4, §METHOD).  Asynchronous on the
+ * stream; non-finite states are reported by mg_sync. */
+mg_status mg_step(mg_sim *sim, int32_t k);
+
+/* As mg_step, also writing the state after every sub-step to traj: device
+ * [k][MG_NTRAJ][n_envs] (component-major per step: p(3) q(4) nu(6)). Never graph-replayed. */
+mg_status mg_step_record(mg_sim *sim, int32_t k, float *traj);
+
+/* State in the record layout [n][MG_NSTATE] = p(3) q(4: w,x,y,z) nu(6) n(8, zero past n_thr);
+ * host or device. */
+mg_status mg_get_state(mg_sim *sim, float *out);
+mg_status mg_set_state(mg_sim *sim, const float *in);
+
+/* Start a new episode for every env whose mask byte is non-zero (mask: host or device
+ * [n_envs]; NULL = all): p = 0, q = identity, n = 0, nu ~ N(0, nu0_sigma) drawn from Philox
+ * keyed by (seed, env id + offset, the env's episode counter), then the counter is
+ * incremented and the env's non-finite flag cleared. */
+mg_status mg_reset(mg_sim *sim, const uint8_t *mask);
+
+/* Wait for the stream; *nonfinite_count (may be NULL) receives how many envs are flagged
+ * non-finite.  Returns MG_ENONFINITE when that count is non-zero. */
+mg_status mg_sync(mg_sim *sim, int64_t *nonfinite_count);
+
+/* Per-env non-finite flags into out [n_envs] (host or device), 1 = flagged. */
+mg_status mg_get_nonfinite(mg_sim *sim, uint8_t *out);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char *mg_last_error(void);
+
+/* Evaluate Philox4x32-10 on the device for n (counter, key) pairs: ctr host [n][4], key host
+ * [n][2], out host [n][4].  The same generator keys every draw above; exposed so it can be
+ * checked bit for bit against the published known answers. */
+mg_status mg_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n);
+
+/* Kernel attributes of the step kernel the sim would launch now (registers per thread,
+ * maximum threads per block, local-memory bytes per thread); any pointer may be NULL. */
+mg_status mg_kernel_info(mg_sim *sim, int32_t *regs, int32_t *max_threads, int32_t *local_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MG_H */

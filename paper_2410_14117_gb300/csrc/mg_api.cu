@@ -1,0 +1,708 @@
+// Host side of the C ABI declared in include/mg.h.
+//
+// A sim owns one device arena holding the state planes, the raw parameter records, the derived
+// parameter planes, per-env flags and episode counters, the per-type thruster geometry and the
+// block list; the action buffer and a staging buffer for host I/O are separate allocations that
+// grow on demand.  Every device operation is issued on the sim's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mg_internal.h"
+
+using namespace mg;
+
+namespace {
+
+thread_local std::string g_err;
+
+mg_status fail(mg_status st, const std::string &msg) {
+  g_err = msg;
+  return st;
+}
+
+mg_status fail_cuda(cudaError_t e, const char *what) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+  return fail(e == cudaErrorMemoryAllocation ? MG_ENOMEM : MG_ECUDA, buf);
+}
+
+#define MG_CK(call)                                      \
+  do {                                                   \
+    cudaError_t _e = (call);                             \
+    if (_e != cudaSuccess) return fail_cuda(_e, #call); \
+  } while (0)
+
+#define MG_NONNULL(p) \
+  do {                \
+    if (!(p)) return fail(MG_EINVAL, #p " is NULL"); \
+  } while (0)
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// True when p can be dereferenced by a kernel (device or managed memory).
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct GraphEntry {
+  int32_t k;
+  int64_t cursor;
+  cudaGraphExec_t exec;
+  uint64_t last_use;
+};
+
+}  // namespace
+
+struct mg_sim {
+  int dev = 0;
+  int64_t n = 0;
+  int32_t n_types = 0;
+  std::vector<int32_t> types_h;
+  std::vector<mg_vehicle_params> vp;
+  NtVariant ntv = NT_6;
+  bool diag = true;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+
+  // arena
+  void *arena = nullptr;
+  StatePlanes st{};
+  ParamPlanes pa{};
+  float *raw = nullptr;
+  int32_t *types_d = nullptr;
+  Geo *geo_d = nullptr;
+  float *nominal_d = nullptr;
+  uint32_t *flags = nullptr;
+  uint32_t *episode = nullptr;
+  unsigned long long *counters = nullptr;  // [0] non-finite envs, [1] non-SPD envs
+  unsigned int *offdiag = nullptr;
+
+  // blocks
+  BlockDesc *blocks_d = nullptr;
+  int n_blocks = 0;
+  int threads = 128;
+
+  // actions
+  float *act = nullptr;
+  size_t act_cap = 0;  // floats
+  int32_t n_seg = 0, hold = 1;
+  int32_t proc = 0;
+  uint64_t cmd_seed = 0;
+  int64_t cursor = 0;
+
+  // knobs
+  int32_t epb = 128, spl = 50;
+  bool use_graph = true;
+  float dt = 0.01f;
+  uint32_t model_flags = 0;
+  int64_t gid0 = 0;
+  uint64_t reset_seed = 0;
+  double nu0_sigma = 0.0;
+
+  // staging for host I/O
+  void *stage = nullptr;
+  size_t stage_cap = 0;
+
+  std::vector<GraphEntry> graphs;
+  uint64_t graph_clock = 0;
+
+  FleetView view() const {
+    FleetView v{};
+    v.st = st;
+    v.pa = pa;
+    v.geo = geo_d;
+    v.n = n;
+    v.gid0 = gid0;
+    v.act = reinterpret_cast<const float4 *>(act);
+    v.n_seg = proc ? 0 : n_seg;
+    v.hold = hold;
+    v.cmd_seed = cmd_seed;
+    v.proc = proc;
+    v.model_flags = model_flags;
+    v.dt = dt;
+    v.flags = flags;
+    v.nonfinite_count = counters;
+    return v;
+  }
+
+  SetupView setup_view() const {
+    SetupView v{};
+    v.n = n;
+    v.gid0 = gid0;
+    v.types = types_d;
+    v.raw = raw;
+    v.pa = pa;
+    v.n_not_spd = counters + 1;
+    v.any_offdiag = offdiag;
+    return v;
+  }
+
+  void drop_graphs() {
+    for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
+    graphs.clear();
+  }
+};
+
+namespace {
+
+mg_status ensure_stage(mg_sim *s, size_t bytes) {
+  if (s->stage_cap >= bytes) return MG_OK;
+  MG_CK(cudaStreamSynchronize(s->stream));
+  if (s->stage) cudaFree(s->stage);
+  s->stage = nullptr;
+  s->stage_cap = 0;
+  MG_CK(cudaMalloc(&s->stage, bytes));
+  s->stage_cap = bytes;
+  return MG_OK;
+}
+
+// Stage a host input into device memory (synchronous w.r.t. the host buffer), or pass a device
+// pointer through.
+mg_status input_ptr(mg_sim *s, const void *in, size_t bytes, const void **dev) {
+  if (is_device_ptr(in)) {
+    *dev = in;
+    return MG_OK;
+  }
+  mg_status st = ensure_stage(s, bytes);
+  if (st != MG_OK) return st;
+  MG_CK(cudaMemcpyAsync(s->stage, in, bytes, cudaMemcpyHostToDevice, s->stream));
+  *dev = s->stage;
+  return MG_OK;
+}
+
+// Build the block list: runs of equal vehicle type, cut into chunks of at most epb envs.
+mg_status build_blocks(mg_sim *s) {
+  std::vector<BlockDesc> b;
+  int64_t e = 0;
+  while (e < s->n) {
+    const int32_t t = s->types_h[e];
+    int64_t end = e;
+    while (end < s->n && s->types_h[end] == t) ++end;
+    for (int64_t a = e; a < end; a += s->epb) {
+      BlockDesc d;
+      d.env0 = (int32_t)a;
+      d.count = (int32_t)std::min<int64_t>(s->epb, end - a);
+      d.type = t;
+      d.n_thr = s->vp[t].n_thr;
+      b.push_back(d);
+    }
+    e = end;
+  }
+  if (s->blocks_d) {
+    MG_CK(cudaStreamSynchronize(s->stream));
+    cudaFree(s->blocks_d);
+    s->blocks_d = nullptr;
+  }
+  MG_CK(cudaMalloc(&s->blocks_d, b.size() * sizeof(BlockDesc)));
+  MG_CK(cudaMemcpy(s->blocks_d, b.data(), b.size() * sizeof(BlockDesc), cudaMemcpyHostToDevice));
+  s->n_blocks = (int)b.size();
+  s->threads = (int)align_up((size_t)s->epb, 32);
+  s->drop_graphs();
+  return MG_OK;
+}
+
+mg_status launch_chunks(mg_sim *s, int32_t k, float *traj, cudaStream_t stream) {
+  const FleetView v = s->view();
+  for (int32_t done = 0; done < k;) {
+    const int32_t kk = std::min(s->spl, k - done);
+    float *t = traj ? traj + (int64_t)done * MG_NTRAJ * s->n : nullptr;
+    MG_CK(launch_fleet(v, s->blocks_d, s->n_blocks, s->threads, s->ntv, s->diag,
+                       s->cursor + done, kk, t, stream));
+    done += kk;
+  }
+  return MG_OK;
+}
+
+mg_status read_counter(mg_sim *s, int idx, unsigned long long *out) {
+  MG_CK(cudaMemcpyAsync(out, s->counters + idx, sizeof(*out), cudaMemcpyDeviceToHost,
+                        s->stream));
+  MG_CK(cudaStreamSynchronize(s->stream));
+  return MG_OK;
+}
+
+// After a parameter change: count non-SPD envs and pick the diagonal or general kernel.
+mg_status finish_params(mg_sim *s) {
+  unsigned long long bad = 0;
+  unsigned int off = 0;
+  MG_CK(cudaMemcpyAsync(&off, s->offdiag, sizeof off, cudaMemcpyDeviceToHost, s->stream));
+  mg_status st = read_counter(s, 1, &bad);
+  if (st != MG_OK) return st;
+  const bool diag = (off == 0);
+  if (diag != s->diag) s->drop_graphs();
+  s->diag = diag;
+  if (bad) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "%llu envs have a mass matrix that is not positive definite", bad);
+    return fail(MG_ENOTSPD, buf);
+  }
+  return MG_OK;
+}
+
+mg_status begin_params(mg_sim *s) {
+  MG_CK(cudaMemsetAsync(s->counters + 1, 0, sizeof(unsigned long long), s->stream));
+  MG_CK(cudaMemsetAsync(s->offdiag, 0, sizeof(unsigned int), s->stream));
+  return MG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mg_last_error(void) { return g_err.c_str(); }
+
+mg_status mg_create(int64_t n_envs, const int32_t *vehicle_types,
+                    const mg_vehicle_params *params, int32_t n_types, mg_sim **out) {
+  MG_NONNULL(out);
+  *out = nullptr;
+  MG_NONNULL(vehicle_types);
+  MG_NONNULL(params);
+  if (n_envs < 1 || n_envs > (int64_t)INT32_MAX - 1024)
+    return fail(MG_EINVAL, "n_envs must be in [1, 2^31 - 1025]");
+  if (n_types < 1 || n_types > MG_MAX_TYPES) return fail(MG_EINVAL, "n_types out of range");
+  for (int32_t t = 0; t < n_types; ++t)
+    if (params[t].n_thr < 1 || params[t].n_thr > MG_MAX_THR)
+      return fail(MG_EINVAL, "n_thr out of [1, MG_MAX_THR]");
+  std::vector<int32_t> types(vehicle_types, vehicle_types + n_envs);
+  bool seen[MG_MAX_TYPES] = {};
+  for (int64_t e = 0; e < n_envs; ++e) {
+    if (types[e] < 0 || types[e] >= n_types) return fail(MG_EINVAL, "vehicle type out of range");
+    seen[types[e]] = true;
+  }
+
+  mg_sim *s = new mg_sim();
+  s->n = n_envs;
+  s->n_types = n_types;
+  s->types_h = std::move(types);
+  s->vp.assign(params, params + n_types);
+  cudaGetDevice(&s->dev);
+
+  // Kernel variant from the thruster counts present.
+  int nt_seen = -1;
+  bool uniform = true;
+  for (int32_t t = 0; t < n_types; ++t) {
+    if (!seen[t]) continue;
+    if (nt_seen < 0) nt_seen = params[t].n_thr;
+    else if (nt_seen != params[t].n_thr) uniform = false;
+  }
+  s->ntv = (uniform && nt_seen == 6) ? NT_6 : (uniform && nt_seen == 8) ? NT_8 : NT_MIXED;
+
+  // Arena layout.
+  const int64_t n = n_envs;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  const size_t o_s4[5] = {take(16 * n), take(16 * n), take(16 * n), take(16 * n), take(16 * n)};
+  const size_t o_s5 = take(4 * n);
+  size_t o_d[8];
+  for (auto &x : o_d) x = take(16 * n);
+  const size_t o_d8 = take(8 * n);
+  size_t o_g[5];
+  for (auto &x : o_g) x = take(16 * n);
+  const size_t o_g5 = take(4 * n);
+  const size_t o_raw = take(4 * n * MG_NPARAM);
+  const size_t o_types = take(4 * n);
+  const size_t o_geo = take(sizeof(Geo) * n_types);
+  const size_t o_nom = take(4 * MG_NPARAM * n_types);
+  const size_t o_flags = take(4 * n);
+  const size_t o_ep = take(4 * n);
+  const size_t o_cnt = take(2 * sizeof(unsigned long long));
+  const size_t o_off = take(sizeof(unsigned int));
+  cudaError_t e = cudaMalloc(&s->arena, off);
+  if (e != cudaSuccess) {
+    delete s;
+    return fail_cuda(e, "cudaMalloc(arena)");
+  }
+  char *a = static_cast<char *>(s->arena);
+  s->st.s0 = (float4 *)(a + o_s4[0]);
+  s->st.s1 = (float4 *)(a + o_s4[1]);
+  s->st.s2 = (float4 *)(a + o_s4[2]);
+  s->st.s3 = (float4 *)(a + o_s4[3]);
+  s->st.s4 = (float4 *)(a + o_s4[4]);
+  s->st.s5 = (float *)(a + o_s5);
+  float4 **dp[8] = {&s->pa.d0, &s->pa.d1, &s->pa.d2, &s->pa.d3,
+                    &s->pa.d4, &s->pa.d5, &s->pa.d6, &s->pa.d7};
+  for (int i = 0; i < 8; ++i) *dp[i] = (float4 *)(a + o_d[i]);
+  s->pa.d8 = (float2 *)(a + o_d8);
+  float4 **gp[5] = {&s->pa.g0, &s->pa.g1, &s->pa.g2, &s->pa.g3, &s->pa.g4};
+  for (int i = 0; i < 5; ++i) *gp[i] = (float4 *)(a + o_g[i]);
+  s->pa.g5 = (float *)(a + o_g5);
+  s->raw = (float *)(a + o_raw);
+  s->types_d = (int32_t *)(a + o_types);
+  s->geo_d = (Geo *)(a + o_geo);
+  s->nominal_d = (float *)(a + o_nom);
+  s->flags = (uint32_t *)(a + o_flags);
+  s->episode = (uint32_t *)(a + o_ep);
+  s->counters = (unsigned long long *)(a + o_cnt);
+  s->offdiag = (unsigned int *)(a + o_off);
+
+  // Per-type geometry and nominal records.
+  std::vector<Geo> geo(n_types);
+  std::vector<float> nom((size_t)n_types * MG_NPARAM, 0.f);
+  for (int32_t t = 0; t < n_types; ++t) {
+    const mg_vehicle_params &v = params[t];
+    Geo &g = geo[t];
+    memset(&g, 0, sizeof g);
+    g.n_thr = v.n_thr;
+    for (int i = 0; i < v.n_thr; ++i) {
+      const float *r = v.r[i], *d = v.d[i];
+      g.dir[i] = make_float4(d[0], d[1], d[2], 0.f);
+      g.arm[i] = make_float4(r[1] * d[2] - r[2] * d[1], r[2] * d[0] - r[0] * d[2],
+                             r[0] * d[1] - r[1] * d[0], 0.f);
+    }
+    float *p = &nom[(size_t)t * MG_NPARAM];
+    p[MG_P_M] = v.m;
+    p[MG_P_IG] = v.Ixx;
+    p[MG_P_IG + 1] = v.Iyy;
+    p[MG_P_IG + 2] = v.Izz;
+    for (int i = 0; i < 6; ++i) {
+      p[MG_P_MA + i] = v.MA[i];
+      p[MG_P_DL + i] = v.Dl[i];
+      p[MG_P_DQ + i] = v.Dq[i];
+    }
+    p[MG_P_W] = v.W;
+    p[MG_P_B] = v.B;
+    for (int i = 0; i < 3; ++i) {
+      p[MG_P_RG + i] = v.rg[i];
+      p[MG_P_RB + i] = v.rb[i];
+    }
+    p[MG_P_KT] = v.kT;
+    p[MG_P_TAU] = v.tau_m;
+  }
+  auto bail = [&](mg_status st) {
+    mg_destroy(s);
+    return st;
+  };
+  mg_status st;
+#define MG_CKB(call)                                              \
+  do {                                                            \
+    cudaError_t _e = (call);                                      \
+    if (_e != cudaSuccess) return bail(fail_cuda(_e, #call));     \
+  } while (0)
+  MG_CKB(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+  MG_CKB(cudaMemcpy(s->geo_d, geo.data(), sizeof(Geo) * n_types, cudaMemcpyHostToDevice));
+  MG_CKB(cudaMemcpy(s->nominal_d, nom.data(), nom.size() * 4, cudaMemcpyHostToDevice));
+  MG_CKB(cudaMemcpy(s->types_d, s->types_h.data(), 4 * n, cudaMemcpyHostToDevice));
+  MG_CKB(cudaMemset(s->flags, 0, 4 * n));
+  MG_CKB(cudaMemset(s->episode, 0, 4 * n));
+  MG_CKB(cudaMemset(s->counters, 0, 2 * sizeof(unsigned long long)));
+  MG_CKB(cudaMemset(s->offdiag, 0, sizeof(unsigned int)));
+  // Nominal parameters: a randomisation with zero width.
+  MG_CKB(launch_randomize(s->setup_view(), s->nominal_d, 0, 1.0, 1.0, 0.0, s->stream));
+  if ((st = finish_params(s)) != MG_OK) return bail(st);
+  // Zero state with identity attitude.
+  MG_CKB(cudaMemset(s->arena, 0, o_s5 + 4 * n));
+  MG_CKB(launch_reset(s->st, n, 0, nullptr, 0, 0.0, s->episode, s->flags, s->counters,
+                      s->stream));
+  MG_CKB(cudaMemset(s->episode, 0, 4 * n));
+  if ((st = build_blocks(s)) != MG_OK) return bail(st);
+  MG_CKB(cudaStreamSynchronize(s->stream));
+#undef MG_CKB
+  *out = s;
+  return MG_OK;
+}
+
+mg_status mg_destroy(mg_sim *s) {
+  if (!s) return MG_OK;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  cudaDeviceSynchronize();
+  s->drop_graphs();
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  cudaFree(s->blocks_d);
+  cudaFree(s->act);
+  cudaFree(s->stage);
+  cudaFree(s->arena);
+  delete s;
+  return MG_OK;
+}
+
+mg_status mg_set_stream(mg_sim *s, void *stream) {
+  MG_NONNULL(s);
+  s->stream = static_cast<cudaStream_t>(stream);
+  return MG_OK;
+}
+
+mg_status mg_set_env_id_offset(mg_sim *s, int64_t offset) {
+  MG_NONNULL(s);
+  if (offset < 0) return fail(MG_EINVAL, "offset must be >= 0");
+  s->gid0 = offset;
+  s->drop_graphs();
+  return MG_OK;
+}
+
+mg_status mg_set_model_flags(mg_sim *s, uint32_t flags) {
+  MG_NONNULL(s);
+  if (flags & ~MG_MODEL_NO_CURRENT_ACCEL) return fail(MG_EINVAL, "unknown model flag");
+  s->model_flags = flags;
+  s->drop_graphs();
+  return MG_OK;
+}
+
+mg_status mg_set_timestep(mg_sim *s, float dt) {
+  MG_NONNULL(s);
+  if (!(dt > 0.f && dt <= 1.f)) return fail(MG_EINVAL, "dt must be in (0, 1]");
+  s->dt = dt;
+  s->drop_graphs();
+  return MG_OK;
+}
+
+mg_status mg_set_launch(mg_sim *s, int32_t envs_per_block, int32_t steps_per_launch,
+                        int32_t use_graph) {
+  MG_NONNULL(s);
+  if (envs_per_block < 32 || envs_per_block > 256)
+    return fail(MG_EINVAL, "envs_per_block must be in [32, 256]");
+  if (steps_per_launch < 1) return fail(MG_EINVAL, "steps_per_launch must be >= 1");
+  s->spl = steps_per_launch;
+  s->use_graph = use_graph != 0;
+  s->drop_graphs();
+  if (envs_per_block != s->epb) {
+    s->epb = envs_per_block;
+    return build_blocks(s);
+  }
+  return MG_OK;
+}
+
+mg_status mg_randomize(mg_sim *s, uint64_t seed, const mg_ranges *r) {
+  MG_NONNULL(s);
+  MG_NONNULL(r);
+  if (!(r->lo > 0.f) || !(r->lo <= r->hi) || !(r->current_sigma >= 0.f) ||
+      !(r->nu0_sigma >= 0.f) || r->flags != 0)
+    return fail(MG_EINVAL, "ranges: need 0 < lo <= hi, sigmas >= 0, flags == 0");
+  mg_status st = begin_params(s);
+  if (st != MG_OK) return st;
+  MG_CK(launch_randomize(s->setup_view(), s->nominal_d, seed, (double)r->lo, (double)r->hi,
+                         (double)r->current_sigma, s->stream));
+  MG_CK(cudaMemsetAsync(s->episode, 0, 4 * s->n, s->stream));
+  s->reset_seed = seed;
+  s->nu0_sigma = (double)r->nu0_sigma;
+  return finish_params(s);
+}
+
+mg_status mg_set_params(mg_sim *s, const float *in) {
+  MG_NONNULL(s);
+  MG_NONNULL(in);
+  const void *d = nullptr;
+  mg_status st = input_ptr(s, in, (size_t)s->n * MG_NPARAM * 4, &d);
+  if (st != MG_OK) return st;
+  if ((st = begin_params(s)) != MG_OK) return st;
+  MG_CK(launch_import_params(s->setup_view(), static_cast<const float *>(d), s->stream));
+  return finish_params(s);
+}
+
+mg_status mg_get_params(mg_sim *s, float *out) {
+  MG_NONNULL(s);
+  MG_NONNULL(out);
+  const size_t bytes = (size_t)s->n * MG_NPARAM * 4;
+  if (is_device_ptr(out)) {
+    MG_CK(launch_export_params(s->setup_view(), out, s->stream));
+    return MG_OK;
+  }
+  mg_status st = ensure_stage(s, bytes);
+  if (st != MG_OK) return st;
+  MG_CK(launch_export_params(s->setup_view(), static_cast<float *>(s->stage), s->stream));
+  MG_CK(cudaMemcpyAsync(out, s->stage, bytes, cudaMemcpyDeviceToHost, s->stream));
+  MG_CK(cudaStreamSynchronize(s->stream));
+  return MG_OK;
+}
+
+mg_status mg_set_actions(mg_sim *s, const float *a, int32_t n_seg, int32_t hold_steps) {
+  MG_NONNULL(s);
+  if (n_seg < 0 || hold_steps < 1) return fail(MG_EINVAL, "need n_seg >= 0 and hold_steps >= 1");
+  if (n_seg > 0 && !a) return fail(MG_EINVAL, "a is NULL with n_seg > 0");
+  const size_t floats = (size_t)n_seg * s->n * MG_MAX_THR;
+  if (floats > s->act_cap) {
+    MG_CK(cudaStreamSynchronize(s->stream));
+    cudaFree(s->act);
+    s->act = nullptr;
+    s->act_cap = 0;
+    MG_CK(cudaMalloc(&s->act, floats * 4));
+    s->act_cap = floats;
+    s->drop_graphs();
+  }
+  if (n_seg > 0) {
+    const bool dev = is_device_ptr(a);
+    MG_CK(cudaMemcpyAsync(s->act, a, floats * 4,
+                          dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->stream));
+    if (!dev) MG_CK(cudaStreamSynchronize(s->stream));
+  }
+  if (s->proc || s->n_seg != n_seg || s->hold != hold_steps) s->drop_graphs();
+  s->proc = 0;
+  s->n_seg = n_seg;
+  s->hold = hold_steps;
+  s->cursor = 0;
+  return MG_OK;
+}
+
+mg_status mg_set_procedural_actions(mg_sim *s, uint64_t cmd_seed, int32_t hold_steps) {
+  MG_NONNULL(s);
+  if (hold_steps < 1) return fail(MG_EINVAL, "hold_steps must be >= 1");
+  s->drop_graphs();
+  s->proc = 1;
+  s->cmd_seed = cmd_seed;
+  s->hold = hold_steps;
+  s->n_seg = 0;
+  s->cursor = 0;
+  return MG_OK;
+}
+
+mg_status mg_step(mg_sim *s, int32_t k) {
+  MG_NONNULL(s);
+  if (k < 1) return fail(MG_EINVAL, "k must be >= 1");
+  if (!s->use_graph) {
+    mg_status st = launch_chunks(s, k, nullptr, s->stream);
+    if (st != MG_OK) return st;
+    s->cursor += k;
+    return MG_OK;
+  }
+  GraphEntry *hit = nullptr;
+  for (auto &g : s->graphs)
+    if (g.k == k && g.cursor == s->cursor) hit = &g;
+  if (!hit) {
+    if (s->graphs.size() >= 16) {
+      auto lru = std::min_element(s->graphs.begin(), s->graphs.end(),
+                                  [](const GraphEntry &x, const GraphEntry &y) {
+                                    return x.last_use < y.last_use;
+                                  });
+      cudaGraphExecDestroy(lru->exec);
+      s->graphs.erase(lru);
+    }
+    cudaGraph_t graph = nullptr;
+    MG_CK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+    mg_status st = launch_chunks(s, k, nullptr, s->cap_stream);
+    cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &graph);
+    if (st != MG_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    MG_CK(ce);
+    GraphEntry g{k, s->cursor, nullptr, 0};
+    ce = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    MG_CK(ce);
+    s->graphs.push_back(g);
+    hit = &s->graphs.back();
+  }
+  hit->last_use = ++s->graph_clock;
+  MG_CK(cudaGraphLaunch(hit->exec, s->stream));
+  s->cursor += k;
+  return MG_OK;
+}
+
+mg_status mg_step_record(mg_sim *s, int32_t k, float *traj) {
+  MG_NONNULL(s);
+  MG_NONNULL(traj);
+  if (k < 1) return fail(MG_EINVAL, "k must be >= 1");
+  if (!is_device_ptr(traj)) return fail(MG_EINVAL, "traj must be device memory");
+  mg_status st = launch_chunks(s, k, traj, s->stream);
+  if (st != MG_OK) return st;
+  s->cursor += k;
+  return MG_OK;
+}
+
+mg_status mg_get_state(mg_sim *s, float *out) {
+  MG_NONNULL(s);
+  MG_NONNULL(out);
+  const size_t bytes = (size_t)s->n * MG_NSTATE * 4;
+  if (is_device_ptr(out)) {
+    MG_CK(launch_export_state(s->st, s->n, out, s->stream));
+    return MG_OK;
+  }
+  mg_status st = ensure_stage(s, bytes);
+  if (st != MG_OK) return st;
+  MG_CK(launch_export_state(s->st, s->n, static_cast<float *>(s->stage), s->stream));
+  MG_CK(cudaMemcpyAsync(out, s->stage, bytes, cudaMemcpyDeviceToHost, s->stream));
+  MG_CK(cudaStreamSynchronize(s->stream));
+  return MG_OK;
+}
+
+mg_status mg_set_state(mg_sim *s, const float *in) {
+  MG_NONNULL(s);
+  MG_NONNULL(in);
+  const void *d = nullptr;
+  mg_status st = input_ptr(s, in, (size_t)s->n * MG_NSTATE * 4, &d);
+  if (st != MG_OK) return st;
+  MG_CK(launch_import_state(s->st, s->n, static_cast<const float *>(d), s->stream));
+  if (d == s->stage) MG_CK(cudaStreamSynchronize(s->stream));
+  return MG_OK;
+}
+
+mg_status mg_reset(mg_sim *s, const uint8_t *mask) {
+  MG_NONNULL(s);
+  const void *d = nullptr;
+  if (mask) {
+    mg_status st = input_ptr(s, mask, (size_t)s->n, &d);
+    if (st != MG_OK) return st;
+  }
+  MG_CK(launch_reset(s->st, s->n, s->gid0, static_cast<const uint8_t *>(d), s->reset_seed,
+                     s->nu0_sigma, s->episode, s->flags, s->counters, s->stream));
+  if (d && d == s->stage) MG_CK(cudaStreamSynchronize(s->stream));
+  return MG_OK;
+}
+
+mg_status mg_sync(mg_sim *s, int64_t *nonfinite_count) {
+  MG_NONNULL(s);
+  unsigned long long c = 0;
+  mg_status st = read_counter(s, 0, &c);
+  if (st != MG_OK) return st;
+  if (nonfinite_count) *nonfinite_count = (int64_t)c;
+  if (c) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "%llu envs have a non-finite state", c);
+    return fail(MG_ENONFINITE, buf);
+  }
+  return MG_OK;
+}
+
+mg_status mg_get_nonfinite(mg_sim *s, uint8_t *out) {
+  MG_NONNULL(s);
+  MG_NONNULL(out);
+  if (is_device_ptr(out)) {
+    MG_CK(launch_flags_to_bytes(s->flags, s->n, out, s->stream));
+    return MG_OK;
+  }
+  mg_status st = ensure_stage(s, (size_t)s->n);
+  if (st != MG_OK) return st;
+  MG_CK(launch_flags_to_bytes(s->flags, s->n, static_cast<uint8_t *>(s->stage), s->stream));
+  MG_CK(cudaMemcpyAsync(out, s->stage, (size_t)s->n, cudaMemcpyDeviceToHost, s->stream));
+  MG_CK(cudaStreamSynchronize(s->stream));
+  return MG_OK;
+}
+
+mg_status mg_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n) {
+  MG_NONNULL(ctr);
+  MG_NONNULL(key);
+  MG_NONNULL(out);
+  if (n < 1) return fail(MG_EINVAL, "n must be >= 1");
+  uint32_t *d = nullptr;
+  MG_CK(cudaMalloc(&d, (size_t)n * 40));
+  cudaError_t e = cudaMemcpy(d, ctr, (size_t)n * 16, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d + 4 * n, key, (size_t)n * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_philox(d, d + 4 * n, d + 6 * n, n, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(out, d + 6 * n, (size_t)n * 16, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail_cuda(e, "mg_philox4x32_10");
+  return MG_OK;
+}
+
+mg_status mg_kernel_info(mg_sim *s, int32_t *regs, int32_t *max_threads, int32_t *local_bytes) {
+  MG_NONNULL(s);
+  cudaFuncAttributes a;
+  MG_CK(fleet_kernel_attributes(s->ntv, s->diag, false, &a));
+  if (regs) *regs = a.numRegs;
+  if (max_threads) *max_threads = a.maxThreadsPerBlock;
+  if (local_bytes) *local_bytes = (int32_t)a.localSizeBytes;
+  return MG_OK;
+}
+
+}  // extern "C"

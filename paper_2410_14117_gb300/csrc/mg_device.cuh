@@ -1,0 +1,283 @@
+// Device-side building blocks of the fused Fossen step: Philox draws, the right-hand side of
+// Eq. 1 (§METHOD) for one vehicle held in registers, and the RK4 sub-step.
+//
+// Formulation (same mathematics as Eq. 1, arranged for one thread per vehicle in FP32):
+//   - Coriolis terms in Kirchhoff's vector form: with [P1;P2] = M_RB nu and [Q1;Q2] = M_A nu_r,
+//       C_RB(nu) nu   = [w x P1 ; v x P1 + w x P2]
+//       C_A(nu_r)nu_r = [w x Q1 ; v_r x Q1 + w x Q2]
+//     which is what Fossen's momentum-block matrices multiply out to; the two are summed before
+//     the cross products.
+//   - Restoring vector from the third row of R(q): k = R^T e3, g = -[(W - B) k ; G x k],
+//     G = W r_g - B r_b.
+//   - The mass matrix M = M_RB + M_A is inverted once per parameter change (FP64 Cholesky, see
+//     mg_setup.cu); the step multiplies by the stored FP32 inverse.
+#pragma once
+
+#include <type_traits>
+
+#include "mg_internal.h"
+
+namespace mg {
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC 2011): ten
+// rounds of two 32x32->64-bit products; the key is bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+  constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  constexpr uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+    const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += W0;
+    k.y += W1;
+  }
+  return c;
+}
+
+// Draw block `block` of stream `stream` for env id `gid` under key `seed`.
+__device__ __forceinline__ uint4 draw4(uint64_t seed, uint64_t gid, uint32_t stream,
+                                       uint32_t block) {
+  return philox4x32_10(make_uint4((uint32_t)gid, (uint32_t)(gid >> 32), stream, block),
+                       make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// Open-interval uniform from the top 23 bits: ((x >> 9) + 1/2) 2^-23 (exact in FP32).
+__device__ __forceinline__ float u01f(uint32_t x) {
+  return ((float)(x >> 9) + 0.5f) * (1.0f / 8388608.0f);
+}
+__device__ __forceinline__ double u01d(uint32_t x) {
+  return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0);
+}
+
+// Counter streams of the draws (shared with the host-side documentation in mg.h).
+enum : uint32_t { STREAM_PARAMS = 0, STREAM_CURRENT = 1, STREAM_RESET = 2, STREAM_CMD = 3 };
+
+// ---------------------------------------------------------------- per-env registers
+template <int MT>
+struct St {
+  float p[3], q[4], v[3], w[3], n[MT];
+};
+
+// Diagonal-mass parameters (34 floats).
+struct ParDiag {
+  float m, ma0, ma1, ma2;   // mass, translational added mass
+  float J0, J1, J2, wb;     // diag(I_o) + rotational added mass, W - B
+  float dl[6], dq[6];       // linear, quadratic damping
+  float G0, G1, G2, kT;     // W r_g - B r_b, thrust coefficient
+  float vc0, vc1, vc2, itau;  // NED current, 1 / tau_m
+  float mi[6];              // diagonal of M^-1
+};
+
+// General parameters: off-centre gravity (off-diagonal M_RB, full M^-1).
+struct ParGen : ParDiag {
+  float mrg0, mrg1, mrg2;   // m r_g
+  float Ixy, Ixz, Iyz;      // off-diagonal of I_o = I_g - m S(r_g)^2
+  float mo[15];             // off-diagonal of M^-1: 01 02 03 04 05 12 13 14 15 23 24 25 34 35 45
+};
+
+template <bool DIAG>
+using Par = typename std::conditional<DIAG, ParDiag, ParGen>::type;
+
+__device__ __forceinline__ float4 ldg4(const float4 *p, int64_t e) { return __ldg(p + e); }
+
+template <bool DIAG>
+__device__ __forceinline__ void load_par(const ParamPlanes &pa, int64_t e, Par<DIAG> &P) {
+  float4 a = ldg4(pa.d0, e), b = ldg4(pa.d1, e), c = ldg4(pa.d2, e), d = ldg4(pa.d3, e);
+  float4 f = ldg4(pa.d4, e), g = ldg4(pa.d5, e), h = ldg4(pa.d6, e), i = ldg4(pa.d7, e);
+  float2 j = __ldg(pa.d8 + e);
+  P.m = a.x; P.ma0 = a.y; P.ma1 = a.z; P.ma2 = a.w;
+  P.J0 = b.x; P.J1 = b.y; P.J2 = b.z; P.wb = b.w;
+  P.dl[0] = c.x; P.dl[1] = c.y; P.dl[2] = c.z; P.dl[3] = c.w;
+  P.dl[4] = d.x; P.dl[5] = d.y; P.dq[0] = d.z; P.dq[1] = d.w;
+  P.dq[2] = f.x; P.dq[3] = f.y; P.dq[4] = f.z; P.dq[5] = f.w;
+  P.G0 = g.x; P.G1 = g.y; P.G2 = g.z; P.kT = g.w;
+  P.vc0 = h.x; P.vc1 = h.y; P.vc2 = h.z; P.itau = h.w;
+  P.mi[0] = i.x; P.mi[1] = i.y; P.mi[2] = i.z; P.mi[3] = i.w; P.mi[4] = j.x; P.mi[5] = j.y;
+  if constexpr (!DIAG) {
+    float4 k0 = ldg4(pa.g0, e), k1 = ldg4(pa.g1, e), k2 = ldg4(pa.g2, e), k3 = ldg4(pa.g3, e);
+    float4 k4 = ldg4(pa.g4, e);
+    float k5 = __ldg(pa.g5 + e);
+    P.mrg0 = k0.x; P.mrg1 = k0.y; P.mrg2 = k0.z; P.Ixy = k0.w;
+    P.Ixz = k1.x; P.Iyz = k1.y; P.mo[0] = k1.z; P.mo[1] = k1.w;
+    P.mo[2] = k2.x; P.mo[3] = k2.y; P.mo[4] = k2.z; P.mo[5] = k2.w;
+    P.mo[6] = k3.x; P.mo[7] = k3.y; P.mo[8] = k3.z; P.mo[9] = k3.w;
+    P.mo[10] = k4.x; P.mo[11] = k4.y; P.mo[12] = k4.z; P.mo[13] = k4.w;
+    P.mo[14] = k5;
+  }
+}
+
+template <int MT>
+__device__ __forceinline__ void load_state(const StatePlanes &sp, int64_t e, St<MT> &s) {
+  const float4 a = sp.s0[e], b = sp.s1[e], c = sp.s2[e], d = sp.s3[e], f = sp.s4[e];
+  s.p[0] = a.x; s.p[1] = a.y; s.p[2] = a.z; s.q[0] = a.w;
+  s.q[1] = b.x; s.q[2] = b.y; s.q[3] = b.z; s.v[0] = b.w;
+  s.v[1] = c.x; s.v[2] = c.y; s.w[0] = c.z; s.w[1] = c.w;
+  s.w[2] = d.x; s.n[0] = d.y; s.n[1] = d.z; s.n[2] = d.w;
+  s.n[3] = f.x; s.n[4] = f.y; s.n[5] = f.z;
+  if constexpr (MT > 6) {
+    s.n[6] = f.w;
+    s.n[7] = sp.s5[e];
+  }
+}
+
+template <int MT>
+__device__ __forceinline__ void store_state(const StatePlanes &sp, int64_t e, const St<MT> &s) {
+  sp.s0[e] = make_float4(s.p[0], s.p[1], s.p[2], s.q[0]);
+  sp.s1[e] = make_float4(s.q[1], s.q[2], s.q[3], s.v[0]);
+  sp.s2[e] = make_float4(s.v[1], s.v[2], s.w[0], s.w[1]);
+  sp.s3[e] = make_float4(s.w[2], s.n[0], s.n[1], s.n[2]);
+  if constexpr (MT > 6) {
+    sp.s4[e] = make_float4(s.n[3], s.n[4], s.n[5], s.n[6]);
+    sp.s5[e] = s.n[7];
+  } else {
+    sp.s4[e] = make_float4(s.n[3], s.n[4], s.n[5], 0.0f);
+  }
+}
+
+// ---------------------------------------------------------------- right-hand side of Eq. 1
+// d = f(s; c).  gdir/garm: the block's vehicle type's thruster directions and moment arms (in
+// shared memory); nt = its thruster count (only read when MIXED).
+template <int MT, bool DIAG, bool MIXED>
+__device__ __forceinline__ void rhs(const St<MT> &s, const float (&c)[MT], const Par<DIAG> &P,
+                                    const float4 *gdir, const float4 *garm, int nt,
+                                    bool current_accel, St<MT> &d) {
+  // Thrusters (Eq. 3 actions): F_i = kT n_i|n_i| along d_i at r_i; n_i' = (c_i - n_i) / tau_m.
+  float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f, t4 = 0.f, t5 = 0.f;
+#pragma unroll
+  for (int i = 0; i < MT; ++i) {
+    if (!MIXED || i < nt) {
+      const float f = s.n[i] * fabsf(s.n[i]);
+      const float4 dd = gdir[i], aa = garm[i];
+      t0 = fmaf(f, dd.x, t0); t1 = fmaf(f, dd.y, t1); t2 = fmaf(f, dd.z, t2);
+      t3 = fmaf(f, aa.x, t3); t4 = fmaf(f, aa.y, t4); t5 = fmaf(f, aa.z, t5);
+      d.n[i] = (c[i] - s.n[i]) * P.itau;
+    } else {
+      d.n[i] = 0.f;
+    }
+  }
+
+  // Attitude matrix R(q) = I + 2 q_w S(eps) + 2 S(eps)^2 (body -> NED).
+  const float qw = s.q[0], qx = s.q[1], qy = s.q[2], qz = s.q[3];
+  const float x2 = qx + qx, y2 = qy + qy, z2 = qz + qz;
+  const float xx = qx * x2, yy = qy * y2, zz = qz * z2;
+  const float xy = qx * y2, xz = qx * z2, yz = qy * z2;
+  const float wx = qw * x2, wy = qw * y2, wz = qw * z2;
+  const float R00 = 1.f - yy - zz, R01 = xy - wz, R02 = xz + wy;
+  const float R10 = xy + wz, R11 = 1.f - xx - zz, R12 = yz - wx;
+  const float R20 = xz - wy, R21 = yz + wx, R22 = 1.f - xx - yy;
+
+  const float v0 = s.v[0], v1 = s.v[1], v2 = s.v[2];
+  const float w0 = s.w[0], w1 = s.w[1], w2 = s.w[2];
+
+  // Current constant in NED, seen from the body: v_c^b = R^T v_c; relative velocity v_r.
+  const float cb0 = R00 * P.vc0 + R10 * P.vc1 + R20 * P.vc2;
+  const float cb1 = R01 * P.vc0 + R11 * P.vc1 + R21 * P.vc2;
+  const float cb2 = R02 * P.vc0 + R12 * P.vc1 + R22 * P.vc2;
+  const float r0 = v0 - cb0, r1 = v1 - cb1, r2 = v2 - cb2;
+
+  // Momenta: Q1 = M_A,lin v_r; P1 + Q1 = m v + Q1 (+ w x m r_g);
+  //          P2 + Q2 = (diag(I_o) + M_A,rot) w (+ off-diagonal I_o w + m r_g x v).
+  const float q0 = P.ma0 * r0, q1 = P.ma1 * r1, q2 = P.ma2 * r2;
+  float h0 = fmaf(P.m, v0, q0), h1 = fmaf(P.m, v1, q1), h2 = fmaf(P.m, v2, q2);
+  float k0 = P.J0 * w0, k1 = P.J1 * w1, k2 = P.J2 * w2;
+  // Rotational Coriolis: v_r x Q1 (+ v x P1, which is v x (w x m r_g) as v x m v = 0).
+  float cr0 = r1 * q2 - r2 * q1, cr1 = r2 * q0 - r0 * q2, cr2 = r0 * q1 - r1 * q0;
+  if constexpr (!DIAG) {
+    const float a0 = w1 * P.mrg2 - w2 * P.mrg1;  // w x m r_g
+    const float a1 = w2 * P.mrg0 - w0 * P.mrg2;
+    const float a2 = w0 * P.mrg1 - w1 * P.mrg0;
+    h0 += a0; h1 += a1; h2 += a2;
+    cr0 += v1 * a2 - v2 * a1; cr1 += v2 * a0 - v0 * a2; cr2 += v0 * a1 - v1 * a0;
+    k0 += P.Ixy * w1 + P.Ixz * w2 + (P.mrg1 * v2 - P.mrg2 * v1);
+    k1 += P.Ixy * w0 + P.Iyz * w2 + (P.mrg2 * v0 - P.mrg0 * v2);
+    k2 += P.Ixz * w0 + P.Iyz * w1 + (P.mrg0 * v1 - P.mrg1 * v0);
+  }
+  const float cl0 = w1 * h2 - w2 * h1, cl1 = w2 * h0 - w0 * h2, cl2 = w0 * h1 - w1 * h0;
+  cr0 += w1 * k2 - w2 * k1;
+  cr1 += w2 * k0 - w0 * k2;
+  cr2 += w0 * k1 - w1 * k0;
+
+  // Restoring: k = R^T e3; the generalised force -g = [(W - B) k ; G x k].
+  const float e0 = R20, e1 = R21, e2 = R22;
+
+  // Generalised force f = tau - C nu - D(nu_r) nu_r - g [- M_A (w x v_c^b)].
+  float f0 = P.kT * t0 - cl0 - fmaf(P.dq[0], fabsf(r0), P.dl[0]) * r0 + P.wb * e0;
+  float f1 = P.kT * t1 - cl1 - fmaf(P.dq[1], fabsf(r1), P.dl[1]) * r1 + P.wb * e1;
+  float f2 = P.kT * t2 - cl2 - fmaf(P.dq[2], fabsf(r2), P.dl[2]) * r2 + P.wb * e2;
+  const float f3 = P.kT * t3 - cr0 - fmaf(P.dq[3], fabsf(w0), P.dl[3]) * w0 +
+                   (P.G1 * e2 - P.G2 * e1);
+  const float f4 = P.kT * t4 - cr1 - fmaf(P.dq[4], fabsf(w1), P.dl[4]) * w1 +
+                   (P.G2 * e0 - P.G0 * e2);
+  const float f5 = P.kT * t5 - cr2 - fmaf(P.dq[5], fabsf(w2), P.dl[5]) * w2 +
+                   (P.G0 * e1 - P.G1 * e0);
+  if (current_accel) {
+    f0 -= P.ma0 * (w1 * cb2 - w2 * cb1);
+    f1 -= P.ma1 * (w2 * cb0 - w0 * cb2);
+    f2 -= P.ma2 * (w0 * cb1 - w1 * cb0);
+  }
+
+  // nu' = M^-1 f.
+  if constexpr (DIAG) {
+    d.v[0] = P.mi[0] * f0; d.v[1] = P.mi[1] * f1; d.v[2] = P.mi[2] * f2;
+    d.w[0] = P.mi[3] * f3; d.w[1] = P.mi[4] * f4; d.w[2] = P.mi[5] * f5;
+  } else {
+    const float *o = P.mo;
+    d.v[0] = P.mi[0] * f0 + o[0] * f1 + o[1] * f2 + o[2] * f3 + o[3] * f4 + o[4] * f5;
+    d.v[1] = o[0] * f0 + P.mi[1] * f1 + o[5] * f2 + o[6] * f3 + o[7] * f4 + o[8] * f5;
+    d.v[2] = o[1] * f0 + o[5] * f1 + P.mi[2] * f2 + o[9] * f3 + o[10] * f4 + o[11] * f5;
+    d.w[0] = o[2] * f0 + o[6] * f1 + o[9] * f2 + P.mi[3] * f3 + o[12] * f4 + o[13] * f5;
+    d.w[1] = o[3] * f0 + o[7] * f1 + o[10] * f2 + o[12] * f3 + P.mi[4] * f4 + o[14] * f5;
+    d.w[2] = o[4] * f0 + o[8] * f1 + o[11] * f2 + o[13] * f3 + o[14] * f4 + P.mi[5] * f5;
+  }
+
+  // Kinematics: p' = R v; q' = 1/2 q (x) (0, w).
+  d.p[0] = R00 * v0 + R01 * v1 + R02 * v2;
+  d.p[1] = R10 * v0 + R11 * v1 + R12 * v2;
+  d.p[2] = R20 * v0 + R21 * v1 + R22 * v2;
+  d.q[0] = -0.5f * (qx * w0 + qy * w1 + qz * w2);
+  d.q[1] = 0.5f * (qw * w0 - qz * w1 + qy * w2);
+  d.q[2] = 0.5f * (qz * w0 + qw * w1 - qx * w2);
+  d.q[3] = 0.5f * (-qy * w0 + qx * w1 + qw * w2);
+}
+
+template <int MT>
+__device__ __forceinline__ void axpy(St<MT> &y, const St<MT> &x, float a, const St<MT> &k) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) y.p[i] = fmaf(a, k.p[i], x.p[i]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) y.q[i] = fmaf(a, k.q[i], x.q[i]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) y.v[i] = fmaf(a, k.v[i], x.v[i]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) y.w[i] = fmaf(a, k.w[i], x.w[i]);
+#pragma unroll
+  for (int i = 0; i < MT; ++i) y.n[i] = fmaf(a, k.n[i], x.n[i]);
+}
+
+// One sub-step (§METHOD): classical RK4 of size h, command held, then q <- q / |q|.
+template <int MT, bool DIAG, bool MIXED>
+__device__ __forceinline__ void rk4_step(St<MT> &s, const float (&c)[MT], const Par<DIAG> &P,
+                                         const float4 *gdir, const float4 *garm, int nt,
+                                         bool current_accel, float h) {
+  const float hh = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f);
+  St<MT> k, y, acc;
+  rhs<MT, DIAG, MIXED>(s, c, P, gdir, garm, nt, current_accel, k);
+  axpy(acc, s, h6, k);
+  axpy(y, s, hh, k);
+  rhs<MT, DIAG, MIXED>(y, c, P, gdir, garm, nt, current_accel, k);
+  axpy(acc, acc, h3, k);
+  axpy(y, s, hh, k);
+  rhs<MT, DIAG, MIXED>(y, c, P, gdir, garm, nt, current_accel, k);
+  axpy(acc, acc, h3, k);
+  axpy(y, s, h, k);
+  rhs<MT, DIAG, MIXED>(y, c, P, gdir, garm, nt, current_accel, k);
+  axpy(s, acc, h6, k);
+  const float inv = rsqrtf(s.q[0] * s.q[0] + s.q[1] * s.q[1] + s.q[2] * s.q[2] +
+                           s.q[3] * s.q[3]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) s.q[i] *= inv;
+}
+
+}  // namespace mg

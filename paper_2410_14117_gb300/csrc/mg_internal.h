@@ -1,0 +1,117 @@
+// Internal data layout of a fleet in HBM and the launch-side structs shared by the host API
+// and the kernels.  Everything is structure-of-arrays: plane j of a quantity is an array over
+// envs, so that thread e's 16-byte load of plane j and thread e+1's are adjacent and a warp
+// reads 512 contiguous bytes per plane.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mg.h"
+
+namespace mg {
+
+// ---------------------------------------------------------------- state planes
+// 13 + n_thr floats per env packed into float4 planes (the 21-float record of mg.h minus
+// padding):
+//   S0 (px, py, pz, qw) | S1 (qx, qy, qz, u) | S2 (v, w, p, q) | S3 (r, n0, n1, n2)
+//   S4 (n3, n4, n5, n6) | S5 n7 (a float plane, only touched by 8-thruster vehicles)
+struct StatePlanes {
+  float4 *s0, *s1, *s2, *s3, *s4;
+  float *s5;
+};
+
+// ---------------------------------------------------------------- derived parameter planes
+// What the step needs, derived once per parameter change (FP64 on the device, stored FP32).
+// Diagonal-mass fleets (r_g = 0 everywhere, so M = M_RB + M_A is diagonal) read D0..D8 only:
+//   D0 (m, Ma_u, Ma_v, Ma_w)       D1 (Jx, Jy, Jz, W - B)   J = diag(I_o) + Ma_rot
+//   D2 (Dl_u, Dl_v, Dl_w, Dl_p)    D3 (Dl_q, Dl_r, Dq_u, Dq_v)   D4 (Dq_w, Dq_p, Dq_q, Dq_r)
+//   D5 (Gx, Gy, Gz, kT)            G = W r_g - B r_b
+//   D6 (vc_x, vc_y, vc_z, 1/tau_m) NED current
+//   D7 (Mi00, Mi11, Mi22, Mi33)    D8 (Mi44, Mi55)            Mi = M^-1 (packed, symmetric)
+// General fleets (some r_g != 0) also read:
+//   G0 (m rg_x, m rg_y, m rg_z, Io_xy)   G1 (Io_xz, Io_yz, Mi01, Mi02)
+//   G2 (Mi03, Mi04, Mi05, Mi12)          G3 (Mi13, Mi14, Mi15, Mi23)
+//   G4 (Mi24, Mi25, Mi34, Mi35)          G5 Mi45
+struct ParamPlanes {
+  float4 *d0, *d1, *d2, *d3, *d4, *d5, *d6, *d7;
+  float2 *d8;
+  float4 *g0, *g1, *g2, *g3, *g4;
+  float *g5;
+};
+
+// Per vehicle type: thruster count, unit directions d_i and moment arms r_i x d_i (w unused).
+struct Geo {
+  int32_t n_thr;
+  int32_t pad[3];
+  float4 dir[MG_MAX_THR];
+  float4 arm[MG_MAX_THR];
+};
+
+// One thread block's slice of the fleet: envs [env0, env0 + count) all of vehicle type `type`.
+struct BlockDesc {
+  int32_t env0;
+  int32_t count;
+  int32_t type;
+  int32_t n_thr;
+};
+
+// Everything a step kernel reads besides its block list; passed by value.
+struct FleetView {
+  StatePlanes st;
+  ParamPlanes pa;
+  const Geo *geo;            // device [n_types]
+  int64_t n;                 // envs
+  int64_t gid0;              // env id offset for counter-based draws
+  const float4 *act;         // [n_seg][n][8] as float4 pairs, or null
+  int32_t n_seg;
+  int32_t hold;
+  uint64_t cmd_seed;         // procedural actions when proc != 0
+  int32_t proc;
+  uint32_t model_flags;
+  float dt;
+  uint32_t *flags;           // [n] bit 0 = non-finite
+  unsigned long long *nonfinite_count;
+};
+
+// Kernel variants: thruster count fixed at 6 or 8, or mixed (up to 8, read per block).
+enum NtVariant { NT_6 = 0, NT_8 = 1, NT_MIXED = 2 };
+
+// ---------------------------------------------------------------- launchers (mg_step.cu)
+cudaError_t launch_fleet(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
+                         NtVariant ntv, bool diag, int64_t step0, int32_t k, float *traj,
+                         cudaStream_t stream);
+cudaError_t fleet_kernel_attributes(NtVariant ntv, bool diag, bool record,
+                                    cudaFuncAttributes *attr);
+
+// ---------------------------------------------------------------- launchers (mg_setup.cu)
+struct SetupView {
+  int64_t n;
+  int64_t gid0;
+  const int32_t *types;      // device [n]
+  float *raw;                // device [MG_NPARAM][n] (parameter-major)
+  ParamPlanes pa;
+  unsigned long long *n_not_spd;
+  unsigned int *any_offdiag;
+};
+
+cudaError_t launch_randomize(const SetupView &v, const float *nominal /*dev [n_types][35]*/,
+                             uint64_t seed, double lo, double hi, double current_sigma,
+                             cudaStream_t stream);
+cudaError_t launch_import_params(const SetupView &v, const float *in /*dev [n][35]*/,
+                                 cudaStream_t stream);
+cudaError_t launch_export_params(const SetupView &v, float *out /*dev [n][35]*/,
+                                 cudaStream_t stream);
+cudaError_t launch_reset(const StatePlanes &st, int64_t n, int64_t gid0, const uint8_t *mask,
+                         uint64_t seed, double nu0_sigma, uint32_t *episode, uint32_t *flags,
+                         unsigned long long *nonfinite_count, cudaStream_t stream);
+cudaError_t launch_export_state(const StatePlanes &st, int64_t n, float *out,
+                                cudaStream_t stream);
+cudaError_t launch_import_state(const StatePlanes &st, int64_t n, const float *in,
+                                cudaStream_t stream);
+cudaError_t launch_flags_to_bytes(const uint32_t *flags, int64_t n, uint8_t *out,
+                                  cudaStream_t stream);
+cudaError_t launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,
+                          cudaStream_t stream);
+
+}  // namespace mg

@@ -1,0 +1,289 @@
+// Set-up kernels, run when parameters or episodes change (not per sub-step):
+//   - domain randomisation (§METHOD) from Philox4x32-10 draws, in FP64, stored FP32;
+//   - derivation of what the step reads, including M^-1 of the 6x6 mass matrix M_RB + M_A of
+//     Eq. 1 by an FP64 Cholesky factorisation (M is symmetric positive definite for any
+//     physical vehicle; a non-positive pivot is counted and reported);
+//   - episode reset, and conversions between the SoA planes and the record layouts of mg.h.
+#include <type_traits>
+
+#include "mg_device.cuh"
+
+namespace mg {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int blocks_for(int64_t n) { return (int)((n + kThreads - 1) / kThreads); }
+
+// Indices of the 27 randomised scalars in the parameter record, in draw order.
+__constant__ int c_rand_idx[27] = {
+    MG_P_M, MG_P_IG, MG_P_IG + 1, MG_P_IG + 2,
+    MG_P_MA, MG_P_MA + 1, MG_P_MA + 2, MG_P_MA + 3, MG_P_MA + 4, MG_P_MA + 5,
+    MG_P_DL, MG_P_DL + 1, MG_P_DL + 2, MG_P_DL + 3, MG_P_DL + 4, MG_P_DL + 5,
+    MG_P_DQ, MG_P_DQ + 1, MG_P_DQ + 2, MG_P_DQ + 3, MG_P_DQ + 4, MG_P_DQ + 5,
+    MG_P_W, MG_P_B, MG_P_RB + 2, MG_P_KT, MG_P_TAU};
+
+__device__ __forceinline__ void box_muller(double u1, double u2, double &z0, double &z1) {
+  const double r = sqrt(-2.0 * log(u1));
+  double s, c;
+  sincospi(2.0 * u2, &s, &c);
+  z0 = r * c;
+  z1 = r * s;
+}
+
+// Derive the step's parameter planes for env e from its FP64 record p[MG_NPARAM].
+__device__ void derive(const SetupView &v, int64_t e, const double *p) {
+  const double m = p[MG_P_M];
+  const double rg[3] = {p[MG_P_RG], p[MG_P_RG + 1], p[MG_P_RG + 2]};
+  const double *ma = p + MG_P_MA;
+  const double r2 = rg[0] * rg[0] + rg[1] * rg[1] + rg[2] * rg[2];
+  // I_o = I_g - m S(r_g)^2 = I_g + m (|r_g|^2 I - r_g r_g^T)  (inertia about the body origin)
+  double Io[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      Io[i][j] = (i == j ? p[MG_P_IG + i] + m * r2 : 0.0) - m * rg[i] * rg[j];
+
+  // M = M_RB + M_A = [[m I + Ma_lin, -m S(r_g)], [m S(r_g), I_o + Ma_rot]].
+  double M[6][6];
+  const double S[3][3] = {{0.0, -rg[2], rg[1]}, {rg[2], 0.0, -rg[0]}, {-rg[1], rg[0], 0.0}};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      M[i][j] = (i == j) ? m + ma[i] : 0.0;
+      M[i][3 + j] = -m * S[i][j];
+      M[3 + i][j] = m * S[i][j];
+      M[3 + i][3 + j] = Io[i][j] + ((i == j) ? ma[3 + i] : 0.0);
+    }
+
+  // Cholesky M = L L^T; L^-1 by forward substitution; M^-1 = L^-T L^-1.
+  double L[6][6] = {}, Li[6][6] = {};
+  bool spd = true;
+  for (int j = 0; j < 6; ++j) {
+    double d = M[j][j];
+    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+    if (!(d > 0.0)) {
+      spd = false;
+      d = 1.0;
+    }
+    L[j][j] = sqrt(d);
+    for (int i = j + 1; i < 6; ++i) {
+      double s = M[i][j];
+      for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+      L[i][j] = s / L[j][j];
+    }
+  }
+  for (int j = 0; j < 6; ++j) {
+    Li[j][j] = 1.0 / L[j][j];
+    for (int i = j + 1; i < 6; ++i) {
+      double s = 0.0;
+      for (int k = j; k < i; ++k) s += L[i][k] * Li[k][j];
+      Li[i][j] = -s / L[i][i];
+    }
+  }
+  double Mi[6][6];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) {
+      double s = 0.0;
+      for (int k = (i > j ? i : j); k < 6; ++k) s += Li[k][i] * Li[k][j];
+      Mi[i][j] = s;
+    }
+  if (!spd) atomicAdd(v.n_not_spd, 1ull);
+  if (rg[0] != 0.0 || rg[1] != 0.0 || rg[2] != 0.0) atomicOr(v.any_offdiag, 1u);
+
+  const double W = p[MG_P_W], B = p[MG_P_B];
+  const double G[3] = {W * rg[0] - B * p[MG_P_RB], W * rg[1] - B * p[MG_P_RB + 1],
+                       W * rg[2] - B * p[MG_P_RB + 2]};
+  const ParamPlanes &pa = v.pa;
+  auto f = [](double x) { return (float)x; };
+  pa.d0[e] = make_float4(f(m), f(ma[0]), f(ma[1]), f(ma[2]));
+  pa.d1[e] = make_float4(f(Io[0][0] + ma[3]), f(Io[1][1] + ma[4]), f(Io[2][2] + ma[5]),
+                         f(W - B));
+  pa.d2[e] = make_float4(f(p[MG_P_DL]), f(p[MG_P_DL + 1]), f(p[MG_P_DL + 2]),
+                         f(p[MG_P_DL + 3]));
+  pa.d3[e] = make_float4(f(p[MG_P_DL + 4]), f(p[MG_P_DL + 5]), f(p[MG_P_DQ]),
+                         f(p[MG_P_DQ + 1]));
+  pa.d4[e] = make_float4(f(p[MG_P_DQ + 2]), f(p[MG_P_DQ + 3]), f(p[MG_P_DQ + 4]),
+                         f(p[MG_P_DQ + 5]));
+  pa.d5[e] = make_float4(f(G[0]), f(G[1]), f(G[2]), f(p[MG_P_KT]));
+  pa.d6[e] = make_float4(f(p[MG_P_VC]), f(p[MG_P_VC + 1]), f(p[MG_P_VC + 2]),
+                         f(1.0 / p[MG_P_TAU]));
+  pa.d7[e] = make_float4(f(Mi[0][0]), f(Mi[1][1]), f(Mi[2][2]), f(Mi[3][3]));
+  pa.d8[e] = make_float2(f(Mi[4][4]), f(Mi[5][5]));
+  pa.g0[e] = make_float4(f(m * rg[0]), f(m * rg[1]), f(m * rg[2]), f(Io[0][1]));
+  pa.g1[e] = make_float4(f(Io[0][2]), f(Io[1][2]), f(Mi[0][1]), f(Mi[0][2]));
+  pa.g2[e] = make_float4(f(Mi[0][3]), f(Mi[0][4]), f(Mi[0][5]), f(Mi[1][2]));
+  pa.g3[e] = make_float4(f(Mi[1][3]), f(Mi[1][4]), f(Mi[1][5]), f(Mi[2][3]));
+  pa.g4[e] = make_float4(f(Mi[2][4]), f(Mi[2][5]), f(Mi[3][4]), f(Mi[3][5]));
+  pa.g5[e] = f(Mi[4][5]);
+}
+
+__global__ void k_randomize(const SetupView v, const float *__restrict__ nominal, uint64_t seed,
+                            double lo, double hi, double current_sigma) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= v.n) return;
+  const uint64_t gid = (uint64_t)(v.gid0 + e);
+  const float *nom = nominal + (int64_t)v.types[e] * MG_NPARAM;
+  double p[MG_NPARAM];
+  for (int j = 0; j < MG_NPARAM; ++j) p[j] = (double)nom[j];
+  uint4 x = make_uint4(0, 0, 0, 0);
+  for (int j = 0; j < 27; ++j) {
+    if (j % 4 == 0) x = draw4(seed, gid, STREAM_PARAMS, (uint32_t)(j / 4));
+    const uint32_t w = (j % 4 == 0) ? x.x : (j % 4 == 1) ? x.y : (j % 4 == 2) ? x.z : x.w;
+    const int idx = c_rand_idx[j];
+    p[idx] = (double)nom[idx] * (lo + (hi - lo) * u01d(w));
+  }
+  const uint4 c = draw4(seed, gid, STREAM_CURRENT, 0u);
+  double z0, z1, z2, z3;
+  box_muller(u01d(c.x), u01d(c.y), z0, z1);
+  box_muller(u01d(c.z), u01d(c.w), z2, z3);
+  p[MG_P_VC] += current_sigma * z0;
+  p[MG_P_VC + 1] += current_sigma * z1;
+  p[MG_P_VC + 2] += current_sigma * z2;
+  // Store FP32; derive from the stored values so that everything the step reads is consistent
+  // with what mg_get_params reports.
+  for (int j = 0; j < MG_NPARAM; ++j) {
+    const float f = (float)p[j];
+    v.raw[(int64_t)j * v.n + e] = f;
+    p[j] = (double)f;
+  }
+  derive(v, e, p);
+}
+
+__global__ void k_import_params(const SetupView v, const float *__restrict__ in) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= v.n) return;
+  double p[MG_NPARAM];
+  for (int j = 0; j < MG_NPARAM; ++j) {
+    const float f = in[e * MG_NPARAM + j];
+    v.raw[(int64_t)j * v.n + e] = f;
+    p[j] = (double)f;
+  }
+  derive(v, e, p);
+}
+
+__global__ void k_export_params(const SetupView v, float *__restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= v.n) return;
+  for (int j = 0; j < MG_NPARAM; ++j) out[e * MG_NPARAM + j] = v.raw[(int64_t)j * v.n + e];
+}
+
+__global__ void k_reset(const StatePlanes st, int64_t n, int64_t gid0,
+                        const uint8_t *__restrict__ mask, uint64_t seed, double sigma,
+                        uint32_t *__restrict__ episode, uint32_t *__restrict__ flags,
+                        unsigned long long *nonfinite_count) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n || (mask && !mask[e])) return;
+  const uint64_t gid = (uint64_t)(gid0 + e);
+  const uint32_t ep = episode[e];
+  const uint4 a = draw4(seed, gid, STREAM_RESET, 2u * ep);
+  const uint4 b = draw4(seed, gid, STREAM_RESET, 2u * ep + 1u);
+  double z[6];
+  box_muller(u01d(a.x), u01d(a.y), z[0], z[1]);
+  box_muller(u01d(a.z), u01d(a.w), z[2], z[3]);
+  box_muller(u01d(b.x), u01d(b.y), z[4], z[5]);
+  float nu[6];
+  for (int i = 0; i < 6; ++i) nu[i] = (float)(sigma * z[i]);
+  st.s0[e] = make_float4(0.f, 0.f, 0.f, 1.f);
+  st.s1[e] = make_float4(0.f, 0.f, 0.f, nu[0]);
+  st.s2[e] = make_float4(nu[1], nu[2], nu[3], nu[4]);
+  st.s3[e] = make_float4(nu[5], 0.f, 0.f, 0.f);
+  st.s4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  st.s5[e] = 0.f;
+  episode[e] = ep + 1u;
+  if (flags[e] & 1u) atomicAdd(nonfinite_count, ~0ull);  // decrement
+  flags[e] = 0u;
+}
+
+__global__ void k_export_state(const StatePlanes st, int64_t n, float *__restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const float4 a = st.s0[e], b = st.s1[e], c = st.s2[e], d = st.s3[e], f = st.s4[e];
+  const float r[MG_NSTATE] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z,
+                              c.w, d.x, d.y, d.z, d.w, f.x, f.y, f.z, f.w, st.s5[e]};
+  float *o = out + e * MG_NSTATE;
+  for (int j = 0; j < MG_NSTATE; ++j) o[j] = r[j];
+}
+
+__global__ void k_import_state(const StatePlanes st, int64_t n, const float *__restrict__ in) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const float *r = in + e * MG_NSTATE;
+  st.s0[e] = make_float4(r[0], r[1], r[2], r[3]);
+  st.s1[e] = make_float4(r[4], r[5], r[6], r[7]);
+  st.s2[e] = make_float4(r[8], r[9], r[10], r[11]);
+  st.s3[e] = make_float4(r[12], r[13], r[14], r[15]);
+  st.s4[e] = make_float4(r[16], r[17], r[18], r[19]);
+  st.s5[e] = r[20];
+}
+
+__global__ void k_flags_to_bytes(const uint32_t *__restrict__ flags, int64_t n,
+                                 uint8_t *__restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = (uint8_t)(flags[e] & 1u);
+}
+
+__global__ void k_philox(const uint32_t *__restrict__ ctr, const uint32_t *__restrict__ key,
+                         uint32_t *__restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 r = philox4x32_10(make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2],
+                                           ctr[4 * i + 3]),
+                                make_uint2(key[2 * i], key[2 * i + 1]));
+  out[4 * i] = r.x;
+  out[4 * i + 1] = r.y;
+  out[4 * i + 2] = r.z;
+  out[4 * i + 3] = r.w;
+}
+
+}  // namespace
+
+cudaError_t launch_randomize(const SetupView &v, const float *nominal, uint64_t seed, double lo,
+                             double hi, double current_sigma, cudaStream_t stream) {
+  k_randomize<<<blocks_for(v.n), kThreads, 0, stream>>>(v, nominal, seed, lo, hi,
+                                                        current_sigma);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_import_params(const SetupView &v, const float *in, cudaStream_t stream) {
+  k_import_params<<<blocks_for(v.n), kThreads, 0, stream>>>(v, in);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_params(const SetupView &v, float *out, cudaStream_t stream) {
+  k_export_params<<<blocks_for(v.n), kThreads, 0, stream>>>(v, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reset(const StatePlanes &st, int64_t n, int64_t gid0, const uint8_t *mask,
+                         uint64_t seed, double nu0_sigma, uint32_t *episode, uint32_t *flags,
+                         unsigned long long *nonfinite_count, cudaStream_t stream) {
+  k_reset<<<blocks_for(n), kThreads, 0, stream>>>(st, n, gid0, mask, seed, nu0_sigma, episode,
+                                                  flags, nonfinite_count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_state(const StatePlanes &st, int64_t n, float *out,
+                                cudaStream_t stream) {
+  k_export_state<<<blocks_for(n), kThreads, 0, stream>>>(st, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_import_state(const StatePlanes &st, int64_t n, const float *in,
+                                cudaStream_t stream) {
+  k_import_state<<<blocks_for(n), kThreads, 0, stream>>>(st, n, in);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flags_to_bytes(const uint32_t *flags, int64_t n, uint8_t *out,
+                                  cudaStream_t stream) {
+  k_flags_to_bytes<<<blocks_for(n), kThreads, 0, stream>>>(flags, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,
+                          cudaStream_t stream) {
+  k_philox<<<blocks_for(n), kThreads, 0, stream>>>(ctr, key, out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace mg

@@ -1,0 +1,203 @@
+"""``Sim``: a fleet of vehicles advanced by the extended Fossen equation (§METHOD, Eq. 1) on the
+GPU.  A thin wrapper of the C ABI: every computation runs in libmg.so's kernels; PyTorch only
+provides device memory and the stream.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import MG_MAX_THR, MG_NPARAM, MG_NSTATE, MG_NTRAJ, MGError, Ranges, VehicleParams, call
+
+__all__ = ["Sim", "vehicle_struct", "MGError"]
+
+
+def vehicle_struct(v) -> VehicleParams:
+    """Convert a vehicle definition (``params`` [35] array, ``n_thr``, ``r`` [8,3], ``d`` [8,3]
+    — e.g. ``inputs.bluerov2()``) to the C struct."""
+    p = np.asarray(v.params, dtype=np.float64)
+    s = VehicleParams()
+    s.m, s.Ixx, s.Iyy, s.Izz = p[0], p[1], p[2], p[3]
+    for i in range(6):
+        s.MA[i], s.Dl[i], s.Dq[i] = p[4 + i], p[10 + i], p[16 + i]
+    s.W, s.B = p[22], p[23]
+    for i in range(3):
+        s.rg[i], s.rb[i] = p[24 + i], p[27 + i]
+    s.kT, s.tau_m = p[30], p[31]
+    s.n_thr = int(v.n_thr)
+    r = np.asarray(v.r, dtype=np.float64)
+    d = np.asarray(v.d, dtype=np.float64)
+    for i in range(MG_MAX_THR):
+        for j in range(3):
+            s.r[i][j] = r[i, j]
+            s.d[i][j] = d[i, j]
+    return s
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    if isinstance(t, torch.Tensor):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(t.ctypes.data)
+    raise TypeError(f"expected a torch tensor or numpy array, got {type(t)}")
+
+
+def _check(t, shape, dtype):
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    if isinstance(t, torch.Tensor) and t.dtype != dtype:
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
+    if isinstance(t, np.ndarray) and t.dtype != np.dtype(str(dtype).split(".")[-1]):
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
+
+
+class Sim:
+    """A fleet of ``n_envs`` vehicles on the current CUDA device.
+
+    ``vehicle_types``: int array [n_envs] indexing ``vehicles`` (a list of vehicle definitions).
+    The sim runs on ``stream`` (default: torch's current stream at construction).
+    """
+
+    def __init__(self, n_envs: int, vehicle_types, vehicles, stream=None):
+        self._h = None
+        types = np.ascontiguousarray(np.broadcast_to(np.asarray(vehicle_types, dtype=np.int32),
+                                                     (n_envs,)))
+        arr = (VehicleParams * len(vehicles))(*[vehicle_struct(v) for v in vehicles])
+        h = ctypes.c_void_p()
+        call("mg_create", n_envs, types.ctypes.data, arr, len(vehicles), ctypes.byref(h))
+        self._h = h
+        self.n = int(n_envs)
+        self.types = types
+        self.n_thr = np.array([int(vehicles[t].n_thr) for t in types], dtype=np.int32)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.set_stream(stream if stream is not None else torch.cuda.current_stream())
+
+    # ------------------------------------------------------------------ configuration
+    def set_stream(self, stream):
+        self.stream = stream
+        call("mg_set_stream", self._h, ctypes.c_void_p(stream.cuda_stream))
+
+    def set_env_id_offset(self, offset: int):
+        call("mg_set_env_id_offset", self._h, int(offset))
+
+    def set_model_flags(self, flags: int):
+        call("mg_set_model_flags", self._h, int(flags))
+
+    def set_timestep(self, dt: float):
+        call("mg_set_timestep", self._h, float(dt))
+
+    def set_launch(self, envs_per_block: int = 128, steps_per_launch: int = 50,
+                   use_graph: bool = True):
+        call("mg_set_launch", self._h, int(envs_per_block), int(steps_per_launch),
+             1 if use_graph else 0)
+
+    def kernel_info(self) -> dict:
+        r, t, l = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        call("mg_kernel_info", self._h, ctypes.byref(r), ctypes.byref(t), ctypes.byref(l))
+        return {"regs": r.value, "max_threads": t.value, "local_bytes": l.value}
+
+    # ------------------------------------------------------------------ parameters
+    def randomize(self, seed: int, lo: float = 0.8, hi: float = 1.2, current_sigma: float = 0.2,
+                  nu0_sigma: float = 0.3):
+        r = Ranges(lo, hi, current_sigma, nu0_sigma, 0)
+        call("mg_randomize", self._h, ctypes.c_uint64(seed), ctypes.byref(r))
+
+    def set_params(self, params):
+        _check(params, (self.n, MG_NPARAM), torch.float32)
+        call("mg_set_params", self._h, _ptr(params))
+
+    def get_params(self, out=None):
+        if out is None:
+            out = torch.empty((self.n, MG_NPARAM), dtype=torch.float32, device=self.device)
+        _check(out, (self.n, MG_NPARAM), torch.float32)
+        call("mg_get_params", self._h, _ptr(out))
+        return out
+
+    # ------------------------------------------------------------------ actions and stepping
+    def set_actions(self, actions, hold_steps: int = 1):
+        """``actions``: float32 [n_seg, n_envs, 8] (device tensor, or host tensor/array)."""
+        if actions is None:
+            call("mg_set_actions", self._h, None, 0, int(hold_steps))
+            return
+        if actions.ndim != 3 or actions.shape[1:] != (self.n, MG_MAX_THR):
+            raise ValueError(f"actions must be [n_seg, {self.n}, {MG_MAX_THR}]")
+        _check(actions, actions.shape, torch.float32)
+        call("mg_set_actions", self._h, _ptr(actions), int(actions.shape[0]), int(hold_steps))
+
+    def set_procedural_actions(self, cmd_seed: int, hold_steps: int):
+        call("mg_set_procedural_actions", self._h, ctypes.c_uint64(cmd_seed), int(hold_steps))
+
+    def step(self, k: int = 1):
+        call("mg_step", self._h, int(k))
+
+    def step_record(self, k: int, traj=None):
+        """Advance k sub-steps writing the state after each to ``traj`` [k, 13, n] (device)."""
+        if traj is None:
+            traj = torch.empty((k, MG_NTRAJ, self.n), dtype=torch.float32, device=self.device)
+        _check(traj, (k, MG_NTRAJ, self.n), torch.float32)
+        call("mg_step_record", self._h, int(k), _ptr(traj))
+        return traj
+
+    # ------------------------------------------------------------------ state
+    def get_state(self, out=None):
+        if out is None:
+            out = torch.empty((self.n, MG_NSTATE), dtype=torch.float32, device=self.device)
+        _check(out, (self.n, MG_NSTATE), torch.float32)
+        call("mg_get_state", self._h, _ptr(out))
+        return out
+
+    def set_state(self, state):
+        _check(state, (self.n, MG_NSTATE), torch.float32)
+        call("mg_set_state", self._h, _ptr(state))
+
+    def reset(self, mask=None):
+        if mask is None:
+            call("mg_reset", self._h, None)
+            return
+        _check(mask, (self.n,), torch.uint8)
+        call("mg_reset", self._h, _ptr(mask))
+
+    def sync(self) -> int:
+        """Wait for the stream; return how many envs are flagged non-finite."""
+        c = ctypes.c_int64()
+        call("mg_sync", self._h, ctypes.byref(c), ok=(0, 4))
+        return c.value
+
+    def nonfinite_mask(self):
+        out = torch.empty(self.n, dtype=torch.uint8, device=self.device)
+        call("mg_get_nonfinite", self._h, _ptr(out))
+        return out
+
+    # ------------------------------------------------------------------ lifetime
+    def close(self):
+        if self._h is not None:
+            _lib.load().mg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """Evaluate Philox4x32-10 on the device for arrays ctr [n,4], key [n,2] (uint32)."""
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    key = np.ascontiguousarray(key, dtype=np.uint32).reshape(-1, 2)
+    out = np.zeros_like(ctr)
+    call("mg_philox4x32_10", ctr.ctypes.data, key.ctypes.data, out.ctypes.data, ctr.shape[0])
+    return out

@@ -132,6 +132,18 @@ mg_status mg_set_timestep(mg_sim *sim, float dt);
 mg_status mg_set_launch(mg_sim *sim, int32_t envs_per_block, int32_t steps_per_launch,
                         int32_t use_graph);
 
+/* Schedule of mg_step.  work_queue != 0 runs all k sub-steps in one launch in which
+ * warps claim (32-env slice, steps_per_launch-chunk) units from a queue in chunk-major order,
+ * each unit waiting (bounded, see MG_ETIMEOUT in mg_sync) for its slice's previous chunk; faster
+ * warps take more units, which balances the SMs when the fleet has more 32-env slices than
+ * resident warps.  wide != 0 gives that kernel 168 registers per thread instead of
+ * 128 (diagonal-mass fleets; the general kernel always has 168); warps_per_sm > 0 caps its
+ * resident warps per SM (0 = as many as fit).  work_queue = 0 (default) launches a static grid of
+ * envs_per_block-env blocks per steps_per_launch sub-steps (steps_per_launch = 1: the plain
+ * per-step form).  All choices give bit-identical results.  mg_step_record always uses the
+ * static grid.  MG_EINVAL unless 0 <= warps_per_sm <= 64. */
+mg_status mg_set_schedule(mg_sim *sim, int32_t work_queue, int32_t wide, int32_t warps_per_sm);
+
 /* Domain randomisation (§METHOD; §EXPERIMENTS "supports domain randomization"): per env, draws
  * from Philox4x32-10 keyed by (seed, env id + offset), then builds M = M_RB + M_A in FP64 and
  * inverts it by Cholesky.  Also records (seed, nu0_sigma) for mg_reset and zeroes every env's
@@ -167,6 +179,28 @@ mg_status mg_step(mg_sim *sim, int32_t k);
  * [k][MG_NTRAJ][n_envs] (component-major per step: p(3) q(4) nu(6)). Never graph-replayed. */
 mg_status mg_step_record(mg_sim *sim, int32_t k, float *traj);
 
+/* Forward rollout for differentiation: T sub-steps from the current state and action cursor
+ * (static grid, as mg_step_record), writing the state after every sub-step to traj, device
+ * [T][MG_NTRAJ][n], and the full state before sub-steps 0, C, 2C, ... to ckpt, device
+ * [ceil(T / C)][MG_NSTATE][n] (component-major).  *step0_out (may be NULL) receives the action
+ * cursor at the start; pass it to mg_rollout_backward.  Errors: MG_EINVAL (T < 1, C outside
+ * [1, 32], host buffers). */
+mg_status mg_rollout_forward(mg_sim *sim, int32_t T, int32_t C, float *traj, float *ckpt,
+                             int64_t *step0_out);
+
+/* Reverse pass of that rollout: the discrete adjoint of the FP32 RK4 sub-steps (renormalisation
+ * included), re-running each C-step segment from its checkpoint.  dtraj: device
+ * [T][MG_NTRAJ][n], the loss gradient with respect to traj.  Writes dcoef, device [n][18], the
+ * gradient with respect to each env's added-mass, linear-damping and quadratic-damping diagonals
+ * (record entries 4..21, §METHOD Eq. 1 hydrodynamic term); adds the gradient with respect to the
+ * buffered actions (Eq. 3) into dact, device [n_seg][n][MG_MAX_THR] (may be NULL); writes the
+ * gradient with respect to the start state into dstate0, device [n][MG_NSTATE] (may be NULL).
+ * Parameters and actions must be those of the forward; the sim's state is not read or changed.
+ * Errors: MG_EINVAL (bad sizes, host buffers, a fleet with r_g != 0, procedural actions). */
+mg_status mg_rollout_backward(mg_sim *sim, int32_t T, int32_t C, const float *ckpt,
+                              const float *dtraj, int64_t step0, float *dcoef, float *dact,
+                              float *dstate0);
+
 /* State in the record layout [n][MG_NSTATE] = p(3) q(4: w,x,y,z) nu(6) n(8, zero past n_thr);
  * host or device. */
 mg_status mg_get_state(mg_sim *sim, float *out);
@@ -179,7 +213,9 @@ mg_status mg_set_state(mg_sim *sim, const float *in);
 mg_status mg_reset(mg_sim *sim, const uint8_t *mask);
 
 /* Wait for the stream; *nonfinite_count (may be NULL) receives how many envs are flagged
- * non-finite.  Returns MG_ENONFINITE when that count is non-zero. */
+ * non-finite.  Returns MG_ETIMEOUT if a work-queue wait ever gave up (results since then are
+ * unreliable; this is not expected to happen), else MG_ENONFINITE when that count is
+ * non-zero. */
 mg_status mg_sync(mg_sim *sim, int64_t *nonfinite_count);
 
 /* Per-env non-finite flags into out [n_envs] (host or device), 1 = flagged. */

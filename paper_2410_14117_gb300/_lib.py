@@ -57,6 +57,7 @@ SIGNATURES = {
     "mg_set_model_flags": [_P, _U32],
     "mg_set_timestep": [_P, _F],
     "mg_set_launch": [_P, _I32, _I32, _I32],
+    "mg_set_schedule": [_P, _I32, _I32, _I32],
     "mg_randomize": [_P, _U64, ctypes.POINTER(Ranges)],
     "mg_set_params": [_P, _P],
     "mg_get_params": [_P, _P],
@@ -64,6 +65,8 @@ SIGNATURES = {
     "mg_set_procedural_actions": [_P, _U64, _I32],
     "mg_step": [_P, _I32],
     "mg_step_record": [_P, _I32, _P],
+    "mg_rollout_forward": [_P, _I32, _I32, _P, _P, ctypes.POINTER(_I64)],
+    "mg_rollout_backward": [_P, _I32, _I32, _P, _P, _I64, _P, _P, _P],
     "mg_get_state": [_P, _P],
     "mg_set_state": [_P, _P],
     "mg_reset": [_P, _P],

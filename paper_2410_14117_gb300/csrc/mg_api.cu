@@ -83,13 +83,22 @@ struct mg_sim {
   float *nominal_d = nullptr;
   uint32_t *flags = nullptr;
   uint32_t *episode = nullptr;
-  unsigned long long *counters = nullptr;  // [0] non-finite envs, [1] non-SPD envs
+  unsigned long long *counters = nullptr;  // [0] non-finite envs, [1] non-SPD envs,
+                                           // [2] work-queue wait time-outs
   unsigned int *offdiag = nullptr;
 
-  // blocks
+  // static-schedule blocks
   BlockDesc *blocks_d = nullptr;
   int n_blocks = 0;
   int threads = 128;
+  // work-queue schedule: 32-env slices and the scheduler words
+  BlockDesc *slices_d = nullptr;
+  int n_slices = 0;
+  uint32_t *sched = nullptr;
+  int n_sm = 1;
+  bool queue = false;
+  bool queue_wide = true;
+  int32_t queue_warps_per_sm = 0;
 
   // actions
   float *act = nullptr;
@@ -120,6 +129,7 @@ struct mg_sim {
     v.st = st;
     v.pa = pa;
     v.geo = geo_d;
+    v.n_types = n_types;
     v.n = n;
     v.gid0 = gid0;
     v.act = reinterpret_cast<const float4 *>(act);
@@ -130,7 +140,7 @@ struct mg_sim {
     v.model_flags = model_flags;
     v.dt = dt;
     v.flags = flags;
-    v.nonfinite_count = counters;
+    v.counters = counters;
     return v;
   }
 
@@ -179,24 +189,30 @@ mg_status input_ptr(mg_sim *s, const void *in, size_t bytes, const void **dev) {
   return MG_OK;
 }
 
-// Build the block list: runs of equal vehicle type, cut into chunks of at most epb envs.
-mg_status build_blocks(mg_sim *s) {
+// Runs of equal vehicle type, cut into pieces of at most `width` envs.
+std::vector<BlockDesc> cut_runs(const mg_sim *s, int width) {
   std::vector<BlockDesc> b;
   int64_t e = 0;
   while (e < s->n) {
     const int32_t t = s->types_h[e];
     int64_t end = e;
     while (end < s->n && s->types_h[end] == t) ++end;
-    for (int64_t a = e; a < end; a += s->epb) {
+    for (int64_t a = e; a < end; a += width) {
       BlockDesc d;
       d.env0 = (int32_t)a;
-      d.count = (int32_t)std::min<int64_t>(s->epb, end - a);
+      d.count = (int32_t)std::min<int64_t>(width, end - a);
       d.type = t;
       d.n_thr = s->vp[t].n_thr;
       b.push_back(d);
     }
     e = end;
   }
+  return b;
+}
+
+// Build the static-schedule block list (pieces of at most epb envs).
+mg_status build_blocks(mg_sim *s) {
+  const std::vector<BlockDesc> b = cut_runs(s, s->epb);
   if (s->blocks_d) {
     MG_CK(cudaStreamSynchronize(s->stream));
     cudaFree(s->blocks_d);
@@ -212,6 +228,12 @@ mg_status build_blocks(mg_sim *s) {
 
 mg_status launch_chunks(mg_sim *s, int32_t k, float *traj, cudaStream_t stream) {
   const FleetView v = s->view();
+  if (s->queue && !traj) {
+    MG_CK(launch_fleet_queue(v, s->slices_d, s->n_slices, s->ntv, s->diag, s->queue_wide,
+                             s->queue_warps_per_sm, s->cursor, k, s->spl, s->sched, s->n_sm,
+                             stream));
+    return MG_OK;
+  }
   for (int32_t done = 0; done < k;) {
     const int32_t kk = std::min(s->spl, k - done);
     float *t = traj ? traj + (int64_t)done * MG_NTRAJ * s->n : nullptr;
@@ -317,7 +339,11 @@ mg_status mg_create(int64_t n_envs, const int32_t *vehicle_types,
   const size_t o_nom = take(4 * MG_NPARAM * n_types);
   const size_t o_flags = take(4 * n);
   const size_t o_ep = take(4 * n);
-  const size_t o_cnt = take(2 * sizeof(unsigned long long));
+  const std::vector<BlockDesc> slices = cut_runs(s, 32);
+  s->n_slices = (int)slices.size();
+  const size_t o_slices = take(sizeof(BlockDesc) * slices.size());
+  const size_t o_sched = take(queue_sched_bytes(s->n_slices));
+  const size_t o_cnt = take(3 * sizeof(unsigned long long));
   const size_t o_off = take(sizeof(unsigned int));
   cudaError_t e = cudaMalloc(&s->arena, off);
   if (e != cudaSuccess) {
@@ -345,6 +371,12 @@ mg_status mg_create(int64_t n_envs, const int32_t *vehicle_types,
   s->flags = (uint32_t *)(a + o_flags);
   s->episode = (uint32_t *)(a + o_ep);
   s->counters = (unsigned long long *)(a + o_cnt);
+  s->slices_d = (BlockDesc *)(a + o_slices);
+  s->sched = (uint32_t *)(a + o_sched);
+  {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, s->dev) == cudaSuccess) s->n_sm = prop.multiProcessorCount;
+  }
   s->offdiag = (unsigned int *)(a + o_off);
 
   // Per-type geometry and nominal records.
@@ -396,7 +428,9 @@ mg_status mg_create(int64_t n_envs, const int32_t *vehicle_types,
   MG_CKB(cudaMemcpy(s->types_d, s->types_h.data(), 4 * n, cudaMemcpyHostToDevice));
   MG_CKB(cudaMemset(s->flags, 0, 4 * n));
   MG_CKB(cudaMemset(s->episode, 0, 4 * n));
-  MG_CKB(cudaMemset(s->counters, 0, 2 * sizeof(unsigned long long)));
+  MG_CKB(cudaMemset(s->counters, 0, 3 * sizeof(unsigned long long)));
+  MG_CKB(cudaMemcpy(s->slices_d, slices.data(), sizeof(BlockDesc) * slices.size(),
+                    cudaMemcpyHostToDevice));
   MG_CKB(cudaMemset(s->offdiag, 0, sizeof(unsigned int)));
   // Nominal parameters: a randomisation with zero width.
   MG_CKB(launch_randomize(s->setup_view(), s->nominal_d, 0, 1.0, 1.0, 0.0, s->stream));
@@ -470,6 +504,16 @@ mg_status mg_set_launch(mg_sim *s, int32_t envs_per_block, int32_t steps_per_lau
     s->epb = envs_per_block;
     return build_blocks(s);
   }
+  return MG_OK;
+}
+
+mg_status mg_set_schedule(mg_sim *s, int32_t work_queue, int32_t wide, int32_t warps_per_sm) {
+  MG_NONNULL(s);
+  if (warps_per_sm < 0 || warps_per_sm > 64) return fail(MG_EINVAL, "warps_per_sm in [0, 64]");
+  s->queue = work_queue != 0;
+  s->queue_wide = wide != 0;
+  s->queue_warps_per_sm = warps_per_sm;
+  s->drop_graphs();
   return MG_OK;
 }
 
@@ -610,6 +654,49 @@ mg_status mg_step_record(mg_sim *s, int32_t k, float *traj) {
   return MG_OK;
 }
 
+mg_status mg_rollout_forward(mg_sim *s, int32_t T, int32_t C, float *traj, float *ckpt,
+                             int64_t *step0_out) {
+  MG_NONNULL(s);
+  MG_NONNULL(traj);
+  MG_NONNULL(ckpt);
+  if (T < 1 || C < 1 || C > adjoint_max_interval())
+    return fail(MG_EINVAL, "need T >= 1 and 1 <= C <= 32");
+  if (!is_device_ptr(traj) || !is_device_ptr(ckpt))
+    return fail(MG_EINVAL, "traj and ckpt must be device memory");
+  const FleetView v = s->view();
+  const int64_t step0 = s->cursor;
+  for (int32_t t0 = 0; t0 < T; t0 += C) {
+    const int32_t len = std::min(C, T - t0);
+    MG_CK(launch_checkpoint(s->st, s->n, ckpt + (int64_t)(t0 / C) * MG_NSTATE * s->n,
+                            s->stream));
+    MG_CK(launch_fleet(v, s->blocks_d, s->n_blocks, s->threads, s->ntv, s->diag, step0 + t0,
+                       len, traj + (int64_t)t0 * MG_NTRAJ * s->n, s->stream));
+  }
+  s->cursor += T;
+  if (step0_out) *step0_out = step0;
+  return MG_OK;
+}
+
+mg_status mg_rollout_backward(mg_sim *s, int32_t T, int32_t C, const float *ckpt,
+                              const float *dtraj, int64_t step0, float *dcoef, float *dact,
+                              float *dstate0) {
+  MG_NONNULL(s);
+  MG_NONNULL(ckpt);
+  MG_NONNULL(dtraj);
+  MG_NONNULL(dcoef);
+  if (T < 1 || C < 1 || C > adjoint_max_interval() || step0 < 0)
+    return fail(MG_EINVAL, "need T >= 1, 1 <= C <= 32, step0 >= 0");
+  if (!s->diag) return fail(MG_EINVAL, "the adjoint needs a diagonal mass matrix (r_g = 0)");
+  if (s->proc) return fail(MG_EINVAL, "the adjoint needs buffered actions (mg_set_actions)");
+  for (const void *p : {(const void *)ckpt, (const void *)dtraj, (const void *)dcoef})
+    if (!is_device_ptr(p)) return fail(MG_EINVAL, "adjoint buffers must be device memory");
+  if ((dact && !is_device_ptr(dact)) || (dstate0 && !is_device_ptr(dstate0)))
+    return fail(MG_EINVAL, "adjoint buffers must be device memory");
+  MG_CK(launch_adjoint(s->view(), s->types_d, s->ntv != NT_6, ckpt, dtraj, T, C, step0, dcoef,
+                       dact, dstate0, s->stream));
+  return MG_OK;
+}
+
 mg_status mg_get_state(mg_sim *s, float *out) {
   MG_NONNULL(s);
   MG_NONNULL(out);
@@ -652,10 +739,16 @@ mg_status mg_reset(mg_sim *s, const uint8_t *mask) {
 
 mg_status mg_sync(mg_sim *s, int64_t *nonfinite_count) {
   MG_NONNULL(s);
-  unsigned long long c = 0;
-  mg_status st = read_counter(s, 0, &c);
+  unsigned long long c = 0, to = 0;
+  mg_status st = read_counter(s, 2, &to);
   if (st != MG_OK) return st;
+  if ((st = read_counter(s, 0, &c)) != MG_OK) return st;
   if (nonfinite_count) *nonfinite_count = (int64_t)c;
+  if (to) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "%llu work-queue waits timed out", to);
+    return fail(MG_ETIMEOUT, buf);
+  }
   if (c) {
     char buf[128];
     snprintf(buf, sizeof buf, "%llu envs have a non-finite state", c);
@@ -698,7 +791,9 @@ mg_status mg_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *o
 mg_status mg_kernel_info(mg_sim *s, int32_t *regs, int32_t *max_threads, int32_t *local_bytes) {
   MG_NONNULL(s);
   cudaFuncAttributes a;
-  MG_CK(fleet_kernel_attributes(s->ntv, s->diag, false, &a));
+  int per_sm = 0;
+  if (s->queue) MG_CK(queue_kernel_attributes(s->ntv, s->diag, s->queue_wide, &a, &per_sm));
+  else MG_CK(fleet_kernel_attributes(s->ntv, s->diag, false, &a));
   if (regs) *regs = a.numRegs;
   if (max_threads) *max_threads = a.maxThreadsPerBlock;
   if (local_bytes) *local_bytes = (int32_t)a.localSizeBytes;

@@ -108,9 +108,13 @@ __device__ __forceinline__ void load_par(const ParamPlanes &pa, int64_t e, Par<D
   }
 }
 
-template <int MT>
+// L2 = true loads through L2 only (ld.cg): needed when another SM may have written the state
+// during the same kernel (work-queue schedule), so that no stale L1 line is read.
+template <int MT, bool L2 = false>
 __device__ __forceinline__ void load_state(const StatePlanes &sp, int64_t e, St<MT> &s) {
-  const float4 a = sp.s0[e], b = sp.s1[e], c = sp.s2[e], d = sp.s3[e], f = sp.s4[e];
+  const float4 a = L2 ? __ldcg(sp.s0 + e) : sp.s0[e], b = L2 ? __ldcg(sp.s1 + e) : sp.s1[e];
+  const float4 c = L2 ? __ldcg(sp.s2 + e) : sp.s2[e], d = L2 ? __ldcg(sp.s3 + e) : sp.s3[e];
+  const float4 f = L2 ? __ldcg(sp.s4 + e) : sp.s4[e];
   s.p[0] = a.x; s.p[1] = a.y; s.p[2] = a.z; s.q[0] = a.w;
   s.q[1] = b.x; s.q[2] = b.y; s.q[3] = b.z; s.v[0] = b.w;
   s.v[1] = c.x; s.v[2] = c.y; s.w[0] = c.z; s.w[1] = c.w;
@@ -118,7 +122,7 @@ __device__ __forceinline__ void load_state(const StatePlanes &sp, int64_t e, St<
   s.n[3] = f.x; s.n[4] = f.y; s.n[5] = f.z;
   if constexpr (MT > 6) {
     s.n[6] = f.w;
-    s.n[7] = sp.s5[e];
+    s.n[7] = L2 ? __ldcg(sp.s5 + e) : sp.s5[e];
   }
 }
 
@@ -137,10 +141,16 @@ __device__ __forceinline__ void store_state(const StatePlanes &sp, int64_t e, co
 }
 
 // ---------------------------------------------------------------- right-hand side of Eq. 1
-// d = f(s; c).  gdir/garm: the block's vehicle type's thruster directions and moment arms (in
-// shared memory); nt = its thruster count (only read when MIXED).
+// d = f(s; c) with two storage conventions that save multiplies in the hot loop:
+//   - cs[i] = c_i / tau_m (the command pre-divided by the lag constant once per segment), so
+//     n_i' = cs_i - n_i / tau_m is a single FMA;
+//   - d.q holds 2 q' (the 1/2 of q' = 1/2 q (x) (0, w) is folded into the RK4 weights).
+// Every sum is written as a chain of FMAs into the generalised force (same terms as Eq. 1; only
+// the rounding order differs from a term-by-term evaluation).
+// gdir/garm: the block's vehicle type's thruster directions and moment arms (shared memory);
+// nt = its thruster count (only read when MIXED).
 template <int MT, bool DIAG, bool MIXED>
-__device__ __forceinline__ void rhs(const St<MT> &s, const float (&c)[MT], const Par<DIAG> &P,
+__device__ __forceinline__ void rhs(const St<MT> &s, const float (&cs)[MT], const Par<DIAG> &P,
                                     const float4 *gdir, const float4 *garm, int nt,
                                     bool current_accel, St<MT> &d) {
   // Thrusters (Eq. 3 actions): F_i = kT n_i|n_i| along d_i at r_i; n_i' = (c_i - n_i) / tau_m.
@@ -152,71 +162,83 @@ __device__ __forceinline__ void rhs(const St<MT> &s, const float (&c)[MT], const
       const float4 dd = gdir[i], aa = garm[i];
       t0 = fmaf(f, dd.x, t0); t1 = fmaf(f, dd.y, t1); t2 = fmaf(f, dd.z, t2);
       t3 = fmaf(f, aa.x, t3); t4 = fmaf(f, aa.y, t4); t5 = fmaf(f, aa.z, t5);
-      d.n[i] = (c[i] - s.n[i]) * P.itau;
+      d.n[i] = fmaf(-s.n[i], P.itau, cs[i]);
     } else {
       d.n[i] = 0.f;
     }
   }
 
-  // Attitude matrix R(q) = I + 2 q_w S(eps) + 2 S(eps)^2 (body -> NED).
+  // Attitude matrix R(q) = I + 2 q_w S(eps) + 2 S(eps)^2 (body -> NED), written out.
   const float qw = s.q[0], qx = s.q[1], qy = s.q[2], qz = s.q[3];
-  const float x2 = qx + qx, y2 = qy + qy, z2 = qz + qz;
-  const float xx = qx * x2, yy = qy * y2, zz = qz * z2;
-  const float xy = qx * y2, xz = qx * z2, yz = qy * z2;
-  const float wx = qw * x2, wy = qw * y2, wz = qw * z2;
-  const float R00 = 1.f - yy - zz, R01 = xy - wz, R02 = xz + wy;
-  const float R10 = xy + wz, R11 = 1.f - xx - zz, R12 = yz - wx;
-  const float R20 = xz - wy, R21 = yz + wx, R22 = 1.f - xx - yy;
+  const float tx = qx + qx, ty = qy + qy, tz = qz + qz;
+  const float zdiag = fmaf(-qz, tz, 1.f);
+  const float R00 = fmaf(-qy, ty, zdiag), R11 = fmaf(-qx, tx, zdiag);
+  const float R22 = fmaf(-qx, tx, fmaf(-qy, ty, 1.f));
+  const float xy = qx * ty, xz = qx * tz, yz = qy * tz;
+  const float R01 = fmaf(-qw, tz, xy), R10 = fmaf(qw, tz, xy);
+  const float R02 = fmaf(qw, ty, xz), R20 = fmaf(-qw, ty, xz);
+  const float R12 = fmaf(-qw, tx, yz), R21 = fmaf(qw, tx, yz);
 
   const float v0 = s.v[0], v1 = s.v[1], v2 = s.v[2];
   const float w0 = s.w[0], w1 = s.w[1], w2 = s.w[2];
 
   // Current constant in NED, seen from the body: v_c^b = R^T v_c; relative velocity v_r.
-  const float cb0 = R00 * P.vc0 + R10 * P.vc1 + R20 * P.vc2;
-  const float cb1 = R01 * P.vc0 + R11 * P.vc1 + R21 * P.vc2;
-  const float cb2 = R02 * P.vc0 + R12 * P.vc1 + R22 * P.vc2;
+  const float cb0 = fmaf(R20, P.vc2, fmaf(R10, P.vc1, R00 * P.vc0));
+  const float cb1 = fmaf(R21, P.vc2, fmaf(R11, P.vc1, R01 * P.vc0));
+  const float cb2 = fmaf(R22, P.vc2, fmaf(R12, P.vc1, R02 * P.vc0));
   const float r0 = v0 - cb0, r1 = v1 - cb1, r2 = v2 - cb2;
 
-  // Momenta: Q1 = M_A,lin v_r; P1 + Q1 = m v + Q1 (+ w x m r_g);
-  //          P2 + Q2 = (diag(I_o) + M_A,rot) w (+ off-diagonal I_o w + m r_g x v).
+  // Momenta: Q1 = M_A,lin v_r; h = P1 + Q1 = m v + Q1 (+ w x m r_g);
+  //          k = P2 + Q2 = (diag(I_o) + M_A,rot) w (+ off-diagonal I_o w + m r_g x v).
   const float q0 = P.ma0 * r0, q1 = P.ma1 * r1, q2 = P.ma2 * r2;
   float h0 = fmaf(P.m, v0, q0), h1 = fmaf(P.m, v1, q1), h2 = fmaf(P.m, v2, q2);
   float k0 = P.J0 * w0, k1 = P.J1 * w1, k2 = P.J2 * w2;
-  // Rotational Coriolis: v_r x Q1 (+ v x P1, which is v x (w x m r_g) as v x m v = 0).
-  float cr0 = r1 * q2 - r2 * q1, cr1 = r2 * q0 - r0 * q2, cr2 = r0 * q1 - r1 * q0;
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f;  // w x m r_g
   if constexpr (!DIAG) {
-    const float a0 = w1 * P.mrg2 - w2 * P.mrg1;  // w x m r_g
-    const float a1 = w2 * P.mrg0 - w0 * P.mrg2;
-    const float a2 = w0 * P.mrg1 - w1 * P.mrg0;
+    a0 = fmaf(w1, P.mrg2, -w2 * P.mrg1);
+    a1 = fmaf(w2, P.mrg0, -w0 * P.mrg2);
+    a2 = fmaf(w0, P.mrg1, -w1 * P.mrg0);
     h0 += a0; h1 += a1; h2 += a2;
-    cr0 += v1 * a2 - v2 * a1; cr1 += v2 * a0 - v0 * a2; cr2 += v0 * a1 - v1 * a0;
-    k0 += P.Ixy * w1 + P.Ixz * w2 + (P.mrg1 * v2 - P.mrg2 * v1);
-    k1 += P.Ixy * w0 + P.Iyz * w2 + (P.mrg2 * v0 - P.mrg0 * v2);
-    k2 += P.Ixz * w0 + P.Iyz * w1 + (P.mrg0 * v1 - P.mrg1 * v0);
+    k0 = fmaf(P.Ixy, w1, fmaf(P.Ixz, w2, fmaf(P.mrg1, v2, fmaf(-P.mrg2, v1, k0))));
+    k1 = fmaf(P.Ixy, w0, fmaf(P.Iyz, w2, fmaf(P.mrg2, v0, fmaf(-P.mrg0, v2, k1))));
+    k2 = fmaf(P.Ixz, w0, fmaf(P.Iyz, w1, fmaf(P.mrg0, v1, fmaf(-P.mrg1, v0, k2))));
   }
-  const float cl0 = w1 * h2 - w2 * h1, cl1 = w2 * h0 - w0 * h2, cl2 = w0 * h1 - w1 * h0;
-  cr0 += w1 * k2 - w2 * k1;
-  cr1 += w2 * k0 - w0 * k2;
-  cr2 += w0 * k1 - w1 * k0;
 
-  // Restoring: k = R^T e3; the generalised force -g = [(W - B) k ; G x k].
-  const float e0 = R20, e1 = R21, e2 = R22;
-
-  // Generalised force f = tau - C nu - D(nu_r) nu_r - g [- M_A (w x v_c^b)].
-  float f0 = P.kT * t0 - cl0 - fmaf(P.dq[0], fabsf(r0), P.dl[0]) * r0 + P.wb * e0;
-  float f1 = P.kT * t1 - cl1 - fmaf(P.dq[1], fabsf(r1), P.dl[1]) * r1 + P.wb * e1;
-  float f2 = P.kT * t2 - cl2 - fmaf(P.dq[2], fabsf(r2), P.dl[2]) * r2 + P.wb * e2;
-  const float f3 = P.kT * t3 - cr0 - fmaf(P.dq[3], fabsf(w0), P.dl[3]) * w0 +
-                   (P.G1 * e2 - P.G2 * e1);
-  const float f4 = P.kT * t4 - cr1 - fmaf(P.dq[4], fabsf(w1), P.dl[4]) * w1 +
-                   (P.G2 * e0 - P.G0 * e2);
-  const float f5 = P.kT * t5 - cr2 - fmaf(P.dq[5], fabsf(w2), P.dl[5]) * w2 +
-                   (P.G0 * e1 - P.G1 * e0);
+  // Translational generalised force:
+  //   kT t + (W - B) k_e - w x h - (Dl + Dq |v_r|) v_r [- M_A,lin (w x v_c^b)],
+  // with k_e = R^T e3 = (R20, R21, R22) the restoring direction.
+  float f0 = fmaf(P.wb, R20, P.kT * t0);
+  float f1 = fmaf(P.wb, R21, P.kT * t1);
+  float f2 = fmaf(P.wb, R22, P.kT * t2);
+  f0 = fmaf(w2, h1, fmaf(-w1, h2, f0));
+  f1 = fmaf(w0, h2, fmaf(-w2, h0, f1));
+  f2 = fmaf(w1, h0, fmaf(-w0, h1, f2));
+  f0 = fmaf(-fmaf(P.dq[0], fabsf(r0), P.dl[0]), r0, f0);
+  f1 = fmaf(-fmaf(P.dq[1], fabsf(r1), P.dl[1]), r1, f1);
+  f2 = fmaf(-fmaf(P.dq[2], fabsf(r2), P.dl[2]), r2, f2);
   if (current_accel) {
-    f0 -= P.ma0 * (w1 * cb2 - w2 * cb1);
-    f1 -= P.ma1 * (w2 * cb0 - w0 * cb2);
-    f2 -= P.ma2 * (w0 * cb1 - w1 * cb0);
+    f0 = fmaf(-P.ma0, fmaf(w1, cb2, -w2 * cb1), f0);
+    f1 = fmaf(-P.ma1, fmaf(w2, cb0, -w0 * cb2), f1);
+    f2 = fmaf(-P.ma2, fmaf(w0, cb1, -w1 * cb0), f2);
   }
+  // Rotational: kT t' - v_r x Q1 - w x k [- v x (w x m r_g)] - (Dl + Dq|w|) w + G x k_e.
+  float f3 = fmaf(r2, q1, fmaf(-r1, q2, P.kT * t3));
+  float f4 = fmaf(r0, q2, fmaf(-r2, q0, P.kT * t4));
+  float f5 = fmaf(r1, q0, fmaf(-r0, q1, P.kT * t5));
+  f3 = fmaf(w2, k1, fmaf(-w1, k2, f3));
+  f4 = fmaf(w0, k2, fmaf(-w2, k0, f4));
+  f5 = fmaf(w1, k0, fmaf(-w0, k1, f5));
+  if constexpr (!DIAG) {
+    f3 = fmaf(v2, a1, fmaf(-v1, a2, f3));
+    f4 = fmaf(v0, a2, fmaf(-v2, a0, f4));
+    f5 = fmaf(v1, a0, fmaf(-v0, a1, f5));
+  }
+  f3 = fmaf(-fmaf(P.dq[3], fabsf(w0), P.dl[3]), w0, f3);
+  f4 = fmaf(-fmaf(P.dq[4], fabsf(w1), P.dl[4]), w1, f4);
+  f5 = fmaf(-fmaf(P.dq[5], fabsf(w2), P.dl[5]), w2, f5);
+  f3 = fmaf(-P.G2, R21, fmaf(P.G1, R22, f3));
+  f4 = fmaf(-P.G0, R22, fmaf(P.G2, R20, f4));
+  f5 = fmaf(-P.G1, R20, fmaf(P.G0, R21, f5));
 
   // nu' = M^-1 f.
   if constexpr (DIAG) {
@@ -232,22 +254,24 @@ __device__ __forceinline__ void rhs(const St<MT> &s, const float (&c)[MT], const
     d.w[2] = o[4] * f0 + o[8] * f1 + o[11] * f2 + o[13] * f3 + o[14] * f4 + P.mi[5] * f5;
   }
 
-  // Kinematics: p' = R v; q' = 1/2 q (x) (0, w).
-  d.p[0] = R00 * v0 + R01 * v1 + R02 * v2;
-  d.p[1] = R10 * v0 + R11 * v1 + R12 * v2;
-  d.p[2] = R20 * v0 + R21 * v1 + R22 * v2;
-  d.q[0] = -0.5f * (qx * w0 + qy * w1 + qz * w2);
-  d.q[1] = 0.5f * (qw * w0 - qz * w1 + qy * w2);
-  d.q[2] = 0.5f * (qz * w0 + qw * w1 - qx * w2);
-  d.q[3] = 0.5f * (-qy * w0 + qx * w1 + qw * w2);
+  // Kinematics: p' = R v; 2 q' = q (x) (0, w).
+  d.p[0] = fmaf(R02, v2, fmaf(R01, v1, R00 * v0));
+  d.p[1] = fmaf(R12, v2, fmaf(R11, v1, R10 * v0));
+  d.p[2] = fmaf(R22, v2, fmaf(R21, v1, R20 * v0));
+  d.q[0] = fmaf(-qz, w2, fmaf(-qy, w1, -qx * w0));
+  d.q[1] = fmaf(qy, w2, fmaf(-qz, w1, qw * w0));
+  d.q[2] = fmaf(-qx, w2, fmaf(qw, w1, qz * w0));
+  d.q[3] = fmaf(qw, w2, fmaf(qx, w1, -qy * w0));
 }
 
+// y = x + a k, with the quaternion taking a / 2 (its derivative is stored doubled).
 template <int MT>
 __device__ __forceinline__ void axpy(St<MT> &y, const St<MT> &x, float a, const St<MT> &k) {
+  const float aq = 0.5f * a;
 #pragma unroll
   for (int i = 0; i < 3; ++i) y.p[i] = fmaf(a, k.p[i], x.p[i]);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) y.q[i] = fmaf(a, k.q[i], x.q[i]);
+  for (int i = 0; i < 4; ++i) y.q[i] = fmaf(aq, k.q[i], x.q[i]);
 #pragma unroll
   for (int i = 0; i < 3; ++i) y.v[i] = fmaf(a, k.v[i], x.v[i]);
 #pragma unroll
@@ -256,26 +280,27 @@ __device__ __forceinline__ void axpy(St<MT> &y, const St<MT> &x, float a, const 
   for (int i = 0; i < MT; ++i) y.n[i] = fmaf(a, k.n[i], x.n[i]);
 }
 
-// One sub-step (§METHOD): classical RK4 of size h, command held, then q <- q / |q|.
+// One sub-step (§METHOD): classical RK4 of size h, command held (cs = c / tau_m), then
+// q <- q / |q|.
 template <int MT, bool DIAG, bool MIXED>
-__device__ __forceinline__ void rk4_step(St<MT> &s, const float (&c)[MT], const Par<DIAG> &P,
+__device__ __forceinline__ void rk4_step(St<MT> &s, const float (&cs)[MT], const Par<DIAG> &P,
                                          const float4 *gdir, const float4 *garm, int nt,
                                          bool current_accel, float h) {
   const float hh = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f);
   St<MT> k, y, acc;
-  rhs<MT, DIAG, MIXED>(s, c, P, gdir, garm, nt, current_accel, k);
+  rhs<MT, DIAG, MIXED>(s, cs, P, gdir, garm, nt, current_accel, k);
   axpy(acc, s, h6, k);
   axpy(y, s, hh, k);
-  rhs<MT, DIAG, MIXED>(y, c, P, gdir, garm, nt, current_accel, k);
+  rhs<MT, DIAG, MIXED>(y, cs, P, gdir, garm, nt, current_accel, k);
   axpy(acc, acc, h3, k);
   axpy(y, s, hh, k);
-  rhs<MT, DIAG, MIXED>(y, c, P, gdir, garm, nt, current_accel, k);
+  rhs<MT, DIAG, MIXED>(y, cs, P, gdir, garm, nt, current_accel, k);
   axpy(acc, acc, h3, k);
   axpy(y, s, h, k);
-  rhs<MT, DIAG, MIXED>(y, c, P, gdir, garm, nt, current_accel, k);
+  rhs<MT, DIAG, MIXED>(y, cs, P, gdir, garm, nt, current_accel, k);
   axpy(s, acc, h6, k);
-  const float inv = rsqrtf(s.q[0] * s.q[0] + s.q[1] * s.q[1] + s.q[2] * s.q[2] +
-                           s.q[3] * s.q[3]);
+  const float inv = rsqrtf(fmaf(s.q[0], s.q[0], fmaf(s.q[1], s.q[1],
+                                fmaf(s.q[2], s.q[2], s.q[3] * s.q[3]))));
 #pragma unroll
   for (int i = 0; i < 4; ++i) s.q[i] *= inv;
 }

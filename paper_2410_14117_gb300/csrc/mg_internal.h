@@ -61,6 +61,7 @@ struct FleetView {
   StatePlanes st;
   ParamPlanes pa;
   const Geo *geo;            // device [n_types]
+  int32_t n_types;
   int64_t n;                 // envs
   int64_t gid0;              // env id offset for counter-based draws
   const float4 *act;         // [n_seg][n][8] as float4 pairs, or null
@@ -71,18 +72,34 @@ struct FleetView {
   uint32_t model_flags;
   float dt;
   uint32_t *flags;           // [n] bit 0 = non-finite
-  unsigned long long *nonfinite_count;
+  unsigned long long *counters;  // [0] envs flagged non-finite, [2] work-queue wait time-outs
 };
 
 // Kernel variants: thruster count fixed at 6 or 8, or mixed (up to 8, read per block).
 enum NtVariant { NT_6 = 0, NT_8 = 1, NT_MIXED = 2 };
 
 // ---------------------------------------------------------------- launchers (mg_step.cu)
+// Static schedule: one block per BlockDesc, k sub-steps per launch.
 cudaError_t launch_fleet(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
                          NtVariant ntv, bool diag, int64_t step0, int32_t k, float *traj,
                          cudaStream_t stream);
 cudaError_t fleet_kernel_attributes(NtVariant ntv, bool diag, bool record,
                                     cudaFuncAttributes *attr);
+
+// Work-queue schedule: warps claim (32-env slice, chunk of sub-steps) units in chunk-major
+// order.  sched: device words, zeroed by the launcher: [0] next unit, [1..3] unused,
+// [4 + d] chunks completed by slice d.  One launch covers all k sub-steps (split into several
+// if slices x chunks would not fit 31 bits).
+constexpr int kQueueWarps = 4;
+size_t queue_sched_bytes(int n_slices);
+// wide: 168-register variant of the diagonal-mass step (fewer resident warps, more registers
+// each); warps_per_sm > 0 caps the resident warps per SM.
+cudaError_t launch_fleet_queue(const FleetView &fv, const BlockDesc *slices, int n_slices,
+                               NtVariant ntv, bool diag, bool wide, int warps_per_sm,
+                               int64_t step0, int32_t k, int32_t chunk, uint32_t *sched, int n_sm,
+                               cudaStream_t stream);
+cudaError_t queue_kernel_attributes(NtVariant ntv, bool diag, bool wide,
+                                    cudaFuncAttributes *attr, int *blocks_per_sm);
 
 // ---------------------------------------------------------------- launchers (mg_setup.cu)
 struct SetupView {
@@ -113,5 +130,13 @@ cudaError_t launch_flags_to_bytes(const uint32_t *flags, int64_t n, uint8_t *out
                                   cudaStream_t stream);
 cudaError_t launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,
                           cudaStream_t stream);
+
+// ---------------------------------------------------------------- launchers (mg_adjoint.cu)
+cudaError_t launch_checkpoint(const StatePlanes &st, int64_t n, float *ck, cudaStream_t stream);
+cudaError_t launch_adjoint(const FleetView &fv, const int32_t *types, bool eight,
+                           const float *ckpt, const float *dtraj, int32_t T, int32_t C,
+                           int64_t step0, float *dcoef, float *dact, float *dstate0,
+                           cudaStream_t stream);
+int adjoint_max_interval();
 
 }  // namespace mg

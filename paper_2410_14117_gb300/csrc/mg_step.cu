@@ -1,10 +1,20 @@
-// Fleet step kernel: one thread per vehicle, k RK4 sub-steps of Eq. 1 (§METHOD) per launch with
-// the state and parameters held in registers.  k = 1 is the plain per-step form (state and
-// parameters read from and written to HBM every sub-step); k > 1 is the persistent form (read
-// once, stepped k times, written once).
+// Fleet step kernels: one thread per vehicle advancing Eq. 1 (§METHOD) by RK4 sub-steps with
+// the state and parameters held in registers.
 //
-// Each block covers envs of a single vehicle type (its BlockDesc), so the thruster geometry is a
-// block-wide broadcast from shared memory and no warp diverges on the type.
+// Two schedules share the per-vehicle loop (advance_env):
+//   k_fleet        static grid, one block per BlockDesc, k sub-steps per launch.  k = 1 is the
+//                  plain per-step form (state and parameters through HBM every sub-step); k > 1
+//                  is the persistent form (read once, stepped k times, written once).
+//   k_fleet_queue  one launch for all k sub-steps: each warp repeatedly claims a unit (one
+//                  32-env slice, one chunk of sub-steps) from an atomic counter in chunk-major
+//                  order, waits until that slice's previous chunk is done, and runs it.  Warps
+//                  that run faster claim more units, so the work spreads evenly over the 608
+//                  schedulers whatever the fleet size (a static grid of 65,536 envs gives 3 or 4
+//                  warps to each scheduler and idles the 3-warp ones for a quarter of the time).
+//
+// Blocks / slices cover envs of a single vehicle type, so the thruster geometry is a broadcast
+// from shared memory and no warp diverges on the type.
+#include <algorithm>
 #include <type_traits>
 
 #include "mg_device.cuh"
@@ -14,14 +24,27 @@ namespace mg {
 namespace {
 
 constexpr int kMaxThreads = 256;
-// Register caps: the diagonal-mass step fits 128 registers (16 resident warps per SM, so a
-// 65,536-env fleet runs in a single wave on 152 SMs); the general step keeps 168.
+// Register caps: the diagonal-mass step fits 128 registers (16 resident warps per SM); the
+// general step keeps 168.
 constexpr int kRegsDiag = 128;
 constexpr int kRegsGeneral = 168;
+// Bound on a work-queue wait (polls of ~128 ns each, ~0.5 s); on expiry the wait is counted as a
+// time-out and the unit proceeds.
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 template <int MT>
 __device__ __forceinline__ void load_commands(const FleetView &fv, int64_t e, int64_t seg,
-                                              int nt, float (&c)[MT]) {
+                                              int nt, float itau, float (&c)[MT]) {
   if (fv.proc) {
     const uint64_t gid = (uint64_t)(fv.gid0 + e);
     const uint4 a = draw4(fv.cmd_seed, gid, STREAM_CMD, (uint32_t)(2 * seg));
@@ -47,9 +70,9 @@ __device__ __forceinline__ void load_commands(const FleetView &fv, int64_t e, in
     for (int i = 0; i < MT; ++i) c[i] = 0.f;
   }
   // Entries past the vehicle's thruster count are ignored (the lag state there stays zero).
+  // The step reads the command divided by the lag time constant.
 #pragma unroll
-  for (int i = 0; i < MT; ++i)
-    if (i >= nt) c[i] = 0.f;
+  for (int i = 0; i < MT; ++i) c[i] = (i < nt) ? c[i] * itau : 0.f;
 }
 
 template <int MT>
@@ -76,6 +99,47 @@ __device__ __forceinline__ bool all_finite(const St<MT> &s) {
   return z == 0.f;
 }
 
+// Advance env e by k sub-steps starting at action-cursor position step0.  L2: state (and flag)
+// loads bypass L1 (work-queue schedule, where another SM may have written them).
+template <int MT, bool DIAG, bool MIXED, bool REC, bool L2>
+__device__ __forceinline__ void advance_env(const FleetView &fv, int64_t e, int nt,
+                                            const float4 *gdir, const float4 *garm,
+                                            int64_t step0, int32_t k, float *traj) {
+  const bool current_accel = !(fv.model_flags & MG_MODEL_NO_CURRENT_ACCEL);
+  const float h = fv.dt;
+
+  St<MT> s;
+  load_state<MT, L2>(fv.st, e, s);
+  Par<DIAG> P;
+  load_par<DIAG>(fv.pa, e, P);
+
+  // Action cursor: sub-step j uses segment j / hold (clamped to the last buffered segment).
+  int64_t seg = step0 / fv.hold;
+  int32_t left = fv.hold - (int32_t)(step0 - seg * fv.hold);
+  float c[MT];
+  load_commands<MT>(fv, e, seg, nt, P.itau, c);
+
+  for (int32_t it = 0; it < k; ++it) {
+    if (left == 0) {
+      ++seg;
+      left = fv.hold;
+      load_commands<MT>(fv, e, seg, nt, P.itau, c);
+    }
+    rk4_step<MT, DIAG, MIXED>(s, c, P, gdir, garm, nt, current_accel, h);
+    --left;
+    if constexpr (REC) record<MT>(traj + (int64_t)it * MG_NTRAJ * fv.n, fv.n, e, s);
+  }
+
+  store_state<MT>(fv.st, e, s);
+  if (!all_finite<MT>(s)) {
+    const uint32_t old = L2 ? __ldcg(fv.flags + e) : fv.flags[e];
+    if (!(old & 1u)) {
+      fv.flags[e] = old | 1u;
+      atomicAdd(fv.counters, 1ull);
+    }
+  }
+}
+
 template <int NTV, bool DIAG, bool REC>
 __global__ void __maxnreg__(DIAG ? kRegsDiag : kRegsGeneral)
     k_fleet(const FleetView fv, const BlockDesc *__restrict__ blocks, const int64_t step0,
@@ -91,40 +155,59 @@ __global__ void __maxnreg__(DIAG ? kRegsDiag : kRegsGeneral)
   }
   __syncthreads();
   if ((int)threadIdx.x >= bd.count) return;
+  advance_env<MT, DIAG, MIXED, REC, false>(fv, (int64_t)bd.env0 + threadIdx.x,
+                                           MIXED ? bd.n_thr : MT, sdir, sarm, step0, k, traj);
+}
 
-  const int64_t e = (int64_t)bd.env0 + threadIdx.x;
-  const int nt = MIXED ? bd.n_thr : MT;
-  const bool current_accel = !(fv.model_flags & MG_MODEL_NO_CURRENT_ACCEL);
-  const float h = fv.dt;
-
-  St<MT> s;
-  load_state<MT>(fv.st, e, s);
-  Par<DIAG> P;
-  load_par<DIAG>(fv.pa, e, P);
-
-  // Action cursor: sub-step j uses segment j / hold (clamped to the last buffered segment).
-  int64_t seg = step0 / fv.hold;
-  int32_t left = fv.hold - (int32_t)(step0 - seg * fv.hold);
-  float c[MT];
-  load_commands<MT>(fv, e, seg, nt, c);
-
-  for (int32_t it = 0; it < k; ++it) {
-    if (left == 0) {
-      ++seg;
-      left = fv.hold;
-      load_commands<MT>(fv, e, seg, nt, c);
-    }
-    rk4_step<MT, DIAG, MIXED>(s, c, P, sdir, sarm, nt, current_accel, h);
-    --left;
-    if constexpr (REC) record<MT>(traj + (int64_t)it * MG_NTRAJ * fv.n, fv.n, e, s);
+template <int NTV, bool DIAG, bool WIDE>
+__global__ void __maxnreg__((DIAG && !WIDE) ? kRegsDiag : kRegsGeneral)
+    k_fleet_queue(const FleetView fv, const BlockDesc *__restrict__ slices, const int32_t n_slices,
+                  const int64_t step0, const int32_t k_total, const int32_t chunk,
+                  uint32_t *__restrict__ sched) {
+  constexpr int MT = (NTV == NT_6) ? 6 : 8;
+  constexpr bool MIXED = (NTV == NT_MIXED);
+  // Thruster geometry of every vehicle type at fixed shared addresses (a per-warp copy at a
+  // run-time address costs the sub-step loop dozens of registers).
+  __shared__ float4 sgeo[MG_MAX_TYPES][2 * MG_MAX_THR];
+  for (int i = threadIdx.x; i < fv.n_types * 2 * MG_MAX_THR; i += blockDim.x) {
+    const int t = i / (2 * MG_MAX_THR), j = i % (2 * MG_MAX_THR);
+    sgeo[t][j] = j < MG_MAX_THR ? fv.geo[t].dir[j] : fv.geo[t].arm[j - MG_MAX_THR];
   }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const uint32_t n_chunks = (uint32_t)((k_total + chunk - 1) / chunk);
+  const uint32_t n_units = (uint32_t)n_slices * n_chunks;  // < 2^31, checked by the launcher
 
-  store_state<MT>(fv.st, e, s);
-  if (!all_finite<MT>(s)) {
-    const uint32_t old = fv.flags[e];
-    if (!(old & 1u)) {
-      fv.flags[e] = old | 1u;
-      atomicAdd(fv.nonfinite_count, 1ull);
+  for (;;) {
+    uint32_t u = 0;
+    if (lane == 0) u = atomicAdd(sched, 1u);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= n_units) break;
+    const int32_t c = (int32_t)(u / (uint32_t)n_slices);
+    const int32_t d = (int32_t)(u % (uint32_t)n_slices);
+    if (c > 0 && lane == 0) {
+      // The slice's previous chunk was claimed earlier by a running warp, so it completes.
+      uint32_t polls = 0;
+      while (ld_acquire(sched + 4 + d) < (uint32_t)c) {
+        if (++polls > kSpinLimit) {
+          atomicAdd(fv.counters + 2, 1ull);
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __syncwarp();
+    const BlockDesc bd = slices[d];
+    const float4 *gdir = sgeo[bd.type & (MG_MAX_TYPES - 1)], *garm = gdir + MG_MAX_THR;
+    if (lane < bd.count)
+      advance_env<MT, DIAG, MIXED, false, true>(fv, (int64_t)bd.env0 + lane,
+                                                MIXED ? bd.n_thr : MT, gdir, garm,
+                                                step0 + (int64_t)c * chunk,
+                                                min(chunk, k_total - c * chunk), nullptr);
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence();
+      st_release(sched + 4 + d, (uint32_t)(c + 1));
     }
   }
 }
@@ -155,12 +238,49 @@ const void *kernel_ptr() {
   return reinterpret_cast<const void *>(&k_fleet<NTV, DIAG, REC>);
 }
 
+template <int NTV, bool DIAG>
+const void *queue_ptr(bool wide) {
+  return wide ? reinterpret_cast<const void *>(&k_fleet_queue<NTV, DIAG, true>)
+              : reinterpret_cast<const void *>(&k_fleet_queue<NTV, DIAG, false>);
+}
+
+const void *queue_kernel(NtVariant ntv, bool diag, bool wide) {
+  switch (ntv) {
+    case NT_6: return diag ? queue_ptr<NT_6, true>(wide) : queue_ptr<NT_6, false>(wide);
+    case NT_8: return diag ? queue_ptr<NT_8, true>(wide) : queue_ptr<NT_8, false>(wide);
+    default: return diag ? queue_ptr<NT_MIXED, true>(wide) : queue_ptr<NT_MIXED, false>(wide);
+  }
+}
+
+template <int NTV, bool DIAG>
+void queue_launch_w(bool wide, int grid, const FleetView &fv, const BlockDesc *slices,
+                    int32_t n_slices, int64_t step0, int32_t k, int32_t chunk, uint32_t *sched,
+                    cudaStream_t stream) {
+  if (wide)
+    k_fleet_queue<NTV, DIAG, true><<<grid, kQueueWarps * 32, 0, stream>>>(
+        fv, slices, n_slices, step0, k, chunk, sched);
+  else
+    k_fleet_queue<NTV, DIAG, false><<<grid, kQueueWarps * 32, 0, stream>>>(
+        fv, slices, n_slices, step0, k, chunk, sched);
+}
+
+template <int NTV>
+void queue_launch(bool diag, bool wide, int grid, const FleetView &fv, const BlockDesc *slices,
+                  int32_t n_slices, int64_t step0, int32_t k, int32_t chunk, uint32_t *sched,
+                  cudaStream_t stream) {
+  if (diag) queue_launch_w<NTV, true>(wide, grid, fv, slices, n_slices, step0, k, chunk, sched,
+                                      stream);
+  else queue_launch_w<NTV, false>(wide, grid, fv, slices, n_slices, step0, k, chunk, sched,
+                                  stream);
+}
+
 }  // namespace
 
 cudaError_t launch_fleet(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
                          NtVariant ntv, bool diag, int64_t step0, int32_t k, float *traj,
                          cudaStream_t stream) {
-  if (threads < 32 || threads > kMaxThreads || threads % 32 || n_blocks < 1) return cudaErrorInvalidValue;
+  if (threads < 32 || threads > kMaxThreads || threads % 32 || n_blocks < 1 || k < 1)
+    return cudaErrorInvalidValue;
   switch (ntv) {
     case NT_6: return launch_d<NT_6>(fv, blocks, n_blocks, threads, diag, step0, k, traj, stream);
     case NT_8: return launch_d<NT_8>(fv, blocks, n_blocks, threads, diag, step0, k, traj, stream);
@@ -182,6 +302,61 @@ cudaError_t fleet_kernel_attributes(NtVariant ntv, bool diag, bool rec,
   }
 #undef MG_PICK
   return cudaFuncGetAttributes(attr, f);
+}
+
+size_t queue_sched_bytes(int n_slices) { return 16 + 4 * (size_t)n_slices; }
+
+cudaError_t queue_kernel_attributes(NtVariant ntv, bool diag, bool wide,
+                                    cudaFuncAttributes *attr, int *blocks_per_sm) {
+  const void *f = queue_kernel(ntv, diag, wide);
+  cudaError_t e = cudaFuncGetAttributes(attr, f);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kQueueWarps * 32, 0);
+}
+
+cudaError_t launch_fleet_queue(const FleetView &fv, const BlockDesc *slices, int n_slices,
+                               NtVariant ntv, bool diag, bool wide, int warps_per_sm,
+                               int64_t step0, int32_t k, int32_t chunk, uint32_t *sched, int n_sm,
+                               cudaStream_t stream) {
+  if (n_slices < 1 || k < 1 || chunk < 1 || n_sm < 1) return cudaErrorInvalidValue;
+  cudaFuncAttributes attr;
+  int per_sm = 0;
+  cudaError_t e = queue_kernel_attributes(ntv, diag, wide, &attr, &per_sm);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  // Resident warps: at most what fits (and at most warps_per_sm per SM when that is > 0), and no
+  // more than there are slices in a chunk.
+  if (warps_per_sm > 0) per_sm = std::max(1, std::min(per_sm, warps_per_sm / kQueueWarps));
+  int grid = per_sm * n_sm;
+  const int need = (n_slices + kQueueWarps - 1) / kQueueWarps;
+  if (grid > need) grid = need;
+  // One launch per piece of the horizon whose unit count fits the 31-bit counter.
+  const int64_t max_chunks = ((int64_t)1 << 31) / n_slices;
+  if (max_chunks < 1) return cudaErrorInvalidValue;
+  for (int64_t done = 0; done < k;) {
+    const int64_t left = k - done;
+    const int32_t kk = (int32_t)std::min<int64_t>(left, max_chunks * (int64_t)chunk);
+    e = cudaMemsetAsync(sched, 0, queue_sched_bytes(n_slices), stream);
+    if (e != cudaSuccess) return e;
+    switch (ntv) {
+      case NT_6:
+        queue_launch<NT_6>(diag, wide, grid, fv, slices, n_slices, step0 + done, kk, chunk,
+                           sched, stream);
+        break;
+      case NT_8:
+        queue_launch<NT_8>(diag, wide, grid, fv, slices, n_slices, step0 + done, kk, chunk,
+                           sched, stream);
+        break;
+      default:
+        queue_launch<NT_MIXED>(diag, wide, grid, fv, slices, n_slices, step0 + done, kk, chunk,
+                               sched, stream);
+        break;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    done += kk;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace mg

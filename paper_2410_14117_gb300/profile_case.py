@@ -1,0 +1,55 @@
+"""A small, self-contained workload for profiling the step kernel under ncu.
+
+    python -m paper_2410_14117_gb300.profile_case --n-envs 65536 --k 50 --launches 3
+
+Builds a domain-randomised BlueROV2 fleet with NED current and a buffered throttle schedule
+(commands U[-1,1] held 10 sub-steps), then issues ``launches`` calls of ``mg_step(k)`` (no CUDA graph)
+after a few warm-up calls: with ``--static`` each is one launch of the static-grid kernel running
+``k`` sub-steps; otherwise each is one work-queue launch covering ``k`` sub-steps in chunks of
+``--chunk``.  Holds well under a
+GB of device memory at 65,536 envs.
+"""
+from __future__ import annotations
+
+import argparse
+import math
+
+import numpy as np
+import torch
+
+from . import inputs as I
+from .sim import Sim
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n-envs", type=int, default=65536)
+    ap.add_argument("--k", type=int, default=50)
+    ap.add_argument("--chunk", type=int, default=50)
+    ap.add_argument("--launches", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--epb", type=int, default=128)
+    ap.add_argument("--vehicle", type=int, default=0)
+    ap.add_argument("--static", action="store_true",
+                    help="static grid (one launch per k sub-steps) instead of the work queue")
+    args = ap.parse_args()
+
+    n = args.n_envs
+    vs = I.fleet_vehicles()
+    sim = Sim(n, np.full(n, args.vehicle, dtype=np.int32), vs)
+    sim.set_launch(args.epb, args.k if args.static else args.chunk, False)
+    sim.set_schedule(not args.static)
+    sim.randomize(1234, 0.8, 1.2, 0.2, 0.3)
+    sim.reset()
+    total = (args.warmup + args.launches) * args.k
+    cmds = I.commands(5678, math.ceil(total / 10), n, vs[args.vehicle].n_thr)
+    sim.set_actions(torch.tensor(cmds, device="cuda"), 10)
+    for _ in range(args.warmup + args.launches):
+        sim.step(args.k)
+    bad = sim.sync()
+    sim.close()
+    print(f"profile_case: {n} envs, {args.launches} launches of k={args.k}, non-finite {bad}")
+
+
+if __name__ == "__main__":
+    main()

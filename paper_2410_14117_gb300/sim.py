@@ -98,6 +98,11 @@ class Sim:
         call("mg_set_launch", self._h, int(envs_per_block), int(steps_per_launch),
              1 if use_graph else 0)
 
+    def set_schedule(self, work_queue: bool = False, wide: bool = True, warps_per_sm: int = 0):
+        """Static grid (default) or the work-queue schedule (see mg_set_schedule)."""
+        call("mg_set_schedule", self._h, 1 if work_queue else 0, 1 if wide else 0,
+             int(warps_per_sm))
+
     def kernel_info(self) -> dict:
         r, t, l = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         call("mg_kernel_info", self._h, ctypes.byref(r), ctypes.byref(t), ctypes.byref(l))

@@ -1,0 +1,144 @@
+"""Hand-written discrete adjoint of the rollout (libmg.so, through RolloutFn) against central
+finite differences of the FP64 oracle's rollout: gradients of a trajectory MSE with respect to
+the 18 hydrodynamic coefficients of every env and to every buffered action, relative error
+<= 1e-3 per env."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2410_14117_gb300 import inputs as I
+from paper_2410_14117_gb300.adjoint import COEF_SLICE, rollout
+from paper_2410_14117_gb300.sim import MGError, Sim
+
+from _helpers import f32, oracle_geo, oracle_nominal, vehicles
+
+pytestmark = pytest.mark.gpu
+
+TOL_GRAD = 1e-3
+FD_REL = 1e-6
+
+
+def _problem(n=64, T=200, hold=10, seed=0, vehicle=0):
+    vs = vehicles()
+    types = np.full(n, vehicle, dtype=np.int32)
+    nt = vs[vehicle].n_thr
+    params = I.round_f32(O.randomize(1234 + seed, oracle_nominal(vs), types, f32(0.8), f32(1.2),
+                                     f32(0.2)))
+    s0 = I.initial_states(21 + seed, n)
+    cmds = I.commands(5678 + seed, T // hold, n, nt).astype(np.float64)
+    # target: the same start and commands with coefficients x U[0.9, 1.1]
+    g = np.random.default_rng(99 + seed)
+    pt = params.copy()
+    pt[:, COEF_SLICE] *= g.uniform(0.9, 1.1, size=(n, 18))
+    pt = I.round_f32(pt)
+    _, target = O.rollout(pt, oracle_geo(vs), types, s0, cmds, hold, T, record=True)
+    target = I.round_f32(target[:, :, :13])  # [T, n, 13]
+    return vs, types, params, s0, cmds, target
+
+
+def _oracle_losses(vs, types, params, s0, cmds, target, hold, T):
+    _, traj = O.rollout(params, oracle_geo(vs), types, s0, cmds, hold, T, record=True)
+    d = traj[:, :, :13] - target
+    return (d * d).sum(axis=(0, 2)) / d.size  # per-env share of the mean
+
+
+def _gpu_grads(vs, types, params, s0, cmds, target, hold, T, C=20):
+    n = len(types)
+    sim = Sim(n, types, vs)
+    sim.set_params(torch.tensor(params, dtype=torch.float32, device="cuda"))
+    coeffs = torch.tensor(params[:, COEF_SLICE], dtype=torch.float32, device="cuda",
+                          requires_grad=True)
+    acts = torch.tensor(cmds, dtype=torch.float32, device="cuda", requires_grad=True)
+    st0 = torch.tensor(s0, dtype=torch.float32, device="cuda")
+    traj = rollout(sim, coeffs, acts, st0, hold, T, C)
+    tgt = torch.tensor(target, dtype=torch.float32, device="cuda")
+    loss = ((traj - tgt) ** 2).mean()
+    loss.backward()
+    out = (coeffs.grad.double().cpu().numpy(), acts.grad.double().cpu().numpy(),
+           traj.detach().double().cpu().numpy())
+    sim.close()
+    return out
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b, axis=-1) / np.maximum(np.linalg.norm(b, axis=-1), 1e-30)
+
+
+@pytest.mark.parametrize("vehicle", [0, 1])
+def test_coefficient_gradients_match_fd(vehicle):
+    T, hold = 200, 10
+    vs, types, params, s0, cmds, target = _problem(T=T, hold=hold, vehicle=vehicle)
+    gc, _, traj = _gpu_grads(vs, types, params, s0, cmds, target, hold, T)
+    n = len(types)
+    fd = np.zeros((n, 18))
+    for j in range(18):
+        col = COEF_SLICE.start + j
+        d = FD_REL * np.abs(params[:, col])
+        p1, p2 = params.copy(), params.copy()
+        p1[:, col] += d
+        p2[:, col] -= d
+        fd[:, j] = (_oracle_losses(vs, types, p1, s0, cmds, target, hold, T) -
+                    _oracle_losses(vs, types, p2, s0, cmds, target, hold, T)) / (2 * d)
+    err = _rel(gc, fd)
+    assert err.max() <= TOL_GRAD, (err.max(), np.argmax(err))
+
+
+def test_action_gradients_match_fd():
+    T, hold = 200, 10
+    vs, types, params, s0, cmds, target = _problem(T=T, hold=hold, seed=3)
+    _, ga, _ = _gpu_grads(vs, types, params, s0, cmds, target, hold, T)
+    n_seg = cmds.shape[0]
+    fd = np.zeros_like(cmds)
+    for sg in range(n_seg):
+        for i in range(6):
+            d = FD_REL * np.maximum(np.abs(cmds[sg, :, i]), 1e-3)
+            c1, c2 = cmds.copy(), cmds.copy()
+            c1[sg, :, i] += d
+            c2[sg, :, i] -= d
+            fd[sg, :, i] = (_oracle_losses(vs, types, params, s0, c1, target, hold, T) -
+                            _oracle_losses(vs, types, params, s0, c2, target, hold, T)) / (2 * d)
+    # per env, all segments and thrusters together
+    g = ga.transpose(1, 0, 2).reshape(len(types), -1)
+    f = fd.transpose(1, 0, 2).reshape(len(types), -1)
+    err = _rel(g, f)
+    assert err.max() <= TOL_GRAD, err.max()
+    assert np.all(ga[:, :, 6:] == 0)
+
+
+def test_zero_loss_gradient_gives_zero_and_is_linear():
+    T, hold = 60, 10
+    vs, types, params, s0, cmds, target = _problem(n=32, T=T, hold=hold, seed=5)
+    sim = Sim(32, types, vs)
+    sim.set_params(torch.tensor(params, dtype=torch.float32, device="cuda"))
+    coeffs = torch.tensor(params[:, COEF_SLICE], dtype=torch.float32, device="cuda",
+                          requires_grad=True)
+    acts = torch.tensor(cmds, dtype=torch.float32, device="cuda", requires_grad=True)
+    st0 = torch.tensor(s0, dtype=torch.float32, device="cuda")
+    traj = rollout(sim, coeffs, acts, st0, hold, T, 16)
+    g1 = torch.randn_like(traj)
+    (gc1, ga1) = torch.autograd.grad(traj, (coeffs, acts), g1, retain_graph=True)
+    # scaling by a power of two is exact in FP32, so the adjoint must scale bit for bit
+    (gc2, ga2) = torch.autograd.grad(traj, (coeffs, acts), 4.0 * g1, retain_graph=True)
+    (gc0, ga0) = torch.autograd.grad(traj, (coeffs, acts), torch.zeros_like(traj))
+    assert torch.all(gc0 == 0) and torch.all(ga0 == 0)
+    assert torch.equal(gc2, 4.0 * gc1) and torch.equal(ga2, 4.0 * ga1)
+    sim.close()
+
+
+def test_adjoint_rejects_off_centre_gravity():
+    vs = vehicles()
+    n = 32
+    types = np.zeros(n, dtype=np.int32)
+    params = np.broadcast_to(oracle_nominal(vs)[0], (n, I.NPARAM)).copy()
+    params[:, I.P_RG] = 0.01
+    sim = Sim(n, types, vs)
+    sim.set_params(torch.tensor(params, dtype=torch.float32, device="cuda"))
+    coeffs = torch.tensor(params[:, COEF_SLICE], dtype=torch.float32, device="cuda",
+                          requires_grad=True)
+    acts = torch.zeros((2, n, 8), device="cuda", requires_grad=True)
+    traj = rollout(sim, coeffs, acts, torch.zeros((n, 21), device="cuda") +
+                   torch.tensor([0, 0, 0, 1] + [0] * 17, device="cuda"), 10, 20, 10)
+    with pytest.raises(MGError):
+        traj.sum().backward()
+    sim.close()

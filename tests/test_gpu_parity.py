@@ -17,10 +17,11 @@ pytestmark = pytest.mark.gpu
 H = 0.01
 
 
-def make_sim(types, vs=None, epb=128, spl=50, graph=True):
+def make_sim(types, vs=None, epb=128, spl=50, graph=True, queue=True):
     vs = vs or vehicles()
     sim = Sim(len(types), types, vs)
     sim.set_launch(epb, spl, graph)
+    sim.set_schedule(queue)
     return sim
 
 
@@ -205,19 +206,34 @@ def test_ragged_sizes_and_launch_shapes(n, epb, spl, graph):
     assert qn <= TOL_QNORM
 
 
-def test_launch_shape_does_not_change_results():
-    """Same arithmetic per env whatever the block size, chunking or graph replay: bitwise."""
+@pytest.mark.parametrize("general", [False, True])
+def test_schedule_and_launch_shape_do_not_change_results(general):
+    """Same arithmetic per env whatever the schedule (work queue or static grid), block size,
+    chunking or graph replay: bitwise equal final states."""
     vs = vehicles()
     n = 3000
     types = I.mixed_fleet(4, n, max_group=500)
+    params = None
+    if general:
+        params = I.perturbed_params(3, oracle_nominal(vs)[types], n)
+        params[:, I.P_RG:I.P_RG + 3] = I.round_f32(
+            np.random.default_rng(2).uniform(-0.02, 0.02, (n, 3)))
     out = []
-    for epb, spl, graph in [(128, 50, True), (64, 1, False), (256, 17, True), (32, 300, False)]:
-        sim = make_sim(types, vs, epb=epb, spl=spl, graph=graph)
-        sim.randomize(9, 0.8, 1.2, 0.2, 0.3)
-        sim.reset()
+    for epb, spl, graph, queue in [(128, 50, True, True), (64, 1, False, False),
+                                   (256, 17, True, False), (32, 300, False, True),
+                                   (96, 7, False, True), (128, 1, True, True)]:
+        sim = make_sim(types, vs, epb=epb, spl=spl, graph=graph, queue=queue)
+        if general:
+            sim.set_params(torch.tensor(params, dtype=torch.float32, device="cuda"))
+            sim.set_state(torch.tensor(I.random_states(5, n, [vs[t].n_thr for t in types]),
+                                       dtype=torch.float32, device="cuda"))
+        else:
+            sim.randomize(9, 0.8, 1.2, 0.2, 0.3)
+            sim.reset()
         sim.set_procedural_actions(99, 10)
         sim.step(150)
         sim.step(150)
+        assert sim.sync() == 0
         out.append(gpu_state(sim))
         sim.close()
     for o in out[1:]:

@@ -15,6 +15,7 @@ collective in the data path); the slowest rank's time is reported.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -43,7 +44,7 @@ CMD_BYTES = {6: 6 * 4, 8: 8 * 4}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n-envs", type=int, default=65536)
@@ -54,6 +55,10 @@ def parse():
     ap.add_argument("--no-per-step", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (static grid)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the mixed-fleet, adjoint and serving sections")
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
     return ap.parse_args()
 
 
@@ -132,7 +137,8 @@ def dist_env():
 
 def cpu_baseline(n_envs, horizon, hold, target_s=12.0):
     """The FP64 oracle as it stands, on the host cores, over a bounded sample of the same
-    workload (randomised BlueROV2 fleet with current, same command process)."""
+    workload (randomised BlueROV2 fleet with current, same command process): episodes of
+    min(n_envs, 8192) envs x horizon sub-steps, repeated until about target_s seconds."""
     import numpy as np
     from oracle import oracle as O
     from paper_2410_14117_gb300 import inputs as I
@@ -140,26 +146,25 @@ def cpu_baseline(n_envs, horizon, hold, target_s=12.0):
     vs = I.fleet_vehicles()
     nominal = np.stack([I.round_f32(v.params) for v in vs])
     geo = np.stack([I.round_f32(v.geo()) for v in vs])
-
-    def run(ns, steps):
-        types = np.zeros(ns, dtype=np.int32)
-        par = I.round_f32(O.randomize(1234, nominal, types, float(np.float32(0.8)),
-                                      float(np.float32(1.2)), float(np.float32(0.2))))
-        s0 = I.initial_states(21, ns)
-        cmd = I.commands(5678, max(1, math.ceil(steps / hold)), ns, 6).astype(np.float64)
-        t = time.perf_counter()
+    ns = min(n_envs, 8192)
+    types = np.zeros(ns, dtype=np.int32)
+    par = I.round_f32(O.randomize(1234, nominal, types, float(np.float32(0.8)),
+                                  float(np.float32(1.2)), float(np.float32(0.2))))
+    s0 = I.initial_states(21, ns)
+    cmd = I.commands(5678, max(1, math.ceil(horizon / hold)), ns, 6).astype(np.float64)
+    t = time.perf_counter()
+    O.rollout(par, geo, types, s0, cmd, hold, 20, h=0.01)
+    per_step = (time.perf_counter() - t) / 20
+    steps = int(max(20, min(horizon, target_s / per_step)))
+    reps = max(1, int(target_s / (per_step * steps)))
+    t = time.perf_counter()
+    for _ in range(reps):
         O.rollout(par, geo, types, s0, cmd, hold, steps, h=0.01)
-        return time.perf_counter() - t
-
-    ns = min(n_envs, 4096)
-    probe = run(ns, 20)
-    rate = ns * 20 / probe
-    steps = int(max(20, min(horizon, target_s * rate / ns)))
-    dt = run(ns, steps)
-    return {"value": ns * steps / dt, "unit": "env-steps/s", "cores": O.max_threads(),
+    dt = time.perf_counter() - t
+    return {"value": ns * steps * reps / dt, "unit": "env-steps/s", "cores": O.max_threads(),
             "kind": "oracle",
-            "sample": f"{ns} envs x {steps} sub-steps of the same randomised BlueROV2 workload "
-                      f"(FP64 oracle, OpenMP over envs), {dt:.1f} s"}
+            "sample": f"{reps} x ({ns} envs x {steps} sub-steps) of the same randomised BlueROV2 "
+                      f"workload (FP64 oracle, OpenMP over envs), {dt:.1f} s"}
 
 
 def run_reference(args):
@@ -238,9 +243,16 @@ def run_ours(args):
 
     n, horizon, hold, k = args.n_envs, args.horizon, args.hold, args.k
     vs = I.fleet_vehicles()
-    sim = Sim(n, np.zeros(n, dtype=np.int32), vs)
+    types0 = np.zeros(n, dtype=np.int32)
+    if args.no_tune:
+        from paper_2410_14117_gb300.autotune import LaunchConfig
+        cfg = LaunchConfig("static", args.epb, k)
+    else:
+        from paper_2410_14117_gb300.autotune import Autotuner
+        cfg = Autotuner(horizon=horizon, reps=2).pick(n, types0, vs)
+    sim = Sim(n, types0, vs)
     sim.set_env_id_offset(rank * n)
-    sim.set_launch(args.epb, k, True)
+    cfg.apply(sim)
     n_seg = math.ceil(horizon / hold)
     acts_np = I.commands(5678 + rank, n_seg, n, 6)
     acts_host = torch.from_numpy(acts_np).pin_memory()
@@ -248,7 +260,8 @@ def run_ours(args):
     out_dev = torch.empty((n, 21), dtype=torch.float32, device=dev)
     out_host = torch.empty((n, 21), dtype=torch.float32).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    launches_per_episode = math.ceil(horizon / k)
+    launches_per_episode = (math.ceil(horizon / cfg.steps_per_launch)
+                            if cfg.schedule == "static" else 1)
 
     def episode(seed, a, out):
         sim.randomize(seed, 0.8, 1.2, 0.2, 0.3)
@@ -294,13 +307,15 @@ def run_ours(args):
 
     peaks, peak_kind = load_peaks()
     launch_s = statistics.mean(graph_ms) / 1e3 / launches_per_episode
-    flops = FLOPS_PER_ENV_STEP[6] * n * k
+    flops = FLOPS_PER_ENV_STEP[6] * n * horizon / launches_per_episode
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = fp32_alu_peak_tflops(sm_max)
     achieved = flops / launch_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": None,
-                "kernel": "k_fleet (persistent, 6 thrusters, diagonal mass)",
+                "kernel": ("k_fleet (persistent, static grid" if cfg.schedule == "static"
+                           else "k_fleet_queue (persistent, work queue") +
+                          ", 6 thrusters, diagonal mass)",
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 flops x {sm_max:.0f} MHz "
                                f"({peak_kind} max SM clock)",
                 "flops_per_env_step": FLOPS_PER_ENV_STEP[6],
@@ -309,7 +324,9 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": workload_config(args), "roofline": roofline,
+            "data": "synthetic",
+            "config": dict(workload_config(args), launch=dataclasses.asdict(cfg)),
+            "roofline": roofline,
             "clocks": clk,
             "gpu_launches": args.steps * (launches_per_episode + 3)}
 
@@ -337,6 +354,7 @@ def run_ours(args):
     # ---- the plain per-step form on the same GPU (one launch per sub-step)
     if not args.no_per_step:
         sim.set_actions(acts_dev, hold)
+        sim.set_schedule(False)
         sim.set_launch(args.epb, 1, False)
         sim.randomize(7, 0.8, 1.2, 0.2, 0.3)
         sim.reset()
@@ -379,16 +397,136 @@ def run_ours(args):
                          "frac": ach / hbm, "bytes_per_env_step": bytes_per_launch // n,
                          "launch_us": per_launch_s * 1e6,
                          "peak_source": f"{peak_kind} hbm_gbs"}}
-        sim.set_launch(args.epb, k, True)
+        cfg.apply(sim)
+
+    sim.close()
+    if not args.no_extra and world == 1:
+        line["mixed_fleet"] = bench_mixed_fleet(vs)
+        line["adjoint"] = bench_adjoint(vs)
+        line["serve"] = bench_serve(vs, args.serve_seconds)
 
     if world == 1 and rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(n, horizon, hold)
 
-    sim.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- other configs
+
+def _time_episodes(fn, reps):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def bench_mixed_fleet(vs, n=262144, horizon=500, reps=5):
+    """Mixed BlueROV2 / BlueROV2-Heavy fleet, groups log-uniform in [1, 32768] (60/40 types),
+    randomised; autotuned launch; against a homogeneous BlueROV2 fleet of the same size."""
+    import numpy as np
+    import torch
+    from paper_2410_14117_gb300 import inputs as I
+    from paper_2410_14117_gb300.autotune import Autotuner
+    from paper_2410_14117_gb300.sim import Sim
+
+    out = {}
+    tuner = Autotuner(horizon=horizon, reps=2)
+    for name, types in (("mixed", I.mixed_fleet(3, n)), ("homogeneous", np.zeros(n, np.int32))):
+        cfg = tuner.pick(n, types, vs)
+        sim = Sim(n, types, vs)
+        cfg.apply(sim)
+        sim.randomize(1234, 0.8, 1.2, 0.2, 0.3)
+        sim.reset()
+        sim.set_procedural_actions(5678, 10)
+
+        ms = _time_episodes(lambda: sim.step(horizon), reps)
+        assert sim.sync() == 0
+        out[name] = {"env_steps_per_s": n * horizon / (ms / 1e3), "launch": dataclasses.asdict(cfg)}
+        if name == "mixed":
+            runs = np.flatnonzero(np.diff(types)) + 1
+            out[name]["groups"] = int(runs.size + 1)
+            out[name]["heavy_fraction"] = float((types == 1).mean())
+        sim.close()
+    out["workload"] = (f"{n:,} envs, {horizon} RK4 sub-steps, procedural commands held 10 "
+                       "sub-steps; groups log-uniform in [1, 32768], 60% BlueROV2 / 40% Heavy")
+    out["mixed_over_homogeneous"] = (out["mixed"]["env_steps_per_s"] /
+                                     out["homogeneous"]["env_steps_per_s"])
+    return out
+
+
+def bench_adjoint(vs, n=4096, T=200, C=20, reps=5):
+    """Differentiable rollout: forward (recording + checkpoints) and hand-written adjoint."""
+    import numpy as np
+    import torch
+    from paper_2410_14117_gb300 import inputs as I
+    from paper_2410_14117_gb300.adjoint import COEF_SLICE, rollout
+    from paper_2410_14117_gb300.sim import Sim
+
+    sim = Sim(n, np.zeros(n, np.int32), vs)
+    sim.randomize(1234, 0.8, 1.2, 0.2, 0.3)
+    params = sim.get_params()
+    coeffs = params[:, COEF_SLICE].clone().requires_grad_(True)
+    acts = torch.tensor(I.commands(5678, T // 10, n, 6), device="cuda", requires_grad=True)
+    s0 = torch.tensor(I.initial_states(21, n), dtype=torch.float32, device="cuda")
+    target = torch.zeros((T, n, 13), device="cuda")
+
+    def fwd():
+        return rollout(sim, coeffs, acts, s0, 10, T, C)
+
+    f_ms = _time_episodes(fwd, reps)
+    traj = fwd()
+    loss = ((traj - target) ** 2).mean()
+
+    def fb():
+        tr = rollout(sim, coeffs, acts, s0, 10, T, C)
+        g = torch.autograd.grad(((tr - target) ** 2).mean(), (coeffs, acts))
+        return g
+
+    fb_ms = _time_episodes(fb, reps)
+    sim.close()
+    return {"workload": f"{n:,} BlueROV2 envs, {T} RK4 sub-steps, checkpoints every {C}, "
+                        "MSE on the trajectory",
+            "forward_ms": f_ms, "forward_backward_ms": fb_ms,
+            "backward_over_forward": (fb_ms - f_ms) / f_ms, "loss": float(loss.detach())}
+
+
+def bench_serve(vs, seconds, rate=200.0):
+    """Poisson arrivals of rollout jobs (envs log-uniform [64, 65536], horizon U[50, 1000],
+    type 50/50, randomised parameters and currents) served with continuous batching under a
+    120 GB budget, and the same stream served one job at a time."""
+    from paper_2410_14117_gb300 import inputs as I
+    from paper_2410_14117_gb300.serve import Server, requests_from_specs
+
+    specs = I.serving_jobs(42, seconds, rate_hz=rate)
+    out = {"workload": f"Poisson {rate:.0f} req/s for {seconds:.1f} s ({len(specs)} jobs), envs "
+                       "log-uniform [64, 65536], horizon U[50, 1000], 50/50 BlueROV2/Heavy, "
+                       "trajectory recorded (13 floats per env-step), 120 GB budget"}
+    for mode in ("batched", "serial"):
+        srv = Server(vs, budget_bytes=120e9, capacity_envs=8 << 20, k=50)
+        warm = requests_from_specs(I.serving_jobs(7, 0.05, rate_hz=rate))
+        srv.run(warm, mode=mode)
+        _, st = srv.run(requests_from_specs(specs), mode=mode)
+        srv.close()
+        out[mode] = st
+    # the same job mix at 10x the arrival rate: continuous batching against one job at a time
+    hot = I.serving_jobs(43, seconds / 4, rate_hz=10 * rate)
+    out["stress"] = {"rate_hz": 10 * rate, "jobs": len(hot)}
+    for mode in ("batched", "serial"):
+        srv = Server(vs, budget_bytes=120e9, capacity_envs=8 << 20, k=50)
+        _, st = srv.run(requests_from_specs(hot), mode=mode)
+        srv.close()
+        out["stress"][mode] = {k: st[k] for k in ("p50_ms", "p99_ms", "env_steps_per_s",
+                                                  "max_queue_depth")}
+    return out
 
 
 def main():

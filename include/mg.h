@@ -221,6 +221,60 @@ mg_status mg_sync(mg_sim *sim, int64_t *nonfinite_count);
 /* Per-env non-finite flags into out [n_envs] (host or device), 1 = flagged. */
 mg_status mg_get_nonfinite(mg_sim *sim, uint8_t *out);
 
+/* ------------------------------------------------------------------------------------------
+ * Serving: a job pool with continuous batching.  A pool holds an arena of capacity_envs envs; a
+ * job (one vehicle type, its own parameter and command seeds, hold and horizon) is admitted into
+ * a contiguous free range, randomised and reset with draws keyed by its own seeds and job-local
+ * env ids (its result does not depend on its placement or on the other jobs), and advanced by
+ * mg_pool_tick together with every other running job in one launch.  Commands are procedural
+ * (as mg_set_procedural_actions, keyed by cmd_seed and the job-local env id).
+ * ------------------------------------------------------------------------------------------ */
+typedef struct mg_pool mg_pool;
+
+typedef struct {
+  int64_t n_envs;
+  int32_t vehicle_type;  /* index into the pool's vehicle table */
+  int32_t hold_steps;    /* sub-steps each procedural command is held */
+  int32_t horizon;       /* sub-steps to run */
+  int32_t pad;
+  uint64_t param_seed;   /* randomisation and reset draws */
+  uint64_t cmd_seed;     /* procedural commands */
+  mg_ranges ranges;      /* as mg_randomize */
+} mg_job_spec;
+
+/* Create a pool on the current device; params host [n_types].  Errors as mg_create. */
+mg_status mg_pool_create(int64_t capacity_envs, const mg_vehicle_params *params, int32_t n_types,
+                         mg_pool **out);
+mg_status mg_pool_destroy(mg_pool *pool);
+mg_status mg_pool_set_stream(mg_pool *pool, void *cuda_stream);
+
+/* Admit a job: takes a free range of spec->n_envs envs, randomises and resets them (asynchronous
+ * on the pool's stream).  traj: device [horizon][MG_NTRAJ][n_envs] the ticks will record into,
+ * owned by the caller and kept alive until the job is released, or NULL.  *job_id receives the
+ * job's handle.  Errors: MG_EINVAL (bad spec, host traj), MG_ENOMEM (no free range large
+ * enough; nothing changed). */
+mg_status mg_pool_admit(mg_pool *pool, const mg_job_spec *spec, float *traj, int32_t *job_id);
+
+/* One launch: every admitted job with sub-steps left advances min(k, horizon - done) of them.
+ * *n_running (may be NULL) receives how many jobs advanced.  Asynchronous. */
+mg_status mg_pool_tick(mg_pool *pool, int32_t k, int32_t *n_running);
+
+/* Sub-steps a job has been scheduled for (completed once the stream passes the last tick). */
+mg_status mg_pool_job_progress(mg_pool *pool, int32_t job_id, int32_t *done, int32_t *horizon);
+
+/* A job's state [n_envs][MG_NSTATE], host or device. */
+mg_status mg_pool_get_job_state(mg_pool *pool, int32_t job_id, float *out);
+
+/* Return a job's envs to the pool (its traj buffer is the caller's again). */
+mg_status mg_pool_release(mg_pool *pool, int32_t job_id);
+
+/* Free envs in total and in the largest contiguous range; admitted jobs. */
+mg_status mg_pool_info(mg_pool *pool, int64_t *free_envs, int64_t *largest_free_range,
+                       int32_t *n_jobs);
+
+/* Wait for the pool's stream. */
+mg_status mg_pool_sync(mg_pool *pool);
+
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char *mg_last_error(void);
 

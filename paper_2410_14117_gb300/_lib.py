@@ -44,6 +44,13 @@ class Ranges(ctypes.Structure):
                 ("flags", ctypes.c_uint32)]
 
 
+class JobSpec(ctypes.Structure):
+    _fields_ = [("n_envs", ctypes.c_int64), ("vehicle_type", ctypes.c_int32),
+                ("hold_steps", ctypes.c_int32), ("horizon", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("param_seed", ctypes.c_uint64),
+                ("cmd_seed", ctypes.c_uint64), ("ranges", Ranges)]
+
+
 _P = ctypes.c_void_p
 _I32, _I64, _U32, _U64, _F = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64,
                               ctypes.c_float)
@@ -74,6 +81,16 @@ SIGNATURES = {
     "mg_get_nonfinite": [_P, _P],
     "mg_philox4x32_10": [_P, _P, _P, _I64],
     "mg_kernel_info": [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)],
+    "mg_pool_create": [_I64, ctypes.POINTER(VehicleParams), _I32, ctypes.POINTER(_P)],
+    "mg_pool_destroy": [_P],
+    "mg_pool_set_stream": [_P, _P],
+    "mg_pool_admit": [_P, ctypes.POINTER(JobSpec), _P, ctypes.POINTER(_I32)],
+    "mg_pool_tick": [_P, _I32, ctypes.POINTER(_I32)],
+    "mg_pool_job_progress": [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)],
+    "mg_pool_get_job_state": [_P, _I32, _P],
+    "mg_pool_release": [_P, _I32],
+    "mg_pool_info": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I32)],
+    "mg_pool_sync": [_P],
 }
 
 _lock = threading.Lock()

@@ -24,6 +24,12 @@ mg_status fail(mg_status st, const std::string &msg) {
   return st;
 }
 
+}  // namespace
+
+mg_status mg::set_error(mg_status st, const std::string &msg) { return fail(st, msg); }
+
+namespace {
+
 mg_status fail_cuda(cudaError_t e, const char *what) {
   char buf[512];
   snprintf(buf, sizeof buf, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));

@@ -54,6 +54,22 @@ __device__ __forceinline__ double u01d(uint32_t x) {
 // Counter streams of the draws (shared with the host-side documentation in mg.h).
 enum : uint32_t { STREAM_PARAMS = 0, STREAM_CURRENT = 1, STREAM_RESET = 2, STREAM_CMD = 3 };
 
+// Procedural throttle commands of segment seg for env id gid: c_i = 2u - 1 (stream 3, blocks
+// 2 seg and 2 seg + 1 give thrusters 0..3 and 4..7).
+template <int MT>
+__device__ __forceinline__ void procedural_commands(uint64_t seed, uint64_t gid, int64_t seg,
+                                                    float (&c)[MT]) {
+  const uint4 a = draw4(seed, gid, STREAM_CMD, (uint32_t)(2 * seg));
+  c[0] = 2.f * u01f(a.x) - 1.f; c[1] = 2.f * u01f(a.y) - 1.f;
+  c[2] = 2.f * u01f(a.z) - 1.f; c[3] = 2.f * u01f(a.w) - 1.f;
+  const uint4 b = draw4(seed, gid, STREAM_CMD, (uint32_t)(2 * seg + 1));
+  c[4] = 2.f * u01f(b.x) - 1.f; c[5] = 2.f * u01f(b.y) - 1.f;
+  if constexpr (MT > 6) {
+    c[6] = 2.f * u01f(b.z) - 1.f;
+    c[7] = 2.f * u01f(b.w) - 1.f;
+  }
+}
+
 // ---------------------------------------------------------------- per-env registers
 template <int MT>
 struct St {

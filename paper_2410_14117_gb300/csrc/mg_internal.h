@@ -7,9 +7,14 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "mg.h"
 
 namespace mg {
+
+// Records msg as this thread's mg_last_error() and returns st (mg_api.cu).
+mg_status set_error(mg_status st, const std::string &msg);
 
 // ---------------------------------------------------------------- state planes
 // 13 + n_thr floats per env packed into float4 planes (the 21-float record of mg.h minus
@@ -106,7 +111,7 @@ struct SetupView {
   int64_t n;
   int64_t gid0;
   const int32_t *types;      // device [n]
-  float *raw;                // device [MG_NPARAM][n] (parameter-major)
+  float *raw;                // device [n][MG_NPARAM] (the record layout of mg.h)
   ParamPlanes pa;
   unsigned long long *n_not_spd;
   unsigned int *any_offdiag;

@@ -143,7 +143,7 @@ __global__ void k_randomize(const SetupView v, const float *__restrict__ nominal
   // with what mg_get_params reports.
   for (int j = 0; j < MG_NPARAM; ++j) {
     const float f = (float)p[j];
-    v.raw[(int64_t)j * v.n + e] = f;
+    v.raw[e * MG_NPARAM + j] = f;
     p[j] = (double)f;
   }
   derive(v, e, p);
@@ -155,7 +155,7 @@ __global__ void k_import_params(const SetupView v, const float *__restrict__ in)
   double p[MG_NPARAM];
   for (int j = 0; j < MG_NPARAM; ++j) {
     const float f = in[e * MG_NPARAM + j];
-    v.raw[(int64_t)j * v.n + e] = f;
+    v.raw[e * MG_NPARAM + j] = f;
     p[j] = (double)f;
   }
   derive(v, e, p);
@@ -164,7 +164,7 @@ __global__ void k_import_params(const SetupView v, const float *__restrict__ in)
 __global__ void k_export_params(const SetupView v, float *__restrict__ out) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= v.n) return;
-  for (int j = 0; j < MG_NPARAM; ++j) out[e * MG_NPARAM + j] = v.raw[(int64_t)j * v.n + e];
+  for (int j = 0; j < MG_NPARAM; ++j) out[e * MG_NPARAM + j] = v.raw[e * MG_NPARAM + j];
 }
 
 __global__ void k_reset(const StatePlanes st, int64_t n, int64_t gid0,

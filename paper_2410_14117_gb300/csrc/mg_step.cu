@@ -46,16 +46,7 @@ template <int MT>
 __device__ __forceinline__ void load_commands(const FleetView &fv, int64_t e, int64_t seg,
                                               int nt, float itau, float (&c)[MT]) {
   if (fv.proc) {
-    const uint64_t gid = (uint64_t)(fv.gid0 + e);
-    const uint4 a = draw4(fv.cmd_seed, gid, STREAM_CMD, (uint32_t)(2 * seg));
-    c[0] = 2.f * u01f(a.x) - 1.f; c[1] = 2.f * u01f(a.y) - 1.f;
-    c[2] = 2.f * u01f(a.z) - 1.f; c[3] = 2.f * u01f(a.w) - 1.f;
-    const uint4 b = draw4(fv.cmd_seed, gid, STREAM_CMD, (uint32_t)(2 * seg + 1));
-    c[4] = 2.f * u01f(b.x) - 1.f; c[5] = 2.f * u01f(b.y) - 1.f;
-    if constexpr (MT > 6) {
-      c[6] = 2.f * u01f(b.z) - 1.f;
-      c[7] = 2.f * u01f(b.w) - 1.f;
-    }
+    procedural_commands<MT>(fv.cmd_seed, (uint64_t)(fv.gid0 + e), seg, c);
   } else if (fv.n_seg > 0) {
     const int64_t sg = seg < fv.n_seg - 1 ? seg : fv.n_seg - 1;
     const float4 *a = fv.act + (sg * fv.n + e) * 2;

@@ -1,0 +1,115 @@
+"""Serving: continuous batching over the native job pool.  A job's result is the same alone and
+in a mix (bit for bit: same kernel, draws keyed by the job's own seeds and local env ids), equals
+the plain fleet API doing the same rollout, and matches the FP64 oracle; admission respects the
+HBM budget and the arena's free ranges."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2410_14117_gb300 import inputs as I
+from paper_2410_14117_gb300.serve import Pool, Request, Server
+from paper_2410_14117_gb300.sim import Sim
+
+from _helpers import TOL_ROLLOUT, f32, oracle_geo, oracle_nominal, rel_err, vehicles
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests(seed=3, n_jobs=10):
+    g = np.random.default_rng(seed)
+    out = []
+    for i in range(n_jobs):
+        out.append(Request(arrival_s=0.0005 * i, n_envs=int(g.integers(1, 3000)),
+                           horizon=int(g.integers(30, 260)), vehicle=int(g.integers(0, 2)),
+                           param_seed=int(g.integers(1, 2**40)),
+                           cmd_seed=int(g.integers(1, 2**40)), hold=int(g.integers(1, 12))))
+    return out
+
+
+def _by_key(done):
+    return {(r.param_seed, r.cmd_seed): r for r in done}
+
+
+def test_alone_equals_mix_and_plain_fleet():
+    vs = vehicles()
+    reqs = _requests()
+    srv = Server(vs, budget_bytes=8e9, capacity_envs=1 << 16, k=25, keep_results=True)
+    mix, stats = srv.run([Request(**{k: getattr(r, k) for k in ("arrival_s", "n_envs", "horizon",
+                                                              "vehicle", "param_seed",
+                                                              "cmd_seed", "hold")})
+                          for r in reqs], mode="batched")
+    srv.close()
+    assert stats["jobs"] == len(reqs)
+    srv = Server(vs, budget_bytes=8e9, capacity_envs=1 << 16, k=25, keep_results=True)
+    alone, _ = srv.run(reqs, mode="serial")
+    srv.close()
+    a, m = _by_key(alone), _by_key(mix)
+    for key, r in a.items():
+        torch.testing.assert_close(m[key].final_state, r.final_state, rtol=0, atol=0)
+        torch.testing.assert_close(m[key].traj, r.traj, rtol=0, atol=0)
+    # the plain fleet API with the same seeds gives the same rollout
+    for r in list(a.values())[:4]:
+        sim = Sim(r.n_envs, np.full(r.n_envs, r.vehicle), vs)
+        sim.randomize(r.param_seed, 0.8, 1.2, 0.2, 0.3)
+        sim.reset()
+        sim.set_procedural_actions(r.cmd_seed, r.hold)
+        sim.step(r.horizon)
+        torch.testing.assert_close(sim.get_state()[:, :13], r.final_state[:, :13], rtol=1e-5,
+                                   atol=1e-5)
+        sim.close()
+
+
+def test_served_job_matches_oracle():
+    vs = vehicles()
+    r = Request(arrival_s=0.0, n_envs=700, horizon=300, vehicle=1, param_seed=77, cmd_seed=88,
+                hold=10)
+    srv = Server(vs, budget_bytes=4e9, capacity_envs=1 << 14, k=50, keep_results=True)
+    (res,), _ = srv.run([r], mode="batched")
+    srv.close()
+    types = np.full(r.n_envs, 1, dtype=np.int32)
+    params = I.round_f32(O.randomize(77, oracle_nominal(vs), types, f32(0.8), f32(1.2),
+                                     f32(0.2)))
+    s0 = np.stack([I.round_f32(O.reset_state(77, f32(0.3), e, 0)) for e in range(r.n_envs)])
+    cmds = np.stack([np.stack([O.commands(88, e, sg, 8) for e in range(r.n_envs)])
+                     for sg in range(30)])
+    ref, traj = O.rollout(params, oracle_geo(vs), types, s0, cmds, 10, 300, record=True)
+    got = res.final_state.double().cpu().numpy()
+    assert rel_err(got, ref).max() <= TOL_ROLLOUT
+    g = res.traj.double().cpu().numpy()  # [T, 13, n]
+    np.testing.assert_allclose(g[150].T, traj[150, :, :13], rtol=0, atol=1e-4)
+
+
+def test_budget_and_capacity_bound_admission():
+    vs = vehicles()
+    reqs = _requests(seed=5, n_jobs=12)
+    # a small arena forces jobs to wait for free ranges; a small budget forces waits too
+    per = max(r.horizon * 13 * 4 * r.n_envs for r in reqs)
+    srv = Server(vs, budget_bytes=4096 * 500 + 2.5 * per, capacity_envs=4096, k=40)
+    base = srv.used
+    done, stats = srv.run(reqs, mode="batched")
+    assert stats["jobs"] == len(reqs)
+    assert base < srv.peak_used <= srv.budget
+    assert srv.used == base
+    info = srv.pool.info()
+    assert info["free_envs"] == 4096 and info["largest_free_range"] == 4096
+    srv.close()
+
+
+def test_pool_ranges_coalesce_and_reject():
+    vs = vehicles()
+    pool = Pool(1000, vs)
+    a = pool.admit(300, 0, 10, 1, 2)
+    b = pool.admit(300, 1, 10, 3, 4)
+    c = pool.admit(300, 0, 10, 5, 6)
+    assert pool.admit(200, 0, 10, 7, 8) is None          # only 100 left
+    pool.release(b)
+    assert pool.info()["largest_free_range"] == 300
+    pool.release(a)
+    assert pool.info()["largest_free_range"] == 600       # merged with the freed neighbour
+    d = pool.admit(550, 1, 10, 9, 10)
+    assert d is not None
+    pool.tick(10)
+    pool.sync()
+    assert pool.progress(d) == (10, 10) and pool.progress(c) == (10, 10)
+    pool.close()

@@ -126,6 +126,22 @@ class Clocks:
                 "samples": len(rows)}
 
 
+def reduce_max(x: float, device="cpu") -> float:
+    """Maximum of x over the ranks of the default process group (x itself without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_env_offset(rank: int, n_envs: int) -> int:
+    """First global env id of a rank's fleet (weak scaling: every rank steps n_envs envs)."""
+    return rank * n_envs
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -251,7 +267,7 @@ def run_ours(args):
         from paper_2410_14117_gb300.autotune import Autotuner
         cfg = Autotuner(horizon=horizon, reps=2).pick(n, types0, vs)
     sim = Sim(n, types0, vs)
-    sim.set_env_id_offset(rank * n)
+    sim.set_env_id_offset(rank_env_offset(rank, n))
     cfg.apply(sim)
     n_seg = math.ceil(horizon / hold)
     acts_np = I.commands(5678 + rank, n_seg, n, 6)
@@ -298,11 +314,7 @@ def run_ours(args):
     clk = clocks.stop()
     step_ms = [e[0].elapsed_time(e[3]) for e in ev]
     graph_ms = [e[1].elapsed_time(e[2]) for e in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max(sum(step_ms), dev)
     value = world * n * horizon * args.steps / (total_ms / 1e3)
 
     peaks, peak_kind = load_peaks()
@@ -340,11 +352,7 @@ def run_ours(args):
         for i in range(ke):
             episode(3000 + i, acts_host, out_host)
         torch.cuda.synchronize()
-        el = time.perf_counter() - t
-        if world > 1:
-            tt = torch.tensor([el], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            el = float(tt.item())
+        el = reduce_max(time.perf_counter() - t, dev)
         line["e2e"] = {"value": world * n * horizon * ke / el, "unit": "env-steps/s",
                        "h2d_bytes_per_step": acts_np.nbytes,
                        "d2h_bytes_per_step": n * 21 * 4,

@@ -175,6 +175,23 @@ mg_status mg_set_procedural_actions(mg_sim *sim, uint64_t cmd_seed, int32_t hold
  * stream; non-finite states are reported by mg_sync. */
 mg_status mg_step(mg_sim *sim, int32_t k);
 
+/* As mg_step with the work-queue schedule, for callers that must not allocate device memory
+ * while they step (for instance a real-time control loop whose memory is fixed up front, or code
+ * that runs with its memory pool capped): the call launches the work-queue kernel directly (no
+ * CUDA graph is instantiated, nothing is staged) and keeps the queue's scheduler words in a
+ * fixed 256 KB device array compiled into the library instead of the sim's own buffers.  The
+ * paper has no counterpart; it is an interface convenience around the same kernel.
+ *   - The first call on a device looks up that array's device address (once per device, with
+ *     the device current); make that first call before any stream capture.
+ *   - Fleets of at most 65,536 32-env slices (2,097,152 envs of one vehicle type) are accepted;
+ *     larger ones get MG_EINVAL with a message saying so.
+ *   - All calls, from every sim on the device, share the one array and it keeps the last call's
+ *     contents: each call zeroes the words it uses on the sim's stream before its launch, and
+ *     calls whose launches overlap on the GPU (two sims on different streams) race on it.
+ * Uses the sim's steps_per_launch as the chunk size and the wide / warps_per_sm settings of
+ * mg_set_schedule, whatever the schedule chosen there; results equal mg_step's bit for bit. */
+mg_status mg_step_noalloc(mg_sim *sim, int32_t k);
+
 /* As mg_step, also writing the state after every sub-step to traj: device
  * [k][MG_NTRAJ][n_envs] (component-major per step: p(3) q(4) nu(6)). Never graph-replayed. */
 mg_status mg_step_record(mg_sim *sim, int32_t k, float *traj);

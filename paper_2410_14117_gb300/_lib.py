@@ -71,6 +71,7 @@ SIGNATURES = {
     "mg_set_actions": [_P, _P, _I32, _I32],
     "mg_set_procedural_actions": [_P, _U64, _I32],
     "mg_step": [_P, _I32],
+    "mg_step_noalloc": [_P, _I32],
     "mg_step_record": [_P, _I32, _P],
     "mg_rollout_forward": [_P, _I32, _I32, _P, _P, ctypes.POINTER(_I64)],
     "mg_rollout_backward": [_P, _I32, _I32, _P, _P, _I64, _P, _P, _P],

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -283,9 +284,60 @@ mg_status begin_params(mg_sim *s) {
 
 }  // namespace
 
+// ---------------------------------------------------------------- mg_step_noalloc scratch
+// Scheduler words for mg_step_noalloc: the work-queue counter and one progress word per 32-env
+// slice, in a fixed device array instead of the sim's arena, so that the call itself never
+// allocates.  Every GPU that loads the library holds it (256 KB) until the process exits.
+constexpr int kNoAllocMaxSlices = 65536;  // fleets up to 2,097,152 envs
+static __device__ __align__(256) uint32_t g_noalloc_sched[4 + kNoAllocMaxSlices];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+uint32_t *g_noalloc_ptr[kMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+// Device address of g_noalloc_sched on the current device, looked up once per device.  In host
+// code the array's name is only a host-side stand-in, so kernels must be given this address.
+mg_status noalloc_scratch(uint32_t **out) {
+  int dev = 0;
+  MG_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(MG_EINVAL, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    MG_CK(cudaGetSymbolAddress(&p, g_noalloc_sched));
+    g_noalloc_ptr[dev] = static_cast<uint32_t *>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return MG_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *mg_last_error(void) { return g_err.c_str(); }
+
+mg_status mg_step_noalloc(mg_sim *s, int32_t k) {
+  MG_NONNULL(s);
+  if (k < 1) return fail(MG_EINVAL, "k must be >= 1");
+  if (s->n_slices > kNoAllocMaxSlices) {
+    char buf[200];
+    snprintf(buf, sizeof buf,
+             "fleet has %d 32-env slices; mg_step_noalloc supports at most %d (%d envs of one "
+             "vehicle type)", s->n_slices, kNoAllocMaxSlices, 32 * kNoAllocMaxSlices);
+    return fail(MG_EINVAL, buf);
+  }
+  uint32_t *sched = nullptr;
+  mg_status st = noalloc_scratch(&sched);
+  if (st != MG_OK) return st;
+  MG_CK(launch_fleet_queue(s->view(), s->slices_d, s->n_slices, s->ntv, s->diag, s->queue_wide,
+                           s->queue_warps_per_sm, s->cursor, k, s->spl, sched, s->n_sm,
+                           s->stream));
+  s->cursor += k;
+  return MG_OK;
+}
 
 mg_status mg_create(int64_t n_envs, const int32_t *vehicle_types,
                     const mg_vehicle_params *params, int32_t n_types, mg_sim **out) {

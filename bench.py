@@ -126,6 +126,34 @@ class Clocks:
                 "samples": len(rows)}
 
 
+def kernel_sources_sha() -> str:
+    """Hash of the CUDA sources and the ABI header, to tell whether a committed ncu capture
+    still describes the kernels being timed."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2410_14117_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)) + ["../../include/mg.h"]:
+        path = os.path.normpath(os.path.join(csrc, name))
+        if path.endswith((".cu", ".cuh", ".h")):
+            h.update(name.encode())
+            h.update(open(path, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, units: float):
+    """DRAM bytes (read + write) per launch from profiles/dram_traffic.txt, scaled to a launch of
+    `units` env-sub-steps, or None when no capture of the current sources exists."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    sha = kernel_sources_sha()
+    for line in open(path):
+        f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if f.get("kernel") == kernel and f.get("sources_sha") == sha:
+            return float(f["dram_bytes"]) * units / float(f["units"])
+    return None
+
+
 def reduce_max(x: float, device="cpu") -> float:
     """Maximum of x over the ranks of the default process group (x itself without one)."""
     import torch
@@ -296,6 +324,7 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
     clocks.start()
+    torch.cuda.nvtx.range_push("timed")
     for i in range(args.steps):
         flush.zero_()
         e0, e1, e2 = ev[i]
@@ -310,6 +339,7 @@ def run_ours(args):
         ev[i].append(torch.cuda.Event(enable_timing=True))
         ev[i][3].record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     barrier()
     clk = clocks.stop()
     step_ms = [e[0].elapsed_time(e[3]) for e in ev]
@@ -323,8 +353,10 @@ def run_ours(args):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = fp32_alu_peak_tflops(sm_max)
     achieved = flops / launch_s / 1e12
+    kname = "k_fleet" if cfg.schedule == "static" else "k_fleet_queue"
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": None,
+                "frac": achieved / alu_peak,
+                "traffic": profiled_traffic(kname, n * horizon / launches_per_episode),
                 "kernel": ("k_fleet (persistent, static grid" if cfg.schedule == "static"
                            else "k_fleet_queue (persistent, work queue") +
                           ", 6 thrusters, diagonal mass)",
@@ -395,6 +427,7 @@ def run_ours(args):
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         ach = bytes_per_launch / per_launch_s / 1e9
         fused_ms_episode = statistics.mean(graph_ms)
+        ps_traffic = profiled_traffic("k_fleet_step1", n)
         line["per_step"] = {
             "host_launched": n * horizon / (host_ms / 1e3),
             "graph": n * horizon / (graph_ms_ps / 1e3),
@@ -403,7 +436,7 @@ def run_ours(args):
             "fused_over_graph": graph_ms_ps / fused_ms_episode,
             "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                          "frac": ach / hbm, "bytes_per_env_step": bytes_per_launch // n,
-                         "launch_us": per_launch_s * 1e6,
+                         "launch_us": per_launch_s * 1e6, "traffic": ps_traffic,
                          "peak_source": f"{peak_kind} hbm_gbs"}}
         cfg.apply(sim)
 

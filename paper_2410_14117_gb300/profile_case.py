@@ -32,13 +32,16 @@ def main():
     ap.add_argument("--vehicle", type=int, default=0)
     ap.add_argument("--static", action="store_true",
                     help="static grid (one launch per k sub-steps) instead of the work queue")
+    ap.add_argument("--narrow", action="store_true",
+                    help="work queue with the 128-register kernel instead of the 168-register one")
+    ap.add_argument("--wps", type=int, default=8, help="work queue: resident warps per SM cap")
     args = ap.parse_args()
 
     n = args.n_envs
     vs = I.fleet_vehicles()
     sim = Sim(n, np.full(n, args.vehicle, dtype=np.int32), vs)
     sim.set_launch(args.epb, args.k if args.static else args.chunk, False)
-    sim.set_schedule(not args.static)
+    sim.set_schedule(not args.static, not args.narrow, args.wps)
     sim.randomize(1234, 0.8, 1.2, 0.2, 0.3)
     sim.reset()
     total = (args.warmup + args.launches) * args.k

@@ -29,6 +29,15 @@ mg_status fail(mg_status st, const std::string &msg) {
 
 mg_status mg::set_error(mg_status st, const std::string &msg) { return fail(st, msg); }
 
+bool mg::vectored_layout(const Geo &g) {
+  if (g.n_thr < 4) return false;
+  for (int i = 0; i < g.n_thr; ++i) {
+    if (i < 4 && g.dir[i].z != 0.f) return false;
+    if (i >= 4 && (g.dir[i].x != 0.f || g.dir[i].y != 0.f || g.arm[i].z != 0.f)) return false;
+  }
+  return true;
+}
+
 namespace {
 
 mg_status fail_cuda(cudaError_t e, const char *what) {
@@ -77,6 +86,7 @@ struct mg_sim {
   std::vector<mg_vehicle_params> vp;
   NtVariant ntv = NT_6;
   bool diag = true;
+  bool structured = false;  // every type present has the vectored thruster layout
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
 
@@ -236,15 +246,15 @@ mg_status build_blocks(mg_sim *s) {
 mg_status launch_chunks(mg_sim *s, int32_t k, float *traj, cudaStream_t stream) {
   const FleetView v = s->view();
   if (s->queue && !traj) {
-    MG_CK(launch_fleet_queue(v, s->slices_d, s->n_slices, s->ntv, s->diag, s->queue_wide,
-                             s->queue_warps_per_sm, s->cursor, k, s->spl, s->sched, s->n_sm,
-                             stream));
+    MG_CK(launch_fleet_queue(v, s->slices_d, s->n_slices, s->ntv, s->diag, s->structured,
+                             s->queue_wide, s->queue_warps_per_sm, s->cursor, k, s->spl,
+                             s->sched, s->n_sm, stream));
     return MG_OK;
   }
   for (int32_t done = 0; done < k;) {
     const int32_t kk = std::min(s->spl, k - done);
     float *t = traj ? traj + (int64_t)done * MG_NTRAJ * s->n : nullptr;
-    MG_CK(launch_fleet(v, s->blocks_d, s->n_blocks, s->threads, s->ntv, s->diag,
+    MG_CK(launch_fleet(v, s->blocks_d, s->n_blocks, s->threads, s->ntv, s->diag, s->structured,
                        s->cursor + done, kk, t, stream));
     done += kk;
   }
@@ -332,9 +342,9 @@ mg_status mg_step_noalloc(mg_sim *s, int32_t k) {
   uint32_t *sched = nullptr;
   mg_status st = noalloc_scratch(&sched);
   if (st != MG_OK) return st;
-  MG_CK(launch_fleet_queue(s->view(), s->slices_d, s->n_slices, s->ntv, s->diag, s->queue_wide,
-                           s->queue_warps_per_sm, s->cursor, k, s->spl, sched, s->n_sm,
-                           s->stream));
+  MG_CK(launch_fleet_queue(s->view(), s->slices_d, s->n_slices, s->ntv, s->diag, s->structured,
+                           s->queue_wide, s->queue_warps_per_sm, s->cursor, k, s->spl, sched,
+                           s->n_sm, s->stream));
   s->cursor += k;
   return MG_OK;
 }
@@ -439,6 +449,7 @@ mg_status mg_create(int64_t n_envs, const int32_t *vehicle_types,
 
   // Per-type geometry and nominal records.
   std::vector<Geo> geo(n_types);
+  s->structured = true;
   std::vector<float> nom((size_t)n_types * MG_NPARAM, 0.f);
   for (int32_t t = 0; t < n_types; ++t) {
     const mg_vehicle_params &v = params[t];
@@ -451,6 +462,7 @@ mg_status mg_create(int64_t n_envs, const int32_t *vehicle_types,
       g.arm[i] = make_float4(r[1] * d[2] - r[2] * d[1], r[2] * d[0] - r[0] * d[2],
                              r[0] * d[1] - r[1] * d[0], 0.f);
     }
+    if (seen[t] && !vectored_layout(g)) s->structured = false;
     float *p = &nom[(size_t)t * MG_NPARAM];
     p[MG_P_M] = v.m;
     p[MG_P_IG] = v.Ixx;
@@ -727,8 +739,8 @@ mg_status mg_rollout_forward(mg_sim *s, int32_t T, int32_t C, float *traj, float
     const int32_t len = std::min(C, T - t0);
     MG_CK(launch_checkpoint(s->st, s->n, ckpt + (int64_t)(t0 / C) * MG_NSTATE * s->n,
                             s->stream));
-    MG_CK(launch_fleet(v, s->blocks_d, s->n_blocks, s->threads, s->ntv, s->diag, step0 + t0,
-                       len, traj + (int64_t)t0 * MG_NTRAJ * s->n, s->stream));
+    MG_CK(launch_fleet(v, s->blocks_d, s->n_blocks, s->threads, s->ntv, s->diag, s->structured,
+                       step0 + t0, len, traj + (int64_t)t0 * MG_NTRAJ * s->n, s->stream));
   }
   s->cursor += T;
   if (step0_out) *step0_out = step0;
@@ -850,8 +862,10 @@ mg_status mg_kernel_info(mg_sim *s, int32_t *regs, int32_t *max_threads, int32_t
   MG_NONNULL(s);
   cudaFuncAttributes a;
   int per_sm = 0;
-  if (s->queue) MG_CK(queue_kernel_attributes(s->ntv, s->diag, s->queue_wide, &a, &per_sm));
-  else MG_CK(fleet_kernel_attributes(s->ntv, s->diag, false, &a));
+  if (s->queue)
+    MG_CK(queue_kernel_attributes(s->ntv, s->diag, s->queue_wide, s->structured, &a, &per_sm));
+  else
+    MG_CK(fleet_kernel_attributes(s->ntv, s->diag, s->structured, false, &a));
   if (regs) *regs = a.numRegs;
   if (max_threads) *max_threads = a.maxThreadsPerBlock;
   if (local_bytes) *local_bytes = (int32_t)a.localSizeBytes;

@@ -163,9 +163,14 @@ __device__ __forceinline__ void store_state(const StatePlanes &sp, int64_t e, co
 //   - d.q holds 2 q' (the 1/2 of q' = 1/2 q (x) (0, w) is folded into the RK4 weights).
 // Every sum is written as a chain of FMAs into the generalised force (same terms as Eq. 1; only
 // the rounding order differs from a term-by-term evaluation).
-// gdir/garm: the block's vehicle type's thruster directions and moment arms (shared memory);
-// nt = its thruster count (only read when MIXED).
-template <int MT, bool DIAG, bool MIXED>
+// gdir/garm: the block's vehicle type's thruster directions and moment arms (shared memory),
+// zero past its thruster count; MIXED (fleets with several thruster counts) evaluates all MT
+// thrusters, the absent ones contributing exact zeros (their command is zeroed by the caller and
+// their lag state stays 0), so no warp branches on the count.  NH > 0 selects the vectored layout's
+// allocation: thrusters [0, NH) horizontal (d_z = 0: no heave force), the rest vertical
+// (d_x = d_y = 0, so r x d has no yaw component); the skipped products are exact zeros, so the
+// result is bit-identical to the dense 6 x N allocation (NH = 0).
+template <int MT, bool DIAG, bool MIXED, int NH = 0>
 __device__ __forceinline__ void rhs(const St<MT> &s, const float (&cs)[MT], const Par<DIAG> &P,
                                     const float4 *gdir, const float4 *garm, int nt,
                                     bool current_accel, St<MT> &d) {
@@ -173,16 +178,22 @@ __device__ __forceinline__ void rhs(const St<MT> &s, const float (&cs)[MT], cons
   float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f, t4 = 0.f, t5 = 0.f;
 #pragma unroll
   for (int i = 0; i < MT; ++i) {
-    if (!MIXED || i < nt) {
+    {
       const float f = s.n[i] * fabsf(s.n[i]);
       const float4 dd = gdir[i], aa = garm[i];
-      t0 = fmaf(f, dd.x, t0); t1 = fmaf(f, dd.y, t1); t2 = fmaf(f, dd.z, t2);
-      t3 = fmaf(f, aa.x, t3); t4 = fmaf(f, aa.y, t4); t5 = fmaf(f, aa.z, t5);
+      if (NH == 0) {
+        t0 = fmaf(f, dd.x, t0); t1 = fmaf(f, dd.y, t1); t2 = fmaf(f, dd.z, t2);
+        t3 = fmaf(f, aa.x, t3); t4 = fmaf(f, aa.y, t4); t5 = fmaf(f, aa.z, t5);
+      } else if (i < NH) {
+        t0 = fmaf(f, dd.x, t0); t1 = fmaf(f, dd.y, t1);
+        t3 = fmaf(f, aa.x, t3); t4 = fmaf(f, aa.y, t4); t5 = fmaf(f, aa.z, t5);
+      } else {
+        t2 = fmaf(f, dd.z, t2); t3 = fmaf(f, aa.x, t3); t4 = fmaf(f, aa.y, t4);
+      }
       d.n[i] = fmaf(-s.n[i], P.itau, cs[i]);
-    } else {
-      d.n[i] = 0.f;
     }
   }
+  (void)nt;
 
   // Attitude matrix R(q) = I + 2 q_w S(eps) + 2 S(eps)^2 (body -> NED), written out.
   const float qw = s.q[0], qx = s.q[1], qy = s.q[2], qz = s.q[3];
@@ -280,40 +291,60 @@ __device__ __forceinline__ void rhs(const St<MT> &s, const float (&cs)[MT], cons
   d.q[3] = fmaf(qw, w2, fmaf(qx, w1, -qy * w0));
 }
 
+// Packed FP32x2 FMAs for the RK4 stage updates: measured on GB300 without gain (the pairs cost
+// register moves), so off; kept selectable because the result is bit-identical either way.
+#ifndef MG_PACKED_FMA
+#define MG_PACKED_FMA 0
+#endif
+
+// Two correctly rounded FMAs in one instruction (sm_100+): bit-identical to two fmaf calls.
+__device__ __forceinline__ void fma2(float a0, float a1, float k0, float k1, float x0, float x1,
+                                     float &y0, float &y1) {
+#if MG_PACKED_FMA
+  const float2 r = __ffma2_rn(make_float2(a0, a1), make_float2(k0, k1), make_float2(x0, x1));
+  y0 = r.x;
+  y1 = r.y;
+#else
+  y0 = fmaf(a0, k0, x0);
+  y1 = fmaf(a1, k1, x1);
+#endif
+}
+
 // y = x + a k, with the quaternion taking a / 2 (its derivative is stored doubled).
 template <int MT>
 __device__ __forceinline__ void axpy(St<MT> &y, const St<MT> &x, float a, const St<MT> &k) {
   const float aq = 0.5f * a;
+  fma2(a, a, k.p[0], k.p[1], x.p[0], x.p[1], y.p[0], y.p[1]);
+  fma2(a, a, k.p[2], k.v[0], x.p[2], x.v[0], y.p[2], y.v[0]);
+  fma2(aq, aq, k.q[0], k.q[1], x.q[0], x.q[1], y.q[0], y.q[1]);
+  fma2(aq, aq, k.q[2], k.q[3], x.q[2], x.q[3], y.q[2], y.q[3]);
+  fma2(a, a, k.v[1], k.v[2], x.v[1], x.v[2], y.v[1], y.v[2]);
+  fma2(a, a, k.w[0], k.w[1], x.w[0], x.w[1], y.w[0], y.w[1]);
+  fma2(a, a, k.w[2], k.n[0], x.w[2], x.n[0], y.w[2], y.n[0]);
 #pragma unroll
-  for (int i = 0; i < 3; ++i) y.p[i] = fmaf(a, k.p[i], x.p[i]);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) y.q[i] = fmaf(aq, k.q[i], x.q[i]);
-#pragma unroll
-  for (int i = 0; i < 3; ++i) y.v[i] = fmaf(a, k.v[i], x.v[i]);
-#pragma unroll
-  for (int i = 0; i < 3; ++i) y.w[i] = fmaf(a, k.w[i], x.w[i]);
-#pragma unroll
-  for (int i = 0; i < MT; ++i) y.n[i] = fmaf(a, k.n[i], x.n[i]);
+  for (int i = 1; i + 1 < MT; i += 2)
+    fma2(a, a, k.n[i], k.n[i + 1], x.n[i], x.n[i + 1], y.n[i], y.n[i + 1]);
+  if constexpr (MT % 2 == 0) y.n[MT - 1] = fmaf(a, k.n[MT - 1], x.n[MT - 1]);
 }
 
 // One sub-step (§METHOD): classical RK4 of size h, command held (cs = c / tau_m), then
 // q <- q / |q|.
-template <int MT, bool DIAG, bool MIXED>
+template <int MT, bool DIAG, bool MIXED, int NH = 0>
 __device__ __forceinline__ void rk4_step(St<MT> &s, const float (&cs)[MT], const Par<DIAG> &P,
                                          const float4 *gdir, const float4 *garm, int nt,
                                          bool current_accel, float h) {
   const float hh = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f);
   St<MT> k, y, acc;
-  rhs<MT, DIAG, MIXED>(s, cs, P, gdir, garm, nt, current_accel, k);
+  rhs<MT, DIAG, MIXED, NH>(s, cs, P, gdir, garm, nt, current_accel, k);
   axpy(acc, s, h6, k);
   axpy(y, s, hh, k);
-  rhs<MT, DIAG, MIXED>(y, cs, P, gdir, garm, nt, current_accel, k);
+  rhs<MT, DIAG, MIXED, NH>(y, cs, P, gdir, garm, nt, current_accel, k);
   axpy(acc, acc, h3, k);
   axpy(y, s, hh, k);
-  rhs<MT, DIAG, MIXED>(y, cs, P, gdir, garm, nt, current_accel, k);
+  rhs<MT, DIAG, MIXED, NH>(y, cs, P, gdir, garm, nt, current_accel, k);
   axpy(acc, acc, h3, k);
   axpy(y, s, h, k);
-  rhs<MT, DIAG, MIXED>(y, cs, P, gdir, garm, nt, current_accel, k);
+  rhs<MT, DIAG, MIXED, NH>(y, cs, P, gdir, garm, nt, current_accel, k);
   axpy(s, acc, h6, k);
   const float inv = rsqrtf(fmaf(s.q[0], s.q[0], fmaf(s.q[1], s.q[1],
                                 fmaf(s.q[2], s.q[2], s.q[3] * s.q[3]))));

@@ -85,10 +85,12 @@ enum NtVariant { NT_6 = 0, NT_8 = 1, NT_MIXED = 2 };
 
 // ---------------------------------------------------------------- launchers (mg_step.cu)
 // Static schedule: one block per BlockDesc, k sub-steps per launch.
+// structured: every vehicle type present has the vectored layout (thrusters 0..3 with d_z = 0,
+// the rest with d_x = d_y = 0), so the allocation skips its exact zeros (diagonal mass only).
 cudaError_t launch_fleet(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
-                         NtVariant ntv, bool diag, int64_t step0, int32_t k, float *traj,
-                         cudaStream_t stream);
-cudaError_t fleet_kernel_attributes(NtVariant ntv, bool diag, bool record,
+                         NtVariant ntv, bool diag, bool structured, int64_t step0, int32_t k,
+                         float *traj, cudaStream_t stream);
+cudaError_t fleet_kernel_attributes(NtVariant ntv, bool diag, bool structured, bool record,
                                     cudaFuncAttributes *attr);
 
 // Work-queue schedule: warps claim (32-env slice, chunk of sub-steps) units in chunk-major
@@ -100,11 +102,14 @@ size_t queue_sched_bytes(int n_slices);
 // wide: 168-register variant of the diagonal-mass step (fewer resident warps, more registers
 // each); warps_per_sm > 0 caps the resident warps per SM.
 cudaError_t launch_fleet_queue(const FleetView &fv, const BlockDesc *slices, int n_slices,
-                               NtVariant ntv, bool diag, bool wide, int warps_per_sm,
-                               int64_t step0, int32_t k, int32_t chunk, uint32_t *sched, int n_sm,
-                               cudaStream_t stream);
-cudaError_t queue_kernel_attributes(NtVariant ntv, bool diag, bool wide,
+                               NtVariant ntv, bool diag, bool structured, bool wide,
+                               int warps_per_sm, int64_t step0, int32_t k, int32_t chunk,
+                               uint32_t *sched, int n_sm, cudaStream_t stream);
+cudaError_t queue_kernel_attributes(NtVariant ntv, bool diag, bool wide, bool structured,
                                     cudaFuncAttributes *attr, int *blocks_per_sm);
+
+// True when thrusters [0, 4) of the geometry have d_z = 0 and the rest d_x = d_y = 0.
+bool vectored_layout(const Geo &g);
 
 // ---------------------------------------------------------------- launchers (mg_setup.cu)
 struct SetupView {

@@ -42,7 +42,7 @@ namespace {
 
 constexpr int kServeThreads = 128;
 
-template <bool DIAG>
+template <bool DIAG, int NH>
 __global__ void __maxnreg__(DIAG ? 128 : 168)
     k_serve(const FleetView fv, const JobDesc *__restrict__ jobs,
             const ServeBlock *__restrict__ blocks) {
@@ -80,7 +80,7 @@ __global__ void __maxnreg__(DIAG ? 128 : 168)
       left = jd.hold;
       load(seg);
     }
-    rk4_step<MT, DIAG, true>(s, c, P, sdir, sarm, nt, current_accel, fv.dt);
+    rk4_step<MT, DIAG, true, NH>(s, c, P, sdir, sarm, nt, current_accel, fv.dt);
     --left;
     if (jd.traj) {
       float *t = jd.traj + ((int64_t)(jd.step0 + it) * MG_NTRAJ) * jd.n + el;
@@ -154,6 +154,7 @@ struct mg_pool {
   int32_t n_types = 0;
   std::vector<mg_vehicle_params> vp;
   bool diag = true;
+  bool structured = true;  // every vehicle type has the vectored thruster layout
   cudaStream_t stream = nullptr;
   void *arena = nullptr;
   StatePlanes st{};
@@ -310,6 +311,7 @@ mg_status mg_pool_create(int64_t capacity_envs, const mg_vehicle_params *params,
       g.arm[i] = make_float4(r[1] * d[2] - r[2] * d[1], r[2] * d[0] - r[0] * d[2],
                              r[0] * d[1] - r[1] * d[0], 0.f);
     }
+    if (!vectored_layout(g)) p->structured = false;
     float *q = &nom[(size_t)t * MG_NPARAM];
     q[MG_P_M] = v.m;
     q[MG_P_IG] = v.Ixx;
@@ -465,10 +467,12 @@ mg_status mg_pool_tick(mg_pool *p, int32_t k, int32_t *n_running) {
   const ServeBlock *bl =
       reinterpret_cast<const ServeBlock *>(static_cast<char *>(p->dev_table) + tb);
   const FleetView v = pool_view(p);
-  if (p->diag)
-    k_serve<true><<<(int)blocks.size(), kServeThreads, 0, p->stream>>>(v, jt, bl);
+  if (p->diag && p->structured)
+    k_serve<true, 4><<<(int)blocks.size(), kServeThreads, 0, p->stream>>>(v, jt, bl);
+  else if (p->diag)
+    k_serve<true, 0><<<(int)blocks.size(), kServeThreads, 0, p->stream>>>(v, jt, bl);
   else
-    k_serve<false><<<(int)blocks.size(), kServeThreads, 0, p->stream>>>(v, jt, bl);
+    k_serve<false, 0><<<(int)blocks.size(), kServeThreads, 0, p->stream>>>(v, jt, bl);
   PK(cudaGetLastError());
   return MG_OK;
 }

@@ -55,10 +55,18 @@ __device__ void derive(const SetupView &v, int64_t e, const double *p) {
       M[3 + i][3 + j] = Io[i][j] + ((i == j) ? ma[3 + i] : 0.0);
     }
 
-  // Cholesky M = L L^T; L^-1 by forward substitution; M^-1 = L^-T L^-1.
-  double L[6][6] = {}, Li[6][6] = {};
+  // Cholesky M = L L^T; L^-1 by forward substitution; M^-1 = L^-T L^-1.  With r_g = 0 the
+  // matrix is diagonal (diagonal M_A), its factor is diag(sqrt(M_jj)) and the inverse 1 / M_jj.
+  double L[6][6] = {}, Li[6][6] = {}, Mi[6][6] = {};
   bool spd = true;
-  for (int j = 0; j < 6; ++j) {
+  const bool diagonal = (r2 == 0.0);
+  if (diagonal) {
+    for (int j = 0; j < 6; ++j) {
+      if (!(M[j][j] > 0.0)) spd = false;
+      Mi[j][j] = M[j][j] > 0.0 ? 1.0 / M[j][j] : 0.0;
+    }
+  }
+  for (int j = 0; j < 6 && !diagonal; ++j) {
     double d = M[j][j];
     for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
     if (!(d > 0.0)) {
@@ -72,7 +80,7 @@ __device__ void derive(const SetupView &v, int64_t e, const double *p) {
       L[i][j] = s / L[j][j];
     }
   }
-  for (int j = 0; j < 6; ++j) {
+  for (int j = 0; j < 6 && !diagonal; ++j) {
     Li[j][j] = 1.0 / L[j][j];
     for (int i = j + 1; i < 6; ++i) {
       double s = 0.0;
@@ -80,8 +88,7 @@ __device__ void derive(const SetupView &v, int64_t e, const double *p) {
       Li[i][j] = -s / L[i][i];
     }
   }
-  double Mi[6][6];
-  for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < 6 && !diagonal; ++i)
     for (int j = 0; j < 6; ++j) {
       double s = 0.0;
       for (int k = (i > j ? i : j); k < 6; ++k) s += Li[k][i] * Li[k][j];

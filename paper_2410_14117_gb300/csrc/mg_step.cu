@@ -13,7 +13,9 @@
 //                  warps to each scheduler and idles the 3-warp ones for a quarter of the time).
 //
 // Blocks / slices cover envs of a single vehicle type, so the thruster geometry is a broadcast
-// from shared memory and no warp diverges on the type.
+// from shared memory and no warp diverges on the type.  Fleets whose types have different
+// thruster counts run the 8-thruster loop for every env ("padded"): absent thrusters have zero
+// direction and arm and zero command, so they add exact zeros.
 #include <algorithm>
 #include <type_traits>
 
@@ -92,7 +94,7 @@ __device__ __forceinline__ bool all_finite(const St<MT> &s) {
 
 // Advance env e by k sub-steps starting at action-cursor position step0.  L2: state (and flag)
 // loads bypass L1 (work-queue schedule, where another SM may have written them).
-template <int MT, bool DIAG, bool MIXED, bool REC, bool L2>
+template <int MT, bool DIAG, bool MIXED, bool REC, bool L2, int NH>
 __device__ __forceinline__ void advance_env(const FleetView &fv, int64_t e, int nt,
                                             const float4 *gdir, const float4 *garm,
                                             int64_t step0, int32_t k, float *traj) {
@@ -116,7 +118,7 @@ __device__ __forceinline__ void advance_env(const FleetView &fv, int64_t e, int 
       left = fv.hold;
       load_commands<MT>(fv, e, seg, nt, P.itau, c);
     }
-    rk4_step<MT, DIAG, MIXED>(s, c, P, gdir, garm, nt, current_accel, h);
+    rk4_step<MT, DIAG, MIXED, NH>(s, c, P, gdir, garm, nt, current_accel, h);
     --left;
     if constexpr (REC) record<MT>(traj + (int64_t)it * MG_NTRAJ * fv.n, fv.n, e, s);
   }
@@ -131,7 +133,7 @@ __device__ __forceinline__ void advance_env(const FleetView &fv, int64_t e, int 
   }
 }
 
-template <int NTV, bool DIAG, bool REC>
+template <int NTV, bool DIAG, bool REC, int NH>
 __global__ void __maxnreg__(DIAG ? kRegsDiag : kRegsGeneral)
     k_fleet(const FleetView fv, const BlockDesc *__restrict__ blocks, const int64_t step0,
             const int32_t k, float *__restrict__ traj) {
@@ -146,11 +148,12 @@ __global__ void __maxnreg__(DIAG ? kRegsDiag : kRegsGeneral)
   }
   __syncthreads();
   if ((int)threadIdx.x >= bd.count) return;
-  advance_env<MT, DIAG, MIXED, REC, false>(fv, (int64_t)bd.env0 + threadIdx.x,
-                                           MIXED ? bd.n_thr : MT, sdir, sarm, step0, k, traj);
+  advance_env<MT, DIAG, MIXED, REC, false, NH>(fv, (int64_t)bd.env0 + threadIdx.x,
+                                               MIXED ? bd.n_thr : MT, sdir, sarm, step0, k,
+                                               traj);
 }
 
-template <int NTV, bool DIAG, bool WIDE>
+template <int NTV, bool DIAG, bool WIDE, int NH>
 __global__ void __maxnreg__((DIAG && !WIDE) ? kRegsDiag : kRegsGeneral)
     k_fleet_queue(const FleetView fv, const BlockDesc *__restrict__ slices, const int32_t n_slices,
                   const int64_t step0, const int32_t k_total, const int32_t chunk,
@@ -191,10 +194,10 @@ __global__ void __maxnreg__((DIAG && !WIDE) ? kRegsDiag : kRegsGeneral)
     const BlockDesc bd = slices[d];
     const float4 *gdir = sgeo[bd.type & (MG_MAX_TYPES - 1)], *garm = gdir + MG_MAX_THR;
     if (lane < bd.count)
-      advance_env<MT, DIAG, MIXED, false, true>(fv, (int64_t)bd.env0 + lane,
-                                                MIXED ? bd.n_thr : MT, gdir, garm,
-                                                step0 + (int64_t)c * chunk,
-                                                min(chunk, k_total - c * chunk), nullptr);
+      advance_env<MT, DIAG, MIXED, false, true, NH>(fv, (int64_t)bd.env0 + lane,
+                                                    MIXED ? bd.n_thr : MT, gdir, garm,
+                                                    step0 + (int64_t)c * chunk,
+                                                    min(chunk, k_total - c * chunk), nullptr);
     __syncwarp();
     if (lane == 0) {
       __threadfence();
@@ -203,89 +206,122 @@ __global__ void __maxnreg__((DIAG && !WIDE) ? kRegsDiag : kRegsGeneral)
   }
 }
 
+// Structured allocation (NH = 4) is only instantiated for the diagonal-mass step.
 template <int NTV, bool DIAG, bool REC>
 cudaError_t launch_t(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
-                     int64_t step0, int32_t k, float *traj, cudaStream_t stream) {
-  k_fleet<NTV, DIAG, REC><<<n_blocks, threads, 0, stream>>>(fv, blocks, step0, k, traj);
+                     bool structured, int64_t step0, int32_t k, float *traj,
+                     cudaStream_t stream) {
+  if (DIAG && structured)
+    k_fleet<NTV, DIAG, REC, (DIAG ? 4 : 0)><<<n_blocks, threads, 0, stream>>>(fv, blocks, step0,
+                                                                             k, traj);
+  else
+    k_fleet<NTV, DIAG, REC, 0><<<n_blocks, threads, 0, stream>>>(fv, blocks, step0, k, traj);
   return cudaGetLastError();
 }
 
 template <int NTV, bool DIAG>
 cudaError_t launch_r(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
-                     int64_t step0, int32_t k, float *traj, cudaStream_t stream) {
-  return traj ? launch_t<NTV, DIAG, true>(fv, blocks, n_blocks, threads, step0, k, traj, stream)
-              : launch_t<NTV, DIAG, false>(fv, blocks, n_blocks, threads, step0, k, traj, stream);
+                     bool structured, int64_t step0, int32_t k, float *traj,
+                     cudaStream_t stream) {
+  return traj ? launch_t<NTV, DIAG, true>(fv, blocks, n_blocks, threads, structured, step0, k,
+                                          traj, stream)
+              : launch_t<NTV, DIAG, false>(fv, blocks, n_blocks, threads, structured, step0, k,
+                                           traj, stream);
 }
 
 template <int NTV>
 cudaError_t launch_d(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
-                     bool diag, int64_t step0, int32_t k, float *traj, cudaStream_t stream) {
-  return diag ? launch_r<NTV, true>(fv, blocks, n_blocks, threads, step0, k, traj, stream)
-              : launch_r<NTV, false>(fv, blocks, n_blocks, threads, step0, k, traj, stream);
+                     bool diag, bool structured, int64_t step0, int32_t k, float *traj,
+                     cudaStream_t stream) {
+  return diag ? launch_r<NTV, true>(fv, blocks, n_blocks, threads, structured, step0, k, traj,
+                                    stream)
+              : launch_r<NTV, false>(fv, blocks, n_blocks, threads, structured, step0, k, traj,
+                                     stream);
 }
 
 template <int NTV, bool DIAG, bool REC>
-const void *kernel_ptr() {
-  return reinterpret_cast<const void *>(&k_fleet<NTV, DIAG, REC>);
+const void *kernel_ptr(bool structured) {
+  if (DIAG && structured)
+    return reinterpret_cast<const void *>(&k_fleet<NTV, DIAG, REC, (DIAG ? 4 : 0)>);
+  return reinterpret_cast<const void *>(&k_fleet<NTV, DIAG, REC, 0>);
 }
 
 template <int NTV, bool DIAG>
-const void *queue_ptr(bool wide) {
-  return wide ? reinterpret_cast<const void *>(&k_fleet_queue<NTV, DIAG, true>)
-              : reinterpret_cast<const void *>(&k_fleet_queue<NTV, DIAG, false>);
+const void *queue_ptr(bool wide, bool structured) {
+  constexpr int S = DIAG ? 4 : 0;
+  if (DIAG && structured)
+    return wide ? reinterpret_cast<const void *>(&k_fleet_queue<NTV, DIAG, true, S>)
+                : reinterpret_cast<const void *>(&k_fleet_queue<NTV, DIAG, false, S>);
+  return wide ? reinterpret_cast<const void *>(&k_fleet_queue<NTV, DIAG, true, 0>)
+              : reinterpret_cast<const void *>(&k_fleet_queue<NTV, DIAG, false, 0>);
 }
 
-const void *queue_kernel(NtVariant ntv, bool diag, bool wide) {
+const void *queue_kernel(NtVariant ntv, bool diag, bool wide, bool structured) {
   switch (ntv) {
-    case NT_6: return diag ? queue_ptr<NT_6, true>(wide) : queue_ptr<NT_6, false>(wide);
-    case NT_8: return diag ? queue_ptr<NT_8, true>(wide) : queue_ptr<NT_8, false>(wide);
-    default: return diag ? queue_ptr<NT_MIXED, true>(wide) : queue_ptr<NT_MIXED, false>(wide);
+    case NT_6:
+      return diag ? queue_ptr<NT_6, true>(wide, structured) : queue_ptr<NT_6, false>(wide, false);
+    case NT_8:
+      return diag ? queue_ptr<NT_8, true>(wide, structured) : queue_ptr<NT_8, false>(wide, false);
+    default:
+      return diag ? queue_ptr<NT_MIXED, true>(wide, structured)
+                  : queue_ptr<NT_MIXED, false>(wide, false);
   }
 }
 
-template <int NTV, bool DIAG>
+template <int NTV, bool DIAG, int NH>
 void queue_launch_w(bool wide, int grid, const FleetView &fv, const BlockDesc *slices,
                     int32_t n_slices, int64_t step0, int32_t k, int32_t chunk, uint32_t *sched,
                     cudaStream_t stream) {
   if (wide)
-    k_fleet_queue<NTV, DIAG, true><<<grid, kQueueWarps * 32, 0, stream>>>(
+    k_fleet_queue<NTV, DIAG, true, NH><<<grid, kQueueWarps * 32, 0, stream>>>(
         fv, slices, n_slices, step0, k, chunk, sched);
   else
-    k_fleet_queue<NTV, DIAG, false><<<grid, kQueueWarps * 32, 0, stream>>>(
+    k_fleet_queue<NTV, DIAG, false, NH><<<grid, kQueueWarps * 32, 0, stream>>>(
         fv, slices, n_slices, step0, k, chunk, sched);
 }
 
 template <int NTV>
-void queue_launch(bool diag, bool wide, int grid, const FleetView &fv, const BlockDesc *slices,
-                  int32_t n_slices, int64_t step0, int32_t k, int32_t chunk, uint32_t *sched,
-                  cudaStream_t stream) {
-  if (diag) queue_launch_w<NTV, true>(wide, grid, fv, slices, n_slices, step0, k, chunk, sched,
-                                      stream);
-  else queue_launch_w<NTV, false>(wide, grid, fv, slices, n_slices, step0, k, chunk, sched,
+void queue_launch(bool diag, bool wide, bool structured, int grid, const FleetView &fv,
+                  const BlockDesc *slices, int32_t n_slices, int64_t step0, int32_t k,
+                  int32_t chunk, uint32_t *sched, cudaStream_t stream) {
+  if (diag && structured)
+    queue_launch_w<NTV, true, 4>(wide, grid, fv, slices, n_slices, step0, k, chunk, sched,
+                                 stream);
+  else if (diag)
+    queue_launch_w<NTV, true, 0>(wide, grid, fv, slices, n_slices, step0, k, chunk, sched,
+                                 stream);
+  else
+    queue_launch_w<NTV, false, 0>(wide, grid, fv, slices, n_slices, step0, k, chunk, sched,
                                   stream);
 }
 
 }  // namespace
 
 cudaError_t launch_fleet(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
-                         NtVariant ntv, bool diag, int64_t step0, int32_t k, float *traj,
-                         cudaStream_t stream) {
+                         NtVariant ntv, bool diag, bool structured, int64_t step0, int32_t k,
+                         float *traj, cudaStream_t stream) {
   if (threads < 32 || threads > kMaxThreads || threads % 32 || n_blocks < 1 || k < 1)
     return cudaErrorInvalidValue;
   switch (ntv) {
-    case NT_6: return launch_d<NT_6>(fv, blocks, n_blocks, threads, diag, step0, k, traj, stream);
-    case NT_8: return launch_d<NT_8>(fv, blocks, n_blocks, threads, diag, step0, k, traj, stream);
+    case NT_6:
+      return launch_d<NT_6>(fv, blocks, n_blocks, threads, diag, structured, step0, k, traj,
+                            stream);
+    case NT_8:
+      return launch_d<NT_8>(fv, blocks, n_blocks, threads, diag, structured, step0, k, traj,
+                            stream);
     default:
-      return launch_d<NT_MIXED>(fv, blocks, n_blocks, threads, diag, step0, k, traj, stream);
+      return launch_d<NT_MIXED>(fv, blocks, n_blocks, threads, diag, structured, step0, k, traj,
+                                stream);
   }
 }
 
-cudaError_t fleet_kernel_attributes(NtVariant ntv, bool diag, bool rec,
+cudaError_t fleet_kernel_attributes(NtVariant ntv, bool diag, bool structured, bool rec,
                                     cudaFuncAttributes *attr) {
   const void *f = nullptr;
-#define MG_PICK(N)                                                                  \
-  f = diag ? (rec ? kernel_ptr<N, true, true>() : kernel_ptr<N, true, false>())     \
-           : (rec ? kernel_ptr<N, false, true>() : kernel_ptr<N, false, false>());
+#define MG_PICK(N)                                                                      \
+  f = diag ? (rec ? kernel_ptr<N, true, true>(structured)                               \
+                  : kernel_ptr<N, true, false>(structured))                             \
+           : (rec ? kernel_ptr<N, false, true>(false) : kernel_ptr<N, false, false>(false));
   switch (ntv) {
     case NT_6: MG_PICK(NT_6) break;
     case NT_8: MG_PICK(NT_8) break;
@@ -297,22 +333,22 @@ cudaError_t fleet_kernel_attributes(NtVariant ntv, bool diag, bool rec,
 
 size_t queue_sched_bytes(int n_slices) { return 16 + 4 * (size_t)n_slices; }
 
-cudaError_t queue_kernel_attributes(NtVariant ntv, bool diag, bool wide,
+cudaError_t queue_kernel_attributes(NtVariant ntv, bool diag, bool wide, bool structured,
                                     cudaFuncAttributes *attr, int *blocks_per_sm) {
-  const void *f = queue_kernel(ntv, diag, wide);
+  const void *f = queue_kernel(ntv, diag, wide, structured);
   cudaError_t e = cudaFuncGetAttributes(attr, f);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kQueueWarps * 32, 0);
 }
 
 cudaError_t launch_fleet_queue(const FleetView &fv, const BlockDesc *slices, int n_slices,
-                               NtVariant ntv, bool diag, bool wide, int warps_per_sm,
-                               int64_t step0, int32_t k, int32_t chunk, uint32_t *sched, int n_sm,
-                               cudaStream_t stream) {
+                               NtVariant ntv, bool diag, bool structured, bool wide,
+                               int warps_per_sm, int64_t step0, int32_t k, int32_t chunk,
+                               uint32_t *sched, int n_sm, cudaStream_t stream) {
   if (n_slices < 1 || k < 1 || chunk < 1 || n_sm < 1) return cudaErrorInvalidValue;
   cudaFuncAttributes attr;
   int per_sm = 0;
-  cudaError_t e = queue_kernel_attributes(ntv, diag, wide, &attr, &per_sm);
+  cudaError_t e = queue_kernel_attributes(ntv, diag, wide, structured, &attr, &per_sm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   // Resident warps: at most what fits (and at most warps_per_sm per SM when that is > 0), and no
@@ -331,16 +367,16 @@ cudaError_t launch_fleet_queue(const FleetView &fv, const BlockDesc *slices, int
     if (e != cudaSuccess) return e;
     switch (ntv) {
       case NT_6:
-        queue_launch<NT_6>(diag, wide, grid, fv, slices, n_slices, step0 + done, kk, chunk,
-                           sched, stream);
+        queue_launch<NT_6>(diag, wide, structured, grid, fv, slices, n_slices, step0 + done, kk,
+                           chunk, sched, stream);
         break;
       case NT_8:
-        queue_launch<NT_8>(diag, wide, grid, fv, slices, n_slices, step0 + done, kk, chunk,
-                           sched, stream);
+        queue_launch<NT_8>(diag, wide, structured, grid, fv, slices, n_slices, step0 + done, kk,
+                           chunk, sched, stream);
         break;
       default:
-        queue_launch<NT_MIXED>(diag, wide, grid, fv, slices, n_slices, step0 + done, kk, chunk,
-                               sched, stream);
+        queue_launch<NT_MIXED>(diag, wide, structured, grid, fv, slices, n_slices, step0 + done,
+                               kk, chunk, sched, stream);
         break;
     }
     e = cudaGetLastError();

@@ -166,6 +166,12 @@ mg_status mg_get_params(mg_sim *sim, float *out);
  * Errors: MG_EINVAL (n_seg < 0, hold_steps < 1), MG_ENOMEM, MG_ECUDA. */
 mg_status mg_set_actions(mg_sim *sim, const float *a, int32_t n_seg, int32_t hold_steps);
 
+/* As mg_set_actions, but without a copy: the kernels read a (device, 16-byte aligned,
+ * [n_seg][n_envs][MG_MAX_THR]) in place.  The caller keeps the buffer alive and unchanged until
+ * the stream has passed every mg_step that uses it (e.g. a policy's output tensor consumed by the
+ * next step).  Errors: MG_EINVAL (NULL or host pointer, misaligned, n_seg < 1, hold_steps < 1). */
+mg_status mg_set_actions_borrowed(mg_sim *sim, const float *a, int32_t n_seg, int32_t hold_steps);
+
 /* Procedural actions: throttle c_i = 2u - 1 with u from Philox4x32-10 keyed by (cmd_seed, env
  * id + offset, segment j / hold_steps), no end.  Replaces any action buffer.  Resets the action
  * cursor like mg_set_actions. */

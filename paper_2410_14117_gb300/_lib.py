@@ -69,6 +69,7 @@ SIGNATURES = {
     "mg_set_params": [_P, _P],
     "mg_get_params": [_P, _P],
     "mg_set_actions": [_P, _P, _I32, _I32],
+    "mg_set_actions_borrowed": [_P, _P, _I32, _I32],
     "mg_set_procedural_actions": [_P, _U64, _I32],
     "mg_step": [_P, _I32],
     "mg_step_noalloc": [_P, _I32],

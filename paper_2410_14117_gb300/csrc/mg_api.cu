@@ -117,8 +117,9 @@ struct mg_sim {
   bool queue_wide = true;
   int32_t queue_warps_per_sm = 0;
 
-  // actions
+  // actions (act_src: what the kernels read — the sim's copy, or a caller's borrowed buffer)
   float *act = nullptr;
+  const float *act_src = nullptr;
   size_t act_cap = 0;  // floats
   int32_t n_seg = 0, hold = 1;
   int32_t proc = 0;
@@ -149,7 +150,7 @@ struct mg_sim {
     v.n_types = n_types;
     v.n = n;
     v.gid0 = gid0;
-    v.act = reinterpret_cast<const float4 *>(act);
+    v.act = reinterpret_cast<const float4 *>(act_src);
     v.n_seg = proc ? 0 : n_seg;
     v.hold = hold;
     v.cmd_seed = cmd_seed;
@@ -650,7 +651,25 @@ mg_status mg_set_actions(mg_sim *s, const float *a, int32_t n_seg, int32_t hold_
                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->stream));
     if (!dev) MG_CK(cudaStreamSynchronize(s->stream));
   }
-  if (s->proc || s->n_seg != n_seg || s->hold != hold_steps) s->drop_graphs();
+  if (s->proc || s->n_seg != n_seg || s->hold != hold_steps || s->act_src != s->act)
+    s->drop_graphs();
+  s->act_src = s->act;
+  s->proc = 0;
+  s->n_seg = n_seg;
+  s->hold = hold_steps;
+  s->cursor = 0;
+  return MG_OK;
+}
+
+mg_status mg_set_actions_borrowed(mg_sim *s, const float *a, int32_t n_seg, int32_t hold_steps) {
+  MG_NONNULL(s);
+  MG_NONNULL(a);
+  if (n_seg < 1 || hold_steps < 1) return fail(MG_EINVAL, "need n_seg >= 1 and hold_steps >= 1");
+  if (!is_device_ptr(a)) return fail(MG_EINVAL, "borrowed actions must be device memory");
+  if ((reinterpret_cast<uintptr_t>(a) & 15) != 0)
+    return fail(MG_EINVAL, "borrowed actions must be 16-byte aligned");
+  if (s->proc || s->n_seg != n_seg || s->hold != hold_steps || s->act_src != a) s->drop_graphs();
+  s->act_src = a;
   s->proc = 0;
   s->n_seg = n_seg;
   s->hold = hold_steps;

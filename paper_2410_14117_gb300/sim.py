@@ -136,6 +136,19 @@ class Sim:
         _check(actions, actions.shape, torch.float32)
         call("mg_set_actions", self._h, _ptr(actions), int(actions.shape[0]), int(hold_steps))
 
+    def set_actions_borrowed(self, actions, hold_steps: int = 1):
+        """Read ``actions`` (float32 device tensor [n_seg, n_envs, 8]) in place, without a copy;
+        keep it alive and unchanged until the steps using it have run (mg_set_actions_borrowed).
+        """
+        if not (isinstance(actions, torch.Tensor) and actions.is_cuda):
+            raise ValueError("borrowed actions must be a CUDA tensor")
+        if actions.ndim != 3 or actions.shape[1:] != (self.n, MG_MAX_THR):
+            raise ValueError(f"actions must be [n_seg, {self.n}, {MG_MAX_THR}]")
+        _check(actions, actions.shape, torch.float32)
+        self._borrowed = actions  # keeps the storage alive while the sim may read it
+        call("mg_set_actions_borrowed", self._h, _ptr(actions), int(actions.shape[0]),
+             int(hold_steps))
+
     def set_procedural_actions(self, cmd_seed: int, hold_steps: int):
         call("mg_set_procedural_actions", self._h, ctypes.c_uint64(cmd_seed), int(hold_steps))
 

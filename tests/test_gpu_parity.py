@@ -240,6 +240,31 @@ def test_schedule_and_launch_shape_do_not_change_results(general):
         np.testing.assert_array_equal(o, out[0])
 
 
+def test_borrowed_actions_equal_copied_actions():
+    vs = vehicles()
+    n = 2000
+    types = I.mixed_fleet(8, n, max_group=300)
+    cmds = torch.tensor(I.commands(9, 30, n, [vs[t].n_thr for t in types]), device="cuda")
+    out = []
+    for borrowed in (False, True):
+        sim = make_sim(types, vs, spl=25, queue=borrowed)
+        sim.randomize(3, 0.8, 1.2, 0.2, 0.3)
+        sim.reset()
+        if borrowed:
+            sim.set_actions_borrowed(cmds, 10)
+        else:
+            sim.set_actions(cmds, 10)
+        sim.step(170)
+        sim.step(130)
+        out.append(gpu_state(sim))
+        sim.close()
+    np.testing.assert_array_equal(out[0], out[1])
+    sim = make_sim(types, vs)
+    with pytest.raises(MGError):
+        sim.set_actions_borrowed(cmds.cpu(), 10)
+    sim.close()
+
+
 def test_procedural_commands_match_oracle():
     vs = vehicles()
     n = 512

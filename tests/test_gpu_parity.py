@@ -260,7 +260,7 @@ def test_borrowed_actions_equal_copied_actions():
         sim.close()
     np.testing.assert_array_equal(out[0], out[1])
     sim = make_sim(types, vs)
-    with pytest.raises(MGError):
+    with pytest.raises((ValueError, MGError)):
         sim.set_actions_borrowed(cmds.cpu(), 10)
     sim.close()
 

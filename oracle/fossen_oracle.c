@@ -463,3 +463,75 @@ void orc_commands(uint64_t cmd_seed, int64_t gid, uint32_t seg, int32_t n_thr,
   draw(cmd_seed, (uint64_t)gid, 3u, 2u * seg + 1u, u + 4);
   for (int i = 0; i < ORC_MAXTHR; ++i) c[i] = (i < n_thr) ? 2.0 * u[i] - 1.0 : 0.0;
 }
+
+/* ------------------------------------------------------------------ task layer (§EXPERIMENTS)
+ * Four tasks: 0 station-keeping at a target point, 1 circle, 2 helix, 3 lemniscate tracking.
+ * Readings (the paper names the tasks and gives Eq. 2 and Eq. 4, but no trajectory parameters):
+ *   - every reference lies in NED around the env's centre c = (cx, cy, cz) with phase phi0:
+ *       circle      p_r(t) = c + (R cos(w t + phi0), R sin(w t + phi0), 0)
+ *       helix       p_r(t) = c + (R cos(w t + phi0), R sin(w t + phi0), vz t)
+ *       lemniscate  p_r(t) = c + R (cos s, sin s cos s, 0) / (1 + sin^2 s),  s = w t + phi0
+ *       station     p_r(t) = c
+ *   - the attitude reference is level with heading psi_r, so the attitude error is
+ *     (phi, theta, wrap(psi - psi_r)) from the zyx Euler angles of q;
+ *   - Eq. 2: station keeping observes {eta^e, nu}; tracking observes the errors to the next m
+ *     reference points p_r(t + i dt_look), i = 1..m, and nu; eta^e = (p - p_r, attitude error);
+ *   - Eq. 4: the position error is |p - p_r(t)|; for tracking tasks the sum over the episode's
+ *     evaluation points (one per task step) is accumulated. */
+static double wrap_pi(double a) {
+  const double two_pi = 6.283185307179586476925286766559;
+  a = fmod(a + 3.14159265358979323846, two_pi);
+  if (a < 0) a += two_pi;
+  return a - 3.14159265358979323846;
+}
+
+void orc_euler_zyx(const double q[4], double e[3]) {
+  const double w = q[0], x = q[1], y = q[2], z = q[3];
+  double sp = 2.0 * (w * y - z * x);
+  if (sp > 1.0) sp = 1.0;
+  if (sp < -1.0) sp = -1.0;
+  e[0] = atan2(2.0 * (w * x + y * z), 1.0 - 2.0 * (x * x + y * y));
+  e[1] = asin(sp);
+  e[2] = atan2(2.0 * (w * z + x * y), 1.0 - 2.0 * (y * y + z * z));
+}
+
+void orc_task_reference(int32_t task, const double *c /*cx cy cz phi0*/, double radius,
+                        double omega, double vz, double t, double p[3]) {
+  const double s = omega * t + c[3];
+  p[0] = c[0];
+  p[1] = c[1];
+  p[2] = c[2];
+  if (task == 1 || task == 2) {
+    p[0] += radius * cos(s);
+    p[1] += radius * sin(s);
+    if (task == 2) p[2] += vz * t;
+  } else if (task == 3) {
+    const double d = 1.0 + sin(s) * sin(s);
+    p[0] += radius * cos(s) / d;
+    p[1] += radius * sin(s) * cos(s) / d;
+  }
+}
+
+/* Observation (Eq. 2) and position error (Eq. 4) of one env at task time t.  obs receives
+ * 6 m + 6 values (m = 1 for station keeping): for i = 1..m the position error p - p_r(t + i dt)
+ * and the attitude error, then nu.  Returns |p - p_r(t)|. */
+double orc_task_observe(int32_t task, const double *s, const double *c, double radius,
+                        double omega, double vz, double psi_r, int32_t m, double dt_look,
+                        double t, double *obs) {
+  double e[3], pr[3];
+  orc_euler_zyx(s + S_Q, e);
+  const double att[3] = {e[0], e[1], wrap_pi(e[2] - psi_r)};
+  const int32_t mm = task == 0 ? 1 : m;
+  for (int32_t i = 0; i < mm; ++i) {
+    orc_task_reference(task, c, radius, omega, vz, task == 0 ? t : t + (i + 1) * dt_look, pr);
+    for (int k = 0; k < 3; ++k) {
+      obs[6 * i + k] = s[S_P + k] - pr[k];
+      obs[6 * i + 3 + k] = att[k];
+    }
+  }
+  for (int k = 0; k < 6; ++k) obs[6 * mm + k] = s[S_NU + k];
+  orc_task_reference(task, c, radius, omega, vz, t, pr);
+  double d2 = 0.0;
+  for (int k = 0; k < 3; ++k) d2 += (s[S_P + k] - pr[k]) * (s[S_P + k] - pr[k]);
+  return sqrt(d2);
+}

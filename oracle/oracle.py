@@ -77,6 +77,13 @@ def lib():
                                           ctypes.c_uint32, _D]
             L.orc_commands.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint32,
                                        ctypes.c_int32, _D]
+            L.orc_euler_zyx.argtypes = [_D, _D]
+            L.orc_task_reference.argtypes = [ctypes.c_int32, _D, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_double, _D]
+            L.orc_task_observe.argtypes = [ctypes.c_int32, _D, _D, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_int32, ctypes.c_double, ctypes.c_double, _D]
+            L.orc_task_observe.restype = ctypes.c_double
             _lib = L
     return _lib
 
@@ -228,3 +235,29 @@ def commands(cmd_seed: int, gid: int, seg: int, n_thr: int) -> np.ndarray:
     c = np.zeros(MAX_THR)
     lib().orc_commands(cmd_seed, gid, seg, n_thr, _p(c))
     return c
+
+
+# ------------------------------------------------------------------ task layer (§EXPERIMENTS)
+
+TASK_STATION, TASK_CIRCLE, TASK_HELIX, TASK_LEMNISCATE = 0, 1, 2, 3
+
+
+def euler_zyx(q) -> np.ndarray:
+    e = np.zeros(3)
+    lib().orc_euler_zyx(_p(_f64(q, (4,))), _p(e))
+    return e
+
+
+def task_reference(task: int, centre, radius: float, omega: float, vz: float, t: float):
+    p = np.zeros(3)
+    lib().orc_task_reference(task, _p(_f64(centre, (4,))), radius, omega, vz, t, _p(p))
+    return p
+
+
+def task_observe(task: int, s, centre, radius, omega, vz, psi_r, m, dt_look, t):
+    """(obs [6 m' + 6], position error) of one env (Eq. 2, Eq. 4); m' = 1 for station keeping."""
+    mm = 1 if task == TASK_STATION else m
+    obs = np.zeros(6 * mm + 6)
+    err = lib().orc_task_observe(task, _p(_f64(s, (NSTATE,))), _p(_f64(centre, (4,))), radius,
+                                 omega, vz, psi_r, m, dt_look, t, _p(obs))
+    return obs, err

@@ -590,3 +590,51 @@ def test_procedural_commands_uniform():
     assert c.min() > -1 and c.max() < 1 and abs(c.mean()) < 0.03
     c6 = O.commands(11, 3, 2, 6)
     assert np.all(c6[6:] == 0) and np.all(c6[:6] == O.commands(11, 3, 2, 8)[:6])
+
+
+# ----------------------------------------------------------------------------- task layer
+
+def test_euler_angles_invert_quaternion():
+    g = np.random.default_rng(21)
+    for _ in range(100):
+        phi, theta, psi = g.uniform(-3.1, 3.1), g.uniform(-1.5, 1.5), g.uniform(-3.1, 3.1)
+        np.testing.assert_allclose(O.euler_zyx(quat_from_euler(phi, theta, psi)),
+                                   [phi, theta, psi], atol=1e-12)
+
+
+def test_task_references_lie_on_their_curves():
+    c = np.array([1.0, -2.0, 3.0, 0.7])
+    R, w, vz = 2.5, 0.4, 0.15
+    for t in np.linspace(0.0, 40.0, 97):
+        p = O.task_reference(O.TASK_CIRCLE, c, R, w, vz, t)
+        assert abs(np.hypot(p[0] - c[0], p[1] - c[1]) - R) < 1e-12 and p[2] == c[2]
+        h = O.task_reference(O.TASK_HELIX, c, R, w, vz, t)
+        np.testing.assert_allclose(h[:2], p[:2], atol=1e-15)
+        assert abs(h[2] - (c[2] + vz * t)) < 1e-12
+        x, y, z = O.task_reference(O.TASK_LEMNISCATE, c, R, w, vz, t) - c[:3]
+        assert abs((x * x + y * y) ** 2 - R * R * (x * x - y * y)) < 1e-12 and z == 0
+        np.testing.assert_array_equal(O.task_reference(O.TASK_STATION, c, R, w, vz, t), c[:3])
+    # periodic with period 2 pi / w
+    T = 2 * math.pi / w
+    for task in (O.TASK_CIRCLE, O.TASK_LEMNISCATE):
+        np.testing.assert_allclose(O.task_reference(task, c, R, w, vz, 3.0),
+                                   O.task_reference(task, c, R, w, vz, 3.0 + T), atol=1e-12)
+
+
+def test_task_observation_and_error():
+    c = np.array([1.0, 2.0, -1.0, 0.0])
+    s = state(p=(4.0, 6.0, -1.0), q=quat_from_euler(0.1, -0.2, 3.0),
+              nu=(0.1, 0.2, 0.3, 0.4, 0.5, 0.6))
+    obs, err = O.task_observe(O.TASK_STATION, s, c, 2.0, 0.5, 0.1, -3.0, 4, 0.5, 7.0)
+    assert obs.size == 12 and abs(err - 5.0) < 1e-12
+    np.testing.assert_allclose(obs[:3], [3.0, 4.0, 0.0])
+    # heading error wrapped into (-pi, pi]: 3.0 - (-3.0) = 6.0 -> 6.0 - 2 pi
+    np.testing.assert_allclose(obs[3:6], [0.1, -0.2, 6.0 - 2 * math.pi], atol=1e-12)
+    np.testing.assert_allclose(obs[6:], [0.1, 0.2, 0.3, 0.4, 0.5, 0.6])
+    obs, err = O.task_observe(O.TASK_CIRCLE, s, c, 2.0, 0.5, 0.1, 0.0, 4, 0.5, 7.0)
+    assert obs.size == 30
+    for i in range(4):
+        pr = O.task_reference(O.TASK_CIRCLE, c, 2.0, 0.5, 0.1, 7.0 + (i + 1) * 0.5)
+        np.testing.assert_allclose(obs[6 * i:6 * i + 3], s[:3] - pr, atol=1e-12)
+    assert abs(err - np.linalg.norm(s[:3] - O.task_reference(O.TASK_CIRCLE, c, 2.0, 0.5, 0.1,
+                                                             7.0))) < 1e-12

@@ -178,7 +178,10 @@ mg_status mg_set_actions_borrowed(mg_sim *sim, const float *a, int32_t n_seg, in
 mg_status mg_set_procedural_actions(mg_sim *sim, uint64_t cmd_seed, int32_t hold_steps);
 
 /* Advance every env k >= 1 sub-steps (Eq. 1 integrated by RK4, §METHOD).  Asynchronous on the
- * stream; non-finite states are reported by mg_sync. */
+ * stream; non-finite states are reported by mg_sync.  The action cursor is a word in the sim's
+ * device memory: each step launch reads it when it starts and its last block advances it, so the
+ * CUDA graph cached for a given k replays correctly at any cursor (one graph per distinct k, at
+ * most 16 kept).  Steps of one sim must therefore stay ordered on its stream. */
 mg_status mg_step(mg_sim *sim, int32_t k);
 
 /* As mg_step with the work-queue schedule, for callers that must not allocate device memory
@@ -231,8 +234,8 @@ mg_status mg_set_state(mg_sim *sim, const float *in);
 
 /* Start a new episode for every env whose mask byte is non-zero (mask: host or device
  * [n_envs]; NULL = all): p = 0, q = identity, n = 0, nu ~ N(0, nu0_sigma) drawn from Philox
- * keyed by (seed, env id + offset, the env's episode counter), then the counter is
- * incremented and the env's non-finite flag cleared. */
+ * keyed by (seed, env id + offset, the env's episode counter; Box-Muller evaluated in FP32),
+ * then the counter is incremented and the env's non-finite flag cleared. */
 mg_status mg_reset(mg_sim *sim, const uint8_t *mask);
 
 /* Wait for the stream; *nonfinite_count (may be NULL) receives how many envs are flagged
@@ -243,6 +246,51 @@ mg_status mg_sync(mg_sim *sim, int64_t *nonfinite_count);
 
 /* Per-env non-finite flags into out [n_envs] (host or device), 1 = flagged. */
 mg_status mg_get_nonfinite(mg_sim *sim, uint8_t *out);
+
+/* ------------------------------------------------------------------------------------------
+ * Task layer (§EXPERIMENTS): the four tasks of the paper's experiments on top of the step.  Each
+ * env tracks a reference around its own centre c (NED) with phase phi0, s = omega t + phi0:
+ *   MG_TASK_STATION     p_r = c                                   (station keeping)
+ *   MG_TASK_CIRCLE      p_r = c + (R cos s, R sin s, 0)
+ *   MG_TASK_HELIX       p_r = c + (R cos s, R sin s, vz t)
+ *   MG_TASK_LEMNISCATE  p_r = c + R (cos s, sin s cos s, 0) / (1 + sin^2 s)
+ * with a level attitude reference of heading psi_r.  Observation (Eq. 2), per env, obs_dim =
+ * 6 m + 6 floats: for i = 1..m the position error p - p_r(t + i lookahead_dt) and the attitude
+ * error (roll, pitch, heading - psi_r wrapped to [-pi, pi), zyx Euler angles of q), then nu; m =
+ * 1 and p_r(t) for station keeping.  Position error (Eq. 4): |p - p_r(t)|, summed over an
+ * episode's task steps.  t counts sub-steps since the env's episode started (times dt).
+ * ------------------------------------------------------------------------------------------ */
+#define MG_TASK_STATION 0
+#define MG_TASK_CIRCLE 1
+#define MG_TASK_HELIX 2
+#define MG_TASK_LEMNISCATE 3
+
+typedef struct {
+  int32_t task;           /* MG_TASK_* */
+  int32_t lookahead;      /* m >= 1 reference points observed (tracking tasks) */
+  float radius, omega, vz, psi_r, lookahead_dt;
+  float max_error;        /* an episode ends when |p - p_r| exceeds it (<= 0: never) */
+  int32_t episode_steps;  /* an episode ends after this many sub-steps (<= 0: never) */
+  uint32_t flags;         /* must be 0 */
+} mg_task_spec;
+
+/* Set the task; centres: host or device [n_envs][4] = (cx, cy, cz, phi0).  Every env's episode
+ * clock and error sum restart at 0 (the state is not touched).  Errors: MG_EINVAL (NULL, unknown
+ * task, lookahead < 1 or > 64, flags != 0), MG_ENOMEM. */
+mg_status mg_set_task(mg_sim *sim, const mg_task_spec *spec, const float *centres);
+
+/* Observation length 6 m + 6 of the current task (MG_ESTATE if no task is set). */
+mg_status mg_task_obs_dim(mg_sim *sim, int32_t *obs_dim);
+
+/* One task step: k >= 1 sub-steps (as mg_step), then for every env: err = |p - p_r(t)|, the
+ * episode's clock and error sum advance, and an env whose episode ended (error above max_error,
+ * episode_steps reached, or a non-finite state) gets done = 1, episode_err = its error sum
+ * (including this step), and an automatic reset (as mg_reset); obs is then the new episode's
+ * first observation.  k = 0 only observes (no step, no clock, no reset).  obs: device
+ * [n][obs_dim]; err: device [n]; done: device [n]; episode_err: device [n] or NULL (0 for envs
+ * that did not finish).  Asynchronous.  Errors: MG_ESTATE (no task), MG_EINVAL. */
+mg_status mg_task_step(mg_sim *sim, int32_t k, float *obs, float *err, uint8_t *done,
+                       float *episode_err);
 
 /* ------------------------------------------------------------------------------------------
  * Serving: a job pool with continuous batching.  A pool holds an arena of capacity_envs envs; a

@@ -16,6 +16,7 @@ MG_NTRAJ = 13
 MG_MAX_THR = 8
 MG_MAX_TYPES = 8
 MG_MODEL_NO_CURRENT_ACCEL = 1
+MG_TASK_STATION, MG_TASK_CIRCLE, MG_TASK_HELIX, MG_TASK_LEMNISCATE = 0, 1, 2, 3
 
 STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ECUDA", 4: "MG_ENONFINITE",
           5: "MG_ENOTSPD", 6: "MG_ETIMEOUT", 7: "MG_ESTATE"}
@@ -41,6 +42,14 @@ class VehicleParams(ctypes.Structure):
 class Ranges(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_float), ("hi", ctypes.c_float),
                 ("current_sigma", ctypes.c_float), ("nu0_sigma", ctypes.c_float),
+                ("flags", ctypes.c_uint32)]
+
+
+class TaskSpec(ctypes.Structure):
+    _fields_ = [("task", ctypes.c_int32), ("lookahead", ctypes.c_int32),
+                ("radius", ctypes.c_float), ("omega", ctypes.c_float), ("vz", ctypes.c_float),
+                ("psi_r", ctypes.c_float), ("lookahead_dt", ctypes.c_float),
+                ("max_error", ctypes.c_float), ("episode_steps", ctypes.c_int32),
                 ("flags", ctypes.c_uint32)]
 
 
@@ -83,6 +92,9 @@ SIGNATURES = {
     "mg_get_nonfinite": [_P, _P],
     "mg_philox4x32_10": [_P, _P, _P, _I64],
     "mg_kernel_info": [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)],
+    "mg_set_task": [_P, ctypes.POINTER(TaskSpec), _P],
+    "mg_task_obs_dim": [_P, ctypes.POINTER(_I32)],
+    "mg_task_step": [_P, _I32, _P, _P, _P, _P],
     "mg_pool_create": [_I64, ctypes.POINTER(VehicleParams), _I32, ctypes.POINTER(_P)],
     "mg_pool_destroy": [_P],
     "mg_pool_set_stream": [_P, _P],

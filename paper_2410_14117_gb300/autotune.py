@@ -52,11 +52,17 @@ def _signature(types: np.ndarray, vehicles, general: bool) -> str:
 
 class Autotuner:
     def __init__(self, cache_path: str | None = None, candidates=DEFAULT_CANDIDATES,
-                 horizon: int = 300, reps: int = 3):
+                 horizon: int = 300, reps: int = 3, k_per_call: int | None = None):
+        """``horizon`` sub-steps are timed per repetition, as one ``step(horizon)`` call, or as
+        ``horizon // k_per_call`` calls of ``step(k_per_call)`` when the caller steps in small
+        pieces (a policy loop): the best launch shape differs between the two."""
         self.cache_path = cache_path
         self.candidates = list(candidates)
         self.horizon = horizon
         self.reps = reps
+        self.k_per_call = k_per_call if k_per_call else horizon
+        if not 1 <= self.k_per_call <= horizon:
+            raise ValueError("need 1 <= k_per_call <= horizon")
         self.cache = {}
         if cache_path and os.path.exists(cache_path):
             with open(cache_path) as f:
@@ -64,7 +70,8 @@ class Autotuner:
 
     def key(self, n_envs: int, types, vehicles, general: bool = False) -> str:
         dev = torch.cuda.get_device_name()
-        return f"{dev}|{n_envs}|{_signature(np.asarray(types, dtype=np.int32), vehicles, general)}"
+        sig = _signature(np.asarray(types, dtype=np.int32), vehicles, general)
+        return f"{dev}|{n_envs}|{sig}|k{self.k_per_call}"
 
     def measure(self, n_envs: int, types, vehicles, general: bool = False):
         """Time every candidate; returns [(config, env-steps/s)] sorted fastest first."""
@@ -80,17 +87,18 @@ class Autotuner:
             sim.set_procedural_actions(11, 10)
             out = []
             start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            calls = self.horizon // self.k_per_call
             for cfg in self.candidates:
                 cfg.apply(sim)
-                sim.step(self.horizon)  # warm-up (and graph capture)
+                sim.step(self.k_per_call)  # warm-up (and graph capture)
                 torch.cuda.synchronize()
                 start.record(sim.stream)
-                for _ in range(self.reps):
-                    sim.step(self.horizon)
+                for _ in range(self.reps * calls):
+                    sim.step(self.k_per_call)
                 end.record(sim.stream)
                 torch.cuda.synchronize()
                 ms = start.elapsed_time(end) / self.reps
-                out.append((cfg, n_envs * self.horizon / (ms / 1e3)))
+                out.append((cfg, n_envs * calls * self.k_per_call / (ms / 1e3)))
             sim.sync()
         finally:
             sim.close()

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libmg.so")
 
-SOURCES = ["mg_api.cu", "mg_step.cu", "mg_setup.cu", "mg_adjoint.cu", "mg_pool.cu"]
+SOURCES = ["mg_api.cu", "mg_step.cu", "mg_setup.cu", "mg_adjoint.cu", "mg_pool.cu", "mg_task.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-I" + INCLUDE, "-I" + CSRC]

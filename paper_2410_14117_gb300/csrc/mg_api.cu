@@ -71,7 +71,6 @@ bool is_device_ptr(const void *p) {
 
 struct GraphEntry {
   int32_t k;
-  int64_t cursor;
   cudaGraphExec_t exec;
   uint64_t last_use;
 };
@@ -101,7 +100,8 @@ struct mg_sim {
   uint32_t *flags = nullptr;
   uint32_t *episode = nullptr;
   unsigned long long *counters = nullptr;  // [0] non-finite envs, [1] non-SPD envs,
-                                           // [2] work-queue wait time-outs
+                                           // [2] work-queue wait time-outs, [3] action
+                                           // cursor, [4] finished-block count
   unsigned int *offdiag = nullptr;
 
   // static-schedule blocks
@@ -124,7 +124,7 @@ struct mg_sim {
   int32_t n_seg = 0, hold = 1;
   int32_t proc = 0;
   uint64_t cmd_seed = 0;
-  int64_t cursor = 0;
+  int64_t cursor = 0;  // host copy of the device cursor (counters[3])
 
   // knobs
   int32_t epb = 128, spl = 50;
@@ -138,6 +138,28 @@ struct mg_sim {
   // staging for host I/O
   void *stage = nullptr;
   size_t stage_cap = 0;
+
+  // task layer
+  bool has_task = false;
+  mg_task_spec task{};
+  void *task_buf = nullptr;  // centre [n] float4, clock [n] int32, err_sum [n] float
+  TaskView task_view() const {
+    TaskView v{};
+    v.task = task.task;
+    v.m = task.lookahead;
+    v.radius = task.radius;
+    v.omega = task.omega;
+    v.vz = task.vz;
+    v.psi_r = task.psi_r;
+    v.dt_look = task.lookahead_dt;
+    v.max_err = task.max_error;
+    v.episode_steps = task.episode_steps > 0 ? task.episode_steps : 0;
+    char *b = static_cast<char *>(task_buf);
+    v.centre = reinterpret_cast<const float4 *>(b);
+    v.clock = reinterpret_cast<int32_t *>(b + 16 * n);
+    v.err_sum = reinterpret_cast<float *>(b + 20 * n);
+    return v;
+  }
 
   std::vector<GraphEntry> graphs;
   uint64_t graph_clock = 0;
@@ -159,6 +181,8 @@ struct mg_sim {
     v.dt = dt;
     v.flags = flags;
     v.counters = counters;
+    v.cursor = reinterpret_cast<int64_t *>(counters + 3);
+    v.done_blocks = reinterpret_cast<unsigned int *>(counters + 4);
     return v;
   }
 
@@ -248,15 +272,15 @@ mg_status launch_chunks(mg_sim *s, int32_t k, float *traj, cudaStream_t stream) 
   const FleetView v = s->view();
   if (s->queue && !traj) {
     MG_CK(launch_fleet_queue(v, s->slices_d, s->n_slices, s->ntv, s->diag, s->structured,
-                             s->queue_wide, s->queue_warps_per_sm, s->cursor, k, s->spl,
-                             s->sched, s->n_sm, stream));
+                             s->queue_wide, s->queue_warps_per_sm, k, s->spl, s->sched, s->n_sm,
+                             stream));
     return MG_OK;
   }
   for (int32_t done = 0; done < k;) {
     const int32_t kk = std::min(s->spl, k - done);
     float *t = traj ? traj + (int64_t)done * MG_NTRAJ * s->n : nullptr;
     MG_CK(launch_fleet(v, s->blocks_d, s->n_blocks, s->threads, s->ntv, s->diag, s->structured,
-                       s->cursor + done, kk, t, stream));
+                       kk, t, stream));
     done += kk;
   }
   return MG_OK;
@@ -284,6 +308,13 @@ mg_status finish_params(mg_sim *s) {
     snprintf(buf, sizeof buf, "%llu envs have a mass matrix that is not positive definite", bad);
     return fail(MG_ENOTSPD, buf);
   }
+  return MG_OK;
+}
+
+// Rewind the action cursor (host copy and the device word the step kernels read).
+mg_status rewind_cursor(mg_sim *s) {
+  s->cursor = 0;
+  MG_CK(cudaMemsetAsync(s->counters + 3, 0, sizeof(unsigned long long), s->stream));
   return MG_OK;
 }
 
@@ -344,8 +375,8 @@ mg_status mg_step_noalloc(mg_sim *s, int32_t k) {
   mg_status st = noalloc_scratch(&sched);
   if (st != MG_OK) return st;
   MG_CK(launch_fleet_queue(s->view(), s->slices_d, s->n_slices, s->ntv, s->diag, s->structured,
-                           s->queue_wide, s->queue_warps_per_sm, s->cursor, k, s->spl, sched,
-                           s->n_sm, s->stream));
+                           s->queue_wide, s->queue_warps_per_sm, k, s->spl, sched, s->n_sm,
+                           s->stream));
   s->cursor += k;
   return MG_OK;
 }
@@ -412,7 +443,7 @@ mg_status mg_create(int64_t n_envs, const int32_t *vehicle_types,
   s->n_slices = (int)slices.size();
   const size_t o_slices = take(sizeof(BlockDesc) * slices.size());
   const size_t o_sched = take(queue_sched_bytes(s->n_slices));
-  const size_t o_cnt = take(3 * sizeof(unsigned long long));
+  const size_t o_cnt = take(5 * sizeof(unsigned long long));
   const size_t o_off = take(sizeof(unsigned int));
   cudaError_t e = cudaMalloc(&s->arena, off);
   if (e != cudaSuccess) {
@@ -499,7 +530,7 @@ mg_status mg_create(int64_t n_envs, const int32_t *vehicle_types,
   MG_CKB(cudaMemcpy(s->types_d, s->types_h.data(), 4 * n, cudaMemcpyHostToDevice));
   MG_CKB(cudaMemset(s->flags, 0, 4 * n));
   MG_CKB(cudaMemset(s->episode, 0, 4 * n));
-  MG_CKB(cudaMemset(s->counters, 0, 3 * sizeof(unsigned long long)));
+  MG_CKB(cudaMemset(s->counters, 0, 5 * sizeof(unsigned long long)));
   MG_CKB(cudaMemcpy(s->slices_d, slices.data(), sizeof(BlockDesc) * slices.size(),
                     cudaMemcpyHostToDevice));
   MG_CKB(cudaMemset(s->offdiag, 0, sizeof(unsigned int)));
@@ -525,6 +556,7 @@ mg_status mg_destroy(mg_sim *s) {
   s->drop_graphs();
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   cudaFree(s->blocks_d);
+  cudaFree(s->task_buf);
   cudaFree(s->act);
   cudaFree(s->stage);
   cudaFree(s->arena);
@@ -657,8 +689,7 @@ mg_status mg_set_actions(mg_sim *s, const float *a, int32_t n_seg, int32_t hold_
   s->proc = 0;
   s->n_seg = n_seg;
   s->hold = hold_steps;
-  s->cursor = 0;
-  return MG_OK;
+  return rewind_cursor(s);
 }
 
 mg_status mg_set_actions_borrowed(mg_sim *s, const float *a, int32_t n_seg, int32_t hold_steps) {
@@ -673,8 +704,7 @@ mg_status mg_set_actions_borrowed(mg_sim *s, const float *a, int32_t n_seg, int3
   s->proc = 0;
   s->n_seg = n_seg;
   s->hold = hold_steps;
-  s->cursor = 0;
-  return MG_OK;
+  return rewind_cursor(s);
 }
 
 mg_status mg_set_procedural_actions(mg_sim *s, uint64_t cmd_seed, int32_t hold_steps) {
@@ -685,8 +715,7 @@ mg_status mg_set_procedural_actions(mg_sim *s, uint64_t cmd_seed, int32_t hold_s
   s->cmd_seed = cmd_seed;
   s->hold = hold_steps;
   s->n_seg = 0;
-  s->cursor = 0;
-  return MG_OK;
+  return rewind_cursor(s);
 }
 
 mg_status mg_step(mg_sim *s, int32_t k) {
@@ -700,7 +729,7 @@ mg_status mg_step(mg_sim *s, int32_t k) {
   }
   GraphEntry *hit = nullptr;
   for (auto &g : s->graphs)
-    if (g.k == k && g.cursor == s->cursor) hit = &g;
+    if (g.k == k) hit = &g;
   if (!hit) {
     if (s->graphs.size() >= 16) {
       auto lru = std::min_element(s->graphs.begin(), s->graphs.end(),
@@ -719,7 +748,7 @@ mg_status mg_step(mg_sim *s, int32_t k) {
       return st;
     }
     MG_CK(ce);
-    GraphEntry g{k, s->cursor, nullptr, 0};
+    GraphEntry g{k, nullptr, 0};
     ce = cudaGraphInstantiate(&g.exec, graph, 0);
     cudaGraphDestroy(graph);
     MG_CK(ce);
@@ -759,7 +788,7 @@ mg_status mg_rollout_forward(mg_sim *s, int32_t T, int32_t C, float *traj, float
     MG_CK(launch_checkpoint(s->st, s->n, ckpt + (int64_t)(t0 / C) * MG_NSTATE * s->n,
                             s->stream));
     MG_CK(launch_fleet(v, s->blocks_d, s->n_blocks, s->threads, s->ntv, s->diag, s->structured,
-                       step0 + t0, len, traj + (int64_t)t0 * MG_NTRAJ * s->n, s->stream));
+                       len, traj + (int64_t)t0 * MG_NTRAJ * s->n, s->stream));
   }
   s->cursor += T;
   if (step0_out) *step0_out = step0;
@@ -783,6 +812,55 @@ mg_status mg_rollout_backward(mg_sim *s, int32_t T, int32_t C, const float *ckpt
     return fail(MG_EINVAL, "adjoint buffers must be device memory");
   MG_CK(launch_adjoint(s->view(), s->types_d, s->ntv != NT_6, ckpt, dtraj, T, C, step0, dcoef,
                        dact, dstate0, s->stream));
+  return MG_OK;
+}
+
+mg_status mg_set_task(mg_sim *s, const mg_task_spec *spec, const float *centres) {
+  MG_NONNULL(s);
+  MG_NONNULL(spec);
+  MG_NONNULL(centres);
+  if (spec->task < MG_TASK_STATION || spec->task > MG_TASK_LEMNISCATE || spec->lookahead < 1 ||
+      spec->lookahead > 64 || spec->flags != 0)
+    return fail(MG_EINVAL, "task spec: unknown task, lookahead outside [1, 64] or flags != 0");
+  if (!s->task_buf) MG_CK(cudaMalloc(&s->task_buf, 24 * (size_t)s->n));
+  const void *d = nullptr;
+  mg_status st = input_ptr(s, centres, 16 * (size_t)s->n, &d);
+  if (st != MG_OK) return st;
+  MG_CK(cudaMemcpyAsync(s->task_buf, d, 16 * (size_t)s->n, cudaMemcpyDeviceToDevice, s->stream));
+  MG_CK(cudaMemsetAsync(static_cast<char *>(s->task_buf) + 16 * s->n, 0, 8 * (size_t)s->n,
+                        s->stream));
+  MG_CK(cudaStreamSynchronize(s->stream));
+  s->task = *spec;
+  s->has_task = true;
+  return MG_OK;
+}
+
+mg_status mg_task_obs_dim(mg_sim *s, int32_t *obs_dim) {
+  MG_NONNULL(s);
+  MG_NONNULL(obs_dim);
+  if (!s->has_task) return fail(MG_ESTATE, "no task set");
+  *obs_dim = 6 * (s->task.task == MG_TASK_STATION ? 1 : s->task.lookahead) + 6;
+  return MG_OK;
+}
+
+mg_status mg_task_step(mg_sim *s, int32_t k, float *obs, float *err, uint8_t *done,
+                       float *episode_err) {
+  MG_NONNULL(s);
+  MG_NONNULL(obs);
+  MG_NONNULL(err);
+  MG_NONNULL(done);
+  if (!s->has_task) return fail(MG_ESTATE, "no task set");
+  if (k < 0) return fail(MG_EINVAL, "k must be >= 0");
+  for (const void *p : {(const void *)obs, (const void *)err, (const void *)done})
+    if (!is_device_ptr(p)) return fail(MG_EINVAL, "task outputs must be device memory");
+  if (episode_err && !is_device_ptr(episode_err))
+    return fail(MG_EINVAL, "task outputs must be device memory");
+  if (k > 0) {
+    mg_status st = mg_step(s, k);
+    if (st != MG_OK) return st;
+  }
+  MG_CK(launch_task(s->st, s->task_view(), s->n, s->gid0, k, s->dt, obs, err, done, episode_err,
+                    s->reset_seed, s->nu0_sigma, s->episode, s->flags, s->counters, s->stream));
   return MG_OK;
 }
 

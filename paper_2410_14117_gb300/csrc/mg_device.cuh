@@ -70,6 +70,54 @@ __device__ __forceinline__ void procedural_commands(uint64_t seed, uint64_t gid,
   }
 }
 
+// Box-Muller pair from two open-interval uniforms (FP64).
+__device__ __forceinline__ void box_muller(double u1, double u2, double &z0, double &z1) {
+  const double r = sqrt(-2.0 * log(u1));
+  double s, c;
+  sincospi(2.0 * u2, &s, &c);
+  z0 = r * c;
+  z1 = r * s;
+}
+
+// Box-Muller in FP32, for the episode-start draws: the same uniforms (exact in FP32) and the
+// same formula, each result within a few ulp of the FP64 form.  Resets run inside step-time
+// kernels (auto-reset), where a warp with one resetting env would otherwise pay GB300's
+// reduced-rate FP64 transcendentals for all 32 lanes.
+__device__ __forceinline__ void box_muller_f(float u1, float u2, float &z0, float &z1) {
+  const float r = sqrtf(-2.f * logf(u1));
+  float s, c;
+  sincospif(2.f * u2, &s, &c);
+  z0 = r * c;
+  z1 = r * s;
+}
+
+// New episode for env e (episode reset, §METHOD randomisation of the start): p = 0, q =
+// identity, n = 0, nu = sigma N(0,1)^6 from stream 2 of env id gid at the env's episode counter
+// (blocks 2 ep, 2 ep + 1); the counter is incremented and the non-finite flag cleared.
+__device__ __forceinline__ void reset_env(const StatePlanes &st, int64_t e, uint64_t gid,
+                                          uint64_t seed, double sigma, uint32_t *episode,
+                                          uint32_t *flags, unsigned long long *nonfinite_count) {
+  const uint32_t ep = episode[e];
+  const uint4 a = draw4(seed, gid, STREAM_RESET, 2u * ep);
+  const uint4 b = draw4(seed, gid, STREAM_RESET, 2u * ep + 1u);
+  float z[6];
+  box_muller_f(u01f(a.x), u01f(a.y), z[0], z[1]);
+  box_muller_f(u01f(a.z), u01f(a.w), z[2], z[3]);
+  box_muller_f(u01f(b.x), u01f(b.y), z[4], z[5]);
+  const float sg = (float)sigma;
+  float nu[6];
+  for (int i = 0; i < 6; ++i) nu[i] = sg * z[i];
+  st.s0[e] = make_float4(0.f, 0.f, 0.f, 1.f);
+  st.s1[e] = make_float4(0.f, 0.f, 0.f, nu[0]);
+  st.s2[e] = make_float4(nu[1], nu[2], nu[3], nu[4]);
+  st.s3[e] = make_float4(nu[5], 0.f, 0.f, 0.f);
+  st.s4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  st.s5[e] = 0.f;
+  episode[e] = ep + 1u;
+  if (flags[e] & 1u) atomicAdd(nonfinite_count, ~0ull);  // decrement
+  flags[e] = 0u;
+}
+
 // ---------------------------------------------------------------- per-env registers
 template <int MT>
 struct St {

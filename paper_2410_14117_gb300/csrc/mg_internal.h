@@ -78,6 +78,11 @@ struct FleetView {
   float dt;
   uint32_t *flags;           // [n] bit 0 = non-finite
   unsigned long long *counters;  // [0] envs flagged non-finite, [2] work-queue wait time-outs
+  // Action cursor (sub-steps since the actions were set) in device memory: every step launch
+  // reads it at start and its last block to finish advances it, so a captured launch sequence
+  // is valid whatever the cursor.  done_blocks counts finished blocks (reset by the last one).
+  int64_t *cursor;
+  unsigned int *done_blocks;
 };
 
 // Kernel variants: thruster count fixed at 6 or 8, or mixed (up to 8, read per block).
@@ -88,8 +93,8 @@ enum NtVariant { NT_6 = 0, NT_8 = 1, NT_MIXED = 2 };
 // structured: every vehicle type present has the vectored layout (thrusters 0..3 with d_z = 0,
 // the rest with d_x = d_y = 0), so the allocation skips its exact zeros (diagonal mass only).
 cudaError_t launch_fleet(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
-                         NtVariant ntv, bool diag, bool structured, int64_t step0, int32_t k,
-                         float *traj, cudaStream_t stream);
+                         NtVariant ntv, bool diag, bool structured, int32_t k, float *traj,
+                         cudaStream_t stream);
 cudaError_t fleet_kernel_attributes(NtVariant ntv, bool diag, bool structured, bool record,
                                     cudaFuncAttributes *attr);
 
@@ -103,8 +108,8 @@ size_t queue_sched_bytes(int n_slices);
 // each); warps_per_sm > 0 caps the resident warps per SM.
 cudaError_t launch_fleet_queue(const FleetView &fv, const BlockDesc *slices, int n_slices,
                                NtVariant ntv, bool diag, bool structured, bool wide,
-                               int warps_per_sm, int64_t step0, int32_t k, int32_t chunk,
-                               uint32_t *sched, int n_sm, cudaStream_t stream);
+                               int warps_per_sm, int32_t k, int32_t chunk, uint32_t *sched,
+                               int n_sm, cudaStream_t stream);
 cudaError_t queue_kernel_attributes(NtVariant ntv, bool diag, bool wide, bool structured,
                                     cudaFuncAttributes *attr, int *blocks_per_sm);
 
@@ -148,5 +153,21 @@ cudaError_t launch_adjoint(const FleetView &fv, const int32_t *types, bool eight
                            int64_t step0, float *dcoef, float *dact, float *dstate0,
                            cudaStream_t stream);
 int adjoint_max_interval();
+
+// ---------------------------------------------------------------- launchers (mg_task.cu)
+struct TaskView {
+  int32_t task, m;           // MG_TASK_*, look-ahead points
+  float radius, omega, vz, psi_r, dt_look, max_err;
+  int32_t episode_steps;     // auto-reset after this many sub-steps (0: never)
+  const float4 *centre;      // [n] (cx, cy, cz, phi0)
+  int32_t *clock;            // [n] sub-steps since the episode started
+  float *err_sum;            // [n] Eq. 4 error summed over the episode's task steps
+};
+
+cudaError_t launch_task(const StatePlanes &st, const TaskView &tv, int64_t n, int64_t gid0,
+                        int32_t k, float dt, float *obs, float *err, uint8_t *done,
+                        float *ep_err, uint64_t seed, double sigma, uint32_t *episode,
+                        uint32_t *flags, unsigned long long *nonfinite_count,
+                        cudaStream_t stream);
 
 }  // namespace mg

@@ -24,14 +24,6 @@ __constant__ int c_rand_idx[27] = {
     MG_P_DQ, MG_P_DQ + 1, MG_P_DQ + 2, MG_P_DQ + 3, MG_P_DQ + 4, MG_P_DQ + 5,
     MG_P_W, MG_P_B, MG_P_RB + 2, MG_P_KT, MG_P_TAU};
 
-__device__ __forceinline__ void box_muller(double u1, double u2, double &z0, double &z1) {
-  const double r = sqrt(-2.0 * log(u1));
-  double s, c;
-  sincospi(2.0 * u2, &s, &c);
-  z0 = r * c;
-  z1 = r * s;
-}
-
 // Derive the step's parameter planes for env e from its FP64 record p[MG_NPARAM].
 __device__ void derive(const SetupView &v, int64_t e, const double *p) {
   const double m = p[MG_P_M];
@@ -180,25 +172,7 @@ __global__ void k_reset(const StatePlanes st, int64_t n, int64_t gid0,
                         unsigned long long *nonfinite_count) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n || (mask && !mask[e])) return;
-  const uint64_t gid = (uint64_t)(gid0 + e);
-  const uint32_t ep = episode[e];
-  const uint4 a = draw4(seed, gid, STREAM_RESET, 2u * ep);
-  const uint4 b = draw4(seed, gid, STREAM_RESET, 2u * ep + 1u);
-  double z[6];
-  box_muller(u01d(a.x), u01d(a.y), z[0], z[1]);
-  box_muller(u01d(a.z), u01d(a.w), z[2], z[3]);
-  box_muller(u01d(b.x), u01d(b.y), z[4], z[5]);
-  float nu[6];
-  for (int i = 0; i < 6; ++i) nu[i] = (float)(sigma * z[i]);
-  st.s0[e] = make_float4(0.f, 0.f, 0.f, 1.f);
-  st.s1[e] = make_float4(0.f, 0.f, 0.f, nu[0]);
-  st.s2[e] = make_float4(nu[1], nu[2], nu[3], nu[4]);
-  st.s3[e] = make_float4(nu[5], 0.f, 0.f, 0.f);
-  st.s4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-  st.s5[e] = 0.f;
-  episode[e] = ep + 1u;
-  if (flags[e] & 1u) atomicAdd(nonfinite_count, ~0ull);  // decrement
-  flags[e] = 0u;
+  reset_env(st, e, (uint64_t)(gid0 + e), seed, sigma, episode, flags, nonfinite_count);
 }
 
 __global__ void k_export_state(const StatePlanes st, int64_t n, float *__restrict__ out) {

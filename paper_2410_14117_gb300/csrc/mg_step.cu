@@ -44,6 +44,45 @@ __device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Action cursor at launch start (read through L2: the previous launch's last block wrote it).
+__device__ __forceinline__ int64_t launch_cursor(const FleetView &fv) {
+  return (int64_t)__ldcg(reinterpret_cast<const unsigned long long *>(fv.cursor));
+}
+
+// Called by every thread of every block once it is done: the last block to finish advances the
+// cursor by k and re-arms the counter.  Every block read the cursor before it counted itself
+// finished, so all of them saw the launch's starting value.
+__device__ __forceinline__ void finish_launch(const FleetView &fv, int32_t k) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(fv.done_blocks, 1u);
+    if (prev == gridDim.x - 1) {
+      atomicAdd(reinterpret_cast<unsigned long long *>(fv.cursor), (unsigned long long)k);
+      atomicExch(fv.done_blocks, 0u);
+      __threadfence();
+    }
+  }
+}
+
+// k_fleet's form of finish_launch, counted in envs (one thread per env, idle threads already
+// gone): each warp adds its finished envs, and the warp that completes the fleet's count
+// advances the cursor by k and re-arms the counter.
+__device__ __forceinline__ void finish_envs(const FleetView &fv, int32_t k) {
+  const unsigned mask = __activemask();
+  __syncwarp(mask);
+  if ((threadIdx.x & 31) == (unsigned)(__ffs(mask) - 1)) {
+    const unsigned add = __popc(mask);
+    __threadfence();
+    const unsigned prev = atomicAdd(fv.done_blocks, add);
+    if ((int64_t)prev + add == fv.n) {
+      atomicAdd(reinterpret_cast<unsigned long long *>(fv.cursor), (unsigned long long)k);
+      atomicExch(fv.done_blocks, 0u);
+      __threadfence();
+    }
+  }
+}
+
 template <int MT>
 __device__ __forceinline__ void load_commands(const FleetView &fv, int64_t e, int64_t seg,
                                               int nt, float itau, float (&c)[MT]) {
@@ -135,8 +174,8 @@ __device__ __forceinline__ void advance_env(const FleetView &fv, int64_t e, int 
 
 template <int NTV, bool DIAG, bool REC, int NH>
 __global__ void __maxnreg__(DIAG ? kRegsDiag : kRegsGeneral)
-    k_fleet(const FleetView fv, const BlockDesc *__restrict__ blocks, const int64_t step0,
-            const int32_t k, float *__restrict__ traj) {
+    k_fleet(const FleetView fv, const BlockDesc *__restrict__ blocks, const int32_t k,
+            float *__restrict__ traj) {
   constexpr int MT = (NTV == NT_6) ? 6 : 8;
   constexpr bool MIXED = (NTV == NT_MIXED);
   __shared__ float4 sdir[MG_MAX_THR], sarm[MG_MAX_THR];
@@ -149,15 +188,15 @@ __global__ void __maxnreg__(DIAG ? kRegsDiag : kRegsGeneral)
   __syncthreads();
   if ((int)threadIdx.x >= bd.count) return;
   advance_env<MT, DIAG, MIXED, REC, false, NH>(fv, (int64_t)bd.env0 + threadIdx.x,
-                                               MIXED ? bd.n_thr : MT, sdir, sarm, step0, k,
-                                               traj);
+                                               MIXED ? bd.n_thr : MT, sdir, sarm,
+                                               launch_cursor(fv), k, traj);
+  finish_envs(fv, k);
 }
 
 template <int NTV, bool DIAG, bool WIDE, int NH>
 __global__ void __maxnreg__((DIAG && !WIDE) ? kRegsDiag : kRegsGeneral)
     k_fleet_queue(const FleetView fv, const BlockDesc *__restrict__ slices, const int32_t n_slices,
-                  const int64_t step0, const int32_t k_total, const int32_t chunk,
-                  uint32_t *__restrict__ sched) {
+                  const int32_t k_total, const int32_t chunk, uint32_t *__restrict__ sched) {
   constexpr int MT = (NTV == NT_6) ? 6 : 8;
   constexpr bool MIXED = (NTV == NT_MIXED);
   // Thruster geometry of every vehicle type at fixed shared addresses (a per-warp copy at a
@@ -167,6 +206,7 @@ __global__ void __maxnreg__((DIAG && !WIDE) ? kRegsDiag : kRegsGeneral)
     const int t = i / (2 * MG_MAX_THR), j = i % (2 * MG_MAX_THR);
     sgeo[t][j] = j < MG_MAX_THR ? fv.geo[t].dir[j] : fv.geo[t].arm[j - MG_MAX_THR];
   }
+  const int64_t step0 = launch_cursor(fv);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const uint32_t n_chunks = (uint32_t)((k_total + chunk - 1) / chunk);
@@ -204,39 +244,35 @@ __global__ void __maxnreg__((DIAG && !WIDE) ? kRegsDiag : kRegsGeneral)
       st_release(sched + 4 + d, (uint32_t)(c + 1));
     }
   }
+  finish_launch(fv, k_total);
 }
 
 // Structured allocation (NH = 4) is only instantiated for the diagonal-mass step.
 template <int NTV, bool DIAG, bool REC>
 cudaError_t launch_t(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
-                     bool structured, int64_t step0, int32_t k, float *traj,
-                     cudaStream_t stream) {
+                     bool structured, int32_t k, float *traj, cudaStream_t stream) {
   if (DIAG && structured)
-    k_fleet<NTV, DIAG, REC, (DIAG ? 4 : 0)><<<n_blocks, threads, 0, stream>>>(fv, blocks, step0,
-                                                                             k, traj);
+    k_fleet<NTV, DIAG, REC, (DIAG ? 4 : 0)><<<n_blocks, threads, 0, stream>>>(fv, blocks, k,
+                                                                             traj);
   else
-    k_fleet<NTV, DIAG, REC, 0><<<n_blocks, threads, 0, stream>>>(fv, blocks, step0, k, traj);
+    k_fleet<NTV, DIAG, REC, 0><<<n_blocks, threads, 0, stream>>>(fv, blocks, k, traj);
   return cudaGetLastError();
 }
 
 template <int NTV, bool DIAG>
 cudaError_t launch_r(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
-                     bool structured, int64_t step0, int32_t k, float *traj,
-                     cudaStream_t stream) {
-  return traj ? launch_t<NTV, DIAG, true>(fv, blocks, n_blocks, threads, structured, step0, k,
-                                          traj, stream)
-              : launch_t<NTV, DIAG, false>(fv, blocks, n_blocks, threads, structured, step0, k,
-                                           traj, stream);
+                     bool structured, int32_t k, float *traj, cudaStream_t stream) {
+  return traj ? launch_t<NTV, DIAG, true>(fv, blocks, n_blocks, threads, structured, k, traj,
+                                          stream)
+              : launch_t<NTV, DIAG, false>(fv, blocks, n_blocks, threads, structured, k, traj,
+                                           stream);
 }
 
 template <int NTV>
 cudaError_t launch_d(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
-                     bool diag, bool structured, int64_t step0, int32_t k, float *traj,
-                     cudaStream_t stream) {
-  return diag ? launch_r<NTV, true>(fv, blocks, n_blocks, threads, structured, step0, k, traj,
-                                    stream)
-              : launch_r<NTV, false>(fv, blocks, n_blocks, threads, structured, step0, k, traj,
-                                     stream);
+                     bool diag, bool structured, int32_t k, float *traj, cudaStream_t stream) {
+  return diag ? launch_r<NTV, true>(fv, blocks, n_blocks, threads, structured, k, traj, stream)
+              : launch_r<NTV, false>(fv, blocks, n_blocks, threads, structured, k, traj, stream);
 }
 
 template <int NTV, bool DIAG, bool REC>
@@ -270,47 +306,42 @@ const void *queue_kernel(NtVariant ntv, bool diag, bool wide, bool structured) {
 
 template <int NTV, bool DIAG, int NH>
 void queue_launch_w(bool wide, int grid, const FleetView &fv, const BlockDesc *slices,
-                    int32_t n_slices, int64_t step0, int32_t k, int32_t chunk, uint32_t *sched,
+                    int32_t n_slices, int32_t k, int32_t chunk, uint32_t *sched,
                     cudaStream_t stream) {
   if (wide)
     k_fleet_queue<NTV, DIAG, true, NH><<<grid, kQueueWarps * 32, 0, stream>>>(
-        fv, slices, n_slices, step0, k, chunk, sched);
+        fv, slices, n_slices, k, chunk, sched);
   else
     k_fleet_queue<NTV, DIAG, false, NH><<<grid, kQueueWarps * 32, 0, stream>>>(
-        fv, slices, n_slices, step0, k, chunk, sched);
+        fv, slices, n_slices, k, chunk, sched);
 }
 
 template <int NTV>
 void queue_launch(bool diag, bool wide, bool structured, int grid, const FleetView &fv,
-                  const BlockDesc *slices, int32_t n_slices, int64_t step0, int32_t k,
-                  int32_t chunk, uint32_t *sched, cudaStream_t stream) {
+                  const BlockDesc *slices, int32_t n_slices, int32_t k, int32_t chunk,
+                  uint32_t *sched, cudaStream_t stream) {
   if (diag && structured)
-    queue_launch_w<NTV, true, 4>(wide, grid, fv, slices, n_slices, step0, k, chunk, sched,
-                                 stream);
+    queue_launch_w<NTV, true, 4>(wide, grid, fv, slices, n_slices, k, chunk, sched, stream);
   else if (diag)
-    queue_launch_w<NTV, true, 0>(wide, grid, fv, slices, n_slices, step0, k, chunk, sched,
-                                 stream);
+    queue_launch_w<NTV, true, 0>(wide, grid, fv, slices, n_slices, k, chunk, sched, stream);
   else
-    queue_launch_w<NTV, false, 0>(wide, grid, fv, slices, n_slices, step0, k, chunk, sched,
-                                  stream);
+    queue_launch_w<NTV, false, 0>(wide, grid, fv, slices, n_slices, k, chunk, sched, stream);
 }
 
 }  // namespace
 
 cudaError_t launch_fleet(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
-                         NtVariant ntv, bool diag, bool structured, int64_t step0, int32_t k,
-                         float *traj, cudaStream_t stream) {
+                         NtVariant ntv, bool diag, bool structured, int32_t k, float *traj,
+                         cudaStream_t stream) {
   if (threads < 32 || threads > kMaxThreads || threads % 32 || n_blocks < 1 || k < 1)
     return cudaErrorInvalidValue;
   switch (ntv) {
     case NT_6:
-      return launch_d<NT_6>(fv, blocks, n_blocks, threads, diag, structured, step0, k, traj,
-                            stream);
+      return launch_d<NT_6>(fv, blocks, n_blocks, threads, diag, structured, k, traj, stream);
     case NT_8:
-      return launch_d<NT_8>(fv, blocks, n_blocks, threads, diag, structured, step0, k, traj,
-                            stream);
+      return launch_d<NT_8>(fv, blocks, n_blocks, threads, diag, structured, k, traj, stream);
     default:
-      return launch_d<NT_MIXED>(fv, blocks, n_blocks, threads, diag, structured, step0, k, traj,
+      return launch_d<NT_MIXED>(fv, blocks, n_blocks, threads, diag, structured, k, traj,
                                 stream);
   }
 }
@@ -343,8 +374,8 @@ cudaError_t queue_kernel_attributes(NtVariant ntv, bool diag, bool wide, bool st
 
 cudaError_t launch_fleet_queue(const FleetView &fv, const BlockDesc *slices, int n_slices,
                                NtVariant ntv, bool diag, bool structured, bool wide,
-                               int warps_per_sm, int64_t step0, int32_t k, int32_t chunk,
-                               uint32_t *sched, int n_sm, cudaStream_t stream) {
+                               int warps_per_sm, int32_t k, int32_t chunk, uint32_t *sched,
+                               int n_sm, cudaStream_t stream) {
   if (n_slices < 1 || k < 1 || chunk < 1 || n_sm < 1) return cudaErrorInvalidValue;
   cudaFuncAttributes attr;
   int per_sm = 0;
@@ -367,16 +398,13 @@ cudaError_t launch_fleet_queue(const FleetView &fv, const BlockDesc *slices, int
     if (e != cudaSuccess) return e;
     switch (ntv) {
       case NT_6:
-        queue_launch<NT_6>(diag, wide, structured, grid, fv, slices, n_slices, step0 + done, kk,
-                           chunk, sched, stream);
+        queue_launch<NT_6>(diag, wide, structured, grid, fv, slices, n_slices, kk, chunk, sched, stream);
         break;
       case NT_8:
-        queue_launch<NT_8>(diag, wide, structured, grid, fv, slices, n_slices, step0 + done, kk,
-                           chunk, sched, stream);
+        queue_launch<NT_8>(diag, wide, structured, grid, fv, slices, n_slices, kk, chunk, sched, stream);
         break;
       default:
-        queue_launch<NT_MIXED>(diag, wide, structured, grid, fv, slices, n_slices, step0 + done,
-                               kk, chunk, sched, stream);
+        queue_launch<NT_MIXED>(diag, wide, structured, grid, fv, slices, n_slices, kk, chunk, sched, stream);
         break;
     }
     e = cudaGetLastError();

@@ -10,7 +10,8 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import MG_MAX_THR, MG_NPARAM, MG_NSTATE, MG_NTRAJ, MGError, Ranges, VehicleParams, call
+from ._lib import (MG_MAX_THR, MG_NPARAM, MG_NSTATE, MG_NTRAJ, MGError, Ranges, TaskSpec,
+                   VehicleParams, call)
 
 __all__ = ["Sim", "vehicle_struct", "MGError"]
 
@@ -162,6 +163,31 @@ class Sim:
         _check(traj, (k, MG_NTRAJ, self.n), torch.float32)
         call("mg_step_record", self._h, int(k), _ptr(traj))
         return traj
+
+    # ------------------------------------------------------------------ task layer
+    def set_task(self, task: int, centres, radius: float = 2.0, omega: float = 0.3,
+                 vz: float = 0.1, psi_r: float = 0.0, lookahead: int = 4,
+                 lookahead_dt: float = 0.5, max_error: float = 0.0, episode_steps: int = 0):
+        """Task of §EXPERIMENTS (MG_TASK_*); centres: float32 [n, 4] (cx, cy, cz, phi0)."""
+        spec = TaskSpec(int(task), int(lookahead), radius, omega, vz, psi_r, lookahead_dt,
+                        max_error, int(episode_steps), 0)
+        _check(centres, (self.n, 4), torch.float32)
+        call("mg_set_task", self._h, ctypes.byref(spec), _ptr(centres))
+        d = ctypes.c_int32()
+        call("mg_task_obs_dim", self._h, ctypes.byref(d))
+        self.obs_dim = d.value
+        dev = self.device
+        self._task_out = (torch.empty((self.n, self.obs_dim), dtype=torch.float32, device=dev),
+                          torch.empty(self.n, dtype=torch.float32, device=dev),
+                          torch.empty(self.n, dtype=torch.uint8, device=dev),
+                          torch.empty(self.n, dtype=torch.float32, device=dev))
+
+    def task_step(self, k: int):
+        """(obs [n, obs_dim], err [n], done [n], episode_err [n]) after k sub-steps (k = 0:
+        observe only).  The tensors are reused by the next call."""
+        obs, err, done, ep = self._task_out
+        call("mg_task_step", self._h, int(k), _ptr(obs), _ptr(err), _ptr(done), _ptr(ep))
+        return obs, err, done, ep
 
     # ------------------------------------------------------------------ state
     def get_state(self, out=None):

@@ -286,7 +286,9 @@ mg_status mg_task_obs_dim(mg_sim *sim, int32_t *obs_dim);
  * episode's clock and error sum advance, and an env whose episode ended (error above max_error,
  * episode_steps reached, or a non-finite state) gets done = 1, episode_err = its error sum
  * (including this step), and an automatic reset (as mg_reset); obs is then the new episode's
- * first observation.  k = 0 only observes (no step, no clock, no reset).  obs: device
+ * first observation.  The last min(k, steps_per_launch) sub-steps and all of the above run in
+ * one fused launch on the static grid (earlier sub-steps as mg_step, with its schedule), so the
+ * state is stored once.  k = 0 only observes (no step, no clock, no reset).  obs: device
  * [n][obs_dim]; err: device [n]; done: device [n]; episode_err: device [n] or NULL (0 for envs
  * that did not finish).  Asynchronous.  Errors: MG_ESTATE (no task), MG_EINVAL. */
 mg_status mg_task_step(mg_sim *sim, int32_t k, float *obs, float *err, uint8_t *done,

@@ -855,12 +855,24 @@ mg_status mg_task_step(mg_sim *s, int32_t k, float *obs, float *err, uint8_t *do
     if (!is_device_ptr(p)) return fail(MG_EINVAL, "task outputs must be device memory");
   if (episode_err && !is_device_ptr(episode_err))
     return fail(MG_EINVAL, "task outputs must be device memory");
-  if (k > 0) {
-    mg_status st = mg_step(s, k);
+  if (k == 0) {  // observe only
+    MG_CK(launch_task(s->st, s->task_view(), s->n, s->gid0, 0, s->dt, obs, err, done,
+                      episode_err, s->reset_seed, s->nu0_sigma, s->episode, s->flags,
+                      s->counters, s->stream));
+    return MG_OK;
+  }
+  // Leading sub-steps as mg_step; the last static chunk carries the fused task epilogue.
+  const int32_t k_last = (k - 1) % s->spl + 1;
+  if (k > k_last) {
+    mg_status st = mg_step(s, k - k_last);
     if (st != MG_OK) return st;
   }
-  MG_CK(launch_task(s->st, s->task_view(), s->n, s->gid0, k, s->dt, obs, err, done, episode_err,
-                    s->reset_seed, s->nu0_sigma, s->episode, s->flags, s->counters, s->stream));
+  int32_t obs_dim = 0;
+  mg_task_obs_dim(s, &obs_dim);
+  TaskOut to{obs, err, done, episode_err, obs_dim, 0, s->reset_seed, s->nu0_sigma, s->episode};
+  MG_CK(launch_fleet_task(s->view(), s->blocks_d, s->n_blocks, s->threads, s->ntv, s->diag,
+                          s->structured, k_last, k, s->task_view(), to, s->stream));
+  s->cursor += k_last;
   return MG_OK;
 }
 

@@ -91,13 +91,10 @@ __device__ __forceinline__ void box_muller_f(float u1, float u2, float &z0, floa
   z1 = r * s;
 }
 
-// New episode for env e (episode reset, §METHOD randomisation of the start): p = 0, q =
-// identity, n = 0, nu = sigma N(0,1)^6 from stream 2 of env id gid at the env's episode counter
-// (blocks 2 ep, 2 ep + 1); the counter is incremented and the non-finite flag cleared.
-__device__ __forceinline__ void reset_env(const StatePlanes &st, int64_t e, uint64_t gid,
-                                          uint64_t seed, double sigma, uint32_t *episode,
-                                          uint32_t *flags, unsigned long long *nonfinite_count) {
-  const uint32_t ep = episode[e];
+// Initial body velocity of episode ep of env id gid: nu = sigma N(0,1)^6 from stream 2 (blocks
+// 2 ep, 2 ep + 1).
+__device__ __forceinline__ void reset_nu(uint64_t seed, uint64_t gid, uint32_t ep, double sigma,
+                                         float (&nu)[6]) {
   const uint4 a = draw4(seed, gid, STREAM_RESET, 2u * ep);
   const uint4 b = draw4(seed, gid, STREAM_RESET, 2u * ep + 1u);
   float z[6];
@@ -105,8 +102,19 @@ __device__ __forceinline__ void reset_env(const StatePlanes &st, int64_t e, uint
   box_muller_f(u01f(a.z), u01f(a.w), z[2], z[3]);
   box_muller_f(u01f(b.x), u01f(b.y), z[4], z[5]);
   const float sg = (float)sigma;
-  float nu[6];
+#pragma unroll
   for (int i = 0; i < 6; ++i) nu[i] = sg * z[i];
+}
+
+// New episode for env e (episode reset, §METHOD randomisation of the start): p = 0, q =
+// identity, n = 0, nu from reset_nu at the env's episode counter; the counter is incremented and
+// the non-finite flag cleared.
+__device__ __forceinline__ void reset_env(const StatePlanes &st, int64_t e, uint64_t gid,
+                                          uint64_t seed, double sigma, uint32_t *episode,
+                                          uint32_t *flags, unsigned long long *nonfinite_count) {
+  const uint32_t ep = episode[e];
+  float nu[6];
+  reset_nu(seed, gid, ep, sigma, nu);
   st.s0[e] = make_float4(0.f, 0.f, 0.f, 1.f);
   st.s1[e] = make_float4(0.f, 0.f, 0.f, nu[0]);
   st.s2[e] = make_float4(nu[1], nu[2], nu[3], nu[4]);

@@ -164,6 +164,26 @@ struct TaskView {
   float *err_sum;            // [n] Eq. 4 error summed over the episode's task steps
 };
 
+// Outputs and reset inputs of the fused task step.
+struct TaskOut {
+  float *obs;        // [n][obs_dim]
+  float *err;        // [n]
+  uint8_t *done;     // [n]
+  float *ep_err;     // [n] or null
+  int32_t obs_dim;
+  int32_t stage;     // set by the launcher: rows staged through shared memory
+  uint64_t seed;     // episode-start draws (as mg_reset)
+  double sigma;
+  uint32_t *episode;
+};
+
+// Final launch of a task step: k_launch sub-steps (static grid), then the task epilogue for a
+// task step of k_task sub-steps in total.
+cudaError_t launch_fleet_task(const FleetView &fv, const BlockDesc *blocks, int n_blocks,
+                              int threads, NtVariant ntv, bool diag, bool structured,
+                              int32_t k_launch, int32_t k_task, const TaskView &tv, TaskOut to,
+                              cudaStream_t stream);
+
 cudaError_t launch_task(const StatePlanes &st, const TaskView &tv, int64_t n, int64_t gid0,
                         int32_t k, float dt, float *obs, float *err, uint8_t *done,
                         float *ep_err, uint64_t seed, double sigma, uint32_t *episode,

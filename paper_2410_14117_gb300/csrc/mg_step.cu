@@ -19,17 +19,13 @@
 #include <algorithm>
 #include <type_traits>
 
-#include "mg_device.cuh"
+#include "mg_advance.cuh"
 
 namespace mg {
 
 namespace {
 
 constexpr int kMaxThreads = 256;
-// Register caps: the diagonal-mass step fits 128 registers (16 resident warps per SM); the
-// general step keeps 168.
-constexpr int kRegsDiag = 128;
-constexpr int kRegsGeneral = 168;
 // Bound on a work-queue wait (polls of ~128 ns each, ~0.5 s); on expiry the wait is counted as a
 // time-out and the unit proceeds.
 constexpr uint32_t kSpinLimit = 1u << 22;
@@ -42,134 +38,6 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
 
 __device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Action cursor at launch start (read through L2: the previous launch's last block wrote it).
-__device__ __forceinline__ int64_t launch_cursor(const FleetView &fv) {
-  return (int64_t)__ldcg(reinterpret_cast<const unsigned long long *>(fv.cursor));
-}
-
-// Called by every thread of every block once it is done: the last block to finish advances the
-// cursor by k and re-arms the counter.  Every block read the cursor before it counted itself
-// finished, so all of them saw the launch's starting value.
-__device__ __forceinline__ void finish_launch(const FleetView &fv, int32_t k) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned prev = atomicAdd(fv.done_blocks, 1u);
-    if (prev == gridDim.x - 1) {
-      atomicAdd(reinterpret_cast<unsigned long long *>(fv.cursor), (unsigned long long)k);
-      atomicExch(fv.done_blocks, 0u);
-      __threadfence();
-    }
-  }
-}
-
-// k_fleet's form of finish_launch, counted in envs (one thread per env, idle threads already
-// gone): each warp adds its finished envs, and the warp that completes the fleet's count
-// advances the cursor by k and re-arms the counter.
-__device__ __forceinline__ void finish_envs(const FleetView &fv, int32_t k) {
-  const unsigned mask = __activemask();
-  __syncwarp(mask);
-  if ((threadIdx.x & 31) == (unsigned)(__ffs(mask) - 1)) {
-    const unsigned add = __popc(mask);
-    __threadfence();
-    const unsigned prev = atomicAdd(fv.done_blocks, add);
-    if ((int64_t)prev + add == fv.n) {
-      atomicAdd(reinterpret_cast<unsigned long long *>(fv.cursor), (unsigned long long)k);
-      atomicExch(fv.done_blocks, 0u);
-      __threadfence();
-    }
-  }
-}
-
-template <int MT>
-__device__ __forceinline__ void load_commands(const FleetView &fv, int64_t e, int64_t seg,
-                                              int nt, float itau, float (&c)[MT]) {
-  if (fv.proc) {
-    procedural_commands<MT>(fv.cmd_seed, (uint64_t)(fv.gid0 + e), seg, c);
-  } else if (fv.n_seg > 0) {
-    const int64_t sg = seg < fv.n_seg - 1 ? seg : fv.n_seg - 1;
-    const float4 *a = fv.act + (sg * fv.n + e) * 2;
-    const float4 lo = __ldg(a), hi = __ldg(a + 1);
-    c[0] = lo.x; c[1] = lo.y; c[2] = lo.z; c[3] = lo.w; c[4] = hi.x; c[5] = hi.y;
-    if constexpr (MT > 6) {
-      c[6] = hi.z;
-      c[7] = hi.w;
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < MT; ++i) c[i] = 0.f;
-  }
-  // Entries past the vehicle's thruster count are ignored (the lag state there stays zero).
-  // The step reads the command divided by the lag time constant.
-#pragma unroll
-  for (int i = 0; i < MT; ++i) c[i] = (i < nt) ? c[i] * itau : 0.f;
-}
-
-template <int MT>
-__device__ __forceinline__ void record(float *__restrict__ traj, int64_t n, int64_t e,
-                                       const St<MT> &s) {
-  float *t = traj + e;
-  t[0 * n] = s.p[0]; t[1 * n] = s.p[1]; t[2 * n] = s.p[2];
-  t[3 * n] = s.q[0]; t[4 * n] = s.q[1]; t[5 * n] = s.q[2]; t[6 * n] = s.q[3];
-  t[7 * n] = s.v[0]; t[8 * n] = s.v[1]; t[9 * n] = s.v[2];
-  t[10 * n] = s.w[0]; t[11 * n] = s.w[1]; t[12 * n] = s.w[2];
-}
-
-template <int MT>
-__device__ __forceinline__ bool all_finite(const St<MT> &s) {
-  // x * 0 is 0 for finite x and NaN for +-Inf or NaN, so the sum is 0 exactly when all are
-  // finite.
-  float z = 0.f;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) z += s.p[i] * 0.f + s.v[i] * 0.f + s.w[i] * 0.f;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) z += s.q[i] * 0.f;
-#pragma unroll
-  for (int i = 0; i < MT; ++i) z += s.n[i] * 0.f;
-  return z == 0.f;
-}
-
-// Advance env e by k sub-steps starting at action-cursor position step0.  L2: state (and flag)
-// loads bypass L1 (work-queue schedule, where another SM may have written them).
-template <int MT, bool DIAG, bool MIXED, bool REC, bool L2, int NH>
-__device__ __forceinline__ void advance_env(const FleetView &fv, int64_t e, int nt,
-                                            const float4 *gdir, const float4 *garm,
-                                            int64_t step0, int32_t k, float *traj) {
-  const bool current_accel = !(fv.model_flags & MG_MODEL_NO_CURRENT_ACCEL);
-  const float h = fv.dt;
-
-  St<MT> s;
-  load_state<MT, L2>(fv.st, e, s);
-  Par<DIAG> P;
-  load_par<DIAG>(fv.pa, e, P);
-
-  // Action cursor: sub-step j uses segment j / hold (clamped to the last buffered segment).
-  int64_t seg = step0 / fv.hold;
-  int32_t left = fv.hold - (int32_t)(step0 - seg * fv.hold);
-  float c[MT];
-  load_commands<MT>(fv, e, seg, nt, P.itau, c);
-
-  for (int32_t it = 0; it < k; ++it) {
-    if (left == 0) {
-      ++seg;
-      left = fv.hold;
-      load_commands<MT>(fv, e, seg, nt, P.itau, c);
-    }
-    rk4_step<MT, DIAG, MIXED, NH>(s, c, P, gdir, garm, nt, current_accel, h);
-    --left;
-    if constexpr (REC) record<MT>(traj + (int64_t)it * MG_NTRAJ * fv.n, fv.n, e, s);
-  }
-
-  store_state<MT>(fv.st, e, s);
-  if (!all_finite<MT>(s)) {
-    const uint32_t old = L2 ? __ldcg(fv.flags + e) : fv.flags[e];
-    if (!(old & 1u)) {
-      fv.flags[e] = old | 1u;
-      atomicAdd(fv.counters, 1ull);
-    }
-  }
 }
 
 template <int NTV, bool DIAG, bool REC, int NH>
@@ -187,9 +55,11 @@ __global__ void __maxnreg__(DIAG ? kRegsDiag : kRegsGeneral)
   }
   __syncthreads();
   if ((int)threadIdx.x >= bd.count) return;
-  advance_env<MT, DIAG, MIXED, REC, false, NH>(fv, (int64_t)bd.env0 + threadIdx.x,
-                                               MIXED ? bd.n_thr : MT, sdir, sarm,
-                                               launch_cursor(fv), k, traj);
+  const int64_t e = (int64_t)bd.env0 + threadIdx.x;
+  St<MT> st;
+  advance_env<MT, DIAG, MIXED, REC, false, NH>(fv, e, MIXED ? bd.n_thr : MT, sdir, sarm,
+                                               launch_cursor(fv), k, traj, st);
+  store_and_flag<MT, false>(fv, e, st);
   finish_envs(fv, k);
 }
 
@@ -233,11 +103,15 @@ __global__ void __maxnreg__((DIAG && !WIDE) ? kRegsDiag : kRegsGeneral)
     __syncwarp();
     const BlockDesc bd = slices[d];
     const float4 *gdir = sgeo[bd.type & (MG_MAX_TYPES - 1)], *garm = gdir + MG_MAX_THR;
-    if (lane < bd.count)
-      advance_env<MT, DIAG, MIXED, false, true, NH>(fv, (int64_t)bd.env0 + lane,
-                                                    MIXED ? bd.n_thr : MT, gdir, garm,
+    if (lane < bd.count) {
+      const int64_t e = (int64_t)bd.env0 + lane;
+      St<MT> st;
+      advance_env<MT, DIAG, MIXED, false, true, NH>(fv, e, MIXED ? bd.n_thr : MT, gdir, garm,
                                                     step0 + (int64_t)c * chunk,
-                                                    min(chunk, k_total - c * chunk), nullptr);
+                                                    min(chunk, k_total - c * chunk), nullptr,
+                                                    st);
+      store_and_flag<MT, true>(fv, e, st);
+    }
     __syncwarp();
     if (lane == 0) {
       __threadfence();

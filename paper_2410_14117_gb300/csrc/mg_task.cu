@@ -11,7 +11,7 @@
 // Attitude reference: level, heading psi_r; attitude error = (phi, theta, wrap(psi - psi_r)) from
 // the zyx Euler angles of q.  Observation: for i = 1..m (m = 1 for station keeping) the position
 // error to p_r(t + i dt_look) followed by the attitude error, then nu.
-#include "mg_device.cuh"
+#include "mg_advance.cuh"
 
 namespace mg {
 
@@ -43,12 +43,11 @@ __device__ __forceinline__ float wrap_pi(float a) {
   return a - pi;
 }
 
-// Writes the observation of env e at task time t; returns |p - p_r(t)|.
-__device__ float observe(const TaskView &tv, const StatePlanes &st, int64_t e, float t,
-                         float *__restrict__ obs) {
-  const float4 a = st.s0[e], b = st.s1[e], c = st.s2[e], d = st.s3[e];
-  const float px = a.x, py = a.y, pz = a.z, qw = a.w, qx = b.x, qy = b.y, qz = b.z;
-  const float nu[6] = {b.w, c.x, c.y, c.z, c.w, d.x};
+// Writes the observation of env e at task time t from its position p, attitude q and body
+// velocity nu; returns |p - p_r(t)|.
+__device__ __forceinline__ float observe(const TaskView &tv, int64_t e, float t, float px,
+                                         float py, float pz, float qw, float qx, float qy,
+                                         float qz, const float (&nu)[6], float *__restrict__ obs) {
   const float sp = fminf(1.f, fmaxf(-1.f, 2.f * (qw * qy - qz * qx)));
   const float phi = atan2f(2.f * (qw * qx + qy * qz), 1.f - 2.f * (qx * qx + qy * qy));
   const float theta = asinf(sp);
@@ -74,6 +73,13 @@ __device__ float observe(const TaskView &tv, const StatePlanes &st, int64_t e, f
   return sqrtf((px - x) * (px - x) + (py - y) * (py - y) + (pz - z) * (pz - z));
 }
 
+__device__ __forceinline__ float observe_planes(const TaskView &tv, const StatePlanes &st,
+                                                int64_t e, float t, float *__restrict__ obs) {
+  const float4 a = st.s0[e], b = st.s1[e], c = st.s2[e], d = st.s3[e];
+  const float nu[6] = {b.w, c.x, c.y, c.z, c.w, d.x};
+  return observe(tv, e, t, a.x, a.y, a.z, a.w, b.x, b.y, b.z, nu, obs);
+}
+
 // Envs per block; the block's observations are staged in shared memory and written out as one
 // contiguous, coalesced run (obs is env-major [n][obs_dim], so a thread's own row is strided
 // across the warp).
@@ -92,7 +98,7 @@ __global__ void __launch_bounds__(kTaskThreads)
   if (e < n) {
     float *o = sobs + threadIdx.x * obs_dim;
     const int32_t clock = tv.clock[e] + k;
-    const float e0 = observe(tv, st, e, (float)clock * dt, o);
+    const float e0 = observe_planes(tv, st, e, (float)clock * dt, o);
     if (k == 0) {  // observation only
       err[e] = e0;
       done[e] = 0;
@@ -109,7 +115,7 @@ __global__ void __launch_bounds__(kTaskThreads)
         reset_env(st, e, (uint64_t)(gid0 + e), seed, sigma, episode, flags, nonfinite_count);
         tv.clock[e] = 0;
         tv.err_sum[e] = 0.f;
-        observe(tv, st, e, 0.f, o);
+        observe_planes(tv, st, e, 0.f, o);
       } else {
         done[e] = 0;
         if (ep_err) ep_err[e] = 0.f;
@@ -133,6 +139,122 @@ __global__ void __launch_bounds__(kTaskThreads)
   for (int i = i0 + threadIdx.x; i < total; i += kTaskThreads) dst[i] = sobs[i];
 }
 
+// ---------------------------------------------------------------- fused task step
+// The last launch of a task step: the env's final sub-steps as in k_fleet, then, from the state
+// still in registers, the Eq. 4 error, the Eq. 2 observation, the episode bookkeeping and the
+// auto-reset, so the state is stored once and never re-read.  Each warp stages its 32 rows of
+// the observation in shared memory (when they fit) and writes them out as one contiguous run.
+template <int NTV, bool DIAG, int NH>
+__global__ void __maxnreg__(DIAG ? kRegsDiag : kRegsGeneral)
+    k_fleet_task(const FleetView fv, const BlockDesc *__restrict__ blocks, const int32_t k_launch,
+                 const int32_t k_task, const TaskView tv, const TaskOut to) {
+  constexpr int MT = (NTV == NT_6) ? 6 : 8;
+  constexpr bool MIXED = (NTV == NT_MIXED);
+  __shared__ float4 sdir[MG_MAX_THR], sarm[MG_MAX_THR];
+  extern __shared__ float sobs[];  // [blockDim.x][obs_dim] when to.stage
+
+  const BlockDesc bd = blocks[blockIdx.x];
+  if (threadIdx.x < MG_MAX_THR) {
+    sdir[threadIdx.x] = fv.geo[bd.type].dir[threadIdx.x];
+    sarm[threadIdx.x] = fv.geo[bd.type].arm[threadIdx.x];
+  }
+  __syncthreads();
+  if ((int)threadIdx.x >= bd.count) return;
+  const int64_t e = (int64_t)bd.env0 + threadIdx.x;
+  St<MT> s;
+  advance_env<MT, DIAG, MIXED, false, false, NH>(fv, e, MIXED ? bd.n_thr : MT, sdir, sarm,
+                                                 launch_cursor(fv), k_launch, nullptr, s);
+
+  const int obs_dim = to.obs_dim;
+  float *row = to.stage ? sobs + threadIdx.x * obs_dim : to.obs + e * obs_dim;
+  const int32_t clock = tv.clock[e] + k_task;
+  float t = (float)clock * fv.dt;
+  float rx, ry, rz;
+  reference(tv, tv.centre[e], t, rx, ry, rz);
+  const float e0 = sqrtf((s.p[0] - rx) * (s.p[0] - rx) + (s.p[1] - ry) * (s.p[1] - ry) +
+                         (s.p[2] - rz) * (s.p[2] - rz));
+  const uint32_t flag = fv.flags[e];
+  const bool bad = !all_finite<MT>(s) || (flag & 1u) || !(e0 == e0) || isinf(e0);
+  const bool over = (tv.max_err > 0.f && e0 > tv.max_err) ||
+                    (tv.episode_steps > 0 && clock >= tv.episode_steps);
+  const float sum = tv.err_sum[e] + e0;
+  to.err[e] = e0;
+  float nu[6] = {s.v[0], s.v[1], s.v[2], s.w[0], s.w[1], s.w[2]};
+  if (bad || over) {
+    // new episode (as reset_env), built in registers so it is observed without a re-read
+    const uint32_t ep = to.episode[e];
+    reset_nu(to.seed, (uint64_t)(fv.gid0 + e), ep, to.sigma, nu);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      s.p[i] = 0.f;
+      s.v[i] = nu[i];
+      s.w[i] = nu[3 + i];
+    }
+    s.q[0] = 1.f;
+    s.q[1] = s.q[2] = s.q[3] = 0.f;
+#pragma unroll
+    for (int i = 0; i < MT; ++i) s.n[i] = 0.f;
+    if (MT == 6) fv.st.s5[e] = 0.f;
+    to.episode[e] = ep + 1u;
+    if (flag & 1u) atomicAdd(fv.counters, ~0ull);  // decrement
+    fv.flags[e] = 0u;
+    to.done[e] = 1;
+    if (to.ep_err) to.ep_err[e] = sum;
+    tv.clock[e] = 0;
+    tv.err_sum[e] = 0.f;
+    t = 0.f;
+  } else {
+    to.done[e] = 0;
+    if (to.ep_err) to.ep_err[e] = 0.f;
+    tv.clock[e] = clock;
+    tv.err_sum[e] = sum;
+  }
+  store_state<MT>(fv.st, e, s);
+  observe(tv, e, t, s.p[0], s.p[1], s.p[2], s.q[0], s.q[1], s.q[2], s.q[3], nu, row);
+  finish_envs(fv, k_launch);
+  if (!to.stage) return;
+  // Warp copy-out: the warp's live lanes are its low lanes (threads below bd.count).
+  const int lane = threadIdx.x & 31;
+  const int wbase = threadIdx.x & ~31;
+  const int n_act = min(32, bd.count - wbase);
+  __syncwarp(n_act == 32 ? 0xffffffffu : ((1u << n_act) - 1u));
+  const int total = n_act * obs_dim;
+  const float *src = sobs + wbase * obs_dim;
+  float *dst = to.obs + ((int64_t)bd.env0 + wbase) * obs_dim;
+  int i0 = 0;
+  if (((reinterpret_cast<uintptr_t>(dst) | (uintptr_t)(wbase * obs_dim * 4)) & 15) == 0) {
+    const int n4 = total >> 2;
+    for (int i = lane; i < n4; i += n_act)
+      reinterpret_cast<float4 *>(dst)[i] = reinterpret_cast<const float4 *>(src)[i];
+    i0 = n4 << 2;
+  }
+  for (int i = i0 + lane; i < total; i += n_act) dst[i] = src[i];
+}
+
+template <int NTV, bool DIAG, int NH>
+cudaError_t fleet_task_t(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
+                         int32_t k_launch, int32_t k_task, const TaskView &tv, const TaskOut &to,
+                         size_t smem, cudaStream_t stream) {
+  k_fleet_task<NTV, DIAG, NH><<<n_blocks, threads, smem, stream>>>(fv, blocks, k_launch, k_task,
+                                                                   tv, to);
+  return cudaGetLastError();
+}
+
+template <int NTV>
+cudaError_t fleet_task_d(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
+                         bool diag, bool structured, int32_t k_launch, int32_t k_task,
+                         const TaskView &tv, const TaskOut &to, size_t smem,
+                         cudaStream_t stream) {
+  if (diag && structured)
+    return fleet_task_t<NTV, true, 4>(fv, blocks, n_blocks, threads, k_launch, k_task, tv, to,
+                                      smem, stream);
+  if (diag)
+    return fleet_task_t<NTV, true, 0>(fv, blocks, n_blocks, threads, k_launch, k_task, tv, to,
+                                      smem, stream);
+  return fleet_task_t<NTV, false, 0>(fv, blocks, n_blocks, threads, k_launch, k_task, tv, to,
+                                     smem, stream);
+}
+
 }  // namespace
 
 cudaError_t launch_task(const StatePlanes &st, const TaskView &tv, int64_t n, int64_t gid0,
@@ -153,6 +275,30 @@ cudaError_t launch_task(const StatePlanes &st, const TaskView &tv, int64_t n, in
                                                          err, done, ep_err, seed, sigma, episode,
                                                          flags, nonfinite_count);
   return cudaGetLastError();
+}
+
+cudaError_t launch_fleet_task(const FleetView &fv, const BlockDesc *blocks, int n_blocks,
+                              int threads, NtVariant ntv, bool diag, bool structured,
+                              int32_t k_launch, int32_t k_task, const TaskView &tv, TaskOut to,
+                              cudaStream_t stream) {
+  if (threads < 32 || threads > 256 || threads % 32 || n_blocks < 1 || k_launch < 1 ||
+      k_task < k_launch)
+    return cudaErrorInvalidValue;
+  // Stage the observation rows in shared memory when the block's rows fit in 48 KB.
+  const size_t smem = sizeof(float) * threads * to.obs_dim;
+  to.stage = smem <= 48 * 1024 ? 1 : 0;
+  const size_t dyn = to.stage ? smem : 0;
+  switch (ntv) {
+    case NT_6:
+      return fleet_task_d<NT_6>(fv, blocks, n_blocks, threads, diag, structured, k_launch,
+                                k_task, tv, to, dyn, stream);
+    case NT_8:
+      return fleet_task_d<NT_8>(fv, blocks, n_blocks, threads, diag, structured, k_launch,
+                                k_task, tv, to, dyn, stream);
+    default:
+      return fleet_task_d<NT_MIXED>(fv, blocks, n_blocks, threads, diag, structured, k_launch,
+                                    k_task, tv, to, dyn, stream);
+  }
 }
 
 }  // namespace mg

@@ -28,17 +28,24 @@ def _centres(n, seed=1):
     return c
 
 
-@pytest.mark.parametrize("task", [O.TASK_STATION, O.TASK_CIRCLE, O.TASK_HELIX,
-                                  O.TASK_LEMNISCATE])
-def test_task_step_matches_oracle(task):
+# (task, look-ahead points, envs per block, sub-steps per launch, work queue): the last launch of
+# a task step carries the fused epilogue; with 3 sub-steps per launch the first 9 of the 10 run
+# as plain step launches first.  40 look-ahead points (246 floats per row) exceed the shared-memory
+# staging and take the direct-write path.
+@pytest.mark.parametrize("task,m,epb,spl,queue", [
+    (O.TASK_STATION, 3, 64, 50, False), (O.TASK_CIRCLE, 3, 128, 50, False),
+    (O.TASK_HELIX, 40, 64, 50, False), (O.TASK_LEMNISCATE, 3, 96, 3, True),
+    (O.TASK_CIRCLE, 10, 128, 4, False)])
+def test_task_step_matches_oracle(task, m, epb, spl, queue):
     vs = vehicles()
     n = 384
     types = I.mixed_fleet(task + 5, n, max_group=100)
-    spec = dict(radius=2.0, omega=0.4, vz=0.1, psi_r=0.3, lookahead=3, lookahead_dt=0.5,
+    spec = dict(radius=2.0, omega=0.4, vz=0.1, psi_r=0.3, lookahead=m, lookahead_dt=0.5,
                 max_error=2.6, episode_steps=150)
     centres = _centres(n, task)
     sim = Sim(n, types, vs)
-    sim.set_launch(64, 50, False)
+    sim.set_launch(epb, spl, False)
+    sim.set_schedule(queue)
     sim.randomize(SEED, 0.8, 1.2, 0.2, SIGMA)
     sim.reset()
     sim.set_procedural_actions(CMD_SEED, K)

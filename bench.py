@@ -127,17 +127,24 @@ class Clocks:
                 "samples": len(rows)}
 
 
-def kernel_sources_sha() -> str:
-    """Hash of the CUDA sources and the ABI header, to tell whether a committed ncu capture
-    still describes the kernels being timed."""
+# Sources that make up the step kernels (k_fleet, k_fleet_queue); a committed ncu capture
+# describes them only while these files are unchanged.
+STEP_KERNEL_SOURCES = ("paper_2410_14117_gb300/csrc/mg_step.cu",
+                       "paper_2410_14117_gb300/csrc/mg_advance.cuh",
+                       "paper_2410_14117_gb300/csrc/mg_device.cuh",
+                       "paper_2410_14117_gb300/csrc/mg_internal.h",
+                       "include/mg.h")
+
+
+def kernel_sources_sha(files=STEP_KERNEL_SOURCES) -> str:
+    """Hash of the sources a kernel is compiled from, to tell whether a committed ncu capture
+    still describes the kernel being timed."""
     import hashlib
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2410_14117_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)) + ["../../include/mg.h"]:
-        path = os.path.normpath(os.path.join(csrc, name))
-        if path.endswith((".cu", ".cuh", ".h")):
-            h.update(name.encode())
-            h.update(open(path, "rb").read())
+    for rel in files:
+        h.update(rel.encode())
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -262,10 +269,8 @@ def run_reference(args):
 def workload_config(args):
     return {"workload": f"{args.n_envs:,} domain-randomised BlueROV2 envs (params U[0.8,1.2]"
                         f"x nominal, NED current N(0,0.2)), {args.horizon:,} RK4 sub-steps of "
-                        f"0.01 s per episode, commands U[-1,1] held {args.hold} sub-steps; "
-                        f"persistent k={args.k} under one CUDA graph",
-            "n_envs": args.n_envs, "horizon": args.horizon, "steps_per_launch": args.k,
-            "envs_per_block": args.epb,
+                        f"0.01 s per episode, commands U[-1,1] held {args.hold} sub-steps",
+            "n_envs": args.n_envs, "horizon": args.horizon,
             "l2": "flushed between timed steps (256 MB write, outside the events)"}
 
 

@@ -12,7 +12,8 @@ namespace mg {
 constexpr int kRegsDiag = 128;
 constexpr int kRegsGeneral = 168;
 
-// Action cursor at launch start (read through L2: the previous launch's last block wrote it).
+// Action cursor at the start of the launch's mg_step call (read through L2: the previous call's
+// last block wrote it).
 __device__ __forceinline__ int64_t launch_cursor(const FleetView &fv) {
   return (int64_t)__ldcg(reinterpret_cast<const unsigned long long *>(fv.cursor));
 }
@@ -33,20 +34,22 @@ __device__ __forceinline__ void finish_launch(const FleetView &fv, int32_t k) {
   }
 }
 
-// k_fleet's form of finish_launch, counted in envs (one thread per env, idle threads already
-// gone): each warp adds its finished envs, and the warp that completes the fleet's count
-// advances the cursor by k and re-arms the counter.
-__device__ __forceinline__ void finish_envs(const FleetView &fv, int32_t k) {
+// Static-grid form of finish_launch, for kernels whose idle threads have already returned (no
+// block barrier possible): each warp adds its live lanes to the block's shared counter s_done
+// (zeroed before the block's first barrier); the warp that completes the block's count of live
+// envs adds one finished block to the grid's counter, and the block that completes the grid
+// advances the cursor by k and re-arms the counter.  Every thread read the cursor before its
+// warp counted itself, so every block saw the launch's starting value.
+__device__ __forceinline__ void finish_envs(const FleetView &fv, unsigned *s_done, int count,
+                                            int32_t k) {
   const unsigned mask = __activemask();
   __syncwarp(mask);
   if ((threadIdx.x & 31) == (unsigned)(__ffs(mask) - 1)) {
     const unsigned add = __popc(mask);
-    __threadfence();
-    const unsigned prev = atomicAdd(fv.done_blocks, add);
-    if ((int64_t)prev + add == fv.n) {
+    if (atomicAdd(s_done, add) + add == (unsigned)count &&
+        atomicAdd(fv.done_blocks, 1u) == gridDim.x - 1) {
       atomicAdd(reinterpret_cast<unsigned long long *>(fv.cursor), (unsigned long long)k);
       atomicExch(fv.done_blocks, 0u);
-      __threadfence();
     }
   }
 }

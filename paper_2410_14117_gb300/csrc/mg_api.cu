@@ -268,9 +268,12 @@ mg_status build_blocks(mg_sim *s) {
   return MG_OK;
 }
 
+// The launches of one call of k sub-steps: each reads the device cursor plus its offset in the
+// call, and the last advances the cursor by k.
 mg_status launch_chunks(mg_sim *s, int32_t k, float *traj, cudaStream_t stream) {
-  const FleetView v = s->view();
+  FleetView v = s->view();
   if (s->queue && !traj) {
+    v.cursor_adv = k;
     MG_CK(launch_fleet_queue(v, s->slices_d, s->n_slices, s->ntv, s->diag, s->structured,
                              s->queue_wide, s->queue_warps_per_sm, k, s->spl, s->sched, s->n_sm,
                              stream));
@@ -279,6 +282,8 @@ mg_status launch_chunks(mg_sim *s, int32_t k, float *traj, cudaStream_t stream) 
   for (int32_t done = 0; done < k;) {
     const int32_t kk = std::min(s->spl, k - done);
     float *t = traj ? traj + (int64_t)done * MG_NTRAJ * s->n : nullptr;
+    v.cursor_off = done;
+    v.cursor_adv = (done + kk == k) ? k : 0;
     MG_CK(launch_fleet(v, s->blocks_d, s->n_blocks, s->threads, s->ntv, s->diag, s->structured,
                        kk, t, stream));
     done += kk;
@@ -374,7 +379,9 @@ mg_status mg_step_noalloc(mg_sim *s, int32_t k) {
   uint32_t *sched = nullptr;
   mg_status st = noalloc_scratch(&sched);
   if (st != MG_OK) return st;
-  MG_CK(launch_fleet_queue(s->view(), s->slices_d, s->n_slices, s->ntv, s->diag, s->structured,
+  FleetView v = s->view();
+  v.cursor_adv = k;
+  MG_CK(launch_fleet_queue(v, s->slices_d, s->n_slices, s->ntv, s->diag, s->structured,
                            s->queue_wide, s->queue_warps_per_sm, k, s->spl, sched, s->n_sm,
                            s->stream));
   s->cursor += k;
@@ -781,12 +788,14 @@ mg_status mg_rollout_forward(mg_sim *s, int32_t T, int32_t C, float *traj, float
     return fail(MG_EINVAL, "need T >= 1 and 1 <= C <= 32");
   if (!is_device_ptr(traj) || !is_device_ptr(ckpt))
     return fail(MG_EINVAL, "traj and ckpt must be device memory");
-  const FleetView v = s->view();
+  FleetView v = s->view();
   const int64_t step0 = s->cursor;
   for (int32_t t0 = 0; t0 < T; t0 += C) {
     const int32_t len = std::min(C, T - t0);
     MG_CK(launch_checkpoint(s->st, s->n, ckpt + (int64_t)(t0 / C) * MG_NSTATE * s->n,
                             s->stream));
+    v.cursor_off = t0;
+    v.cursor_adv = (t0 + len == T) ? T : 0;
     MG_CK(launch_fleet(v, s->blocks_d, s->n_blocks, s->threads, s->ntv, s->diag, s->structured,
                        len, traj + (int64_t)t0 * MG_NTRAJ * s->n, s->stream));
   }
@@ -870,7 +879,9 @@ mg_status mg_task_step(mg_sim *s, int32_t k, float *obs, float *err, uint8_t *do
   int32_t obs_dim = 0;
   mg_task_obs_dim(s, &obs_dim);
   TaskOut to{obs, err, done, episode_err, obs_dim, 0, s->reset_seed, s->nu0_sigma, s->episode};
-  MG_CK(launch_fleet_task(s->view(), s->blocks_d, s->n_blocks, s->threads, s->ntv, s->diag,
+  FleetView v = s->view();
+  v.cursor_adv = k_last;
+  MG_CK(launch_fleet_task(v, s->blocks_d, s->n_blocks, s->threads, s->ntv, s->diag,
                           s->structured, k_last, k, s->task_view(), to, s->stream));
   s->cursor += k_last;
   return MG_OK;

@@ -83,6 +83,11 @@ struct FleetView {
   // is valid whatever the cursor.  done_blocks counts finished blocks (reset by the last one).
   int64_t *cursor;
   unsigned int *done_blocks;
+  // Per launch: the launch's sub-steps start at *cursor + cursor_off (the launch's offset within
+  // its mg_step call), and a launch with cursor_adv != 0 (the call's last) advances *cursor by
+  // cursor_adv once all its blocks are done.  Only that launch pays for the completion count.
+  int32_t cursor_off;
+  int32_t cursor_adv;
 };
 
 // Kernel variants: thruster count fixed at 6 or 8, or mixed (up to 8, read per block).

@@ -47,20 +47,26 @@ __global__ void __maxnreg__(DIAG ? kRegsDiag : kRegsGeneral)
   constexpr int MT = (NTV == NT_6) ? 6 : 8;
   constexpr bool MIXED = (NTV == NT_MIXED);
   __shared__ float4 sdir[MG_MAX_THR], sarm[MG_MAX_THR];
+  __shared__ unsigned s_done;
+  __shared__ int64_t s_cursor;
 
   const BlockDesc bd = blocks[blockIdx.x];
   if (threadIdx.x < MG_MAX_THR) {
     sdir[threadIdx.x] = fv.geo[bd.type].dir[threadIdx.x];
     sarm[threadIdx.x] = fv.geo[bd.type].arm[threadIdx.x];
   }
+  if (threadIdx.x == 0) {  // the cursor load overlaps the geometry loads
+    s_done = 0u;
+    s_cursor = launch_cursor(fv);
+  }
   __syncthreads();
   if ((int)threadIdx.x >= bd.count) return;
   const int64_t e = (int64_t)bd.env0 + threadIdx.x;
   St<MT> st;
   advance_env<MT, DIAG, MIXED, REC, false, NH>(fv, e, MIXED ? bd.n_thr : MT, sdir, sarm,
-                                               launch_cursor(fv), k, traj, st);
+                                               s_cursor + fv.cursor_off, k, traj, st);
   store_and_flag<MT, false>(fv, e, st);
-  finish_envs(fv, k);
+  if (fv.cursor_adv) finish_envs(fv, &s_done, bd.count, fv.cursor_adv);
 }
 
 template <int NTV, bool DIAG, bool WIDE, int NH>
@@ -76,7 +82,7 @@ __global__ void __maxnreg__((DIAG && !WIDE) ? kRegsDiag : kRegsGeneral)
     const int t = i / (2 * MG_MAX_THR), j = i % (2 * MG_MAX_THR);
     sgeo[t][j] = j < MG_MAX_THR ? fv.geo[t].dir[j] : fv.geo[t].arm[j - MG_MAX_THR];
   }
-  const int64_t step0 = launch_cursor(fv);
+  const int64_t step0 = launch_cursor(fv) + fv.cursor_off;
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const uint32_t n_chunks = (uint32_t)((k_total + chunk - 1) / chunk);
@@ -118,7 +124,7 @@ __global__ void __maxnreg__((DIAG && !WIDE) ? kRegsDiag : kRegsGeneral)
       st_release(sched + 4 + d, (uint32_t)(c + 1));
     }
   }
-  finish_launch(fv, k_total);
+  if (fv.cursor_adv) finish_launch(fv, fv.cursor_adv);
 }
 
 // Structured allocation (NH = 4) is only instantiated for the diagonal-mass step.
@@ -270,15 +276,21 @@ cudaError_t launch_fleet_queue(const FleetView &fv, const BlockDesc *slices, int
     const int32_t kk = (int32_t)std::min<int64_t>(left, max_chunks * (int64_t)chunk);
     e = cudaMemsetAsync(sched, 0, queue_sched_bytes(n_slices), stream);
     if (e != cudaSuccess) return e;
+    FleetView piece = fv;  // this piece's offset in the call; only the last piece advances
+    piece.cursor_off = fv.cursor_off + (int32_t)done;
+    piece.cursor_adv = (done + kk == k) ? fv.cursor_adv : 0;
     switch (ntv) {
       case NT_6:
-        queue_launch<NT_6>(diag, wide, structured, grid, fv, slices, n_slices, kk, chunk, sched, stream);
+        queue_launch<NT_6>(diag, wide, structured, grid, piece, slices, n_slices, kk, chunk,
+                           sched, stream);
         break;
       case NT_8:
-        queue_launch<NT_8>(diag, wide, structured, grid, fv, slices, n_slices, kk, chunk, sched, stream);
+        queue_launch<NT_8>(diag, wide, structured, grid, piece, slices, n_slices, kk, chunk,
+                           sched, stream);
         break;
       default:
-        queue_launch<NT_MIXED>(diag, wide, structured, grid, fv, slices, n_slices, kk, chunk, sched, stream);
+        queue_launch<NT_MIXED>(diag, wide, structured, grid, piece, slices, n_slices, kk, chunk,
+                               sched, stream);
         break;
     }
     e = cudaGetLastError();

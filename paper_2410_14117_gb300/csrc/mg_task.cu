@@ -151,6 +151,8 @@ __global__ void __maxnreg__(DIAG ? kRegsDiag : kRegsGeneral)
   constexpr int MT = (NTV == NT_6) ? 6 : 8;
   constexpr bool MIXED = (NTV == NT_MIXED);
   __shared__ float4 sdir[MG_MAX_THR], sarm[MG_MAX_THR];
+  __shared__ unsigned s_done;
+  __shared__ int64_t s_cursor;
   extern __shared__ float sobs[];  // [blockDim.x][obs_dim] when to.stage
 
   const BlockDesc bd = blocks[blockIdx.x];
@@ -158,12 +160,17 @@ __global__ void __maxnreg__(DIAG ? kRegsDiag : kRegsGeneral)
     sdir[threadIdx.x] = fv.geo[bd.type].dir[threadIdx.x];
     sarm[threadIdx.x] = fv.geo[bd.type].arm[threadIdx.x];
   }
+  if (threadIdx.x == 0) {  // the cursor load overlaps the geometry loads
+    s_done = 0u;
+    s_cursor = launch_cursor(fv);
+  }
   __syncthreads();
   if ((int)threadIdx.x >= bd.count) return;
   const int64_t e = (int64_t)bd.env0 + threadIdx.x;
   St<MT> s;
   advance_env<MT, DIAG, MIXED, false, false, NH>(fv, e, MIXED ? bd.n_thr : MT, sdir, sarm,
-                                                 launch_cursor(fv), k_launch, nullptr, s);
+                                                 s_cursor + fv.cursor_off, k_launch, nullptr,
+                                                 s);
 
   const int obs_dim = to.obs_dim;
   float *row = to.stage ? sobs + threadIdx.x * obs_dim : to.obs + e * obs_dim;
@@ -211,7 +218,7 @@ __global__ void __maxnreg__(DIAG ? kRegsDiag : kRegsGeneral)
   }
   store_state<MT>(fv.st, e, s);
   observe(tv, e, t, s.p[0], s.p[1], s.p[2], s.q[0], s.q[1], s.q[2], s.q[3], nu, row);
-  finish_envs(fv, k_launch);
+  if (fv.cursor_adv) finish_envs(fv, &s_done, bd.count, fv.cursor_adv);
   if (!to.stage) return;
   // Warp copy-out: the warp's live lanes are its low lanes (threads below bd.count).
   const int lane = threadIdx.x & 31;

@@ -6,8 +6,9 @@ Builds a domain-randomised BlueROV2 fleet with NED current and a buffered thrott
 (commands U[-1,1] held 10 sub-steps), then issues ``launches`` calls of ``mg_step(k)`` (no CUDA graph)
 after a few warm-up calls: with ``--static`` each is one launch of the static-grid kernel running
 ``k`` sub-steps; otherwise each is one work-queue launch covering ``k`` sub-steps in chunks of
-``--chunk``.  Holds well under a
-GB of device memory at 65,536 envs.
+``--chunk``; with ``--task`` each is one circle-tracking task step (``k`` sub-steps and the fused
+observation / error / auto-reset epilogue, static grid).  Holds well under a GB of device memory
+at 65,536 envs.
 """
 from __future__ import annotations
 
@@ -35,6 +36,9 @@ def main():
     ap.add_argument("--narrow", action="store_true",
                     help="work queue with the 128-register kernel instead of the 168-register one")
     ap.add_argument("--wps", type=int, default=8, help="work queue: resident warps per SM cap")
+    ap.add_argument("--task", action="store_true",
+                    help="circle-tracking task steps of k sub-steps (fused task epilogue) instead "
+                         "of plain steps; static grid")
     args = ap.parse_args()
 
     n = args.n_envs
@@ -47,8 +51,19 @@ def main():
     total = (args.warmup + args.launches) * args.k
     cmds = I.commands(5678, math.ceil(total / 10), n, vs[args.vehicle].n_thr)
     sim.set_actions(torch.tensor(cmds, device="cuda"), 10)
+    if args.task:
+        sim.set_schedule(False)
+        g = np.random.default_rng(5)
+        phase = g.uniform(0.0, 2 * np.pi, n)
+        centres = np.c_[-2.0 * np.cos(phase), -2.0 * np.sin(phase), np.zeros(n), phase]
+        sim.set_task(1, torch.tensor(centres, dtype=torch.float32, device="cuda"), radius=2.0,
+                     omega=0.4, lookahead=3, lookahead_dt=0.5, max_error=3.0,
+                     episode_steps=1000)
     for _ in range(args.warmup + args.launches):
-        sim.step(args.k)
+        if args.task:
+            sim.task_step(args.k)
+        else:
+            sim.step(args.k)
     bad = sim.sync()
     sim.close()
     print(f"profile_case: {n} envs, {args.launches} launches of k={args.k}, non-finite {bad}")

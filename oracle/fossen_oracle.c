@@ -535,3 +535,141 @@ double orc_task_observe(int32_t task, const double *s, const double *c, double r
   for (int k = 0; k < 3; ++k) d2 += (s[S_P + k] - pr[k]) * (s[S_P + k] - pr[k]);
   return sqrt(d2);
 }
+
+/* ------------------------------------------------------------------ split integration
+ * The paper's own arrangement of Eq. 1 (§METHOD): the rigid-body term is integrated by the
+ * physics engine, while the hydrodynamic term (added mass, added-mass Coriolis, damping,
+ * buoyancy) is computed by a separate module and applied to the body as an external force.
+ * Reading of one sub-step of size h (the engine's semi-implicit Euler; the added-mass force
+ * needs nu', which is not known yet, so the previous sub-step's acceleration a stands in):
+ *
+ *   tau_h = -( M_A (a + [w x v_c^b; 0]) + C_A(nu_r) nu_r + D(nu_r) nu_r + g_A(eta) )
+ *   nu'   = M_RB^-1 ( tau + tau_h - C_RB(nu) nu - g_RB(eta) )
+ *   nu+ = nu + h nu',   p+ = p + h R(q) v+,   q+ = (q + h/2 q (x) (0, w+)) / |.|,
+ *   n+  = n + h (c - n) / tau_m,   a+ = nu'
+ *
+ * g_RB is the weight part of the restoring vector (acting at r_g), g_A the buoyancy part (at
+ * r_b); the current term M_A [w x v_c^b; 0] follows the coupled reading and shares its flag.
+ * a = 0 at an episode start. */
+static void restoring_parts(const double *par, const double q[4], double g_rb[6],
+                            double g_a[6]) {
+  double Rf[9], R[3][3];
+  orc_rotation(q, Rf);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) R[i][j] = Rf[3 * i + j];
+  double fgn[3] = {0.0, 0.0, par[P_W]}, fbn[3] = {0.0, 0.0, -par[P_B]};
+  double fg[3], fb[3];
+  mat3T_vec(R, fgn, fg);
+  mat3T_vec(R, fbn, fb);
+  double rg[3] = {par[P_RG], par[P_RG + 1], par[P_RG + 2]};
+  double rb[3] = {par[P_RB], par[P_RB + 1], par[P_RB + 2]};
+  double mg[3], mb[3];
+  cross3(rg, fg, mg);
+  cross3(rb, fb, mb);
+  for (int i = 0; i < 3; ++i) {
+    g_rb[i] = -fg[i];
+    g_rb[3 + i] = -mg[i];
+    g_a[i] = -fb[i];
+    g_a[3 + i] = -mb[i];
+  }
+}
+
+int orc_split_step(const double *par, const double *geo, const double *s, const double *a,
+                   const double *c, double h, int flags, double *out, double *a_out) {
+  const double *p = s + S_P, *q = s + S_Q, *nu = s + S_NU, *n = s + S_N;
+  int nthr = (int)geo[0];
+  double Rf[9], R[3][3];
+  orc_rotation(q, Rf);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) R[i][j] = Rf[3 * i + j];
+  double vcn[3] = {par[P_VC], par[P_VC + 1], par[P_VC + 2]}, vcb[3];
+  mat3T_vec(R, vcn, vcb);
+  double nu_r[6];
+  for (int i = 0; i < 3; ++i) {
+    nu_r[i] = nu[i] - vcb[i];
+    nu_r[3 + i] = nu[3 + i];
+  }
+
+  /* hydrodynamic module: an external generalised force */
+  double Ma[36], Ca[36], D[36], g_rb[6], g_a[6];
+  orc_mass_a(par, Ma);
+  orc_coriolis_a(par, nu_r, Ca);
+  orc_damping(par, nu_r, D);
+  restoring_parts(par, q, g_rb, g_a);
+  double acc[6];
+  for (int i = 0; i < 6; ++i) acc[i] = a[i];
+  if (!(flags & ORC_NO_CURRENT_ACCEL)) {
+    double wx[3];
+    cross3(nu + 3, vcb, wx);
+    for (int i = 0; i < 3; ++i) acc[i] += wx[i];
+  }
+  double ma[6], ca[6], dd[6], tau_h[6];
+  mat6_vec((const double(*)[6])Ma, acc, ma);
+  mat6_vec((const double(*)[6])Ca, nu_r, ca);
+  mat6_vec((const double(*)[6])D, nu_r, dd);
+  for (int i = 0; i < 6; ++i) tau_h[i] = -(ma[i] + ca[i] + dd[i] + g_a[i]);
+
+  /* rigid body: M_RB nu' = tau + tau_h - C_RB(nu) nu - g_RB */
+  double Mrb[36], Crb[36], crb[6], tau[6], rhs[6], nudot[6];
+  orc_mass_rb(par, Mrb);
+  orc_coriolis_rb(par, nu, Crb);
+  mat6_vec((const double(*)[6])Crb, nu, crb);
+  orc_thrust(par, geo, n, tau);
+  for (int i = 0; i < 6; ++i) rhs[i] = tau[i] + tau_h[i] - crb[i] - g_rb[i];
+  if (solve6((const double(*)[6])Mrb, rhs, nudot) != 0) return -1;
+
+  /* semi-implicit Euler: velocities first, then the pose with the new velocities */
+  double nu1[6];
+  for (int i = 0; i < 6; ++i) nu1[i] = nu[i] + h * nudot[i];
+  double pd[3];
+  mat3_vec((const double(*)[3])R, nu1, pd);
+  for (int i = 0; i < 3; ++i) out[S_P + i] = p[i] + h * pd[i];
+  const double *w = nu1 + 3;
+  double qd[4];
+  qd[0] = -0.5 * (q[1] * w[0] + q[2] * w[1] + q[3] * w[2]);
+  qd[1] = 0.5 * (q[0] * w[0] + q[2] * w[2] - q[3] * w[1]);
+  qd[2] = 0.5 * (q[0] * w[1] + q[3] * w[0] - q[1] * w[2]);
+  qd[3] = 0.5 * (q[0] * w[2] + q[1] * w[1] - q[2] * w[0]);
+  double q1[4], nq = 0.0;
+  for (int i = 0; i < 4; ++i) {
+    q1[i] = q[i] + h * qd[i];
+    nq += q1[i] * q1[i];
+  }
+  nq = sqrt(nq);
+  for (int i = 0; i < 4; ++i) out[S_Q + i] = q1[i] / nq;
+  for (int i = 0; i < 6; ++i) {
+    out[S_NU + i] = nu1[i];
+    a_out[i] = nudot[i];
+  }
+  for (int i = 0; i < ORC_MAXTHR; ++i)
+    out[S_N + i] = (i < nthr) ? n[i] + h * (c[i] - n[i]) / par[P_TAU] : 0.0;
+  return 0;
+}
+
+/* Fleet rollout of the split scheme; as orc_rollout, with the acceleration memory acc [n][6]
+ * advanced in place alongside s. */
+int64_t orc_split_rollout(int64_t n, const double *par, const double *geo, const int32_t *types,
+                          double *s, double *acc, const double *cmd, int32_t n_seg, int32_t hold,
+                          int32_t n_steps, double h, int32_t flags, int32_t nthreads) {
+  int64_t fails = 0;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : fails)
+#endif
+  for (int64_t e = 0; e < n; ++e) {
+    const double *pe = par + e * ORC_NPARAM;
+    const double *ge = geo + (int64_t)types[e] * ORC_NGEO;
+    double *se = s + e * ORC_NSTATE, *ae = acc + e * 6, next[ORC_NSTATE], an[6];
+    int bad = 0;
+    for (int32_t j = 0; j < n_steps; ++j) {
+      int32_t seg = j / hold;
+      if (seg > n_seg - 1) seg = n_seg - 1;
+      const double *c = cmd + ((int64_t)seg * n + e) * ORC_MAXTHR;
+      bad |= orc_split_step(pe, ge, se, ae, c, h, flags, next, an);
+      memcpy(se, next, sizeof next);
+      memcpy(ae, an, sizeof an);
+    }
+    fails += bad ? 1 : 0;
+  }
+  return fails;
+}

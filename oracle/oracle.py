@@ -84,6 +84,13 @@ def lib():
                                            ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_int32, ctypes.c_double, ctypes.c_double, _D]
             L.orc_task_observe.restype = ctypes.c_double
+            L.orc_split_step.argtypes = [_D, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D,
+                                         _D]
+            L.orc_split_step.restype = ctypes.c_int
+            L.orc_split_rollout.argtypes = [ctypes.c_int64, _D, _D, _I32, _D, _D, _D,
+                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_double, ctypes.c_int32, ctypes.c_int32]
+            L.orc_split_rollout.restype = ctypes.c_int64
             _lib = L
     return _lib
 
@@ -261,3 +268,39 @@ def task_observe(task: int, s, centre, radius, omega, vz, psi_r, m, dt_look, t):
     err = lib().orc_task_observe(task, _p(_f64(s, (NSTATE,))), _p(_f64(centre, (4,))), radius,
                                  omega, vz, psi_r, m, dt_look, t, _p(obs))
     return obs, err
+
+
+# ------------------------------------------------------------------ split integration (§METHOD)
+
+def split_step(par, geo, s, a, c, h: float, flags: int = 0):
+    """One sub-step of the split scheme (rigid body by semi-implicit Euler, hydrodynamic term as
+    an external force with the previous acceleration ``a`` in its added-mass part).  Returns
+    (state, acceleration)."""
+    out = np.zeros(NSTATE)
+    a_out = np.zeros(6)
+    c8 = np.zeros(MAX_THR)
+    c = np.asarray(c, dtype=np.float64)
+    c8[:c.size] = c
+    rc = lib().orc_split_step(_p(_f64(par, (NPARAM,))), _p(_f64(geo, (NGEO,))),
+                              _p(_f64(s, (NSTATE,))), _p(_f64(a, (6,))), _p(c8), h, flags,
+                              _p(out), _p(a_out))
+    if rc != 0:
+        raise FloatingPointError("singular rigid-body mass matrix")
+    return out, a_out
+
+
+def split_rollout(par, geo, types, s0, a0, cmd, hold: int, n_steps: int, h: float = 0.01,
+                  flags: int = 0, nthreads: int = 0):
+    """Fleet rollout of the split scheme; returns (state [n, NSTATE], acceleration [n, 6])."""
+    par = _f64(par)
+    n = par.shape[0]
+    geo = _f64(geo).reshape(-1, NGEO)
+    types = np.ascontiguousarray(types, dtype=np.int32).reshape(n)
+    s = _f64(s0).reshape(n, NSTATE).copy()
+    a = _f64(a0).reshape(n, 6).copy()
+    cmd = _f64(cmd).reshape(-1, n, MAX_THR)
+    fails = lib().orc_split_rollout(n, _p(par), _p(geo), _p(types, _I32), _p(s), _p(a), _p(cmd),
+                                    cmd.shape[0], hold, n_steps, h, flags, nthreads)
+    if fails:
+        raise FloatingPointError(f"{fails} envs had a singular rigid-body mass matrix")
+    return s, a

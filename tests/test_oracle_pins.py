@@ -638,3 +638,120 @@ def test_task_observation_and_error():
         np.testing.assert_allclose(obs[6 * i:6 * i + 3], s[:3] - pr, atol=1e-12)
     assert abs(err - np.linalg.norm(s[:3] - O.task_reference(O.TASK_CIRCLE, c, 2.0, 0.5, 0.1,
                                                              7.0))) < 1e-12
+
+
+# ----------------------------------------------------------------------------- split scheme
+
+def split_run(par, geo, s0, c, n_steps, h=0.01, flags=0):
+    """Split-scheme sub-steps of one env from rest of the acceleration memory; returns the
+    states and accelerations after every sub-step."""
+    s, a = s0.copy(), np.zeros(6)
+    ss, aa = [], []
+    for _ in range(n_steps):
+        s, a = O.split_step(par, geo, s, a, c, h, flags)
+        ss.append(s)
+        aa.append(a)
+    return np.array(ss), np.array(aa)
+
+
+def stable_added_mass(par, scale=0.5):
+    p = par.copy()
+    p[I.P_MA:I.P_MA + 6] *= scale
+    return p
+
+
+def test_split_free_motion_is_semi_implicit_euler():
+    """No added mass, damping, restoring force or thrust: the body coasts, p_k = p_0 + k h v
+    exactly and q stays put (nothing is lagged when M_A = 0)."""
+    par = undamped(neutral(V.params))
+    par[I.P_MA:I.P_MA + 6] = 0.0
+    v = np.array([0.3, -0.2, 0.1])
+    s0 = state(p=(1.0, 2.0, 3.0), nu=(*v, 0, 0, 0))
+    ss, aa = split_run(par, GEO, s0, np.zeros(6), 50)
+    for k in (1, 10, 50):
+        np.testing.assert_allclose(ss[k - 1][I.S_P:I.S_P + 3], [1.0, 2.0, 3.0] + k * 0.01 * v,
+                                   rtol=1e-13)
+    np.testing.assert_allclose(ss[-1][I.S_Q:I.S_Q + 4], [1, 0, 0, 0], atol=1e-15)
+    assert np.abs(aa).max() < 1e-14  # v x (m v) rounds to ~1e-16, not to 0
+
+
+@pytest.mark.parametrize("ma_scale", [0.5, 1.2])
+def test_split_pure_surge_is_the_lagged_linear_recurrence(ma_scale):
+    """Pure surge, linear damping d, surge added mass a_m: the lagged added-mass force makes
+    a_k = -(d v_k + a_m a_{k-1}) / m and v_{k+1} = v_k + h a_k, i.e. the 2x2 linear map
+    [v_{k+1}; a_k] = A [v_k; a_{k-1}], solved here by matrix powers."""
+    par = neutral(V.params)
+    par[I.P_DQ:I.P_DQ + 6] = 0.0
+    m, d = par[I.P_M], par[I.P_DL]
+    am = ma_scale * m
+    par[I.P_MA] = am
+    h, K = 0.01, 120
+    ss, aa = split_run(par, GEO, state(nu=(0.4, 0, 0, 0, 0, 0)), np.zeros(6), K, h)
+    A = np.array([[1 - h * d / m, -h * am / m], [-d / m, -am / m]])
+    x = 0.0
+    for k in range(1, K + 1):
+        v_k, a_km1 = np.linalg.matrix_power(A, k) @ np.array([0.4, 0.0])
+        x += h * v_k  # semi-implicit: the position moves with the new velocity
+        if k in (1, 7, 60, K):
+            np.testing.assert_allclose(ss[k - 1][I.S_NU], v_k, rtol=1e-10, atol=1e-13)
+            np.testing.assert_allclose(aa[k - 1][0], a_km1, rtol=1e-10, atol=1e-13)
+            np.testing.assert_allclose(ss[k - 1][I.S_P], x, rtol=1e-10, atol=1e-13)
+    # the lagged added-mass mode has eigenvalue ~ -a_m/m: it dies out for a_m < m and grows
+    # (alternating in sign) for a_m > m, at the rate of A's dominant eigenvalue
+    lam = np.linalg.eigvals(A)
+    mode = lam[np.argmin(lam.real)]
+    assert abs(mode + am / m) < 0.02
+    if ma_scale > 1:
+        r = aa[K - 1][0] / aa[K - 2][0]
+        assert abs(r - mode.real) < 1e-6 and abs(aa[K - 1][0]) > 1e3 * abs(aa[0][0])
+
+
+def test_split_pure_yaw_attitude_update():
+    """Pure yaw with linear yaw damping and no added mass: r_k = r_0 (1 - h d / I)^k, and the
+    normalised update q + h/2 q (x) (0, 0, 0, r_k) turns the heading by 2 atan(h r_k / 2) with
+    the new rate r_k."""
+    par = neutral(V.params)
+    par[I.P_MA:I.P_MA + 6] = 0.0
+    par[I.P_DQ:I.P_DQ + 6] = 0.0
+    d, Iz, h, r0 = par[I.P_DL + 5], par[I.P_IG + 2], 0.01, 0.8
+    ss, _ = split_run(par, GEO, state(nu=(0, 0, 0, 0, 0, r0)), np.zeros(6), 200, h)
+    psi = 0.0
+    for k in range(1, 201):
+        r_k = r0 * (1 - h * d / Iz) ** k
+        psi += 2 * math.atan(h * r_k / 2)
+        if k in (1, 50, 200):
+            np.testing.assert_allclose(ss[k - 1][I.S_NU + 5], r_k, rtol=1e-12)
+            q = ss[k - 1][I.S_Q:I.S_Q + 4]
+            np.testing.assert_allclose(q, [math.cos(psi / 2), 0, 0, math.sin(psi / 2)],
+                                       atol=1e-12)
+
+
+def test_split_equilibrium_equals_the_coupled_one():
+    """At a steady state nu' = 0 and the lagged acceleration is 0, so the split scheme's fixed
+    point is the coupled Eq. 1's equilibrium: held throttles, both integrated to rest."""
+    par = stable_added_mass(V.params, 0.5)
+    c = np.array([0.6, 0.6, -0.6, -0.6, 0.3, -0.3])
+    ss, aa = split_run(par, GEO, state(), c, 10000)
+    s_rk4, _ = rollout1(par, GEO, state(), c, 10000)
+    assert np.abs(aa[-1]).max() < 1e-9
+    # (the held throttles spin the vehicle about the vertical: nu is steady, the heading is not,
+    # so the two runs' headings differ by their phase error and nu agrees to ~3e-8)
+    np.testing.assert_allclose(ss[-1][I.S_NU:I.S_NU + 6], s_rk4[I.S_NU:I.S_NU + 6], rtol=1e-6,
+                               atol=1e-8)
+
+
+def test_split_converges_to_the_coupled_solution_at_first_order():
+    """With every added mass below the rigid-body mass the split scheme is stable and its error
+    against the coupled equation (RK4 at a fine step) halves with h: first order."""
+    par = stable_added_mass(V.params, 0.5)
+    par[I.P_VC:I.P_VC + 3] = [0.1, -0.05, 0.02]
+    c = np.array([0.5, -0.3, 0.2, 0.4, -0.6, 0.1])
+    s0 = state(q=quat_from_euler(0.2, -0.1, 0.5), nu=(0.2, -0.1, 0.05, 0.1, -0.2, 0.15))
+    T = 1.0
+    ref, _ = rollout1(par, GEO, s0, c, 4000, h=T / 4000)
+    errs = []
+    for h in (0.01, 0.005, 0.0025):
+        ss, _ = split_run(par, GEO, s0, c, int(round(T / h)), h)
+        errs.append(np.abs(ss[-1][I.S_NU:I.S_NU + 6] - ref[I.S_NU:I.S_NU + 6]).max())
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 1.7 < e1 / e2 < 2.3, errs

@@ -184,6 +184,21 @@ mg_status mg_set_procedural_actions(mg_sim *sim, uint64_t cmd_seed, int32_t hold
  * most 16 kept).  Steps of one sim must therefore stay ordered on its stream. */
 mg_status mg_step(mg_sim *sim, int32_t k);
 
+/* Split-integration comparison step (§METHOD: the physics engine integrates the rigid-body term
+ * of Eq. 1 and the hydrodynamic term is applied to the body as an external force), for
+ * measuring the coupled (M_RB + M_A)^-1 step against the paper's own arrangement.  Per sub-step
+ * of dt: tau_h = -(M_A (a + [w x v_c^b; 0]) + C_A(nu_r) nu_r + D(nu_r) nu_r + g_A), then
+ * nu' = M_RB^-1 (tau + tau_h - C_RB(nu) nu - g_RB) and a semi-implicit Euler update (nu first,
+ * then p with the new v, q with the new w, renormalised; explicit Euler on the throttle lag);
+ * a <- nu'.  a stands in for the unknown nu' in the added-mass force (the previous sub-step's
+ * acceleration), which makes the scheme unstable in any degree of freedom whose added mass
+ * exceeds the rigid-body mass.  accel: device [6][n_envs] (component-major), in: the previous
+ * sub-step's acceleration (zeros at an episode start), out: the last sub-step's.  Uses and
+ * advances the action cursor like mg_step, the static grid with the sim's envs_per_block and
+ * steps_per_launch, no graph; non-finite states are flagged as by mg_step.  Errors: MG_EINVAL
+ * (k < 1, accel NULL or not device memory, a fleet with off-centre gravity). */
+mg_status mg_step_split(mg_sim *sim, int32_t k, float *accel);
+
 /* As mg_step with the work-queue schedule, for callers that must not allocate device memory
  * while they step (for instance a real-time control loop whose memory is fixed up front, or code
  * that runs with its memory pool capped): the call launches the work-queue kernel directly (no

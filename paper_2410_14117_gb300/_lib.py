@@ -83,6 +83,7 @@ SIGNATURES = {
     "mg_step": [_P, _I32],
     "mg_step_noalloc": [_P, _I32],
     "mg_step_record": [_P, _I32, _P],
+    "mg_step_split": [_P, _I32, _P],
     "mg_rollout_forward": [_P, _I32, _I32, _P, _P, ctypes.POINTER(_I64)],
     "mg_rollout_backward": [_P, _I32, _I32, _P, _P, _I64, _P, _P, _P],
     "mg_get_state": [_P, _P],

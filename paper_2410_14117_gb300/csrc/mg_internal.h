@@ -169,6 +169,12 @@ struct TaskView {
   float *err_sum;            // [n] Eq. 4 error summed over the episode's task steps
 };
 
+// Split-integration comparison step (mg_split.cu): k sub-steps of the engine-style scheme on the
+// static grid; raw [n][MG_NPARAM] parameter records, accel [6][n] acceleration memory (in/out).
+cudaError_t launch_split(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
+                         NtVariant ntv, const float *raw, float *accel, int32_t k,
+                         cudaStream_t stream);
+
 // Outputs and reset inputs of the fused task step.
 struct TaskOut {
   float *obs;        // [n][obs_dim]

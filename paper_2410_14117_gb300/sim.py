@@ -164,6 +164,13 @@ class Sim:
         call("mg_step_record", self._h, int(k), _ptr(traj))
         return traj
 
+    def step_split(self, k: int, accel):
+        """k sub-steps of the split-integration comparison scheme; ``accel`` [6, n] (device,
+        float32) carries the previous sub-step's acceleration in and the last one out."""
+        _check(accel, (6, self.n), torch.float32)
+        call("mg_step_split", self._h, int(k), _ptr(accel))
+        return accel
+
     # ------------------------------------------------------------------ task layer
     def set_task(self, task: int, centres, radius: float = 2.0, omega: float = 0.3,
                  vz: float = 0.1, psi_r: float = 0.0, lookahead: int = 4,

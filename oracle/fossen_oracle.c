@@ -43,6 +43,11 @@ enum {
 enum { ORC_MAXTHR = 8, ORC_NGEO = 1 + 6 * ORC_MAXTHR, ORC_NSTATE = 21 };
 enum { S_P = 0, S_Q = 3, S_NU = 7, S_N = 13 };
 enum { ORC_NO_CURRENT_ACCEL = 1 };
+/* Off-diagonal hydrodynamic extension (per env, optional): X_MA the 15 entries of M_A above its
+ * diagonal, row-major ((0,1), (0,2), ..., (4,5)), mirrored below it; X_DL the 30 off-diagonal
+ * entries of the linear damping D_l, row-major with the diagonal skipped.  The diagonals stay in
+ * the parameter record; an all-zero extension is the diagonal model. */
+enum { X_MA = 0, X_DL = 15, ORC_NXPARAM = 45 };
 
 /* ------------------------------------------------------------------ small linear algebra */
 
@@ -146,11 +151,22 @@ void orc_mass_rb(const double *par, double M[36]) {
   }
 }
 
-/* Added mass M_A (Eq. 1, hydrodynamic term): diagonal. */
-void orc_mass_a(const double *par, double M[36]) {
+/* Added mass M_A (Eq. 1, hydrodynamic term): the diagonal from the parameter record, the
+ * symmetric off-diagonal part from the extension x (NULL: none). */
+void orc_mass_a_x(const double *par, const double *x, double M[36]) {
   memset(M, 0, 36 * sizeof(double));
   for (int i = 0; i < 6; ++i) M[6 * i + i] = par[P_MA + i];
+  if (!x) return;
+  int t = X_MA;
+  for (int i = 0; i < 6; ++i)
+    for (int j = i + 1; j < 6; ++j) {
+      M[6 * i + j] = x[t];
+      M[6 * j + i] = x[t];
+      ++t;
+    }
 }
+
+void orc_mass_a(const double *par, double M[36]) { orc_mass_a_x(par, NULL, M); }
 
 /* Coriolis-centripetal matrix of a 6x6 inertia M evaluated at velocity x, in the momentum-block
  * form  C(x) = [[0, -S(M11 x1 + M12 x2)], [-S(M11 x1 + M12 x2), -S(M21 x1 + M22 x2)]]. */
@@ -184,16 +200,31 @@ void orc_coriolis_rb(const double *par, const double nu[6], double C[36]) {
 }
 
 /* C_A(nu_r) (Eq. 1), evaluated on the current-relative velocity. */
-void orc_coriolis_a(const double *par, const double nu_r[6], double C[36]) {
+void orc_coriolis_a_x(const double *par, const double *x, const double nu_r[6], double C[36]) {
   double M[36];
-  orc_mass_a(par, M);
+  orc_mass_a_x(par, x, M);
   coriolis_of(M, nu_r, C);
 }
 
-/* D(nu_r) (Eq. 1): linear plus quadratic diagonal damping, D = diag(Dl + Dq |nu_r|). */
-void orc_damping(const double *par, const double nu_r[6], double D[36]) {
+void orc_coriolis_a(const double *par, const double nu_r[6], double C[36]) {
+  orc_coriolis_a_x(par, NULL, nu_r, C);
+}
+
+/* D(nu_r) (Eq. 1): linear plus quadratic damping, D = D_l + diag(Dq |nu_r|), with D_l's
+ * diagonal from the parameter record and its off-diagonal entries from the extension x (NULL:
+ * none). */
+void orc_damping_x(const double *par, const double *x, const double nu_r[6], double D[36]) {
   memset(D, 0, 36 * sizeof(double));
   for (int i = 0; i < 6; ++i) D[6 * i + i] = par[P_DL + i] + par[P_DQ + i] * fabs(nu_r[i]);
+  if (!x) return;
+  int t = X_DL;
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j)
+      if (j != i) D[6 * i + j] = x[t++];
+}
+
+void orc_damping(const double *par, const double nu_r[6], double D[36]) {
+  orc_damping_x(par, NULL, nu_r, D);
 }
 
 /* Restoring vector g_RB(eta) + g_A(eta) (Eq. 1): weight W acts down (+z NED) at r_g, buoyancy B
@@ -235,9 +266,10 @@ void orc_thrust(const double *par, const double *geo, const double *n, double ta
   }
 }
 
-/* State derivative f(s; c).  s = (p, q, nu, n); returns 0, or -1 if M is singular. */
-int orc_rhs(const double *par, const double *geo, const double *s, const double *c, int flags,
-            double *ds) {
+/* State derivative f(s; c).  s = (p, q, nu, n); x: the off-diagonal extension or NULL.
+ * Returns 0, or -1 if M is singular. */
+int orc_rhs_x(const double *par, const double *x, const double *geo, const double *s,
+              const double *c, int flags, double *ds) {
   const double *q = s + S_Q, *nu = s + S_NU, *n = s + S_N;
   int nthr = (int)geo[0];
   double Rf[9], R[3][3];
@@ -256,10 +288,10 @@ int orc_rhs(const double *par, const double *geo, const double *s, const double 
 
   double Mrb[36], Ma[36], Crb[36], Ca[36], D[36], g[6], tau[6];
   orc_mass_rb(par, Mrb);
-  orc_mass_a(par, Ma);
+  orc_mass_a_x(par, x, Ma);
   orc_coriolis_rb(par, nu, Crb);
-  orc_coriolis_a(par, nu_r, Ca);
-  orc_damping(par, nu_r, D);
+  orc_coriolis_a_x(par, x, nu_r, Ca);
+  orc_damping_x(par, x, nu_r, D);
   orc_restoring(par, q, g);
   orc_thrust(par, geo, n, tau);
 
@@ -305,18 +337,23 @@ int orc_rhs(const double *par, const double *geo, const double *s, const double 
   return 0;
 }
 
+int orc_rhs(const double *par, const double *geo, const double *s, const double *c, int flags,
+            double *ds) {
+  return orc_rhs_x(par, NULL, geo, s, c, flags, ds);
+}
+
 /* One sub-step: classical RK4 of size h with the command held, then q <- q / |q|. */
-int orc_rk4_step(const double *par, const double *geo, const double *s, const double *c,
-                 double h, int flags, double *out) {
+int orc_rk4_step_x(const double *par, const double *x, const double *geo, const double *s,
+                   const double *c, double h, int flags, double *out) {
   double k1[ORC_NSTATE], k2[ORC_NSTATE], k3[ORC_NSTATE], k4[ORC_NSTATE], y[ORC_NSTATE];
   int err = 0;
-  err |= orc_rhs(par, geo, s, c, flags, k1);
+  err |= orc_rhs_x(par, x, geo, s, c, flags, k1);
   for (int i = 0; i < ORC_NSTATE; ++i) y[i] = s[i] + 0.5 * h * k1[i];
-  err |= orc_rhs(par, geo, y, c, flags, k2);
+  err |= orc_rhs_x(par, x, geo, y, c, flags, k2);
   for (int i = 0; i < ORC_NSTATE; ++i) y[i] = s[i] + 0.5 * h * k2[i];
-  err |= orc_rhs(par, geo, y, c, flags, k3);
+  err |= orc_rhs_x(par, x, geo, y, c, flags, k3);
   for (int i = 0; i < ORC_NSTATE; ++i) y[i] = s[i] + h * k3[i];
-  err |= orc_rhs(par, geo, y, c, flags, k4);
+  err |= orc_rhs_x(par, x, geo, y, c, flags, k4);
   for (int i = 0; i < ORC_NSTATE; ++i)
     out[i] = s[i] + h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
   double nq = sqrt(out[S_Q] * out[S_Q] + out[S_Q + 1] * out[S_Q + 1] +
@@ -325,14 +362,20 @@ int orc_rk4_step(const double *par, const double *geo, const double *s, const do
   return err;
 }
 
+int orc_rk4_step(const double *par, const double *geo, const double *s, const double *c,
+                 double h, int flags, double *out) {
+  return orc_rk4_step_x(par, NULL, geo, s, c, h, flags, out);
+}
+
 /* Fleet rollout.  For env e and step j (0-based), the command is cmd[seg][e][*] with
  * seg = min(j / hold, n_seg - 1).  par [n][NPARAM], types [n] index geo [n_types][NGEO],
  * s [n][NSTATE] is advanced in place; traj, if not NULL, receives the state after every step,
  * [n_steps][n][NSTATE].  nthreads <= 0 keeps the OpenMP default.  Returns the number of envs
  * whose solve failed. */
-int64_t orc_rollout(int64_t n, const double *par, const double *geo, const int32_t *types,
-                    double *s, const double *cmd, int32_t n_seg, int32_t hold, int32_t n_steps,
-                    double h, int32_t flags, double *traj, int32_t nthreads) {
+int64_t orc_rollout_x(int64_t n, const double *par, const double *xpar /*[n][NXPARAM] or NULL*/,
+                      const double *geo, const int32_t *types, double *s, const double *cmd,
+                      int32_t n_seg, int32_t hold, int32_t n_steps, double h, int32_t flags,
+                      double *traj, int32_t nthreads) {
   int64_t fails = 0;
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -340,6 +383,7 @@ int64_t orc_rollout(int64_t n, const double *par, const double *geo, const int32
 #endif
   for (int64_t e = 0; e < n; ++e) {
     const double *pe = par + e * ORC_NPARAM;
+    const double *xe = xpar ? xpar + e * ORC_NXPARAM : NULL;
     const double *ge = geo + (int64_t)types[e] * ORC_NGEO;
     double *se = s + e * ORC_NSTATE, next[ORC_NSTATE];
     int bad = 0;
@@ -347,13 +391,20 @@ int64_t orc_rollout(int64_t n, const double *par, const double *geo, const int32
       int32_t seg = j / hold;
       if (seg > n_seg - 1) seg = n_seg - 1;
       const double *c = cmd + ((int64_t)seg * n + e) * ORC_MAXTHR;
-      bad |= orc_rk4_step(pe, ge, se, c, h, flags, next);
+      bad |= orc_rk4_step_x(pe, xe, ge, se, c, h, flags, next);
       memcpy(se, next, sizeof next);
       if (traj) memcpy(traj + ((int64_t)j * n + e) * ORC_NSTATE, se, sizeof next);
     }
     fails += bad ? 1 : 0;
   }
   return fails;
+}
+
+int64_t orc_rollout(int64_t n, const double *par, const double *geo, const int32_t *types,
+                    double *s, const double *cmd, int32_t n_seg, int32_t hold, int32_t n_steps,
+                    double h, int32_t flags, double *traj, int32_t nthreads) {
+  return orc_rollout_x(n, par, NULL, geo, types, s, cmd, n_seg, hold, n_steps, h, flags, traj,
+                       nthreads);
 }
 
 int orc_max_threads(void) {
@@ -416,10 +467,12 @@ static const int RAND_IDX[27] = {
 /* Domain randomisation (§METHOD; §EXPERIMENTS "domain randomization"): every scalar of the
  * randomised set is the nominal value times U[lo, hi] (uniform j of stream 0, block j/4, word
  * j%4); the NED current is the nominal one plus current_sigma * N(0,1)^3 (stream 1, block 0,
- * Box-Muller on words (0,1) and (2,3)).  Counter = (gid lo, gid hi, stream, block), key = seed. */
+ * Box-Muller on words (0,1) and (2,3)); with rg_halfwidth > 0 the centre of gravity is the
+ * nominal one plus rg_halfwidth * (2u - 1) per axis (stream 0, block 7, words 0..2).
+ * Counter = (gid lo, gid hi, stream, block), key = seed. */
 void orc_randomize(int64_t n, uint64_t seed, double lo, double hi, double current_sigma,
-                   const double *nominal /*[n_types][NPARAM]*/, const int32_t *types,
-                   int64_t gid0, double *par /*[n][NPARAM]*/) {
+                   double rg_halfwidth, const double *nominal /*[n_types][NPARAM]*/,
+                   const int32_t *types, int64_t gid0, double *par /*[n][NPARAM]*/) {
   for (int64_t e = 0; e < n; ++e) {
     uint64_t gid = (uint64_t)(gid0 + e);
     const double *nom = nominal + (int64_t)types[e] * ORC_NPARAM;
@@ -435,6 +488,10 @@ void orc_randomize(int64_t n, uint64_t seed, double lo, double hi, double curren
     box_muller(u[0], u[1], &z[0], &z[1]);
     box_muller(u[2], u[3], &z[2], &z[3]);
     for (int i = 0; i < 3; ++i) pe[P_VC + i] = nom[P_VC + i] + current_sigma * z[i];
+    if (rg_halfwidth > 0.0) {
+      draw(seed, gid, 0u, 7u, u);
+      for (int i = 0; i < 3; ++i) pe[P_RG + i] = nom[P_RG + i] + rg_halfwidth * (2.0 * u[i] - 1.0);
+    }
   }
 }
 

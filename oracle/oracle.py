@@ -20,6 +20,7 @@ NSTATE = 21
 NGEO = 49
 MAX_THR = 8
 NO_CURRENT_ACCEL = 1
+NXPARAM = 45        # off-diagonal extension: M_A above the diagonal (15), D_l off-diagonal (30)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fossen_oracle.c")
@@ -71,8 +72,17 @@ def lib():
             L.orc_max_threads.restype = ctypes.c_int
             L.orc_philox4x32_10.argtypes = [_U32, _U32, _U32]
             L.orc_randomize.argtypes = [ctypes.c_int64, ctypes.c_uint64, ctypes.c_double,
-                                        ctypes.c_double, ctypes.c_double, _D, _I32,
-                                        ctypes.c_int64, _D]
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, _D,
+                                        _I32, ctypes.c_int64, _D]
+            L.orc_mass_a_x.argtypes = [_D, _D, _D]
+            L.orc_coriolis_a_x.argtypes = [_D, _D, _D, _D]
+            L.orc_damping_x.argtypes = [_D, _D, _D, _D]
+            L.orc_rhs_x.argtypes = [_D, _D, _D, _D, _D, ctypes.c_int, _D]
+            L.orc_rhs_x.restype = ctypes.c_int
+            L.orc_rollout_x.argtypes = [ctypes.c_int64, _D, _D, _D, _I32, _D, _D, ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                        ctypes.c_int32, _D, ctypes.c_int32]
+            L.orc_rollout_x.restype = ctypes.c_int64
             L.orc_reset_state.argtypes = [ctypes.c_uint64, ctypes.c_double, ctypes.c_int64,
                                           ctypes.c_uint32, _D]
             L.orc_commands.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint32,
@@ -127,20 +137,34 @@ def mass_rb(par):
     return _mat("orc_mass_rb", par)
 
 
-def mass_a(par):
-    return _mat("orc_mass_a", par)
+def mass_a(par, xpar=None):
+    if xpar is None:
+        return _mat("orc_mass_a", par)
+    out = np.zeros(36)
+    lib().orc_mass_a_x(_p(_f64(par, (NPARAM,))), _p(_f64(xpar, (NXPARAM,))), _p(out))
+    return out.reshape(6, 6)
 
 
 def coriolis_rb(par, nu):
     return _mat("orc_coriolis_rb", par, nu)
 
 
-def coriolis_a(par, nu_r):
-    return _mat("orc_coriolis_a", par, nu_r)
+def coriolis_a(par, nu_r, xpar=None):
+    if xpar is None:
+        return _mat("orc_coriolis_a", par, nu_r)
+    out = np.zeros(36)
+    lib().orc_coriolis_a_x(_p(_f64(par, (NPARAM,))), _p(_f64(xpar, (NXPARAM,))),
+                           _p(_f64(nu_r, (6,))), _p(out))
+    return out.reshape(6, 6)
 
 
-def damping(par, nu_r):
-    return _mat("orc_damping", par, nu_r)
+def damping(par, nu_r, xpar=None):
+    if xpar is None:
+        return _mat("orc_damping", par, nu_r)
+    out = np.zeros(36)
+    lib().orc_damping_x(_p(_f64(par, (NPARAM,))), _p(_f64(xpar, (NXPARAM,))),
+                        _p(_f64(nu_r, (6,))), _p(out))
+    return out.reshape(6, 6)
 
 
 def restoring(par, q) -> np.ndarray:
@@ -159,13 +183,14 @@ def thrust(par, geo, n) -> np.ndarray:
     return tau
 
 
-def rhs(par, geo, s, c, flags: int = 0) -> np.ndarray:
+def rhs(par, geo, s, c, flags: int = 0, xpar=None) -> np.ndarray:
     ds = np.zeros(NSTATE)
     c8 = np.zeros(MAX_THR)
     c = np.asarray(c, dtype=np.float64)
     c8[:c.size] = c
-    rc = lib().orc_rhs(_p(_f64(par, (NPARAM,))), _p(_f64(geo, (NGEO,))), _p(_f64(s, (NSTATE,))),
-                       _p(c8), flags, _p(ds))
+    xp = None if xpar is None else _p(_f64(xpar, (NXPARAM,)))
+    rc = lib().orc_rhs_x(_p(_f64(par, (NPARAM,))), xp, _p(_f64(geo, (NGEO,))),
+                         _p(_f64(s, (NSTATE,))), _p(c8), flags, _p(ds))
     if rc != 0:
         raise FloatingPointError("singular mass matrix")
     return ds
@@ -186,7 +211,7 @@ def rk4_step(par, geo, s, c, h: float, flags: int = 0) -> np.ndarray:
 # ------------------------------------------------------------------ fleet rollout
 
 def rollout(par, geo, types, s0, cmd, hold: int, n_steps: int, h: float = 0.01,
-            flags: int = 0, record: bool = False, nthreads: int = 0):
+            flags: int = 0, record: bool = False, nthreads: int = 0, xpar=None):
     """Advance every env ``n_steps`` RK4 steps.
 
     par [n, NPARAM]; geo [n_types, NGEO]; types int [n]; s0 [n, NSTATE]; cmd [n_seg, n, 8] with
@@ -199,9 +224,10 @@ def rollout(par, geo, types, s0, cmd, hold: int, n_steps: int, h: float = 0.01,
     s = _f64(s0).reshape(n, NSTATE).copy()
     cmd = _f64(cmd).reshape(-1, n, MAX_THR)
     traj = np.zeros((n_steps, n, NSTATE)) if record else None
-    fails = lib().orc_rollout(n, _p(par), _p(geo), _p(types, _I32), _p(s), _p(cmd),
-                              cmd.shape[0], hold, n_steps, h, flags,
-                              _p(traj) if record else None, nthreads)
+    xp = None if xpar is None else _f64(xpar).reshape(n, NXPARAM)
+    fails = lib().orc_rollout_x(n, _p(par), _p(xp) if xp is not None else None, _p(geo),
+                                _p(types, _I32), _p(s), _p(cmd), cmd.shape[0], hold, n_steps, h,
+                                flags, _p(traj) if record else None, nthreads)
     if fails:
         raise FloatingPointError(f"{fails} envs had a singular mass matrix")
     return (s, traj) if record else s
@@ -222,13 +248,13 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 
 
 def randomize(seed: int, nominal, types, lo: float = 0.8, hi: float = 1.2,
-              current_sigma: float = 0.2, gid0: int = 0) -> np.ndarray:
+              current_sigma: float = 0.2, gid0: int = 0, rg_halfwidth: float = 0.0) -> np.ndarray:
     """Per-env domain-randomised parameters [n, NPARAM] (FP64)."""
     nominal = _f64(nominal).reshape(-1, NPARAM)
     types = np.ascontiguousarray(types, dtype=np.int32)
     out = np.zeros((types.size, NPARAM))
-    lib().orc_randomize(types.size, seed, lo, hi, current_sigma, _p(nominal), _p(types, _I32),
-                        gid0, _p(out))
+    lib().orc_randomize(types.size, seed, lo, hi, current_sigma, rg_halfwidth, _p(nominal),
+                        _p(types, _I32), gid0, _p(out))
     return out
 
 

@@ -755,3 +755,130 @@ def test_split_converges_to_the_coupled_solution_at_first_order():
         errs.append(np.abs(ss[-1][I.S_NU:I.S_NU + 6] - ref[I.S_NU:I.S_NU + 6]).max())
     for e1, e2 in zip(errs, errs[1:]):
         assert 1.7 < e1 / e2 < 2.3, errs
+
+
+# ----------------------------------------------------------------------------- full M_A and D
+
+def xpar_from_matrices(MA, DL):
+    """Pack a full symmetric M_A and a full D_l into the off-diagonal extension: M_A above the
+    diagonal row-major, then D_l's off-diagonal entries row-major."""
+    up = [MA[i, j] for i in range(6) for j in range(i + 1, 6)]
+    off = [DL[i, j] for i in range(6) for j in range(6) if j != i]
+    return np.array(up + off)
+
+
+def random_hydro(g, par):
+    """A random symmetric positive-definite M_A and a D_l with positive-definite symmetric part,
+    keeping the record's diagonals (so that the two stay consistent)."""
+    A = g.normal(size=(6, 6)) * 0.3
+    MA = A @ A.T + np.diag(par[I.P_MA:I.P_MA + 6])
+    B = g.normal(size=(6, 6)) * 0.4
+    DL = B @ B.T + np.diag(par[I.P_DL:I.P_DL + 6]) + 0.5 * (g.normal(size=(6, 6)) -
+                                                             g.normal(size=(6, 6)).T)
+    p = par.copy()
+    p[I.P_MA:I.P_MA + 6] = np.diag(MA)
+    p[I.P_DL:I.P_DL + 6] = np.diag(DL)
+    return p, MA, DL
+
+
+def test_extension_layout_builds_the_full_matrices():
+    g = np.random.default_rng(3)
+    p, MA, DL = random_hydro(g, V.params)
+    x = xpar_from_matrices(MA, DL)
+    np.testing.assert_array_equal(O.mass_a(p, x), MA)
+    nu = g.normal(size=6)
+    want = DL + np.diag(p[I.P_DQ:I.P_DQ + 6] * np.abs(nu))
+    np.testing.assert_allclose(O.damping(p, nu, x), want, rtol=1e-15, atol=1e-15)
+    # a zero extension is the diagonal model
+    np.testing.assert_array_equal(O.mass_a(V.params, np.zeros(O.NXPARAM)), O.mass_a(V.params))
+
+
+def test_full_added_mass_coriolis_skew_symmetric():
+    g = np.random.default_rng(11)
+    for _ in range(200):
+        p, MA, DL = random_hydro(g, V.params)
+        x = xpar_from_matrices(MA, DL)
+        nu = g.normal(size=6)
+        C = O.coriolis_a(p, nu, x)
+        np.testing.assert_allclose(C, -C.T, atol=1e-15)
+        assert abs(nu @ C @ nu) <= 1e-13 * (1 + np.abs(C).max() * nu @ nu)
+
+
+def test_full_hydro_power_balance():
+    """No current, thrust or restoring force: d/dt (1/2 nu^T M nu) = nu^T M nu' must equal
+    -nu^T D(nu) nu (the Coriolis terms do no work), with M = M_RB + M_A and D built here from
+    the extension's documented layout, r_g off centre."""
+    g = np.random.default_rng(12)
+    for _ in range(100):
+        p, MA, DL = random_hydro(g, neutral(V.params))
+        p[I.P_RG:I.P_RG + 3] = g.uniform(-0.03, 0.03, 3)
+        p[I.P_RB:I.P_RB + 3] = p[I.P_RG:I.P_RG + 3]
+        x = xpar_from_matrices(MA, DL)
+        nu = g.normal(size=6)
+        ds = O.rhs(p, GEO, state(q=quat_from_euler(*g.uniform(-1, 1, 3)), nu=nu), np.zeros(6),
+                   xpar=x)
+        M = O.mass_rb(p) + MA
+        D = DL + np.diag(p[I.P_DQ:I.P_DQ + 6] * np.abs(nu))
+        lhs = nu @ M @ ds[I.S_NU:I.S_NU + 6]
+        assert abs(lhs + nu @ D @ nu) <= 1e-12 * (1 + abs(nu @ D @ nu))
+
+
+def test_full_added_mass_energy_conserved_undamped():
+    """Undamped, neutral, no thrust: Kirchhoff's equations with a full M_A conserve
+    T = 1/2 nu^T (M_RB + M_A) nu; RK4's drift over 1 s is tiny and falls ~16x per halving."""
+    g = np.random.default_rng(13)
+    p, MA, _ = random_hydro(g, neutral(V.params))
+    p = undamped(p)
+    x = xpar_from_matrices(MA, np.zeros((6, 6)))
+    M = O.mass_rb(p) + MA
+    s0 = state(nu=(0.4, -0.3, 0.2, 0.8, -0.6, 0.5))
+    T0 = 0.5 * s0[I.S_NU:I.S_NU + 6] @ M @ s0[I.S_NU:I.S_NU + 6]
+    drift = []
+    for h in (0.02, 0.01):
+        s, _ = O.rollout(p[None], GEO[None], [0], s0[None], np.zeros((1, 1, 8)), 1,
+                         int(round(1.0 / h)), h=h, record=True, xpar=x[None])
+        nu = s[0, I.S_NU:I.S_NU + 6]
+        drift.append(abs(0.5 * nu @ M @ nu - T0) / T0)
+    assert drift[1] < 1e-8 and drift[0] / drift[1] > 10, drift
+
+
+def test_randomize_centre_of_gravity():
+    from scipy import stats
+    n = 20000
+    types = np.zeros(n, dtype=np.int32)
+    nom = np.stack([V.params, VH.params])
+    par = O.randomize(1234, nom, types, 0.8, 1.2, 0.2, rg_halfwidth=0.02)
+    base = O.randomize(1234, nom, types, 0.8, 1.2, 0.2)
+    # only r_g changes, and it is nominal + U[-w, w] per axis, independent across axes
+    others = [i for i in range(I.NPARAM) if not I.P_RG <= i < I.P_RG + 3]
+    np.testing.assert_array_equal(par[:, others], base[:, others])
+    d = par[:, I.P_RG:I.P_RG + 3] - V.params[I.P_RG:I.P_RG + 3]
+    assert np.abs(d).max() <= 0.02
+    for j in range(3):
+        assert stats.kstest((d[:, j] + 0.02) / 0.04, "uniform").pvalue > 1e-4
+    assert abs(np.corrcoef(d[:, 0], d[:, 2])[0, 1]) < 0.05
+
+
+def test_full_added_mass_impulse_conserved():
+    """Kirchhoff: for the unforced body in still water the impulses of P = (M_RB + M_A) nu are
+    constant in the inertial frame, linear R(q) P1 and angular R(q) P2 + p x R(q) P1, only if
+    the Coriolis terms are built from the same full M_A as the inertia (energy alone cannot
+    tell)."""
+    g = np.random.default_rng(14)
+    p, MA, _ = random_hydro(g, neutral(V.params))
+    p = undamped(p)
+    p[I.P_RG:I.P_RG + 3] = [0.01, -0.02, 0.015]
+    p[I.P_RB:I.P_RB + 3] = p[I.P_RG:I.P_RG + 3]
+    x = xpar_from_matrices(MA, np.zeros((6, 6)))
+    M = O.mass_rb(p) + MA
+    s0 = state(q=quat_from_euler(0.3, -0.2, 0.7), nu=(0.4, -0.3, 0.2, 0.8, -0.6, 0.5))
+
+    def impulses(s):
+        R = O.rotation(s[I.S_Q:I.S_Q + 4])
+        P = M @ s[I.S_NU:I.S_NU + 6]
+        L = R @ P[:3]
+        return np.r_[L, R @ P[3:] + np.cross(s[I.S_P:I.S_P + 3], L)]
+
+    s, _ = O.rollout(p[None], GEO[None], [0], s0[None], np.zeros((1, 1, 8)), 1, 200, h=0.005,
+                     record=True, xpar=x[None])
+    np.testing.assert_allclose(impulses(s[0]), impulses(s0), rtol=0, atol=1e-8)

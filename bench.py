@@ -477,6 +477,7 @@ def run_ours(args):
         line["adjoint"] = bench_adjoint(vs)
         line["task"] = bench_task(vs)
         line["split"] = bench_split(vs)
+        line["full_hydro"] = bench_full_hydro(vs)
         line["serve"] = bench_serve(vs, args.serve_seconds)
 
     if world == 1 and rank == 0 and not args.no_cpu:
@@ -701,6 +702,38 @@ def bench_split(vs, n=65536, horizon=1000, n_acc=4096, reps=3):
                         "diverged": float(blown.mean()),
                         "diverged_among_predicted_stable": float(blown[~predicted].mean())
                         if (~predicted).any() else None}
+    return out
+
+
+def bench_full_hydro(vs, n=65536, horizon=1000, reps=3):
+    """Full (non-diagonal) added mass and linear damping with randomised centres of gravity:
+    the general path with the off-diagonal coefficients staged per block, against the
+    diagonal-mass path, same fleet size and workload."""
+    import numpy as np
+    import torch
+    from paper_2410_14117_gb300 import inputs as I
+    from paper_2410_14117_gb300.sim import Sim
+
+    out = {"workload": f"{n:,} BlueROV2 envs, parameters x U[0.8,1.2], current N(0,0.2), "
+                       f"{horizon:,} sub-steps, procedural commands held 10; full: r_g ~ "
+                       "U[-2, 2] cm per axis and off-diagonal M_A, D_l at 15 % coupling"}
+    for name in ("diagonal", "full"):
+        sim = Sim(n, np.zeros(n, np.int32), vs)
+        sim.set_launch(128, horizon, True)
+        if name == "full":
+            sim.randomize(1234, 0.8, 1.2, 0.2, 0.3, rg_halfwidth=0.02)
+            p = sim.get_params().double().cpu().numpy()
+            sim.set_hydro_offdiag(torch.tensor(I.hydro_offdiag(9, p), dtype=torch.float32,
+                                               device="cuda"))
+        else:
+            sim.randomize(1234, 0.8, 1.2, 0.2, 0.3)
+        sim.reset()
+        sim.set_procedural_actions(5678, 10)
+        ms = _time_episodes(lambda: sim.step(horizon), reps)
+        assert sim.sync() == 0
+        sim.close()
+        out[f"{name}_env_substeps_per_s"] = n * horizon / (ms / 1e3)
+    out["full_over_diagonal"] = out["full_env_substeps_per_s"] / out["diagonal_env_substeps_per_s"]
     return out
 
 

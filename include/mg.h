@@ -59,6 +59,14 @@ extern "C" {
 #define MG_P_TAU 31
 #define MG_P_VC 32
 
+/* Off-diagonal hydrodynamic extension (MG_NXPARAM floats per env, optional; mg_set_hydro_offdiag):
+ *   0..14  added mass M_A above its diagonal, row-major: (0,1) (0,2) (0,3) (0,4) (0,5) (1,2)
+ *          (1,3) (1,4) (1,5) (2,3) (2,4) (2,5) (3,4) (3,5) (4,5); M_A is symmetric
+ *   15..44 linear damping D_l off its diagonal, row-major with the diagonal skipped:
+ *          (0,1)..(0,5) (1,0) (1,2)..(1,5) ... (5,0)..(5,4)
+ * The diagonals stay in the parameter record; an all-zero extension is the diagonal model. */
+#define MG_NXPARAM 45
+
 typedef struct mg_sim mg_sim; /* opaque; owns all of a fleet's device buffers */
 
 typedef enum {
@@ -86,13 +94,16 @@ typedef struct {
 
 /* Domain-randomisation ranges (§METHOD "physical parameter domain randomization"): each of the
  * 27 scalars m, Ixx, Iyy, Izz, M_A(6), Dl(6), Dq(6), W, B, r_b.z, k_T, tau_m is scaled by
- * U[lo, hi]; the NED current is N(0, current_sigma) per axis; mg_reset draws the initial body
+ * U[lo, hi]; the NED current is N(0, current_sigma) per axis; with rg_halfwidth > 0 the centre
+ * of gravity is the nominal one plus U[-rg_halfwidth, rg_halfwidth] m per axis (off-centre
+ * gravity: the fleet then takes the general mass-matrix path); mg_reset draws the initial body
  * velocity N(0, nu0_sigma) per component.  flags must be 0. */
 typedef struct {
   float lo, hi;
   float current_sigma;
   float nu0_sigma;
   uint32_t flags;
+  float rg_halfwidth;
 } mg_ranges;
 
 /* Model switch: drop the added-mass inertia of the current, M_A [omega x v_c^b; 0], which
@@ -158,6 +169,19 @@ mg_status mg_set_params(mg_sim *sim, const float *in);
 
 /* Copy every env's parameters into out [n][MG_NPARAM] (host or device). */
 mg_status mg_get_params(mg_sim *sim, float *out);
+
+/* Full (non-diagonal) added mass and linear damping: set every env's off-diagonal extension from
+ * x [n][MG_NXPARAM] (host or device; layout above), or clear it (x = NULL: the diagonal model).
+ * The mass matrices are re-inverted in FP64 with the off-diagonal added mass; a fleet with a
+ * non-zero extension steps on the general path (static grid: mg_set_schedule's work queue is
+ * not used for it; mg_step_split and mg_rollout_backward reject it).  mg_randomize and
+ * mg_set_params keep the extension.  Synchronous.  Errors: MG_EINVAL, MG_ENOMEM, MG_ENOTSPD
+ * (stored, but some M_RB + M_A is not positive definite), MG_ECUDA. */
+mg_status mg_set_hydro_offdiag(mg_sim *sim, const float *x);
+
+/* Copy every env's off-diagonal extension into out [n][MG_NXPARAM] (host or device; zeros when
+ * none is set). */
+mg_status mg_get_hydro_offdiag(mg_sim *sim, float *out);
 
 /* Throttle actions (Eq. 3: one throttle setting per thruster).  a: host or device
  * [n_seg][n_envs][MG_MAX_THR], entries past a vehicle's thruster count ignored.  The library

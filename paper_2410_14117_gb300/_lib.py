@@ -11,6 +11,7 @@ import threading
 from . import build as _build
 
 MG_NPARAM = 35
+MG_NXPARAM = 45
 MG_NSTATE = 21
 MG_NTRAJ = 13
 MG_MAX_THR = 8
@@ -42,7 +43,7 @@ class VehicleParams(ctypes.Structure):
 class Ranges(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_float), ("hi", ctypes.c_float),
                 ("current_sigma", ctypes.c_float), ("nu0_sigma", ctypes.c_float),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("rg_halfwidth", ctypes.c_float)]
 
 
 class TaskSpec(ctypes.Structure):
@@ -84,6 +85,8 @@ SIGNATURES = {
     "mg_step_noalloc": [_P, _I32],
     "mg_step_record": [_P, _I32, _P],
     "mg_step_split": [_P, _I32, _P],
+    "mg_set_hydro_offdiag": [_P, _P],
+    "mg_get_hydro_offdiag": [_P, _P],
     "mg_rollout_forward": [_P, _I32, _I32, _P, _P, ctypes.POINTER(_I64)],
     "mg_rollout_backward": [_P, _I32, _I32, _P, _P, _I64, _P, _P, _P],
     "mg_get_state": [_P, _P],

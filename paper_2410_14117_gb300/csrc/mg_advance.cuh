@@ -11,6 +11,9 @@ namespace mg {
 // general step keeps 168.
 constexpr int kRegsDiag = 128;
 constexpr int kRegsGeneral = 168;
+// With the off-diagonal hydrodynamics the 45 extra coefficients stay in registers too (no
+// spills up to 255; 8 resident warps per SM).
+constexpr int kRegsXH = 255;
 
 // Action cursor at the start of the launch's mg_step call (read through L2: the previous call's
 // last block wrote it).
@@ -52,6 +55,16 @@ __device__ __forceinline__ void finish_envs(const FleetView &fv, unsigned *s_don
       atomicExch(fv.done_blocks, 0u);
     }
   }
+}
+
+// Stage a block's off-diagonal hydrodynamic coefficients in shared memory: row t of sx (stride
+// MG_NXPARAM, coprime with the 32 banks) receives env env0 + t's coefficients from the
+// component-major planes xh [MG_NXPARAM][n] (each component read coalesced).
+__device__ __forceinline__ void stage_xh(const float *__restrict__ xh, int64_t n, int64_t env0,
+                                         int count, float *sx) {
+  for (int c = 0; c < MG_NXPARAM; ++c)
+    for (int t = threadIdx.x; t < count; t += blockDim.x)
+      sx[t * MG_NXPARAM + c] = __ldg(xh + (int64_t)c * n + env0 + t);
 }
 
 template <int MT>
@@ -105,10 +118,12 @@ __device__ __forceinline__ bool all_finite(const St<MT> &s) {
 // Advance env e by k sub-steps starting at action-cursor position step0, leaving the result in
 // s (the caller stores it: store_and_flag, or a fused epilogue).  L2: state loads bypass L1
 // (work-queue schedule, where another SM may have written them).
-template <int MT, bool DIAG, bool MIXED, bool REC, bool L2, int NH>
+// XH: xh is the env's row of staged off-diagonal hydrodynamic coefficients.
+template <int MT, bool DIAG, bool MIXED, bool REC, bool L2, int NH, bool XH = false>
 __device__ __forceinline__ void advance_env(const FleetView &fv, int64_t e, int nt,
                                             const float4 *gdir, const float4 *garm,
-                                            int64_t step0, int32_t k, float *traj, St<MT> &s) {
+                                            int64_t step0, int32_t k, float *traj, St<MT> &s,
+                                            const float *xh = nullptr) {
   const bool current_accel = !(fv.model_flags & MG_MODEL_NO_CURRENT_ACCEL);
   const float h = fv.dt;
 
@@ -128,7 +143,7 @@ __device__ __forceinline__ void advance_env(const FleetView &fv, int64_t e, int 
       left = fv.hold;
       load_commands<MT>(fv, e, seg, nt, P.itau, c);
     }
-    rk4_step<MT, DIAG, MIXED, NH>(s, c, P, gdir, garm, nt, current_accel, h);
+    rk4_step<MT, DIAG, MIXED, NH, XH>(s, c, P, gdir, garm, nt, current_accel, h, xh);
     --left;
     if constexpr (REC) record<MT>(traj + (int64_t)it * MG_NTRAJ * fv.n, fv.n, e, s);
   }

@@ -103,6 +103,9 @@ struct mg_sim {
                                            // [2] work-queue wait time-outs, [3] action
                                            // cursor, [4] finished-block count
   unsigned int *offdiag = nullptr;
+  // off-diagonal hydrodynamics, [MG_NXPARAM][n] planes (mg_set_hydro_offdiag), and whether set
+  float *xh = nullptr;
+  bool has_xh = false;
 
   // static-schedule blocks
   BlockDesc *blocks_d = nullptr;
@@ -181,6 +184,7 @@ struct mg_sim {
     v.dt = dt;
     v.flags = flags;
     v.counters = counters;
+    v.xh = has_xh ? xh : nullptr;
     v.cursor = reinterpret_cast<int64_t *>(counters + 3);
     v.done_blocks = reinterpret_cast<unsigned int *>(counters + 4);
     return v;
@@ -195,6 +199,7 @@ struct mg_sim {
     v.pa = pa;
     v.n_not_spd = counters + 1;
     v.any_offdiag = offdiag;
+    v.xh = has_xh ? xh : nullptr;
     return v;
   }
 
@@ -272,7 +277,7 @@ mg_status build_blocks(mg_sim *s) {
 // call, and the last advances the cursor by k.
 mg_status launch_chunks(mg_sim *s, int32_t k, float *traj, cudaStream_t stream) {
   FleetView v = s->view();
-  if (s->queue && !traj) {
+  if (s->queue && !traj && !s->has_xh) {
     v.cursor_adv = k;
     MG_CK(launch_fleet_queue(v, s->slices_d, s->n_slices, s->ntv, s->diag, s->structured,
                              s->queue_wide, s->queue_warps_per_sm, k, s->spl, s->sched, s->n_sm,
@@ -305,7 +310,7 @@ mg_status finish_params(mg_sim *s) {
   MG_CK(cudaMemcpyAsync(&off, s->offdiag, sizeof off, cudaMemcpyDeviceToHost, s->stream));
   mg_status st = read_counter(s, 1, &bad);
   if (st != MG_OK) return st;
-  const bool diag = (off == 0);
+  const bool diag = (off == 0) && !s->has_xh;  // the extension always takes the general path
   if (diag != s->diag) s->drop_graphs();
   s->diag = diag;
   if (bad) {
@@ -369,6 +374,8 @@ const char *mg_last_error(void) { return g_err.c_str(); }
 mg_status mg_step_noalloc(mg_sim *s, int32_t k) {
   MG_NONNULL(s);
   if (k < 1) return fail(MG_EINVAL, "k must be >= 1");
+  if (s->has_xh)
+    return fail(MG_EINVAL, "the work-queue kernel has no off-diagonal hydrodynamics variant");
   if (s->n_slices > kNoAllocMaxSlices) {
     char buf[200];
     snprintf(buf, sizeof buf,
@@ -542,7 +549,7 @@ mg_status mg_create(int64_t n_envs, const int32_t *vehicle_types,
                     cudaMemcpyHostToDevice));
   MG_CKB(cudaMemset(s->offdiag, 0, sizeof(unsigned int)));
   // Nominal parameters: a randomisation with zero width.
-  MG_CKB(launch_randomize(s->setup_view(), s->nominal_d, 0, 1.0, 1.0, 0.0, s->stream));
+  MG_CKB(launch_randomize(s->setup_view(), s->nominal_d, 0, 1.0, 1.0, 0.0, 0.0, s->stream));
   if ((st = finish_params(s)) != MG_OK) return bail(st);
   // Zero state with identity attitude.
   MG_CKB(cudaMemset(s->arena, 0, o_s5 + 4 * n));
@@ -566,6 +573,7 @@ mg_status mg_destroy(mg_sim *s) {
   cudaFree(s->task_buf);
   cudaFree(s->act);
   cudaFree(s->stage);
+  cudaFree(s->xh);
   cudaFree(s->arena);
   delete s;
   return MG_OK;
@@ -631,12 +639,13 @@ mg_status mg_randomize(mg_sim *s, uint64_t seed, const mg_ranges *r) {
   MG_NONNULL(s);
   MG_NONNULL(r);
   if (!(r->lo > 0.f) || !(r->lo <= r->hi) || !(r->current_sigma >= 0.f) ||
-      !(r->nu0_sigma >= 0.f) || r->flags != 0)
-    return fail(MG_EINVAL, "ranges: need 0 < lo <= hi, sigmas >= 0, flags == 0");
+      !(r->nu0_sigma >= 0.f) || r->flags != 0 || !(r->rg_halfwidth >= 0.f))
+    return fail(MG_EINVAL,
+                "ranges: need 0 < lo <= hi, sigmas >= 0, rg_halfwidth >= 0, flags == 0");
   mg_status st = begin_params(s);
   if (st != MG_OK) return st;
   MG_CK(launch_randomize(s->setup_view(), s->nominal_d, seed, (double)r->lo, (double)r->hi,
-                         (double)r->current_sigma, s->stream));
+                         (double)r->current_sigma, (double)r->rg_halfwidth, s->stream));
   MG_CK(cudaMemsetAsync(s->episode, 0, 4 * s->n, s->stream));
   s->reset_seed = seed;
   s->nu0_sigma = (double)r->nu0_sigma;
@@ -667,6 +676,53 @@ mg_status mg_get_params(mg_sim *s, float *out) {
   MG_CK(launch_export_params(s->setup_view(), static_cast<float *>(s->stage), s->stream));
   MG_CK(cudaMemcpyAsync(out, s->stage, bytes, cudaMemcpyDeviceToHost, s->stream));
   MG_CK(cudaStreamSynchronize(s->stream));
+  return MG_OK;
+}
+
+mg_status mg_set_hydro_offdiag(mg_sim *s, const float *x) {
+  MG_NONNULL(s);
+  mg_status st;
+  if (x) {
+    const size_t bytes = (size_t)s->n * MG_NXPARAM * 4;
+    const void *d = nullptr;
+    if ((st = input_ptr(s, x, bytes, &d)) != MG_OK) return st;
+    if (!s->xh) {
+      MG_CK(cudaStreamSynchronize(s->stream));
+      if (cudaMalloc(&s->xh, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        s->xh = nullptr;
+        return fail(MG_ENOMEM, "cudaMalloc(off-diagonal hydrodynamics)");
+      }
+    }
+    MG_CK(launch_xh_transpose(static_cast<const float *>(d), s->xh, s->n, true, s->stream));
+  }
+  s->has_xh = (x != nullptr);
+  s->drop_graphs();
+  // re-derive every env's planes (M^-1 with the off-diagonal added mass) from its own record
+  if ((st = begin_params(s)) != MG_OK) return st;
+  MG_CK(launch_import_params(s->setup_view(), s->raw, s->stream));
+  return finish_params(s);
+}
+
+mg_status mg_get_hydro_offdiag(mg_sim *s, float *out) {
+  MG_NONNULL(s);
+  MG_NONNULL(out);
+  const size_t bytes = (size_t)s->n * MG_NXPARAM * 4;
+  const bool dev = is_device_ptr(out);
+  float *dst = out;
+  if (!dev) {
+    mg_status st = ensure_stage(s, bytes);
+    if (st != MG_OK) return st;
+    dst = static_cast<float *>(s->stage);
+  }
+  if (s->has_xh)
+    MG_CK(launch_xh_transpose(s->xh, dst, s->n, false, s->stream));
+  else
+    MG_CK(cudaMemsetAsync(dst, 0, bytes, s->stream));
+  if (!dev) {
+    MG_CK(cudaMemcpyAsync(out, s->stage, bytes, cudaMemcpyDeviceToHost, s->stream));
+    MG_CK(cudaStreamSynchronize(s->stream));
+  }
   return MG_OK;
 }
 
@@ -774,7 +830,8 @@ mg_status mg_step_split(mg_sim *s, int32_t k, float *accel) {
   if (k < 1) return fail(MG_EINVAL, "k must be >= 1");
   if (!is_device_ptr(accel)) return fail(MG_EINVAL, "accel must be device memory");
   if (!s->diag)
-    return fail(MG_EINVAL, "the split step covers diagonal-mass fleets (r_g = 0) only");
+    return fail(MG_EINVAL, "the split step covers diagonal-mass fleets (r_g = 0, no "
+                           "off-diagonal hydrodynamics) only");
   FleetView v = s->view();
   for (int32_t done = 0; done < k;) {
     const int32_t kk = std::min(s->spl, k - done);

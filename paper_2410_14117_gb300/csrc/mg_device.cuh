@@ -226,10 +226,16 @@ __device__ __forceinline__ void store_state(const StatePlanes &sp, int64_t e, co
 // allocation: thrusters [0, NH) horizontal (d_z = 0: no heave force), the rest vertical
 // (d_x = d_y = 0, so r x d has no yaw component); the skipped products are exact zeros, so the
 // result is bit-identical to the dense 6 x N allocation (NH = 0).
-template <int MT, bool DIAG, bool MIXED, int NH = 0>
+//
+// XH (general path only): the env's off-diagonal hydrodynamic coefficients xh[MG_NXPARAM]
+// (M_A above its diagonal, then D_l's off-diagonal entries, both row-major; mg.h) enter the
+// added-mass momenta Q = M_A nu_r, the current term M_A [w x v_c^b; 0] and the damping D_l nu_r.
+template <int MT, bool DIAG, bool MIXED, int NH = 0, bool XH = false>
 __device__ __forceinline__ void rhs(const St<MT> &s, const float (&cs)[MT], const Par<DIAG> &P,
                                     const float4 *gdir, const float4 *garm, int nt,
-                                    bool current_accel, St<MT> &d) {
+                                    bool current_accel, St<MT> &d,
+                                    const float *__restrict__ xh = nullptr) {
+  static_assert(!(XH && DIAG), "the off-diagonal hydrodynamics use the general path");
   // Thrusters (Eq. 3 actions): F_i = kT n_i|n_i| along d_i at r_i; n_i' = (c_i - n_i) / tau_m.
   float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f, t4 = 0.f, t5 = 0.f;
 #pragma unroll
@@ -273,9 +279,19 @@ __device__ __forceinline__ void rhs(const St<MT> &s, const float (&cs)[MT], cons
 
   // Momenta: Q1 = M_A,lin v_r; h = P1 + Q1 = m v + Q1 (+ w x m r_g);
   //          k = P2 + Q2 = (diag(I_o) + M_A,rot) w (+ off-diagonal I_o w + m r_g x v).
-  const float q0 = P.ma0 * r0, q1 = P.ma1 * r1, q2 = P.ma2 * r2;
-  float h0 = fmaf(P.m, v0, q0), h1 = fmaf(P.m, v1, q1), h2 = fmaf(P.m, v2, q2);
+  float q0 = P.ma0 * r0, q1 = P.ma1 * r1, q2 = P.ma2 * r2;
   float k0 = P.J0 * w0, k1 = P.J1 * w1, k2 = P.J2 * w2;
+  if constexpr (XH) {
+    // off-diagonal added mass: Q_i += sum_{j != i} M_A,ij nu_r,j (upper triangle, mirrored)
+    const float *A = xh;  // 01 02 03 04 05 12 13 14 15 23 24 25 34 35 45
+    q0 = fmaf(A[0], r1, fmaf(A[1], r2, fmaf(A[2], w0, fmaf(A[3], w1, fmaf(A[4], w2, q0)))));
+    q1 = fmaf(A[0], r0, fmaf(A[5], r2, fmaf(A[6], w0, fmaf(A[7], w1, fmaf(A[8], w2, q1)))));
+    q2 = fmaf(A[1], r0, fmaf(A[5], r1, fmaf(A[9], w0, fmaf(A[10], w1, fmaf(A[11], w2, q2)))));
+    k0 = fmaf(A[2], r0, fmaf(A[6], r1, fmaf(A[9], r2, fmaf(A[12], w1, fmaf(A[13], w2, k0)))));
+    k1 = fmaf(A[3], r0, fmaf(A[7], r1, fmaf(A[10], r2, fmaf(A[12], w0, fmaf(A[14], w2, k1)))));
+    k2 = fmaf(A[4], r0, fmaf(A[8], r1, fmaf(A[11], r2, fmaf(A[13], w0, fmaf(A[14], w1, k2)))));
+  }
+  float h0 = fmaf(P.m, v0, q0), h1 = fmaf(P.m, v1, q1), h2 = fmaf(P.m, v2, q2);
   float a0 = 0.f, a1 = 0.f, a2 = 0.f;  // w x m r_g
   if constexpr (!DIAG) {
     a0 = fmaf(w1, P.mrg2, -w2 * P.mrg1);
@@ -299,10 +315,27 @@ __device__ __forceinline__ void rhs(const St<MT> &s, const float (&cs)[MT], cons
   f0 = fmaf(-fmaf(P.dq[0], fabsf(r0), P.dl[0]), r0, f0);
   f1 = fmaf(-fmaf(P.dq[1], fabsf(r1), P.dl[1]), r1, f1);
   f2 = fmaf(-fmaf(P.dq[2], fabsf(r2), P.dl[2]), r2, f2);
+  float c0 = 0.f, c1 = 0.f, c2 = 0.f;  // w x v_c^b
   if (current_accel) {
-    f0 = fmaf(-P.ma0, fmaf(w1, cb2, -w2 * cb1), f0);
-    f1 = fmaf(-P.ma1, fmaf(w2, cb0, -w0 * cb2), f1);
-    f2 = fmaf(-P.ma2, fmaf(w0, cb1, -w1 * cb0), f2);
+    c0 = fmaf(w1, cb2, -w2 * cb1);
+    c1 = fmaf(w2, cb0, -w0 * cb2);
+    c2 = fmaf(w0, cb1, -w1 * cb0);
+    f0 = fmaf(-P.ma0, c0, f0);
+    f1 = fmaf(-P.ma1, c1, f1);
+    f2 = fmaf(-P.ma2, c2, f2);
+  }
+  if constexpr (XH) {
+    // off-diagonal current term and linear damping of the translational rows
+    const float *A = xh, *Dl = xh + 15;  // Dl: row-major off-diagonal, 5 per row
+    f0 = fmaf(-A[0], c1, fmaf(-A[1], c2, f0));
+    f1 = fmaf(-A[0], c0, fmaf(-A[5], c2, f1));
+    f2 = fmaf(-A[1], c0, fmaf(-A[5], c1, f2));
+    f0 = fmaf(-Dl[0], r1, fmaf(-Dl[1], r2, fmaf(-Dl[2], w0, fmaf(-Dl[3], w1,
+             fmaf(-Dl[4], w2, f0)))));
+    f1 = fmaf(-Dl[5], r0, fmaf(-Dl[6], r2, fmaf(-Dl[7], w0, fmaf(-Dl[8], w1,
+             fmaf(-Dl[9], w2, f1)))));
+    f2 = fmaf(-Dl[10], r0, fmaf(-Dl[11], r1, fmaf(-Dl[12], w0, fmaf(-Dl[13], w1,
+             fmaf(-Dl[14], w2, f2)))));
   }
   // Rotational: kT t' - v_r x Q1 - w x k [- v x (w x m r_g)] - (Dl + Dq|w|) w + G x k_e.
   float f3 = fmaf(r2, q1, fmaf(-r1, q2, P.kT * t3));
@@ -322,6 +355,19 @@ __device__ __forceinline__ void rhs(const St<MT> &s, const float (&cs)[MT], cons
   f3 = fmaf(-P.G2, R21, fmaf(P.G1, R22, f3));
   f4 = fmaf(-P.G0, R22, fmaf(P.G2, R20, f4));
   f5 = fmaf(-P.G1, R20, fmaf(P.G0, R21, f5));
+  if constexpr (XH) {
+    // off-diagonal current term and linear damping of the rotational rows
+    const float *A = xh, *Dl = xh + 15;
+    f3 = fmaf(-A[2], c0, fmaf(-A[6], c1, fmaf(-A[9], c2, f3)));
+    f4 = fmaf(-A[3], c0, fmaf(-A[7], c1, fmaf(-A[10], c2, f4)));
+    f5 = fmaf(-A[4], c0, fmaf(-A[8], c1, fmaf(-A[11], c2, f5)));
+    f3 = fmaf(-Dl[15], r0, fmaf(-Dl[16], r1, fmaf(-Dl[17], r2, fmaf(-Dl[18], w1,
+             fmaf(-Dl[19], w2, f3)))));
+    f4 = fmaf(-Dl[20], r0, fmaf(-Dl[21], r1, fmaf(-Dl[22], r2, fmaf(-Dl[23], w0,
+             fmaf(-Dl[24], w2, f4)))));
+    f5 = fmaf(-Dl[25], r0, fmaf(-Dl[26], r1, fmaf(-Dl[27], r2, fmaf(-Dl[28], w0,
+             fmaf(-Dl[29], w1, f5)))));
+  }
 
   // nu' = M^-1 f.
   if constexpr (DIAG) {
@@ -385,22 +431,23 @@ __device__ __forceinline__ void axpy(St<MT> &y, const St<MT> &x, float a, const 
 
 // One sub-step (§METHOD): classical RK4 of size h, command held (cs = c / tau_m), then
 // q <- q / |q|.
-template <int MT, bool DIAG, bool MIXED, int NH = 0>
+template <int MT, bool DIAG, bool MIXED, int NH = 0, bool XH = false>
 __device__ __forceinline__ void rk4_step(St<MT> &s, const float (&cs)[MT], const Par<DIAG> &P,
                                          const float4 *gdir, const float4 *garm, int nt,
-                                         bool current_accel, float h) {
+                                         bool current_accel, float h,
+                                         const float *__restrict__ xh = nullptr) {
   const float hh = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f);
   St<MT> k, y, acc;
-  rhs<MT, DIAG, MIXED, NH>(s, cs, P, gdir, garm, nt, current_accel, k);
+  rhs<MT, DIAG, MIXED, NH, XH>(s, cs, P, gdir, garm, nt, current_accel, k, xh);
   axpy(acc, s, h6, k);
   axpy(y, s, hh, k);
-  rhs<MT, DIAG, MIXED, NH>(y, cs, P, gdir, garm, nt, current_accel, k);
+  rhs<MT, DIAG, MIXED, NH, XH>(y, cs, P, gdir, garm, nt, current_accel, k, xh);
   axpy(acc, acc, h3, k);
   axpy(y, s, hh, k);
-  rhs<MT, DIAG, MIXED, NH>(y, cs, P, gdir, garm, nt, current_accel, k);
+  rhs<MT, DIAG, MIXED, NH, XH>(y, cs, P, gdir, garm, nt, current_accel, k, xh);
   axpy(acc, acc, h3, k);
   axpy(y, s, h, k);
-  rhs<MT, DIAG, MIXED, NH>(y, cs, P, gdir, garm, nt, current_accel, k);
+  rhs<MT, DIAG, MIXED, NH, XH>(y, cs, P, gdir, garm, nt, current_accel, k, xh);
   axpy(s, acc, h6, k);
   const float inv = rsqrtf(fmaf(s.q[0], s.q[0], fmaf(s.q[1], s.q[1],
                                 fmaf(s.q[2], s.q[2], s.q[3] * s.q[3]))));

@@ -88,6 +88,10 @@ struct FleetView {
   // cursor_adv once all its blocks are done.  Only that launch pays for the completion count.
   int32_t cursor_off;
   int32_t cursor_adv;
+  // Off-diagonal hydrodynamics, device [MG_NXPARAM][n] (component-major), or null: the static
+  // and task kernels then run their XH variants (general path), staging each block's
+  // coefficients in shared memory.
+  const float *xh;
 };
 
 // Kernel variants: thruster count fixed at 6 or 8, or mixed (up to 8, read per block).
@@ -130,13 +134,17 @@ struct SetupView {
   ParamPlanes pa;
   unsigned long long *n_not_spd;
   unsigned int *any_offdiag;
+  const float *xh;           // device [MG_NXPARAM][n] off-diagonal hydrodynamics, or null
 };
 
 cudaError_t launch_randomize(const SetupView &v, const float *nominal /*dev [n_types][35]*/,
                              uint64_t seed, double lo, double hi, double current_sigma,
-                             cudaStream_t stream);
+                             double rg_halfwidth, cudaStream_t stream);
 cudaError_t launch_import_params(const SetupView &v, const float *in /*dev [n][35]*/,
                                  cudaStream_t stream);
+// [n][MG_NXPARAM] records <-> [MG_NXPARAM][n] planes (to_planes: records -> planes).
+cudaError_t launch_xh_transpose(const float *in, float *out, int64_t n, bool to_planes,
+                                cudaStream_t stream);
 cudaError_t launch_export_params(const SetupView &v, float *out /*dev [n][35]*/,
                                  cudaStream_t stream);
 cudaError_t launch_reset(const StatePlanes &st, int64_t n, int64_t gid0, const uint8_t *mask,

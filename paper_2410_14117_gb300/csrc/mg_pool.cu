@@ -372,8 +372,12 @@ mg_status mg_pool_admit(mg_pool *p, const mg_job_spec *spec, float *traj, int32_
   const mg_ranges &r = s.ranges;
   if (s.n_envs < 1 || s.n_envs > p->cap || s.vehicle_type < 0 ||
       s.vehicle_type >= p->n_types || s.hold_steps < 1 || s.horizon < 1 || !(r.lo > 0.f) ||
-      !(r.lo <= r.hi) || !(r.current_sigma >= 0.f) || !(r.nu0_sigma >= 0.f) || r.flags != 0)
+      !(r.lo <= r.hi) || !(r.current_sigma >= 0.f) || !(r.nu0_sigma >= 0.f) || r.flags != 0 ||
+      !(r.rg_halfwidth >= 0.f))
     return pfail(MG_EINVAL, "bad job spec");
+  if (r.rg_halfwidth > 0.f && p->diag)
+    return pfail(MG_EINVAL,
+                 "randomised r_g needs a pool created with an off-centre-gravity vehicle type");
   if (traj && !dev_ptr(traj)) return pfail(MG_EINVAL, "traj must be device memory");
   int64_t env0 = 0;
   if (!take_range(p, s.n_envs, &env0))
@@ -404,7 +408,7 @@ mg_status mg_pool_admit(mg_pool *p, const mg_job_spec *spec, float *traj, int32_
   v.n_not_spd = p->counters + 1;
   v.any_offdiag = p->offdiag;
   PK(launch_randomize(v, p->nominal, s.param_seed, (double)r.lo, (double)r.hi,
-                      (double)r.current_sigma, p->stream));
+                      (double)r.current_sigma, (double)r.rg_halfwidth, p->stream));
   PK(cudaMemsetAsync(p->episode + env0, 0, 4 * n, p->stream));
   PK(launch_reset(sub_state(p->st, env0), n, 0, nullptr, s.param_seed, (double)r.nu0_sigma,
                   p->episode + env0, p->flags + env0, p->counters, p->stream));

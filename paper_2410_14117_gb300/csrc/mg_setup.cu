@@ -36,7 +36,8 @@ __device__ void derive(const SetupView &v, int64_t e, const double *p) {
     for (int j = 0; j < 3; ++j)
       Io[i][j] = (i == j ? p[MG_P_IG + i] + m * r2 : 0.0) - m * rg[i] * rg[j];
 
-  // M = M_RB + M_A = [[m I + Ma_lin, -m S(r_g)], [m S(r_g), I_o + Ma_rot]].
+  // M = M_RB + M_A = [[m I + Ma_lin, -m S(r_g)], [m S(r_g), I_o + Ma_rot]], plus M_A's
+  // off-diagonal entries from the extension (FP32 values, as the step reads them).
   double M[6][6];
   const double S[3][3] = {{0.0, -rg[2], rg[1]}, {rg[2], 0.0, -rg[0]}, {-rg[1], rg[0], 0.0}};
   for (int i = 0; i < 3; ++i)
@@ -46,12 +47,23 @@ __device__ void derive(const SetupView &v, int64_t e, const double *p) {
       M[3 + i][j] = m * S[i][j];
       M[3 + i][3 + j] = Io[i][j] + ((i == j) ? ma[3 + i] : 0.0);
     }
+  bool ma_off = false;
+  if (v.xh) {
+    int t = 0;
+    for (int i = 0; i < 6; ++i)
+      for (int j = i + 1; j < 6; ++j, ++t) {
+        const double a = (double)v.xh[(int64_t)t * v.n + e];
+        M[i][j] += a;
+        M[j][i] += a;
+        ma_off = ma_off || a != 0.0;
+      }
+  }
 
   // Cholesky M = L L^T; L^-1 by forward substitution; M^-1 = L^-T L^-1.  With r_g = 0 the
   // matrix is diagonal (diagonal M_A), its factor is diag(sqrt(M_jj)) and the inverse 1 / M_jj.
   double L[6][6] = {}, Li[6][6] = {}, Mi[6][6] = {};
   bool spd = true;
-  const bool diagonal = (r2 == 0.0);
+  const bool diagonal = (r2 == 0.0) && !ma_off;
   if (diagonal) {
     for (int j = 0; j < 6; ++j) {
       if (!(M[j][j] > 0.0)) spd = false;
@@ -87,7 +99,7 @@ __device__ void derive(const SetupView &v, int64_t e, const double *p) {
       Mi[i][j] = s;
     }
   if (!spd) atomicAdd(v.n_not_spd, 1ull);
-  if (rg[0] != 0.0 || rg[1] != 0.0 || rg[2] != 0.0) atomicOr(v.any_offdiag, 1u);
+  if (!diagonal) atomicOr(v.any_offdiag, 1u);
 
   const double W = p[MG_P_W], B = p[MG_P_B];
   const double G[3] = {W * rg[0] - B * p[MG_P_RB], W * rg[1] - B * p[MG_P_RB + 1],
@@ -117,7 +129,7 @@ __device__ void derive(const SetupView &v, int64_t e, const double *p) {
 }
 
 __global__ void k_randomize(const SetupView v, const float *__restrict__ nominal, uint64_t seed,
-                            double lo, double hi, double current_sigma) {
+                            double lo, double hi, double current_sigma, double rg_halfwidth) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= v.n) return;
   const uint64_t gid = (uint64_t)(v.gid0 + e);
@@ -138,6 +150,12 @@ __global__ void k_randomize(const SetupView v, const float *__restrict__ nominal
   p[MG_P_VC] += current_sigma * z0;
   p[MG_P_VC + 1] += current_sigma * z1;
   p[MG_P_VC + 2] += current_sigma * z2;
+  if (rg_halfwidth > 0.0) {  // off-centre gravity: nominal + U[-w, w] per axis
+    const uint4 r = draw4(seed, gid, STREAM_PARAMS, 7u);
+    p[MG_P_RG] += rg_halfwidth * (2.0 * u01d(r.x) - 1.0);
+    p[MG_P_RG + 1] += rg_halfwidth * (2.0 * u01d(r.y) - 1.0);
+    p[MG_P_RG + 2] += rg_halfwidth * (2.0 * u01d(r.z) - 1.0);
+  }
   // Store FP32; derive from the stored values so that everything the step reads is consistent
   // with what mg_get_params reports.
   for (int j = 0; j < MG_NPARAM; ++j) {
@@ -158,6 +176,20 @@ __global__ void k_import_params(const SetupView v, const float *__restrict__ in)
     p[j] = (double)f;
   }
   derive(v, e, p);
+}
+
+// Off-diagonal hydrodynamics between the record layout [n][MG_NXPARAM] and the planes
+// [MG_NXPARAM][n] the step reads (to_planes), or back.
+__global__ void k_xh_transpose(const float *__restrict__ in, float *__restrict__ out, int64_t n,
+                               bool to_planes) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  for (int c = 0; c < MG_NXPARAM; ++c) {
+    if (to_planes)
+      out[(int64_t)c * n + e] = in[e * MG_NXPARAM + c];
+    else
+      out[e * MG_NXPARAM + c] = in[(int64_t)c * n + e];
+  }
 }
 
 __global__ void k_export_params(const SetupView v, float *__restrict__ out) {
@@ -219,9 +251,16 @@ __global__ void k_philox(const uint32_t *__restrict__ ctr, const uint32_t *__res
 }  // namespace
 
 cudaError_t launch_randomize(const SetupView &v, const float *nominal, uint64_t seed, double lo,
-                             double hi, double current_sigma, cudaStream_t stream) {
+                             double hi, double current_sigma, double rg_halfwidth,
+                             cudaStream_t stream) {
   k_randomize<<<blocks_for(v.n), kThreads, 0, stream>>>(v, nominal, seed, lo, hi,
-                                                        current_sigma);
+                                                        current_sigma, rg_halfwidth);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xh_transpose(const float *in, float *out, int64_t n, bool to_planes,
+                                cudaStream_t stream) {
+  k_xh_transpose<<<blocks_for(n), kThreads, 0, stream>>>(in, out, n, to_planes);
   return cudaGetLastError();
 }
 

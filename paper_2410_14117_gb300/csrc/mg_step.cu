@@ -40,8 +40,10 @@ __device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-template <int NTV, bool DIAG, bool REC, int NH>
-__global__ void __maxnreg__(DIAG ? kRegsDiag : kRegsGeneral)
+// XH: off-diagonal hydrodynamics (general path), the block's coefficients staged in dynamic
+// shared memory [blockDim.x][MG_NXPARAM].
+template <int NTV, bool DIAG, bool REC, int NH, bool XH = false>
+__global__ void __maxnreg__(XH ? kRegsXH : DIAG ? kRegsDiag : kRegsGeneral)
     k_fleet(const FleetView fv, const BlockDesc *__restrict__ blocks, const int32_t k,
             float *__restrict__ traj) {
   constexpr int MT = (NTV == NT_6) ? 6 : 8;
@@ -49,6 +51,7 @@ __global__ void __maxnreg__(DIAG ? kRegsDiag : kRegsGeneral)
   __shared__ float4 sdir[MG_MAX_THR], sarm[MG_MAX_THR];
   __shared__ unsigned s_done;
   __shared__ int64_t s_cursor;
+  extern __shared__ float sxh[];
 
   const BlockDesc bd = blocks[blockIdx.x];
   if (threadIdx.x < MG_MAX_THR) {
@@ -59,12 +62,15 @@ __global__ void __maxnreg__(DIAG ? kRegsDiag : kRegsGeneral)
     s_done = 0u;
     s_cursor = launch_cursor(fv);
   }
+  if constexpr (XH) stage_xh(fv.xh, fv.n, bd.env0, bd.count, sxh);
   __syncthreads();
   if ((int)threadIdx.x >= bd.count) return;
   const int64_t e = (int64_t)bd.env0 + threadIdx.x;
   St<MT> st;
-  advance_env<MT, DIAG, MIXED, REC, false, NH>(fv, e, MIXED ? bd.n_thr : MT, sdir, sarm,
-                                               s_cursor + fv.cursor_off, k, traj, st);
+  advance_env<MT, DIAG, MIXED, REC, false, NH, XH>(fv, e, MIXED ? bd.n_thr : MT, sdir, sarm,
+                                                   s_cursor + fv.cursor_off, k, traj, st,
+                                                   XH ? sxh + threadIdx.x * MG_NXPARAM
+                                                      : nullptr);
   store_and_flag<MT, false>(fv, e, st);
   if (fv.cursor_adv) finish_envs(fv, &s_done, bd.count, fv.cursor_adv);
 }
@@ -127,10 +133,17 @@ __global__ void __maxnreg__((DIAG && !WIDE) ? kRegsDiag : kRegsGeneral)
   if (fv.cursor_adv) finish_launch(fv, fv.cursor_adv);
 }
 
-// Structured allocation (NH = 4) is only instantiated for the diagonal-mass step.
+// Structured allocation (NH = 4) is only instantiated for the diagonal-mass step, the
+// off-diagonal hydrodynamics (XH) only for the general one.
 template <int NTV, bool DIAG, bool REC>
 cudaError_t launch_t(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
                      bool structured, int32_t k, float *traj, cudaStream_t stream) {
+  if constexpr (!DIAG) if (fv.xh) {
+    k_fleet<NTV, false, REC, 0, true><<<n_blocks, threads,
+                                        sizeof(float) * MG_NXPARAM * threads, stream>>>(
+        fv, blocks, k, traj);
+    return cudaGetLastError();
+  }
   if (DIAG && structured)
     k_fleet<NTV, DIAG, REC, (DIAG ? 4 : 0)><<<n_blocks, threads, 0, stream>>>(fv, blocks, k,
                                                                              traj);
@@ -213,7 +226,8 @@ void queue_launch(bool diag, bool wide, bool structured, int grid, const FleetVi
 cudaError_t launch_fleet(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
                          NtVariant ntv, bool diag, bool structured, int32_t k, float *traj,
                          cudaStream_t stream) {
-  if (threads < 32 || threads > kMaxThreads || threads % 32 || n_blocks < 1 || k < 1)
+  if (threads < 32 || threads > kMaxThreads || threads % 32 || n_blocks < 1 || k < 1 ||
+      (fv.xh && diag))
     return cudaErrorInvalidValue;
   switch (ntv) {
     case NT_6:
@@ -256,7 +270,7 @@ cudaError_t launch_fleet_queue(const FleetView &fv, const BlockDesc *slices, int
                                NtVariant ntv, bool diag, bool structured, bool wide,
                                int warps_per_sm, int32_t k, int32_t chunk, uint32_t *sched,
                                int n_sm, cudaStream_t stream) {
-  if (n_slices < 1 || k < 1 || chunk < 1 || n_sm < 1) return cudaErrorInvalidValue;
+  if (n_slices < 1 || k < 1 || chunk < 1 || n_sm < 1 || fv.xh) return cudaErrorInvalidValue;
   cudaFuncAttributes attr;
   int per_sm = 0;
   cudaError_t e = queue_kernel_attributes(ntv, diag, wide, structured, &attr, &per_sm);

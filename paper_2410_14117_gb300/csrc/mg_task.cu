@@ -144,8 +144,8 @@ __global__ void __launch_bounds__(kTaskThreads)
 // still in registers, the Eq. 4 error, the Eq. 2 observation, the episode bookkeeping and the
 // auto-reset, so the state is stored once and never re-read.  Each warp stages its 32 rows of
 // the observation in shared memory (when they fit) and writes them out as one contiguous run.
-template <int NTV, bool DIAG, int NH>
-__global__ void __maxnreg__(DIAG ? kRegsDiag : kRegsGeneral)
+template <int NTV, bool DIAG, int NH, bool XH>
+__global__ void __maxnreg__(XH ? kRegsXH : DIAG ? kRegsDiag : kRegsGeneral)
     k_fleet_task(const FleetView fv, const BlockDesc *__restrict__ blocks, const int32_t k_launch,
                  const int32_t k_task, const TaskView tv, const TaskOut to) {
   constexpr int MT = (NTV == NT_6) ? 6 : 8;
@@ -153,7 +153,11 @@ __global__ void __maxnreg__(DIAG ? kRegsDiag : kRegsGeneral)
   __shared__ float4 sdir[MG_MAX_THR], sarm[MG_MAX_THR];
   __shared__ unsigned s_done;
   __shared__ int64_t s_cursor;
-  extern __shared__ float sobs[];  // [blockDim.x][obs_dim] when to.stage
+  // dynamic: [blockDim.x][MG_NXPARAM] off-diagonal hydrodynamics (XH), then
+  // [blockDim.x][obs_dim] observation rows (to.stage)
+  extern __shared__ float sdyn[];
+  float *sxh = sdyn;
+  float *sobs = sdyn + (XH ? blockDim.x * MG_NXPARAM : 0);
 
   const BlockDesc bd = blocks[blockIdx.x];
   if (threadIdx.x < MG_MAX_THR) {
@@ -164,13 +168,14 @@ __global__ void __maxnreg__(DIAG ? kRegsDiag : kRegsGeneral)
     s_done = 0u;
     s_cursor = launch_cursor(fv);
   }
+  if constexpr (XH) stage_xh(fv.xh, fv.n, bd.env0, bd.count, sxh);
   __syncthreads();
   if ((int)threadIdx.x >= bd.count) return;
   const int64_t e = (int64_t)bd.env0 + threadIdx.x;
   St<MT> s;
-  advance_env<MT, DIAG, MIXED, false, false, NH>(fv, e, MIXED ? bd.n_thr : MT, sdir, sarm,
-                                                 s_cursor + fv.cursor_off, k_launch, nullptr,
-                                                 s);
+  advance_env<MT, DIAG, MIXED, false, false, NH, XH>(
+      fv, e, MIXED ? bd.n_thr : MT, sdir, sarm, s_cursor + fv.cursor_off, k_launch, nullptr, s,
+      XH ? sxh + threadIdx.x * MG_NXPARAM : nullptr);
 
   const int obs_dim = to.obs_dim;
   float *row = to.stage ? sobs + threadIdx.x * obs_dim : to.obs + e * obs_dim;
@@ -238,12 +243,12 @@ __global__ void __maxnreg__(DIAG ? kRegsDiag : kRegsGeneral)
   for (int i = i0 + lane; i < total; i += n_act) dst[i] = src[i];
 }
 
-template <int NTV, bool DIAG, int NH>
+template <int NTV, bool DIAG, int NH, bool XH = false>
 cudaError_t fleet_task_t(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
                          int32_t k_launch, int32_t k_task, const TaskView &tv, const TaskOut &to,
                          size_t smem, cudaStream_t stream) {
-  k_fleet_task<NTV, DIAG, NH><<<n_blocks, threads, smem, stream>>>(fv, blocks, k_launch, k_task,
-                                                                   tv, to);
+  k_fleet_task<NTV, DIAG, NH, XH><<<n_blocks, threads, smem, stream>>>(fv, blocks, k_launch,
+                                                                       k_task, tv, to);
   return cudaGetLastError();
 }
 
@@ -252,6 +257,9 @@ cudaError_t fleet_task_d(const FleetView &fv, const BlockDesc *blocks, int n_blo
                          bool diag, bool structured, int32_t k_launch, int32_t k_task,
                          const TaskView &tv, const TaskOut &to, size_t smem,
                          cudaStream_t stream) {
+  if (fv.xh)
+    return fleet_task_t<NTV, false, 0, true>(fv, blocks, n_blocks, threads, k_launch, k_task, tv,
+                                             to, smem, stream);
   if (diag && structured)
     return fleet_task_t<NTV, true, 4>(fv, blocks, n_blocks, threads, k_launch, k_task, tv, to,
                                       smem, stream);
@@ -289,12 +297,14 @@ cudaError_t launch_fleet_task(const FleetView &fv, const BlockDesc *blocks, int 
                               int32_t k_launch, int32_t k_task, const TaskView &tv, TaskOut to,
                               cudaStream_t stream) {
   if (threads < 32 || threads > 256 || threads % 32 || n_blocks < 1 || k_launch < 1 ||
-      k_task < k_launch)
+      k_task < k_launch || (fv.xh && diag))
     return cudaErrorInvalidValue;
-  // Stage the observation rows in shared memory when the block's rows fit in 48 KB.
+  // The off-diagonal hydrodynamics (if any) come first; the observation rows are staged in
+  // shared memory when both fit in 48 KB.
+  const size_t xh_bytes = fv.xh ? sizeof(float) * threads * MG_NXPARAM : 0;
   const size_t smem = sizeof(float) * threads * to.obs_dim;
-  to.stage = smem <= 48 * 1024 ? 1 : 0;
-  const size_t dyn = to.stage ? smem : 0;
+  to.stage = xh_bytes + smem <= 48 * 1024 ? 1 : 0;
+  const size_t dyn = xh_bytes + (to.stage ? smem : 0);
   switch (ntv) {
     case NT_6:
       return fleet_task_d<NT_6>(fv, blocks, n_blocks, threads, diag, structured, k_launch,

@@ -28,6 +28,7 @@ import math
 import numpy as np
 
 NPARAM = 35
+NXPARAM = 45  # off-diagonal extension: M_A above its diagonal (15), D_l off its diagonal (30)
 NSTATE = 21
 MAX_THR = 8
 NCOEF = 18  # added-mass, linear-damping and quadratic-damping diagonals
@@ -215,6 +216,31 @@ def perturbed_params(seed: int, nominal: np.ndarray, n_envs: int, lo: float = 0.
     p[:, idx] *= g.uniform(lo, hi, size=(n_envs, idx.size))
     p[:, P_VC:P_VC + 3] += g.normal(0.0, current_sigma, size=(n_envs, 3))
     return round_f32(p)
+
+
+def hydro_offdiag(seed: int, params: np.ndarray, coupling: float = 0.15) -> np.ndarray:
+    """Off-diagonal added mass and linear damping for envs with records ``params`` [n, NPARAM]:
+    M_A(i, j) = coupling * u * sqrt(M_A,ii M_A,jj) and D_l(i, j) = coupling * u' *
+    sqrt(D_l,ii D_l,jj), u, u' ~ U[-1, 1] (D_l not symmetric), packed as the extension record
+    (M_A above the diagonal row-major, then D_l off the diagonal row-major).  With coupling <
+    0.2 every M_A stays diagonally dominant, so M_RB + M_A stays positive definite.  float64
+    ``[n, NXPARAM]``, FP32-representable."""
+    g = _rng(seed)
+    n = params.shape[0]
+    ma = params[:, P_MA:P_MA + 6]
+    dl = params[:, P_DL:P_DL + 6]
+    out = np.zeros((n, NXPARAM))
+    t = 0
+    for i in range(6):
+        for j in range(i + 1, 6):
+            out[:, t] = coupling * g.uniform(-1, 1, n) * np.sqrt(ma[:, i] * ma[:, j])
+            t += 1
+    for i in range(6):
+        for j in range(6):
+            if j != i:
+                out[:, t] = coupling * g.uniform(-1, 1, n) * np.sqrt(dl[:, i] * dl[:, j])
+                t += 1
+    return round_f32(out)
 
 
 def mixed_fleet(seed: int, total: int, max_group: int = 32768, p_first: float = 0.6) -> np.ndarray:

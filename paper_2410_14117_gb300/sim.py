@@ -10,7 +10,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (MG_MAX_THR, MG_NPARAM, MG_NSTATE, MG_NTRAJ, MGError, Ranges, TaskSpec,
+from ._lib import (MG_MAX_THR, MG_NPARAM, MG_NSTATE, MG_NXPARAM, MG_NTRAJ, MGError, Ranges, TaskSpec,
                    VehicleParams, call)
 
 __all__ = ["Sim", "vehicle_struct", "MGError"]
@@ -111,8 +111,8 @@ class Sim:
 
     # ------------------------------------------------------------------ parameters
     def randomize(self, seed: int, lo: float = 0.8, hi: float = 1.2, current_sigma: float = 0.2,
-                  nu0_sigma: float = 0.3):
-        r = Ranges(lo, hi, current_sigma, nu0_sigma, 0)
+                  nu0_sigma: float = 0.3, rg_halfwidth: float = 0.0):
+        r = Ranges(lo, hi, current_sigma, nu0_sigma, 0, rg_halfwidth)
         call("mg_randomize", self._h, ctypes.c_uint64(seed), ctypes.byref(r))
 
     def set_params(self, params):
@@ -124,6 +124,22 @@ class Sim:
             out = torch.empty((self.n, MG_NPARAM), dtype=torch.float32, device=self.device)
         _check(out, (self.n, MG_NPARAM), torch.float32)
         call("mg_get_params", self._h, _ptr(out))
+        return out
+
+    def set_hydro_offdiag(self, x):
+        """Off-diagonal added mass and linear damping, float32 [n_envs, MG_NXPARAM] (layout of
+        mg.h), or None for the diagonal model."""
+        if x is None:
+            call("mg_set_hydro_offdiag", self._h, None)
+            return
+        _check(x, (self.n, MG_NXPARAM), torch.float32)
+        call("mg_set_hydro_offdiag", self._h, _ptr(x))
+
+    def get_hydro_offdiag(self, out=None):
+        if out is None:
+            out = torch.empty((self.n, MG_NXPARAM), dtype=torch.float32, device=self.device)
+        _check(out, (self.n, MG_NXPARAM), torch.float32)
+        call("mg_get_hydro_offdiag", self._h, _ptr(out))
         return out
 
     # ------------------------------------------------------------------ actions and stepping

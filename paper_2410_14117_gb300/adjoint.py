@@ -60,3 +60,15 @@ class RolloutFn(torch.autograd.Function):
 def rollout(sim: Sim, coeffs, actions, state0, hold: int, T: int, C: int = 20):
     """Differentiable trajectory [T, n, 13] (see RolloutFn)."""
     return RolloutFn.apply(sim, coeffs, actions, state0, hold, T, C)
+
+
+def shared_coefficient_grad(dcoef, group=None):
+    """Gradient with respect to coefficients shared by every env of every rank (one set of 18
+    for the whole sharded fleet, e.g. when identifying a vehicle model from many runs): the sum
+    of the per-env gradients ``dcoef`` [n_local, 18] over this rank's envs, summed over the ranks
+    of ``group`` by one all-reduce of 18 FP32 values — the only collective of the sharded path.
+    Without an initialised process group it is the local sum."""
+    local = dcoef.sum(dim=0)
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        torch.distributed.all_reduce(local, op=torch.distributed.ReduceOp.SUM, group=group)
+    return local

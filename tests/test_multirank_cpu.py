@@ -1,7 +1,9 @@
 """The multi-rank path on CPU (world size 2, gloo): every rank integrates its own fleet with env
 ids offset by rank, as bench.py does under torchrun (no collective in the data path), and the
 slowest rank's time is the job's.  The union of the shards must equal the single-process fleet,
-which holds because every draw is keyed by the global env id."""
+which holds because every draw is keyed by the global env id.  The one collective of the
+sharded adjoint (the gradient of coefficients shared by the whole fleet) is checked the same
+way."""
 import os
 import socket
 
@@ -59,3 +61,36 @@ def test_two_rank_shards_equal_one_fleet(tmp_path):
     whole = _shard(0, world * n, steps)
     np.testing.assert_array_equal(union, whole)
     assert np.load(out + ".max.npy")[0] == world
+
+
+def _fake_dcoef(gid0, n):
+    """Per-env coefficient gradients keyed by the global env id (stand-ins for the adjoint's
+    output; the reduction does not look at their values)."""
+    g = np.stack([np.random.default_rng(1000 + gid0 + e).normal(size=18) for e in range(n)])
+    return g.astype(np.float32)
+
+
+def _grad_worker(rank, world, port, n, out_path):
+    import sys
+    sys.path.insert(0, ROOT)
+    import torch
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    from paper_2410_14117_gb300.adjoint import shared_coefficient_grad
+    mine = torch.from_numpy(_fake_dcoef(bench.rank_env_offset(rank, n), n))
+    total = shared_coefficient_grad(mine)
+    np.save(out_path + f".{rank}.npy", total.numpy())
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_shared_coefficient_gradient_all_reduce(tmp_path):
+    n, world = 16, 2
+    out = str(tmp_path / "grad")
+    mp.spawn(_grad_worker, args=(world, _free_port(), n, out), nprocs=world, join=True)
+    whole = _fake_dcoef(0, world * n).astype(np.float64).sum(axis=0)
+    for r in range(world):
+        got = np.load(out + f".{r}.npy")
+        np.testing.assert_allclose(got, whole, rtol=1e-5, atol=1e-5)

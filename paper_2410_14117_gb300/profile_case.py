@@ -7,7 +7,8 @@ Builds a domain-randomised BlueROV2 fleet with NED current and a buffered thrott
 after a few warm-up calls: with ``--static`` each is one launch of the static-grid kernel running
 ``k`` sub-steps; otherwise each is one work-queue launch covering ``k`` sub-steps in chunks of
 ``--chunk``; with ``--task`` each is one circle-tracking task step (``k`` sub-steps and the fused
-observation / error / auto-reset epilogue, static grid).  Holds well under a GB of device memory
+observation / error / auto-reset epilogue, static grid); ``--split`` runs the split-integration
+comparison kernel, ``--full`` the general path with off-diagonal hydrodynamics.  Holds well under a GB of device memory
 at 65,536 envs.
 """
 from __future__ import annotations
@@ -39,6 +40,11 @@ def main():
     ap.add_argument("--task", action="store_true",
                     help="circle-tracking task steps of k sub-steps (fused task epilogue) instead "
                          "of plain steps; static grid")
+    ap.add_argument("--split", action="store_true",
+                    help="split-integration comparison steps (mg_step_split), added mass halved")
+    ap.add_argument("--full", action="store_true",
+                    help="off-diagonal added mass and damping, r_g ~ U[-2, 2] cm (general path, "
+                         "static grid)")
     args = ap.parse_args()
 
     n = args.n_envs
@@ -46,8 +52,17 @@ def main():
     sim = Sim(n, np.full(n, args.vehicle, dtype=np.int32), vs)
     sim.set_launch(args.epb, args.k if args.static else args.chunk, False)
     sim.set_schedule(not args.static, not args.narrow, args.wps)
-    sim.randomize(1234, 0.8, 1.2, 0.2, 0.3)
+    sim.randomize(1234, 0.8, 1.2, 0.2, 0.3, rg_halfwidth=0.02 if args.full else 0.0)
+    if args.split:
+        p = sim.get_params()
+        p[:, I.P_MA:I.P_MA + 6] *= 0.5
+        sim.set_params(p)
+    if args.full:
+        p = sim.get_params().double().cpu().numpy()
+        sim.set_hydro_offdiag(torch.tensor(I.hydro_offdiag(9, p), dtype=torch.float32,
+                                           device="cuda"))
     sim.reset()
+    acc = torch.zeros((6, n), device="cuda") if args.split else None
     total = (args.warmup + args.launches) * args.k
     cmds = I.commands(5678, math.ceil(total / 10), n, vs[args.vehicle].n_thr)
     sim.set_actions(torch.tensor(cmds, device="cuda"), 10)
@@ -62,6 +77,8 @@ def main():
     for _ in range(args.warmup + args.launches):
         if args.task:
             sim.task_step(args.k)
+        elif args.split:
+            sim.step_split(args.k, acc)
         else:
             sim.step(args.k)
     bad = sim.sync()

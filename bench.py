@@ -473,6 +473,7 @@ def run_ours(args):
 
     sim.close()
     if not args.no_extra and world == 1:
+        line["size_sweep"] = bench_size_sweep(vs)
         line["mixed_fleet"] = bench_mixed_fleet(vs)
         line["adjoint"] = bench_adjoint(vs)
         line["task"] = bench_task(vs)
@@ -502,6 +503,38 @@ def _time_episodes(fn, reps):
     b.record()
     torch.cuda.synchronize()
     return a.elapsed_time(b) / reps
+
+
+def bench_size_sweep(vs, sizes=(4096, 16384, 65536, 262144, 1048576), horizon=1000, reps=3):
+    """Config-2 sweep: the headline workload's sub-steps (randomised BlueROV2, current,
+    procedural commands held 10) at each fleet size, with the launch the autotuner picks for
+    that size; per-sub-step time and the fraction of the FP32 ALU peak."""
+    import numpy as np
+    from paper_2410_14117_gb300.autotune import Autotuner
+    from paper_2410_14117_gb300.sim import Sim
+
+    peak = fp32_alu_peak_tflops(2070.0)
+    tuner = Autotuner(horizon=horizon, reps=2)
+    out = {"workload": f"BlueROV2, parameters x U[0.8,1.2], current N(0,0.2), {horizon:,} "
+                       "sub-steps per call, procedural commands held 10; autotuned per size",
+           "sizes": []}
+    for n in sizes:
+        types = np.zeros(n, np.int32)
+        cfg = tuner.pick(n, types, vs)
+        sim = Sim(n, types, vs)
+        cfg.apply(sim)
+        sim.randomize(1234, 0.8, 1.2, 0.2, 0.3)
+        sim.reset()
+        sim.set_procedural_actions(5678, 10)
+        ms = _time_episodes(lambda: sim.step(horizon), reps)
+        assert sim.sync() == 0
+        sim.close()
+        rate = n * horizon / (ms / 1e3)
+        out["sizes"].append({"n_envs": n, "env_substeps_per_s": rate,
+                             "us_per_substep": ms * 1e3 / horizon,
+                             "alu_frac": rate * FLOPS_PER_ENV_STEP[6] / (peak * 1e12),
+                             "launch": dataclasses.asdict(cfg)})
+    return out
 
 
 def bench_mixed_fleet(vs, n=262144, horizon=500, reps=5):

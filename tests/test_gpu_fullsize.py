@@ -82,3 +82,24 @@ def test_mixed_fleet_262144_sampled_matches_oracle():
     ref = _oracle_rollout(vs, types, sample, 4321, cmds, hold, 500)
     err = rel_err(got, ref)
     assert err.max() <= TOL_ROLLOUT, err.max(axis=0)
+
+
+def test_largest_sweep_fleet_sampled_matches_oracle():
+    """1,048,576 envs (the top of the fleet-size sweep), static grid, 200 sub-steps."""
+    vs = vehicles()
+    n, hold = 1 << 20, 10
+    types = np.zeros(n, dtype=np.int32)
+    sim = Sim(n, types, vs)
+    LaunchConfig("static", 128, 200).apply(sim)
+    sim.randomize(99, 0.8, 1.2, 0.2, 0.3)
+    sim.reset()
+    cmds = I.commands(98, 20, n, 6)
+    sim.set_actions(torch.tensor(cmds, device="cuda"), hold)
+    sim.step(200)
+    sample = _sample(n, 300, 5)
+    got = sim.get_state().double().cpu().numpy()[sample]
+    assert sim.sync() == 0
+    sim.close()
+    ref = _oracle_rollout(vs, types, sample, 99, cmds, hold, 200)
+    err = rel_err(got, ref)
+    assert err.max() <= TOL_ROLLOUT, err.max(axis=0)

@@ -31,10 +31,11 @@ METRIC = "env-steps/s at 64K envs (fused vs per-step, same GPU); p50/p99 serve l
 
 # Algorithmic FP32 work per env and sub-step of the diagonal-mass step (FMA = 2 flops), counted
 # from the arithmetic of Eq. 1 + RK4 as the kernel performs it for the vectored thruster layout
-# (the allocation's known zeros are not multiplied): 4 right-hand sides (6 thrusters: 268 flops
-# each; 8 thrusters: 286) + RK4 stage updates and combination (248 / 276) + quaternion
-# renormalisation (15).
-FLOPS_PER_ENV_STEP = {6: 4 * 268 + 248 + 15, 8: 4 * 286 + 276 + 15}
+# (the allocation's known zeros are not multiplied): 4 right-hand sides without the lag
+# derivative (6 thrusters: 256 flops each; 8 thrusters: 270) + RK4 stage updates and
+# combination of p, q, nu (164; the unused stage values of p are not formed) + the throttle lag
+# in its closed form (12 per thruster) + quaternion renormalisation (15).
+FLOPS_PER_ENV_STEP = {6: 4 * 256 + 164 + 6 * 12 + 15, 8: 4 * 270 + 164 + 8 * 12 + 15}
 # Algorithmic HBM bytes per env of one launch: state read + written ((13 + n_thr) floats each),
 # the 34 parameter floats of the diagonal-mass step, and one command vector per segment.
 STATE_BYTES = {6: 19 * 4, 8: 21 * 4}

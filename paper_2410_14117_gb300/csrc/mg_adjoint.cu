@@ -333,6 +333,7 @@ __global__ void __launch_bounds__(kAdjThreads)
   const int64_t n = fv.n;
   ParDiag P;
   load_par<true>(fv.pa, e, P);
+  const LagEnv L = lag_env(P.itau, h);  // the forward's throttle-lag update (checkpoint replay)
 
   Grad G;
   for (int i = 0; i < 3; ++i) G.ma[i] = G.J[i] = 0.f;
@@ -355,7 +356,9 @@ __global__ void __launch_bounds__(kAdjThreads)
     for (int32_t j = 1; j < len; ++j) {
       S[j] = S[j - 1];
       commands_at<MT>(fv, e, step0 + t0 + j - 1, nt, P.itau, c);
-      rk4_step<MT, true, true>(S[j], c, P, gdir, garm, nt, ca, h);
+      float b[MT];
+      lag_segment<MT>(c, L, b);
+      rk4_step_lag<MT, true, true>(S[j], b, L, P, gdir, garm, nt, ca, h);
     }
     // walk it backwards
     for (int32_t j = len - 1; j >= 0; --j) {

@@ -118,8 +118,12 @@ __device__ __forceinline__ bool all_finite(const St<MT> &s) {
 // Advance env e by k sub-steps starting at action-cursor position step0, leaving the result in
 // s (the caller stores it: store_and_flag, or a fused epilogue).  L2: state loads bypass L1
 // (work-queue schedule, where another SM may have written them).
-// XH: xh is the env's row of staged off-diagonal hydrodynamic coefficients.
-template <int MT, bool DIAG, bool MIXED, bool REC, bool L2, int NH, bool XH = false>
+// XH: xh is the env's row of staged off-diagonal hydrodynamic coefficients.  CF: the throttle
+// lag in closed form (rk4_step_lag: fewer operations, one more live constant); the fused task
+// kernel's 128-register variants keep the classic update (rk4_step), which fits their epilogue
+// without spilling.  Both are RK4; they differ in the rounding of the lag state.
+template <int MT, bool DIAG, bool MIXED, bool REC, bool L2, int NH, bool XH = false,
+          bool CF = true>
 __device__ __forceinline__ void advance_env(const FleetView &fv, int64_t e, int nt,
                                             const float4 *gdir, const float4 *garm,
                                             int64_t step0, int32_t k, float *traj, St<MT> &s,
@@ -134,16 +138,32 @@ __device__ __forceinline__ void advance_env(const FleetView &fv, int64_t e, int 
   // Action cursor: sub-step j uses segment j / hold (clamped to the last buffered segment).
   int64_t seg = step0 / fv.hold;
   int32_t left = fv.hold - (int32_t)(step0 - seg * fv.hold);
-  float c[MT];
-  load_commands<MT>(fv, e, seg, nt, P.itau, c);
+  const LagEnv L = lag_env(P.itau, h);
+  float b[MT];  // CF: b_i = (h/2) c_i / tau_m; otherwise c_i / tau_m
+  {
+    float c[MT];
+    load_commands<MT>(fv, e, seg, nt, P.itau, c);
+    if constexpr (CF) lag_segment<MT>(c, L, b);
+    else
+#pragma unroll
+      for (int i = 0; i < MT; ++i) b[i] = c[i];
+  }
 
   for (int32_t it = 0; it < k; ++it) {
     if (left == 0) {
       ++seg;
       left = fv.hold;
+      float c[MT];
       load_commands<MT>(fv, e, seg, nt, P.itau, c);
+      if constexpr (CF) lag_segment<MT>(c, L, b);
+      else
+#pragma unroll
+        for (int i = 0; i < MT; ++i) b[i] = c[i];
     }
-    rk4_step<MT, DIAG, MIXED, NH, XH>(s, c, P, gdir, garm, nt, current_accel, h, xh);
+    if constexpr (CF)
+      rk4_step_lag<MT, DIAG, MIXED, NH, XH>(s, b, L, P, gdir, garm, nt, current_accel, h, xh);
+    else
+      rk4_step<MT, DIAG, MIXED, NH, XH>(s, b, P, gdir, garm, nt, current_accel, h, xh);
     --left;
     if constexpr (REC) record<MT>(traj + (int64_t)it * MG_NTRAJ * fv.n, fv.n, e, s);
   }

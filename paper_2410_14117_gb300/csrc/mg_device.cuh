@@ -230,7 +230,8 @@ __device__ __forceinline__ void store_state(const StatePlanes &sp, int64_t e, co
 // XH (general path only): the env's off-diagonal hydrodynamic coefficients xh[MG_NXPARAM]
 // (M_A above its diagonal, then D_l's off-diagonal entries, both row-major; mg.h) enter the
 // added-mass momenta Q = M_A nu_r, the current term M_A [w x v_c^b; 0] and the damping D_l nu_r.
-template <int MT, bool DIAG, bool MIXED, int NH = 0, bool XH = false>
+// LAGD = false leaves d.n unset (the caller integrates the linear throttle lag in closed form).
+template <int MT, bool DIAG, bool MIXED, int NH = 0, bool XH = false, bool LAGD = true>
 __device__ __forceinline__ void rhs(const St<MT> &s, const float (&cs)[MT], const Par<DIAG> &P,
                                     const float4 *gdir, const float4 *garm, int nt,
                                     bool current_accel, St<MT> &d,
@@ -252,7 +253,7 @@ __device__ __forceinline__ void rhs(const St<MT> &s, const float (&cs)[MT], cons
       } else {
         t2 = fmaf(f, dd.z, t2); t3 = fmaf(f, aa.x, t3); t4 = fmaf(f, aa.y, t4);
       }
-      d.n[i] = fmaf(-s.n[i], P.itau, cs[i]);
+      if constexpr (LAGD) d.n[i] = fmaf(-s.n[i], P.itau, cs[i]);
     }
   }
   (void)nt;
@@ -412,8 +413,9 @@ __device__ __forceinline__ void fma2(float a0, float a1, float k0, float k1, flo
 #endif
 }
 
-// y = x + a k, with the quaternion taking a / 2 (its derivative is stored doubled).
-template <int MT>
+// y = x + a k, with the quaternion taking a / 2 (its derivative is stored doubled).  WN = false
+// leaves the throttle states alone.
+template <int MT, bool WN = true>
 __device__ __forceinline__ void axpy(St<MT> &y, const St<MT> &x, float a, const St<MT> &k) {
   const float aq = 0.5f * a;
   fma2(a, a, k.p[0], k.p[1], x.p[0], x.p[1], y.p[0], y.p[1]);
@@ -422,11 +424,44 @@ __device__ __forceinline__ void axpy(St<MT> &y, const St<MT> &x, float a, const 
   fma2(aq, aq, k.q[2], k.q[3], x.q[2], x.q[3], y.q[2], y.q[3]);
   fma2(a, a, k.v[1], k.v[2], x.v[1], x.v[2], y.v[1], y.v[2]);
   fma2(a, a, k.w[0], k.w[1], x.w[0], x.w[1], y.w[0], y.w[1]);
-  fma2(a, a, k.w[2], k.n[0], x.w[2], x.n[0], y.w[2], y.n[0]);
+  if constexpr (WN) {
+    fma2(a, a, k.w[2], k.n[0], x.w[2], x.n[0], y.w[2], y.n[0]);
 #pragma unroll
-  for (int i = 1; i + 1 < MT; i += 2)
-    fma2(a, a, k.n[i], k.n[i + 1], x.n[i], x.n[i + 1], y.n[i], y.n[i + 1]);
-  if constexpr (MT % 2 == 0) y.n[MT - 1] = fmaf(a, k.n[MT - 1], x.n[MT - 1]);
+    for (int i = 1; i + 1 < MT; i += 2)
+      fma2(a, a, k.n[i], k.n[i + 1], x.n[i], x.n[i + 1], y.n[i], y.n[i + 1]);
+    if constexpr (MT % 2 == 0) y.n[MT - 1] = fmaf(a, k.n[MT - 1], x.n[MT - 1]);
+  } else {
+    y.w[2] = fmaf(a, k.w[2], x.w[2]);
+  }
+}
+
+// The throttle lag n' = (c - n) / tau_m is linear with the command held, so RK4 applied to it has
+// closed forms: with g2 = -h / (2 tau_m), g3 = -h / tau_m and b = (h/2) c / tau_m the stage
+// values are y2 = n + g2 n + b, y3 = n + g2 y2 + b, y4 = n + g3 y3 + 2 b, and the step gives
+// n+ = P n + (1 - P) c with P = 1 + z + z^2/2 + z^3/6 + z^4/24, z = g3 (RK4's stability
+// polynomial) — the same numbers as RK4's stage updates and weighted sum, in 6 operations per
+// thruster instead of 11.
+struct LagEnv {
+  float g2, g3, P, lambda, hh;  // lambda = (1 - P) / (g2 tau_m): (1 - P) c = lambda b; hh = h/2
+};
+
+__device__ __forceinline__ LagEnv lag_env(float itau, float h) {
+  LagEnv L;
+  L.hh = 0.5f * h;
+  L.g3 = -h * itau;
+  L.g2 = 0.5f * L.g3;
+  const float z = L.g3;
+  L.P = fmaf(fmaf(fmaf(fmaf(z, 1.f / 24.f, 1.f / 6.f), z, 0.5f), z, 1.f), z, 1.f);
+  L.lambda = (1.f - L.P) / (L.hh * itau);
+  return L;
+}
+
+// Per command segment: b_i = (h/2) c_i / tau_m from cs_i = c_i / tau_m.
+template <int MT>
+__device__ __forceinline__ void lag_segment(const float (&cs)[MT], const LagEnv &L,
+                                            float (&b)[MT]) {
+#pragma unroll
+  for (int i = 0; i < MT; ++i) b[i] = L.hh * cs[i];
 }
 
 // One sub-step (§METHOD): classical RK4 of size h, command held (cs = c / tau_m), then
@@ -449,6 +484,41 @@ __device__ __forceinline__ void rk4_step(St<MT> &s, const float (&cs)[MT], const
   axpy(y, s, h, k);
   rhs<MT, DIAG, MIXED, NH, XH>(y, cs, P, gdir, garm, nt, current_accel, k, xh);
   axpy(s, acc, h6, k);
+  const float inv = rsqrtf(fmaf(s.q[0], s.q[0], fmaf(s.q[1], s.q[1],
+                                fmaf(s.q[2], s.q[2], s.q[3] * s.q[3]))));
+#pragma unroll
+  for (int i = 0; i < 4; ++i) s.q[i] *= inv;
+}
+
+// One sub-step as rk4_step, with the throttle lag in the closed forms above (b from lag_segment
+// for the held command; e = (1 - P) c recovered as lambda b).  Same RK4, different rounding of
+// the lag state.
+template <int MT, bool DIAG, bool MIXED, int NH = 0, bool XH = false>
+__device__ __forceinline__ void rk4_step_lag(St<MT> &s, const float (&b)[MT], const LagEnv &L,
+                                             const Par<DIAG> &P, const float4 *gdir,
+                                             const float4 *garm, int nt, bool current_accel,
+                                             float h, const float *__restrict__ xh = nullptr) {
+  const float hh = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f);
+  St<MT> k, y, acc;
+  rhs<MT, DIAG, MIXED, NH, XH, false>(s, b, P, gdir, garm, nt, current_accel, k, xh);
+  axpy<MT, false>(acc, s, h6, k);
+  axpy<MT, false>(y, s, hh, k);
+#pragma unroll
+  for (int i = 0; i < MT; ++i) y.n[i] = fmaf(L.g2, s.n[i], s.n[i] + b[i]);
+  rhs<MT, DIAG, MIXED, NH, XH, false>(y, b, P, gdir, garm, nt, current_accel, k, xh);
+  axpy<MT, false>(acc, acc, h3, k);
+  axpy<MT, false>(y, s, hh, k);
+#pragma unroll
+  for (int i = 0; i < MT; ++i) y.n[i] = fmaf(L.g2, y.n[i], s.n[i] + b[i]);
+  rhs<MT, DIAG, MIXED, NH, XH, false>(y, b, P, gdir, garm, nt, current_accel, k, xh);
+  axpy<MT, false>(acc, acc, h3, k);
+  axpy<MT, false>(y, s, h, k);
+#pragma unroll
+  for (int i = 0; i < MT; ++i) y.n[i] = fmaf(L.g3, y.n[i], fmaf(2.f, b[i], s.n[i]));
+  rhs<MT, DIAG, MIXED, NH, XH, false>(y, b, P, gdir, garm, nt, current_accel, k, xh);
+  axpy<MT, false>(s, acc, h6, k);
+#pragma unroll
+  for (int i = 0; i < MT; ++i) s.n[i] = fmaf(L.P, s.n[i], L.lambda * b[i]);
   const float inv = rsqrtf(fmaf(s.q[0], s.q[0], fmaf(s.q[1], s.q[1],
                                 fmaf(s.q[2], s.q[2], s.q[3] * s.q[3]))));
 #pragma unroll

@@ -67,11 +67,14 @@ __global__ void __maxnreg__(DIAG ? 128 : 168)
   load_par<DIAG>(fv.pa, e, P);
   int64_t seg = jd.step0 / jd.hold;
   int32_t left = jd.hold - (int32_t)(jd.step0 - seg * jd.hold);
-  float c[MT];
+  const LagEnv L = lag_env(P.itau, fv.dt);
+  float lb[MT];
   auto load = [&](int64_t sg) {
+    float c[MT];
     procedural_commands<MT>(jd.cmd_seed, (uint64_t)el, sg, c);
 #pragma unroll
     for (int i = 0; i < MT; ++i) c[i] = (i < nt) ? c[i] * P.itau : 0.f;
+    lag_segment<MT>(c, L, lb);
   };
   load(seg);
   for (int32_t it = 0; it < jd.steps; ++it) {
@@ -80,7 +83,7 @@ __global__ void __maxnreg__(DIAG ? 128 : 168)
       left = jd.hold;
       load(seg);
     }
-    rk4_step<MT, DIAG, true, NH>(s, c, P, sdir, sarm, nt, current_accel, fv.dt);
+    rk4_step_lag<MT, DIAG, true, NH>(s, lb, L, P, sdir, sarm, nt, current_accel, fv.dt);
     --left;
     if (jd.traj) {
       float *t = jd.traj + ((int64_t)(jd.step0 + it) * MG_NTRAJ) * jd.n + el;

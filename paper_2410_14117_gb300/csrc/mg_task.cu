@@ -173,7 +173,9 @@ __global__ void __maxnreg__(XH ? kRegsXH : DIAG ? kRegsDiag : kRegsGeneral)
   if ((int)threadIdx.x >= bd.count) return;
   const int64_t e = (int64_t)bd.env0 + threadIdx.x;
   St<MT> s;
-  advance_env<MT, DIAG, MIXED, false, false, NH, XH>(
+  // the classic lag update fits the 128-register variants' epilogue; the 255-register XH
+  // variant takes the closed form, as k_fleet does
+  advance_env<MT, DIAG, MIXED, false, false, NH, XH, XH>(
       fv, e, MIXED ? bd.n_thr : MT, sdir, sarm, s_cursor + fv.cursor_off, k_launch, nullptr, s,
       XH ? sxh + threadIdx.x * MG_NXPARAM : nullptr);
 

@@ -388,6 +388,22 @@ def test_invalid_arguments_rejected_on_host():
         with pytest.raises(MGError) as ei:
             fn(*args)
         assert ei.value.code == "MG_EINVAL"
+    bad = [(sim.set_actions, (None, 0)), (sim.set_procedural_actions, (1, 0)),
+           (sim.set_schedule, (True, True, 65)), (sim.step_record, (0,)),
+           (sim.randomize, (1, 0.8, 1.2, -0.1)), (sim.randomize, (1, 0.8, 1.2, 0.2, -0.3)),
+           (sim.randomize, (1, 0.0, 1.2)), (sim.set_timestep, (2.0,))]
+    for fn, args in bad:
+        with pytest.raises(MGError) as ei:
+            fn(*args)
+        assert ei.value.code == "MG_EINVAL", (fn, args)
+    r = sim.get_params()
+    with pytest.raises(MGError):
+        sim.randomize(1, 0.8, 1.2, 0.2, 0.3, rg_halfwidth=-0.01)
+    torch.testing.assert_close(sim.get_params(), r, rtol=0, atol=0)  # nothing changed
+    with pytest.raises(MGError):
+        sim.set_task(0, torch.zeros((10, 4), device="cuda"), lookahead=65)
     with pytest.raises(MGError):
         Sim(10, np.full(10, 5), vs)
+    with pytest.raises((MGError, ValueError)):
+        Sim(0, np.zeros(0, dtype=np.int32), vs)
     sim.close()

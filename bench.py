@@ -578,9 +578,12 @@ def bench_adjoint(vs, n=4096, T=200, C=20, reps=5):
     import torch
     from paper_2410_14117_gb300 import inputs as I
     from paper_2410_14117_gb300.adjoint import COEF_SLICE, rollout
+    from paper_2410_14117_gb300.autotune import Autotuner
     from paper_2410_14117_gb300.sim import Sim
 
     sim = Sim(n, np.zeros(n, np.int32), vs)
+    # the forward's checkpoint segments are launches of C sub-steps: tune for that call size
+    launch = Autotuner(horizon=T, reps=2, k_per_call=C).tune(sim, vs)
     sim.randomize(1234, 0.8, 1.2, 0.2, 0.3)
     params = sim.get_params()
     coeffs = params[:, COEF_SLICE].clone().requires_grad_(True)
@@ -604,6 +607,7 @@ def bench_adjoint(vs, n=4096, T=200, C=20, reps=5):
     sim.close()
     return {"workload": f"{n:,} BlueROV2 envs, {T} RK4 sub-steps, checkpoints every {C}, "
                         "MSE on the trajectory",
+            "launch": dataclasses.asdict(launch),
             "forward_ms": f_ms, "forward_backward_ms": fb_ms,
             "backward_over_forward": (fb_ms - f_ms) / f_ms, "loss": float(loss.detach())}
 

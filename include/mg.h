@@ -102,9 +102,16 @@ typedef struct {
   float lo, hi;
   float current_sigma;
   float nu0_sigma;
-  uint32_t flags;
+  uint32_t flags;     /* 0 or MG_RANDOMIZE_ASYNC */
   float rg_halfwidth;
 } mg_ranges;
+
+/* mg_ranges.flags: return without waiting for the new parameters (the next calls queue behind
+ * them on the stream).  Only for fleets whose mass matrices are known on the host to be diagonal
+ * (every vehicle type with r_g = 0, rg_halfwidth = 0, no off-diagonal extension); a mass matrix
+ * that is not positive definite is then reported by mg_sync (MG_ENOTSPD) instead of by
+ * mg_randomize. */
+#define MG_RANDOMIZE_ASYNC 1u
 
 /* Model switch: drop the added-mass inertia of the current, M_A [omega x v_c^b; 0], which
  * follows from nu_r' = nu' + [omega x v_c^b; 0] for a current constant in NED. */
@@ -158,9 +165,10 @@ mg_status mg_set_schedule(mg_sim *sim, int32_t work_queue, int32_t wide, int32_t
 /* Domain randomisation (§METHOD; §EXPERIMENTS "supports domain randomization"): per env, draws
  * from Philox4x32-10 keyed by (seed, env id + offset), then builds M = M_RB + M_A in FP64 and
  * inverts it by Cholesky.  Also records (seed, nu0_sigma) for mg_reset and zeroes every env's
- * episode counter.  Synchronous.  Errors: MG_EINVAL (ranges NULL, lo > hi, lo <= 0, negative
- * sigma, flags != 0), MG_ENOTSPD (parameters are stored but some mass matrix has a pivot <= 0),
- * MG_ECUDA. */
+ * episode counter.  Synchronous unless ranges->flags has MG_RANDOMIZE_ASYNC.  Errors: MG_EINVAL
+ * (ranges NULL, lo > hi, lo <= 0, negative sigma or half-width, unknown flags, MG_RANDOMIZE_ASYNC
+ * for a fleet whose mass matrices may be full), MG_ENOTSPD (parameters are stored but some mass
+ * matrix has a pivot <= 0), MG_ECUDA. */
 mg_status mg_randomize(mg_sim *sim, uint64_t seed, const mg_ranges *ranges);
 
 /* Set every env's parameters from a [n][MG_NPARAM] record (host or device); inverts the mass
@@ -279,8 +287,8 @@ mg_status mg_reset(mg_sim *sim, const uint8_t *mask);
 
 /* Wait for the stream; *nonfinite_count (may be NULL) receives how many envs are flagged
  * non-finite.  Returns MG_ETIMEOUT if a work-queue wait ever gave up (results since then are
- * unreliable; this is not expected to happen), else MG_ENONFINITE when that count is
- * non-zero. */
+ * unreliable; this is not expected to happen), else MG_ENOTSPD if the current parameters hold a
+ * mass matrix that is not positive definite, else MG_ENONFINITE when that count is non-zero. */
 mg_status mg_sync(mg_sim *sim, int64_t *nonfinite_count);
 
 /* Per-env non-finite flags into out [n_envs] (host or device), 1 = flagged. */

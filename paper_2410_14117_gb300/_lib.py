@@ -12,6 +12,7 @@ from . import build as _build
 
 MG_NPARAM = 35
 MG_NXPARAM = 45
+MG_RANDOMIZE_ASYNC = 1
 MG_NSTATE = 21
 MG_NTRAJ = 13
 MG_MAX_THR = 8

@@ -86,6 +86,7 @@ struct mg_sim {
   NtVariant ntv = NT_6;
   bool diag = true;
   bool structured = false;  // every type present has the vectored thruster layout
+  bool nominal_diag = true;  // every type has r_g = 0 (randomised M_RB + M_A stays diagonal)
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
 
@@ -509,6 +510,7 @@ mg_status mg_create(int64_t n_envs, const int32_t *vehicle_types,
                              r[0] * d[1] - r[1] * d[0], 0.f);
     }
     if (seen[t] && !vectored_layout(g)) s->structured = false;
+    if (v.rg[0] != 0.f || v.rg[1] != 0.f || v.rg[2] != 0.f) s->nominal_diag = false;
     float *p = &nom[(size_t)t * MG_NPARAM];
     p[MG_P_M] = v.m;
     p[MG_P_IG] = v.Ixx;
@@ -639,9 +641,14 @@ mg_status mg_randomize(mg_sim *s, uint64_t seed, const mg_ranges *r) {
   MG_NONNULL(s);
   MG_NONNULL(r);
   if (!(r->lo > 0.f) || !(r->lo <= r->hi) || !(r->current_sigma >= 0.f) ||
-      !(r->nu0_sigma >= 0.f) || r->flags != 0 || !(r->rg_halfwidth >= 0.f))
-    return fail(MG_EINVAL,
-                "ranges: need 0 < lo <= hi, sigmas >= 0, rg_halfwidth >= 0, flags == 0");
+      !(r->nu0_sigma >= 0.f) || (r->flags & ~MG_RANDOMIZE_ASYNC) != 0 ||
+      !(r->rg_halfwidth >= 0.f))
+    return fail(MG_EINVAL, "ranges: need 0 < lo <= hi, sigmas >= 0, rg_halfwidth >= 0, "
+                           "flags 0 or MG_RANDOMIZE_ASYNC");
+  const bool async = (r->flags & MG_RANDOMIZE_ASYNC) != 0;
+  if (async && !(s->nominal_diag && r->rg_halfwidth == 0.f && !s->has_xh))
+    return fail(MG_EINVAL, "MG_RANDOMIZE_ASYNC needs mass matrices known to be diagonal "
+                           "(r_g = 0 for every type, rg_halfwidth = 0, no extension)");
   mg_status st = begin_params(s);
   if (st != MG_OK) return st;
   MG_CK(launch_randomize(s->setup_view(), s->nominal_d, seed, (double)r->lo, (double)r->hi,
@@ -649,6 +656,11 @@ mg_status mg_randomize(mg_sim *s, uint64_t seed, const mg_ranges *r) {
   MG_CK(cudaMemsetAsync(s->episode, 0, 4 * s->n, s->stream));
   s->reset_seed = seed;
   s->nu0_sigma = (double)r->nu0_sigma;
+  if (async) {  // diagonal by construction; a pivot <= 0 is left to mg_sync
+    if (!s->diag) s->drop_graphs();
+    s->diag = true;
+    return MG_OK;
+  }
   return finish_params(s);
 }
 
@@ -1015,6 +1027,13 @@ mg_status mg_sync(mg_sim *s, int64_t *nonfinite_count) {
     char buf[128];
     snprintf(buf, sizeof buf, "%llu work-queue waits timed out", to);
     return fail(MG_ETIMEOUT, buf);
+  }
+  unsigned long long bad = 0;
+  if ((st = read_counter(s, 1, &bad)) != MG_OK) return st;
+  if (bad) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "%llu envs have a mass matrix that is not positive definite", bad);
+    return fail(MG_ENOTSPD, buf);
   }
   if (c) {
     char buf[128];

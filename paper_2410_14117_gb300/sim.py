@@ -10,8 +10,8 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (MG_MAX_THR, MG_NPARAM, MG_NSTATE, MG_NXPARAM, MG_NTRAJ, MGError, Ranges, TaskSpec,
-                   VehicleParams, call)
+from ._lib import (MG_MAX_THR, MG_NPARAM, MG_NSTATE, MG_NTRAJ, MG_NXPARAM, MG_RANDOMIZE_ASYNC,
+                   MGError, Ranges, TaskSpec, VehicleParams, call)
 
 __all__ = ["Sim", "vehicle_struct", "MGError"]
 
@@ -111,8 +111,12 @@ class Sim:
 
     # ------------------------------------------------------------------ parameters
     def randomize(self, seed: int, lo: float = 0.8, hi: float = 1.2, current_sigma: float = 0.2,
-                  nu0_sigma: float = 0.3, rg_halfwidth: float = 0.0):
-        r = Ranges(lo, hi, current_sigma, nu0_sigma, 0, rg_halfwidth)
+                  nu0_sigma: float = 0.3, rg_halfwidth: float = 0.0, wait: bool = True):
+        """Domain randomisation (mg_randomize).  wait=False returns without waiting
+        (MG_RANDOMIZE_ASYNC: diagonal-mass fleets; a non-positive-definite mass matrix is then
+        reported by sync())."""
+        r = Ranges(lo, hi, current_sigma, nu0_sigma, 0 if wait else MG_RANDOMIZE_ASYNC,
+                   rg_halfwidth)
         call("mg_randomize", self._h, ctypes.c_uint64(seed), ctypes.byref(r))
 
     def set_params(self, params):

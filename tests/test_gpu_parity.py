@@ -379,6 +379,43 @@ def test_not_spd_reported():
     sim.close()
 
 
+def test_async_randomize_equals_sync_and_reports_not_spd_at_sync():
+    """MG_RANDOMIZE_ASYNC draws the same parameters without waiting; a mass matrix that is not
+    positive definite then surfaces at mg_sync; fleets whose mass matrix may be full reject it."""
+    import dataclasses
+    vs = vehicles()
+    n = 3000
+    types = I.mixed_fleet(17, n, max_group=400)
+    out = []
+    for wait in (True, False):
+        sim = make_sim(types, vs)
+        sim.randomize(55, 0.8, 1.2, 0.2, 0.3, wait=wait)
+        sim.reset()
+        sim.set_procedural_actions(56, 10)
+        sim.step(100)
+        assert sim.sync() == 0
+        out.append((sim.get_params().cpu(), gpu_state(sim)))
+        sim.close()
+    assert torch.equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    # surge added mass -11 kg against 11.5 kg: the nominal mass matrix is positive definite,
+    # but many draws (m x U[0.8,1.2] + M_A x U[0.8,1.2]) are not; accepted without waiting,
+    # reported by sync
+    bad = [dataclasses.replace(v, params=v.params.copy()) for v in vs]
+    bad[0].params[I.P_MA] = -11.0
+    sim = Sim(64, np.zeros(64, np.int32), bad)
+    sim.randomize(1, 0.8, 1.2, 0.2, 0.3, wait=False)
+    with pytest.raises(MGError) as ei:
+        sim.sync()
+    assert ei.value.code == "MG_ENOTSPD"
+    sim.close()
+    sim = make_sim(types, vs)
+    with pytest.raises(MGError) as ei:
+        sim.randomize(1, 0.8, 1.2, 0.2, 0.3, rg_halfwidth=0.01, wait=False)
+    assert ei.value.code == "MG_EINVAL"
+    sim.close()
+
+
 def test_invalid_arguments_rejected_on_host():
     vs = vehicles()
     sim = make_sim(np.zeros(10, dtype=np.int32), vs)

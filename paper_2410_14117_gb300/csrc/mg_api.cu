@@ -374,6 +374,7 @@ const char *mg_last_error(void) { return g_err.c_str(); }
 
 mg_status mg_step_noalloc(mg_sim *s, int32_t k) {
   MG_NONNULL(s);
+  NvtxRange nvtx("mg_step_noalloc");
   if (k < 1) return fail(MG_EINVAL, "k must be >= 1");
   if (s->has_xh)
     return fail(MG_EINVAL, "the work-queue kernel has no off-diagonal hydrodynamics variant");
@@ -639,6 +640,7 @@ mg_status mg_set_schedule(mg_sim *s, int32_t work_queue, int32_t wide, int32_t w
 
 mg_status mg_randomize(mg_sim *s, uint64_t seed, const mg_ranges *r) {
   MG_NONNULL(s);
+  NvtxRange nvtx("mg_randomize");
   MG_NONNULL(r);
   if (!(r->lo > 0.f) || !(r->lo <= r->hi) || !(r->current_sigma >= 0.f) ||
       !(r->nu0_sigma >= 0.f) || (r->flags & ~MG_RANDOMIZE_ASYNC) != 0 ||
@@ -666,6 +668,7 @@ mg_status mg_randomize(mg_sim *s, uint64_t seed, const mg_ranges *r) {
 
 mg_status mg_set_params(mg_sim *s, const float *in) {
   MG_NONNULL(s);
+  NvtxRange nvtx("mg_set_params");
   MG_NONNULL(in);
   const void *d = nullptr;
   mg_status st = input_ptr(s, in, (size_t)s->n * MG_NPARAM * 4, &d);
@@ -693,6 +696,7 @@ mg_status mg_get_params(mg_sim *s, float *out) {
 
 mg_status mg_set_hydro_offdiag(mg_sim *s, const float *x) {
   MG_NONNULL(s);
+  NvtxRange nvtx("mg_set_hydro_offdiag");
   mg_status st;
   if (x) {
     const size_t bytes = (size_t)s->n * MG_NXPARAM * 4;
@@ -795,6 +799,7 @@ mg_status mg_set_procedural_actions(mg_sim *s, uint64_t cmd_seed, int32_t hold_s
 
 mg_status mg_step(mg_sim *s, int32_t k) {
   MG_NONNULL(s);
+  NvtxRange nvtx("mg_step");
   if (k < 1) return fail(MG_EINVAL, "k must be >= 1");
   if (!s->use_graph) {
     mg_status st = launch_chunks(s, k, nullptr, s->stream);
@@ -838,6 +843,7 @@ mg_status mg_step(mg_sim *s, int32_t k) {
 
 mg_status mg_step_split(mg_sim *s, int32_t k, float *accel) {
   MG_NONNULL(s);
+  NvtxRange nvtx("mg_step_split");
   MG_NONNULL(accel);
   if (k < 1) return fail(MG_EINVAL, "k must be >= 1");
   if (!is_device_ptr(accel)) return fail(MG_EINVAL, "accel must be device memory");
@@ -859,6 +865,7 @@ mg_status mg_step_split(mg_sim *s, int32_t k, float *accel) {
 
 mg_status mg_step_record(mg_sim *s, int32_t k, float *traj) {
   MG_NONNULL(s);
+  NvtxRange nvtx("mg_step_record");
   MG_NONNULL(traj);
   if (k < 1) return fail(MG_EINVAL, "k must be >= 1");
   if (!is_device_ptr(traj)) return fail(MG_EINVAL, "traj must be device memory");
@@ -871,6 +878,7 @@ mg_status mg_step_record(mg_sim *s, int32_t k, float *traj) {
 mg_status mg_rollout_forward(mg_sim *s, int32_t T, int32_t C, float *traj, float *ckpt,
                              int64_t *step0_out) {
   MG_NONNULL(s);
+  NvtxRange nvtx("mg_rollout_forward");
   MG_NONNULL(traj);
   MG_NONNULL(ckpt);
   if (T < 1 || C < 1 || C > adjoint_max_interval())
@@ -897,6 +905,7 @@ mg_status mg_rollout_backward(mg_sim *s, int32_t T, int32_t C, const float *ckpt
                               const float *dtraj, int64_t step0, float *dcoef, float *dact,
                               float *dstate0) {
   MG_NONNULL(s);
+  NvtxRange nvtx("mg_rollout_backward");
   MG_NONNULL(ckpt);
   MG_NONNULL(dtraj);
   MG_NONNULL(dcoef);
@@ -944,6 +953,7 @@ mg_status mg_task_obs_dim(mg_sim *s, int32_t *obs_dim) {
 mg_status mg_task_step(mg_sim *s, int32_t k, float *obs, float *err, uint8_t *done,
                        float *episode_err) {
   MG_NONNULL(s);
+  NvtxRange nvtx("mg_task_step");
   MG_NONNULL(obs);
   MG_NONNULL(err);
   MG_NONNULL(done);
@@ -978,6 +988,7 @@ mg_status mg_task_step(mg_sim *s, int32_t k, float *obs, float *err, uint8_t *do
 
 mg_status mg_get_state(mg_sim *s, float *out) {
   MG_NONNULL(s);
+  NvtxRange nvtx("mg_get_state");
   MG_NONNULL(out);
   const size_t bytes = (size_t)s->n * MG_NSTATE * 4;
   if (is_device_ptr(out)) {
@@ -994,6 +1005,7 @@ mg_status mg_get_state(mg_sim *s, float *out) {
 
 mg_status mg_set_state(mg_sim *s, const float *in) {
   MG_NONNULL(s);
+  NvtxRange nvtx("mg_set_state");
   MG_NONNULL(in);
   const void *d = nullptr;
   mg_status st = input_ptr(s, in, (size_t)s->n * MG_NSTATE * 4, &d);
@@ -1005,6 +1017,7 @@ mg_status mg_set_state(mg_sim *s, const float *in) {
 
 mg_status mg_reset(mg_sim *s, const uint8_t *mask) {
   MG_NONNULL(s);
+  NvtxRange nvtx("mg_reset");
   const void *d = nullptr;
   if (mask) {
     mg_status st = input_ptr(s, mask, (size_t)s->n, &d);
@@ -1018,6 +1031,7 @@ mg_status mg_reset(mg_sim *s, const uint8_t *mask) {
 
 mg_status mg_sync(mg_sim *s, int64_t *nonfinite_count) {
   MG_NONNULL(s);
+  NvtxRange nvtx("mg_sync");
   unsigned long long c = 0, to = 0;
   mg_status st = read_counter(s, 2, &to);
   if (st != MG_OK) return st;

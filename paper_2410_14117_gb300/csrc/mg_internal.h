@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -12,6 +13,14 @@
 #include "mg.h"
 
 namespace mg {
+
+// NVTX range around an entry point, for timeline tools (free when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Records msg as this thread's mg_last_error() and returns st (mg_api.cu).
 mg_status set_error(mg_status st, const std::string &msg);

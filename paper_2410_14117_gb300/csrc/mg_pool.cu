@@ -370,6 +370,7 @@ mg_status mg_pool_set_stream(mg_pool *p, void *stream) {
 }
 
 mg_status mg_pool_admit(mg_pool *p, const mg_job_spec *spec, float *traj, int32_t *job_id) {
+  NvtxRange nvtx("mg_pool_admit");
   if (!p || !spec || !job_id) return pfail(MG_EINVAL, "NULL argument");
   const mg_job_spec &s = *spec;
   const mg_ranges &r = s.ranges;
@@ -420,6 +421,7 @@ mg_status mg_pool_admit(mg_pool *p, const mg_job_spec *spec, float *traj, int32_
 }
 
 mg_status mg_pool_tick(mg_pool *p, int32_t k, int32_t *n_running) {
+  NvtxRange nvtx("mg_pool_tick");
   if (!p) return pfail(MG_EINVAL, "NULL pool");
   if (k < 1) return pfail(MG_EINVAL, "k must be >= 1");
   std::vector<JobDesc> table;

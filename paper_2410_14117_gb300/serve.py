@@ -117,13 +117,20 @@ class Server:
     records); capacity_envs sizes the arena; k is the sub-steps per tick (chunk size)."""
 
     def __init__(self, vehicles, budget_bytes: float = 120e9, capacity_envs: int = 4 << 20,
-                 k: int = 50, record: bool = True, keep_results: bool = False):
+                 k: int = 50, record: bool = True, keep_results: bool = False,
+                 wait_timeout_s: float = 30.0, pool=None, event=None):
+        """wait_timeout_s bounds every host wait on the device (a tick that has not completed by
+        then raises TimeoutError instead of blocking forever); pool and event (a factory of
+        objects with record(stream) and query()) replace the device pool and CUDA events, for
+        host-side tests."""
         self.vehicles = vehicles
         self.budget = float(budget_bytes)
         self.k = int(k)
         self.record = record
         self.keep_results = keep_results
-        self.pool = Pool(capacity_envs, vehicles)
+        self.wait_timeout_s = float(wait_timeout_s)
+        self.pool = pool if pool is not None else Pool(capacity_envs, vehicles)
+        self.event = event if event is not None else torch.cuda.Event
         self.stream = self.pool.stream
         self.used = self.pool.capacity * ARENA_BYTES_PER_ENV
         self.peak_used = self.used
@@ -132,6 +139,10 @@ class Server:
 
     def close(self):
         self.pool.close()
+
+    def _traj_buffer(self, r):
+        dev = getattr(self.pool, "device", None)
+        return torch.empty((r.horizon, MG_NTRAJ, r.n_envs), dtype=torch.float32, device=dev)
 
     def run(self, requests, mode: str = "batched", realtime: bool = True, max_inflight: int = 2):
         """Serve ``requests`` (sorted by arrival_s); returns (served requests, stats)."""
@@ -155,7 +166,12 @@ class Server:
             return time.perf_counter() - t0
 
         def finish(ev, finishing):
-            ev.synchronize()
+            deadline = time.perf_counter() + self.wait_timeout_s
+            while not ev.query():  # polled, never an unbounded wait
+                if time.perf_counter() > deadline:
+                    raise TimeoutError(f"a serving tick did not complete within "
+                                       f"{self.wait_timeout_s} s")
+                time.sleep(20e-6)
             t = now()
             for jid in finishing:
                 r = running.pop(jid)
@@ -182,8 +198,7 @@ class Server:
                 need = traj_bytes(r) if self.record else 0
                 if self.used + need > self.budget:
                     break
-                traj = (torch.empty((r.horizon, MG_NTRAJ, r.n_envs), dtype=torch.float32,
-                                    device=pool.device) if self.record else None)
+                traj = (self._traj_buffer(r) if self.record else None)
                 jid = pool.admit(r.n_envs, r.vehicle, r.horizon, r.param_seed, r.cmd_seed,
                                  r.hold, traj)
                 if jid is None:
@@ -200,7 +215,7 @@ class Server:
                 finishing = [j for j in running
                              if pool.progress(j)[0] >= running[j].horizon and
                              not any(j in f for _, f in inflight)]
-                ev = torch.cuda.Event()
+                ev = self.event()
                 ev.record(self.stream)
                 inflight.append((ev, finishing))
                 while inflight and (len(inflight) > max_inflight or inflight[0][0].query()):

@@ -58,7 +58,12 @@ __global__ void __maxnreg__(XH ? kRegsXH : DIAG ? kRegsDiag : kRegsGeneral)
     sdir[threadIdx.x] = fv.geo[bd.type].dir[threadIdx.x];
     sarm[threadIdx.x] = fv.geo[bd.type].arm[threadIdx.x];
   }
-  if (threadIdx.x == 0) {  // the cursor load overlaps the geometry loads
+  // Programmatic dependent launch: the next launch in the stream may start (and run up to its
+  // own wait) now; everything above reads only buffers written before any step launch, and
+  // everything below waits for the previous launch in the stream to complete.
+  cudaTriggerProgrammaticLaunchCompletion();
+  cudaGridDependencySynchronize();
+  if (threadIdx.x == 0) {
     s_done = 0u;
     s_cursor = launch_cursor(fv);
   }
@@ -133,23 +138,37 @@ __global__ void __maxnreg__((DIAG && !WIDE) ? kRegsDiag : kRegsGeneral)
   if (fv.cursor_adv) finish_launch(fv, fv.cursor_adv);
 }
 
+// Launch a static-grid step kernel with programmatic stream serialisation: it may begin while
+// the previous kernel in the stream finishes (see the wait in k_fleet).
+template <typename Kernel>
+cudaError_t launch_pdl(Kernel kernel, int n_blocks, int threads, size_t smem, cudaStream_t stream,
+                       const FleetView &fv, const BlockDesc *blocks, int32_t k, float *traj) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)n_blocks);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, fv, blocks, k, traj);
+}
+
 // Structured allocation (NH = 4) is only instantiated for the diagonal-mass step, the
 // off-diagonal hydrodynamics (XH) only for the general one.
 template <int NTV, bool DIAG, bool REC>
 cudaError_t launch_t(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
                      bool structured, int32_t k, float *traj, cudaStream_t stream) {
-  if constexpr (!DIAG) if (fv.xh) {
-    k_fleet<NTV, false, REC, 0, true><<<n_blocks, threads,
-                                        sizeof(float) * MG_NXPARAM * threads, stream>>>(
-        fv, blocks, k, traj);
-    return cudaGetLastError();
-  }
+  if constexpr (!DIAG) if (fv.xh)
+    return launch_pdl(k_fleet<NTV, false, REC, 0, true>, n_blocks, threads,
+                      sizeof(float) * MG_NXPARAM * threads, stream, fv, blocks, k, traj);
   if (DIAG && structured)
-    k_fleet<NTV, DIAG, REC, (DIAG ? 4 : 0)><<<n_blocks, threads, 0, stream>>>(fv, blocks, k,
-                                                                             traj);
-  else
-    k_fleet<NTV, DIAG, REC, 0><<<n_blocks, threads, 0, stream>>>(fv, blocks, k, traj);
-  return cudaGetLastError();
+    return launch_pdl(k_fleet<NTV, DIAG, REC, (DIAG ? 4 : 0)>, n_blocks, threads, 0, stream, fv,
+                      blocks, k, traj);
+  return launch_pdl(k_fleet<NTV, DIAG, REC, 0>, n_blocks, threads, 0, stream, fv, blocks, k,
+                    traj);
 }
 
 template <int NTV, bool DIAG>

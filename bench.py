@@ -214,10 +214,18 @@ def cpu_baseline(n_envs, horizon, hold, target_s=12.0):
     for _ in range(reps):
         O.rollout(par, geo, types, s0, cmd, hold, steps, h=0.01)
     dt = time.perf_counter() - t
-    return {"value": ns * steps * reps / dt, "unit": "env-steps/s", "cores": O.max_threads(),
-            "kind": "oracle",
+    cores = O.max_threads()
+    # one core, on a 512-env slice of the same sample, for the per-core figure
+    t1 = time.perf_counter()
+    O.rollout(par[:512], geo, types[:512], s0[:512], cmd[:, :512], hold, 100, h=0.01,
+              nthreads=1)
+    single = 512 * 100 / (time.perf_counter() - t1)
+    O.rollout(par[:8], geo, types[:8], s0[:8], cmd[:, :8], hold, 1, h=0.01, nthreads=cores)
+    return {"value": ns * steps * reps / dt, "unit": "env-steps/s", "cores": cores,
+            "kind": "oracle", "single_core_value": single,
             "sample": f"{reps} x ({ns} envs x {steps} sub-steps) of the same randomised BlueROV2 "
-                      f"workload (FP64 oracle, OpenMP over envs), {dt:.1f} s"}
+                      f"workload (FP64 oracle, OpenMP over envs), {dt:.1f} s; single core: "
+                      "512 envs x 100 sub-steps"}
 
 
 def run_reference(args):

@@ -24,7 +24,7 @@ class LaunchConfig:
     schedule: str          # "static" or "queue"
     envs_per_block: int    # static grid block size
     steps_per_launch: int  # static: sub-steps per launch; queue: sub-steps per unit (chunk)
-    wide: bool = True      # queue: 168-register kernel
+    wide: bool = True      # queue: 200-register kernel (diagonal mass)
     warps_per_sm: int = 0  # queue: resident-warp cap (0 = as many as fit)
 
     def apply(self, sim: Sim, use_graph: bool = True):

@@ -11,6 +11,9 @@ namespace mg {
 // general step keeps 168.
 constexpr int kRegsDiag = 128;
 constexpr int kRegsGeneral = 168;
+// The work-queue kernel's wide diagonal-mass variant runs at 8 warps/SM, where 256 registers
+// per thread would fit; a 200 cap measured best (ptxas uses 184; +1.7 % over 168, none at 255).
+constexpr int kRegsQueueWide = 200;
 // With the off-diagonal hydrodynamics the 45 extra coefficients stay in registers too (no
 // spills up to 255; 8 resident warps per SM).
 constexpr int kRegsXH = 255;

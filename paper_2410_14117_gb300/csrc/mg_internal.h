@@ -122,7 +122,7 @@ cudaError_t fleet_kernel_attributes(NtVariant ntv, bool diag, bool structured, b
 // if slices x chunks would not fit 31 bits).
 constexpr int kQueueWarps = 4;
 size_t queue_sched_bytes(int n_slices);
-// wide: 168-register variant of the diagonal-mass step (fewer resident warps, more registers
+// wide: 200-register variant of the diagonal-mass step (fewer resident warps, more registers
 // each); warps_per_sm > 0 caps the resident warps per SM.
 cudaError_t launch_fleet_queue(const FleetView &fv, const BlockDesc *slices, int n_slices,
                                NtVariant ntv, bool diag, bool structured, bool wide,

@@ -81,7 +81,7 @@ __global__ void __maxnreg__(XH ? kRegsXH : DIAG ? kRegsDiag : kRegsGeneral)
 }
 
 template <int NTV, bool DIAG, bool WIDE, int NH>
-__global__ void __maxnreg__((DIAG && !WIDE) ? kRegsDiag : kRegsGeneral)
+__global__ void __maxnreg__(!DIAG ? kRegsGeneral : WIDE ? kRegsQueueWide : kRegsDiag)
     k_fleet_queue(const FleetView fv, const BlockDesc *__restrict__ slices, const int32_t n_slices,
                   const int32_t k_total, const int32_t chunk, uint32_t *__restrict__ sched) {
   constexpr int MT = (NTV == NT_6) ? 6 : 8;

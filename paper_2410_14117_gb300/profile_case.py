@@ -35,7 +35,7 @@ def main():
     ap.add_argument("--static", action="store_true",
                     help="static grid (one launch per k sub-steps) instead of the work queue")
     ap.add_argument("--narrow", action="store_true",
-                    help="work queue with the 128-register kernel instead of the 168-register one")
+                    help="work queue with the 128-register kernel instead of the 200-register one")
     ap.add_argument("--wps", type=int, default=8, help="work queue: resident warps per SM cap")
     ap.add_argument("--task", action="store_true",
                     help="circle-tracking task steps of k sub-steps (fused task epilogue) instead "

@@ -76,6 +76,7 @@ SIGNATURES = {
     "mg_set_timestep": [_P, _F],
     "mg_set_launch": [_P, _I32, _I32, _I32],
     "mg_set_schedule": [_P, _I32, _I32, _I32],
+    "mg_set_packed": [_P, _I32],
     "mg_randomize": [_P, _U64, ctypes.POINTER(Ranges)],
     "mg_set_params": [_P, _P],
     "mg_get_params": [_P, _P],

@@ -112,9 +112,16 @@ struct mg_sim {
   BlockDesc *blocks_d = nullptr;
   int n_blocks = 0;
   int threads = 128;
-  // work-queue schedule: 32-env slices and the scheduler words
+  // packed (two envs per thread) static blocks of at most 2 x threads envs
+  BlockDesc *pblocks_d = nullptr;
+  int n_pblocks = 0;
+  bool packed = false;
+  // work-queue schedule: 32-env slices (64-env slices for the packed kernel) and the scheduler
+  // words (sized for the 32-env slices, which are at least as many)
   BlockDesc *slices_d = nullptr;
   int n_slices = 0;
+  BlockDesc *pslices_d = nullptr;
+  int n_pslices = 0;
   uint32_t *sched = nullptr;
   int n_sm = 1;
   bool queue = false;
@@ -258,18 +265,25 @@ std::vector<BlockDesc> cut_runs(const mg_sim *s, int width) {
   return b;
 }
 
-// Build the static-schedule block list (pieces of at most epb envs).
+// Build the static-schedule block lists: pieces of at most epb envs (one env per thread), and
+// pieces of at most 2 x threads envs for the packed kernel (two envs per thread).
 mg_status build_blocks(mg_sim *s) {
+  s->threads = (int)align_up((size_t)s->epb, 32);
   const std::vector<BlockDesc> b = cut_runs(s, s->epb);
+  const std::vector<BlockDesc> pb = cut_runs(s, 2 * s->threads);
   if (s->blocks_d) {
     MG_CK(cudaStreamSynchronize(s->stream));
     cudaFree(s->blocks_d);
     s->blocks_d = nullptr;
+    s->pblocks_d = nullptr;
   }
-  MG_CK(cudaMalloc(&s->blocks_d, b.size() * sizeof(BlockDesc)));
+  MG_CK(cudaMalloc(&s->blocks_d, (b.size() + pb.size()) * sizeof(BlockDesc)));
+  s->pblocks_d = s->blocks_d + b.size();
   MG_CK(cudaMemcpy(s->blocks_d, b.data(), b.size() * sizeof(BlockDesc), cudaMemcpyHostToDevice));
+  MG_CK(cudaMemcpy(s->pblocks_d, pb.data(), pb.size() * sizeof(BlockDesc),
+                   cudaMemcpyHostToDevice));
   s->n_blocks = (int)b.size();
-  s->threads = (int)align_up((size_t)s->epb, 32);
+  s->n_pblocks = (int)pb.size();
   s->drop_graphs();
   return MG_OK;
 }
@@ -278,6 +292,24 @@ mg_status build_blocks(mg_sim *s) {
 // call, and the last advances the cursor by k.
 mg_status launch_chunks(mg_sim *s, int32_t k, float *traj, cudaStream_t stream) {
   FleetView v = s->view();
+  const bool packed = s->packed && s->diag && !traj && !s->has_xh;
+  if (packed && s->queue) {
+    v.cursor_adv = k;
+    MG_CK(launch_fleet_queue_pair(v, s->pslices_d, s->n_pslices, s->ntv, s->structured,
+                                  s->queue_warps_per_sm, k, s->spl, s->sched, s->n_sm, stream));
+    return MG_OK;
+  }
+  if (packed) {
+    for (int32_t done = 0; done < k;) {
+      const int32_t kk = std::min(s->spl, k - done);
+      v.cursor_off = done;
+      v.cursor_adv = (done + kk == k) ? k : 0;
+      MG_CK(launch_fleet_pair(v, s->pblocks_d, s->n_pblocks, s->threads, s->ntv, s->structured,
+                              kk, stream));
+      done += kk;
+    }
+    return MG_OK;
+  }
   if (s->queue && !traj && !s->has_xh) {
     v.cursor_adv = k;
     MG_CK(launch_fleet_queue(v, s->slices_d, s->n_slices, s->ntv, s->diag, s->structured,
@@ -458,6 +490,9 @@ mg_status mg_create(int64_t n_envs, const int32_t *vehicle_types,
   const std::vector<BlockDesc> slices = cut_runs(s, 32);
   s->n_slices = (int)slices.size();
   const size_t o_slices = take(sizeof(BlockDesc) * slices.size());
+  const std::vector<BlockDesc> pslices = cut_runs(s, 64);
+  s->n_pslices = (int)pslices.size();
+  const size_t o_pslices = take(sizeof(BlockDesc) * pslices.size());
   const size_t o_sched = take(queue_sched_bytes(s->n_slices));
   const size_t o_cnt = take(5 * sizeof(unsigned long long));
   const size_t o_off = take(sizeof(unsigned int));
@@ -488,6 +523,7 @@ mg_status mg_create(int64_t n_envs, const int32_t *vehicle_types,
   s->episode = (uint32_t *)(a + o_ep);
   s->counters = (unsigned long long *)(a + o_cnt);
   s->slices_d = (BlockDesc *)(a + o_slices);
+  s->pslices_d = (BlockDesc *)(a + o_pslices);
   s->sched = (uint32_t *)(a + o_sched);
   {
     cudaDeviceProp prop;
@@ -549,6 +585,8 @@ mg_status mg_create(int64_t n_envs, const int32_t *vehicle_types,
   MG_CKB(cudaMemset(s->episode, 0, 4 * n));
   MG_CKB(cudaMemset(s->counters, 0, 5 * sizeof(unsigned long long)));
   MG_CKB(cudaMemcpy(s->slices_d, slices.data(), sizeof(BlockDesc) * slices.size(),
+                    cudaMemcpyHostToDevice));
+  MG_CKB(cudaMemcpy(s->pslices_d, pslices.data(), sizeof(BlockDesc) * pslices.size(),
                     cudaMemcpyHostToDevice));
   MG_CKB(cudaMemset(s->offdiag, 0, sizeof(unsigned int)));
   // Nominal parameters: a randomisation with zero width.
@@ -634,6 +672,13 @@ mg_status mg_set_schedule(mg_sim *s, int32_t work_queue, int32_t wide, int32_t w
   s->queue = work_queue != 0;
   s->queue_wide = wide != 0;
   s->queue_warps_per_sm = warps_per_sm;
+  s->drop_graphs();
+  return MG_OK;
+}
+
+mg_status mg_set_packed(mg_sim *s, int32_t packed) {
+  MG_NONNULL(s);
+  s->packed = packed != 0;
   s->drop_graphs();
   return MG_OK;
 }
@@ -1092,7 +1137,9 @@ mg_status mg_kernel_info(mg_sim *s, int32_t *regs, int32_t *max_threads, int32_t
   MG_NONNULL(s);
   cudaFuncAttributes a;
   int per_sm = 0;
-  if (s->queue)
+  if (s->packed && s->diag && !s->has_xh)
+    MG_CK(pair_kernel_attributes(s->ntv, s->structured, s->queue, &a, nullptr));
+  else if (s->queue)
     MG_CK(queue_kernel_attributes(s->ntv, s->diag, s->queue_wide, s->structured, &a, &per_sm));
   else
     MG_CK(fleet_kernel_attributes(s->ntv, s->diag, s->structured, false, &a));

@@ -104,6 +104,10 @@ class Sim:
         call("mg_set_schedule", self._h, 1 if work_queue else 0, 1 if wide else 0,
              int(warps_per_sm))
 
+    def set_packed(self, packed: bool = True):
+        """Two envs per thread with packed FP32x2 arithmetic (see mg_set_packed)."""
+        call("mg_set_packed", self._h, 1 if packed else 0)
+
     def kernel_info(self) -> dict:
         r, t, l = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         call("mg_kernel_info", self._h, ctypes.byref(r), ctypes.byref(t), ctypes.byref(l))

@@ -128,16 +128,21 @@ class Clocks:
                 "samples": len(rows)}
 
 
-# Sources that make up the step kernels (k_fleet, k_fleet_queue); a committed ncu capture
-# describes them only while these files are unchanged.
-STEP_KERNEL_SOURCES = ("paper_2410_14117_gb300/csrc/mg_step.cu",
-                       "paper_2410_14117_gb300/csrc/mg_advance.cuh",
-                       "paper_2410_14117_gb300/csrc/mg_device.cuh",
-                       "paper_2410_14117_gb300/csrc/mg_internal.h",
-                       "include/mg.h")
+# Sources each profiled step kernel is compiled from; a committed ncu capture describes a kernel
+# only while its files are unchanged.
+_COMMON_SOURCES = ("paper_2410_14117_gb300/csrc/mg_advance.cuh",
+                   "paper_2410_14117_gb300/csrc/mg_device.cuh",
+                   "paper_2410_14117_gb300/csrc/mg_internal.h",
+                   "include/mg.h")
+KERNEL_SOURCES = {
+    "k_fleet": ("paper_2410_14117_gb300/csrc/mg_step.cu",) + _COMMON_SOURCES,
+    "k_fleet_queue": ("paper_2410_14117_gb300/csrc/mg_step.cu",) + _COMMON_SOURCES,
+    "k_fleet_step1": ("paper_2410_14117_gb300/csrc/mg_step.cu",) + _COMMON_SOURCES,
+    "k_fleet_pair": ("paper_2410_14117_gb300/csrc/mg_pair.cu",) + _COMMON_SOURCES,
+}
 
 
-def kernel_sources_sha(files=STEP_KERNEL_SOURCES) -> str:
+def kernel_sources_sha(files) -> str:
     """Hash of the sources a kernel is compiled from, to tell whether a committed ncu capture
     still describes the kernel being timed."""
     import hashlib
@@ -149,17 +154,18 @@ def kernel_sources_sha(files=STEP_KERNEL_SOURCES) -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str, units: float):
-    """DRAM bytes (read + write) per launch from profiles/dram_traffic.txt, scaled to a launch of
-    `units` env-sub-steps, or None when no capture of the current sources exists."""
+def profiled_traffic(kernel: str, n_envs: int, k: int):
+    """DRAM bytes (read + write) of one launch of `k` sub-steps over `n_envs` envs, from
+    profiles/dram_traffic.txt: a capture of the current sources with the same sub-steps per
+    launch, scaled by the env count (traffic is per env at a fixed k), else None."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or kernel not in KERNEL_SOURCES:
         return None
-    sha = kernel_sources_sha()
+    sha = kernel_sources_sha(KERNEL_SOURCES[kernel])
     for line in open(path):
         f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
-        if f.get("kernel") == kernel and f.get("sources_sha") == sha:
-            return float(f["dram_bytes"]) * units / float(f["units"])
+        if f.get("kernel") == kernel and f.get("sources_sha") == sha and int(f["k"]) == k:
+            return float(f["dram_bytes"]) * n_envs / float(f["n_envs"])
     return None
 
 
@@ -372,12 +378,14 @@ def run_ours(args):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = fp32_alu_peak_tflops(sm_max)
     achieved = flops / launch_s / 1e12
-    kname = "k_fleet" if cfg.schedule == "static" else "k_fleet_queue"
+    kname = ("k_fleet_queue" if cfg.schedule == "queue" else
+             "k_fleet_pair" if cfg.packed else "k_fleet")
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak,
-                "traffic": profiled_traffic(kname, n * horizon / launches_per_episode),
-                "kernel": ("k_fleet (persistent, static grid" if cfg.schedule == "static"
-                           else "k_fleet_queue (persistent, work queue") +
+                "traffic": profiled_traffic(kname, n, horizon // launches_per_episode),
+                "kernel": ("k_fleet_queue (persistent, work queue" if cfg.schedule == "queue"
+                           else "k_fleet_pair (persistent, static grid, two envs per thread"
+                           if cfg.packed else "k_fleet (persistent, static grid") +
                           ", 6 thrusters, diagonal mass)",
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 flops x {sm_max:.0f} MHz "
                                f"({peak_kind} max SM clock)",
@@ -456,6 +464,7 @@ def run_ours(args):
     if not args.no_per_step:
         sim.set_actions_borrowed(acts_dev, hold)
         sim.set_schedule(False)
+        sim.set_packed(False)
         sim.set_launch(args.epb, 1, False)
         sim.randomize(7, 0.8, 1.2, 0.2, 0.3)
         sim.reset()
@@ -488,7 +497,7 @@ def run_ours(args):
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         ach = bytes_per_launch / per_launch_s / 1e9
         fused_ms_episode = statistics.mean(graph_ms)
-        ps_traffic = profiled_traffic("k_fleet_step1", n)
+        ps_traffic = profiled_traffic("k_fleet_step1", n, 1)
         line["per_step"] = {
             "host_launched": n * horizon / (host_ms / 1e3),
             "graph": n * horizon / (graph_ms_ps / 1e3),

@@ -26,7 +26,7 @@ class LaunchConfig:
     steps_per_launch: int  # static: sub-steps per launch; queue: sub-steps per unit (chunk)
     wide: bool = True      # queue: 200-register kernel (diagonal mass)
     warps_per_sm: int = 0  # queue: resident-warp cap (0 = as many as fit)
-    packed: bool = False   # two envs per thread, packed FP32x2 arithmetic (diagonal mass)
+    packed: bool = False   # static: two envs per thread, packed FP32x2 arithmetic (diag. mass)
 
     def apply(self, sim: Sim, use_graph: bool = True):
         sim.set_launch(self.envs_per_block, self.steps_per_launch, use_graph)
@@ -41,8 +41,6 @@ DEFAULT_CANDIDATES = (
        for ch in (25, 50, 100)]
     + [LaunchConfig("static", epb, spl, packed=True) for epb in (32, 64, 128)
        for spl in (50, 1000)]
-    + [LaunchConfig("queue", 128, ch, True, wps, packed=True) for wps in (8, 4)
-       for ch in (25, 50, 100)]
 )
 
 

@@ -116,12 +116,9 @@ struct mg_sim {
   BlockDesc *pblocks_d = nullptr;
   int n_pblocks = 0;
   bool packed = false;
-  // work-queue schedule: 32-env slices (64-env slices for the packed kernel) and the scheduler
-  // words (sized for the 32-env slices, which are at least as many)
+  // work-queue schedule: 32-env slices and the scheduler words
   BlockDesc *slices_d = nullptr;
   int n_slices = 0;
-  BlockDesc *pslices_d = nullptr;
-  int n_pslices = 0;
   uint32_t *sched = nullptr;
   int n_sm = 1;
   bool queue = false;
@@ -292,14 +289,7 @@ mg_status build_blocks(mg_sim *s) {
 // call, and the last advances the cursor by k.
 mg_status launch_chunks(mg_sim *s, int32_t k, float *traj, cudaStream_t stream) {
   FleetView v = s->view();
-  const bool packed = s->packed && s->diag && !traj && !s->has_xh;
-  if (packed && s->queue) {
-    v.cursor_adv = k;
-    MG_CK(launch_fleet_queue_pair(v, s->pslices_d, s->n_pslices, s->ntv, s->structured,
-                                  s->queue_warps_per_sm, k, s->spl, s->sched, s->n_sm, stream));
-    return MG_OK;
-  }
-  if (packed) {
+  if (s->packed && !s->queue && s->diag && !traj && !s->has_xh) {
     for (int32_t done = 0; done < k;) {
       const int32_t kk = std::min(s->spl, k - done);
       v.cursor_off = done;
@@ -490,9 +480,6 @@ mg_status mg_create(int64_t n_envs, const int32_t *vehicle_types,
   const std::vector<BlockDesc> slices = cut_runs(s, 32);
   s->n_slices = (int)slices.size();
   const size_t o_slices = take(sizeof(BlockDesc) * slices.size());
-  const std::vector<BlockDesc> pslices = cut_runs(s, 64);
-  s->n_pslices = (int)pslices.size();
-  const size_t o_pslices = take(sizeof(BlockDesc) * pslices.size());
   const size_t o_sched = take(queue_sched_bytes(s->n_slices));
   const size_t o_cnt = take(5 * sizeof(unsigned long long));
   const size_t o_off = take(sizeof(unsigned int));
@@ -523,7 +510,6 @@ mg_status mg_create(int64_t n_envs, const int32_t *vehicle_types,
   s->episode = (uint32_t *)(a + o_ep);
   s->counters = (unsigned long long *)(a + o_cnt);
   s->slices_d = (BlockDesc *)(a + o_slices);
-  s->pslices_d = (BlockDesc *)(a + o_pslices);
   s->sched = (uint32_t *)(a + o_sched);
   {
     cudaDeviceProp prop;
@@ -585,8 +571,6 @@ mg_status mg_create(int64_t n_envs, const int32_t *vehicle_types,
   MG_CKB(cudaMemset(s->episode, 0, 4 * n));
   MG_CKB(cudaMemset(s->counters, 0, 5 * sizeof(unsigned long long)));
   MG_CKB(cudaMemcpy(s->slices_d, slices.data(), sizeof(BlockDesc) * slices.size(),
-                    cudaMemcpyHostToDevice));
-  MG_CKB(cudaMemcpy(s->pslices_d, pslices.data(), sizeof(BlockDesc) * pslices.size(),
                     cudaMemcpyHostToDevice));
   MG_CKB(cudaMemset(s->offdiag, 0, sizeof(unsigned int)));
   // Nominal parameters: a randomisation with zero width.
@@ -1137,8 +1121,8 @@ mg_status mg_kernel_info(mg_sim *s, int32_t *regs, int32_t *max_threads, int32_t
   MG_NONNULL(s);
   cudaFuncAttributes a;
   int per_sm = 0;
-  if (s->packed && s->diag && !s->has_xh)
-    MG_CK(pair_kernel_attributes(s->ntv, s->structured, s->queue, &a, nullptr));
+  if (s->packed && !s->queue && s->diag && !s->has_xh)
+    MG_CK(pair_kernel_attributes(s->ntv, s->structured, &a));
   else if (s->queue)
     MG_CK(queue_kernel_attributes(s->ntv, s->diag, s->queue_wide, s->structured, &a, &per_sm));
   else

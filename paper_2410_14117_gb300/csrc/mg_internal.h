@@ -131,18 +131,13 @@ cudaError_t launch_fleet_queue(const FleetView &fv, const BlockDesc *slices, int
 cudaError_t queue_kernel_attributes(NtVariant ntv, bool diag, bool wide, bool structured,
                                     cudaFuncAttributes *attr, int *blocks_per_sm);
 
-// Packed FP32x2 forms of the diagonal-mass step (mg_pair.cu): two envs per thread, results
-// bit-identical to launch_fleet / launch_fleet_queue.  Static grid: block b of `threads` threads
-// covers blocks[b] (at most 2 x threads envs).  Work queue: 64-env slices, sched as above.
+// Packed FP32x2 form of the diagonal-mass static-grid step (mg_pair.cu): two envs per thread,
+// results bit-identical to launch_fleet.  Block b of `threads` threads covers blocks[b] (at most
+// 2 x threads envs).
 cudaError_t launch_fleet_pair(const FleetView &fv, const BlockDesc *blocks, int n_blocks,
                               int threads, NtVariant ntv, bool structured, int32_t k,
                               cudaStream_t stream);
-cudaError_t launch_fleet_queue_pair(const FleetView &fv, const BlockDesc *slices, int n_slices,
-                                    NtVariant ntv, bool structured, int warps_per_sm, int32_t k,
-                                    int32_t chunk, uint32_t *sched, int n_sm,
-                                    cudaStream_t stream);
-cudaError_t pair_kernel_attributes(NtVariant ntv, bool structured, bool queue,
-                                   cudaFuncAttributes *attr, int *blocks_per_sm);
+cudaError_t pair_kernel_attributes(NtVariant ntv, bool structured, cudaFuncAttributes *attr);
 
 // True when thrusters [0, 4) of the geometry have d_z = 0 and the rest d_x = d_y = 0.
 bool vectored_layout(const Geo &g);

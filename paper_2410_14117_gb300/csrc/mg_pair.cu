@@ -10,10 +10,11 @@
 // scalar kernel at 65,536 vehicles.
 //
 // Covered: the diagonal-mass step (r_g = 0, diagonal M_A and D), 6, 8 or mixed thruster
-// counts, dense or vectored allocation, current-acceleration term on or off; static grid (block
-// of T threads = 2T vehicles: thread t takes vehicles env0 + t and env0 + T + t) and work queue
-// (64-vehicle slices: lane l takes env0 + l and env0 + 32 + l).  A thread whose second vehicle
-// is past its block's count evaluates the first one twice and stores it once.
+// counts, dense or vectored allocation, current-acceleration term on or off, on the static grid:
+// a block of T threads covers 2T vehicles, thread t taking vehicles env0 + t and env0 + T + t.  A
+// thread whose second vehicle is past its block's count evaluates the first one twice and
+// stores it once.  (A work-queue form over 64-vehicle slices measured slower than this static
+// grid at every fleet size and is not built.)
 #include <algorithm>
 
 #include "mg_advance.cuh"
@@ -108,6 +109,19 @@ struct GeoPair {
   float2 g[MG_MAX_THR][6];
 };
 
+// Two geometry pairs from shared memory, re-read at every use: an ordinary load of this
+// loop-invariant table is hoisted out of the sub-step loop and would hold ~50 registers for the
+// whole launch; all lanes read the same address (a broadcast), so the re-reads are cheap.
+__device__ __forceinline__ void lds_pairs(const float2 *p, float2 &a, float2 &b) {
+  float4 v;
+  const unsigned s = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(s));
+  a = make_float2(v.x, v.y);
+  b = make_float2(v.z, v.w);
+}
+
 __device__ __forceinline__ void stage_geo_pair(const Geo &src, GeoPair &dst, int i) {
   const float4 d = src.dir[i], a = src.arm[i];
   dst.g[i][0] = psplat(d.x); dst.g[i][1] = psplat(d.y); dst.g[i][2] = psplat(d.z);
@@ -126,7 +140,10 @@ __device__ __forceinline__ void rhs2(const St2<MT> &s, const Par2 &P, const GeoP
 #pragma unroll
   for (int i = 0; i < MT; ++i) {
     const float2 f = pmul(s.n[i], pabs(s.n[i]));
-    const float2 *g = G.g[i];
+    float2 g[6];
+    if (NH == 0 || i < NH) lds_pairs(&G.g[i][0], g[0], g[1]);
+    lds_pairs(&G.g[i][2], g[2], g[3]);
+    lds_pairs(&G.g[i][4], g[4], g[5]);
     if (NH == 0) {
       t0 = pfma(f, g[0], t0); t1 = pfma(f, g[1], t1); t2 = pfma(f, g[2], t2);
       t3 = pfma(f, g[3], t3); t4 = pfma(f, g[4], t4); t5 = pfma(f, g[5], t5);
@@ -360,76 +377,6 @@ __global__ void __maxnreg__(kRegsPair)
   if (fv.cursor_adv) finish_envs(fv, &s_done, live, fv.cursor_adv);
 }
 
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Bound on a work-queue wait (polls of ~128 ns, ~0.5 s), as k_fleet_queue.
-constexpr uint32_t kPairSpinLimit = 1u << 22;
-
-// Work queue over 64-vehicle slices (the schedule of k_fleet_queue: units claimed in
-// chunk-major order, each waiting, bounded, for its slice's previous chunk).
-template <int NTV, int NH>
-__global__ void __maxnreg__(kRegsPair)
-    k_fleet_queue_pair(const FleetView fv, const BlockDesc *__restrict__ slices,
-                       const int32_t n_slices, const int32_t k_total, const int32_t chunk,
-                       uint32_t *__restrict__ sched) {
-  constexpr int MT = (NTV == NT_6) ? 6 : 8;
-  constexpr bool MIXED = (NTV == NT_MIXED);
-  __shared__ GeoPair sgeo[MG_MAX_TYPES];
-  for (int i = threadIdx.x; i < fv.n_types * MG_MAX_THR; i += blockDim.x)
-    stage_geo_pair(fv.geo[i / MG_MAX_THR], sgeo[i / MG_MAX_THR], i % MG_MAX_THR);
-  const int64_t step0 = launch_cursor(fv) + fv.cursor_off;
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const uint32_t n_chunks = (uint32_t)((k_total + chunk - 1) / chunk);
-  const uint32_t n_units = (uint32_t)n_slices * n_chunks;  // < 2^31, checked by the launcher
-
-  for (;;) {
-    uint32_t u = 0;
-    if (lane == 0) u = atomicAdd(sched, 1u);
-    u = __shfl_sync(0xffffffffu, u, 0);
-    if (u >= n_units) break;
-    const int32_t c = (int32_t)(u / (uint32_t)n_slices);
-    const int32_t d = (int32_t)(u % (uint32_t)n_slices);
-    if (c > 0 && lane == 0) {
-      uint32_t polls = 0;
-      while (ld_acquire_u32(sched + 4 + d) < (uint32_t)c) {
-        if (++polls > kPairSpinLimit) {
-          atomicAdd(fv.counters + 2, 1ull);
-          break;
-        }
-        __nanosleep(128);
-      }
-    }
-    __syncwarp();
-    const BlockDesc bd = slices[d];
-    if (lane < bd.count) {
-      const int64_t ea = (int64_t)bd.env0 + lane;
-      const bool has_b = 32 + lane < bd.count;
-      const int64_t eb = has_b ? ea + 32 : ea;
-      St<MT> sa, sb;
-      advance_pair<MT, true, NH>(fv, ea, eb, MIXED ? bd.n_thr : MT,
-                                 sgeo[bd.type & (MG_MAX_TYPES - 1)], step0 + (int64_t)c * chunk,
-                                 min(chunk, k_total - c * chunk), sa, sb);
-      store_and_flag<MT, true>(fv, ea, sa);
-      if (has_b) store_and_flag<MT, true>(fv, eb, sb);
-    }
-    __syncwarp();
-    if (lane == 0) {
-      __threadfence();
-      st_release_u32(sched + 4 + d, (uint32_t)(c + 1));
-    }
-  }
-  if (fv.cursor_adv) finish_launch(fv, fv.cursor_adv);
-}
-
 template <typename Kernel>
 cudaError_t launch_pdl_pair(Kernel kernel, int n_blocks, int threads, cudaStream_t stream,
                             const FleetView &fv, const BlockDesc *blocks, int32_t k) {
@@ -452,18 +399,11 @@ const void *pair_ptr(bool structured) {
                     : reinterpret_cast<const void *>(&k_fleet_pair<NTV, 0>);
 }
 
-template <int NTV>
-const void *queue_pair_ptr(bool structured) {
-  return structured ? reinterpret_cast<const void *>(&k_fleet_queue_pair<NTV, 4>)
-                    : reinterpret_cast<const void *>(&k_fleet_queue_pair<NTV, 0>);
-}
-
-const void *pick_pair(NtVariant ntv, bool structured, bool queue) {
+const void *pick_pair(NtVariant ntv, bool structured) {
   switch (ntv) {
-    case NT_6: return queue ? queue_pair_ptr<NT_6>(structured) : pair_ptr<NT_6>(structured);
-    case NT_8: return queue ? queue_pair_ptr<NT_8>(structured) : pair_ptr<NT_8>(structured);
-    default:
-      return queue ? queue_pair_ptr<NT_MIXED>(structured) : pair_ptr<NT_MIXED>(structured);
+    case NT_6: return pair_ptr<NT_6>(structured);
+    case NT_8: return pair_ptr<NT_8>(structured);
+    default: return pair_ptr<NT_MIXED>(structured);
   }
 }
 
@@ -473,18 +413,6 @@ cudaError_t launch_pair_t(const FleetView &fv, const BlockDesc *blocks, int n_bl
   return structured
              ? launch_pdl_pair(k_fleet_pair<NTV, 4>, n_blocks, threads, stream, fv, blocks, k)
              : launch_pdl_pair(k_fleet_pair<NTV, 0>, n_blocks, threads, stream, fv, blocks, k);
-}
-
-template <int NTV>
-void queue_pair_launch(bool structured, int grid, const FleetView &fv, const BlockDesc *slices,
-                       int32_t n_slices, int32_t k, int32_t chunk, uint32_t *sched,
-                       cudaStream_t stream) {
-  if (structured)
-    k_fleet_queue_pair<NTV, 4><<<grid, kQueueWarps * 32, 0, stream>>>(fv, slices, n_slices, k,
-                                                                      chunk, sched);
-  else
-    k_fleet_queue_pair<NTV, 0><<<grid, kQueueWarps * 32, 0, stream>>>(fv, slices, n_slices, k,
-                                                                      chunk, sched);
 }
 
 }  // namespace
@@ -502,57 +430,8 @@ cudaError_t launch_fleet_pair(const FleetView &fv, const BlockDesc *blocks, int 
   }
 }
 
-cudaError_t pair_kernel_attributes(NtVariant ntv, bool structured, bool queue,
-                                   cudaFuncAttributes *attr, int *blocks_per_sm) {
-  const void *f = pick_pair(ntv, structured, queue);
-  cudaError_t e = cudaFuncGetAttributes(attr, f);
-  if (e != cudaSuccess || !blocks_per_sm) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kQueueWarps * 32, 0);
-}
-
-cudaError_t launch_fleet_queue_pair(const FleetView &fv, const BlockDesc *slices, int n_slices,
-                                    NtVariant ntv, bool structured, int warps_per_sm, int32_t k,
-                                    int32_t chunk, uint32_t *sched, int n_sm,
-                                    cudaStream_t stream) {
-  if (n_slices < 1 || k < 1 || chunk < 1 || n_sm < 1 || fv.xh) return cudaErrorInvalidValue;
-  cudaFuncAttributes attr;
-  int per_sm = 0;
-  cudaError_t e = pair_kernel_attributes(ntv, structured, true, &attr, &per_sm);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  if (warps_per_sm > 0) per_sm = std::max(1, std::min(per_sm, warps_per_sm / kQueueWarps));
-  int grid = per_sm * n_sm;
-  const int need = (n_slices + kQueueWarps - 1) / kQueueWarps;
-  if (grid > need) grid = need;
-  const int64_t max_chunks = ((int64_t)1 << 31) / n_slices;
-  if (max_chunks < 1) return cudaErrorInvalidValue;
-  for (int64_t done = 0; done < k;) {
-    const int64_t left = k - done;
-    const int32_t kk = (int32_t)std::min<int64_t>(left, max_chunks * (int64_t)chunk);
-    e = cudaMemsetAsync(sched, 0, queue_sched_bytes(n_slices), stream);
-    if (e != cudaSuccess) return e;
-    FleetView piece = fv;
-    piece.cursor_off = fv.cursor_off + (int32_t)done;
-    piece.cursor_adv = (done + kk == k) ? fv.cursor_adv : 0;
-    switch (ntv) {
-      case NT_6:
-        queue_pair_launch<NT_6>(structured, grid, piece, slices, n_slices, kk, chunk, sched,
-                                stream);
-        break;
-      case NT_8:
-        queue_pair_launch<NT_8>(structured, grid, piece, slices, n_slices, kk, chunk, sched,
-                                stream);
-        break;
-      default:
-        queue_pair_launch<NT_MIXED>(structured, grid, piece, slices, n_slices, kk, chunk, sched,
-                                    stream);
-        break;
-    }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    done += kk;
-  }
-  return cudaSuccess;
+cudaError_t pair_kernel_attributes(NtVariant ntv, bool structured, cudaFuncAttributes *attr) {
+  return cudaFuncGetAttributes(attr, pick_pair(ntv, structured));
 }
 
 }  // namespace mg

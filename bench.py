@@ -138,7 +138,8 @@ KERNEL_SOURCES = {
     "k_fleet": ("paper_2410_14117_gb300/csrc/mg_step.cu",) + _COMMON_SOURCES,
     "k_fleet_queue": ("paper_2410_14117_gb300/csrc/mg_step.cu",) + _COMMON_SOURCES,
     "k_fleet_step1": ("paper_2410_14117_gb300/csrc/mg_step.cu",) + _COMMON_SOURCES,
-    "k_fleet_pair": ("paper_2410_14117_gb300/csrc/mg_pair.cu",) + _COMMON_SOURCES,
+    "k_fleet_pair": ("paper_2410_14117_gb300/csrc/mg_pair.cu",
+                     "paper_2410_14117_gb300/csrc/mg_pair.cuh") + _COMMON_SOURCES,
 }
 
 

@@ -163,12 +163,12 @@ mg_status mg_set_launch(mg_sim *sim, int32_t envs_per_block, int32_t steps_per_l
 mg_status mg_set_schedule(mg_sim *sim, int32_t work_queue, int32_t wide, int32_t warps_per_sm);
 
 /* Packed arithmetic for the static-grid diagonal-mass step (every env with r_g = 0 and no
- * off-diagonal extension; other fleets, the work-queue schedule, mg_step_record, the task step,
- * the adjoint, the split step and the pool use the one-env-per-thread kernels).  packed != 0:
- * each thread advances two envs and issues every operation of the RK4 sub-step of Eq. 1
- * (§METHOD) as one FP32x2 instruction over the pair (sm_100+: a packed FMA is two correctly
- * rounded FMAs), so results are bit-identical to the one-env-per-thread kernels.  A block of
- * envs_per_block threads covers up to 2 x envs_per_block envs.  Default 0. */
+ * off-diagonal extension; other fleets, the work-queue schedule, mg_step_record, the fused last
+ * launch of mg_task_step, the adjoint, the split step and the pool use the one-env-per-thread
+ * kernels).  packed != 0: each thread advances two envs and issues every operation of the RK4
+ * sub-step of Eq. 1 (§METHOD) as one FP32x2 instruction over the pair (sm_100+: a packed FMA is
+ * two correctly rounded FMAs), so results are bit-identical to the one-env-per-thread kernels.
+ * A block of envs_per_block threads covers up to 2 x envs_per_block envs.  Default 0. */
 mg_status mg_set_packed(mg_sim *sim, int32_t packed);
 
 /* Domain randomisation (§METHOD; §EXPERIMENTS "supports domain randomization"): per env, draws

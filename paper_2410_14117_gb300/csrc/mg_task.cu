@@ -43,9 +43,9 @@ __device__ __forceinline__ float wrap_pi(float a) {
   return a - pi;
 }
 
-// Writes the observation of env e at task time t from its position p, attitude q and body
-// velocity nu; returns |p - p_r(t)|.
-__device__ __forceinline__ float observe(const TaskView &tv, int64_t e, float t, float px,
+// Writes the observation at task time t of an env with reference centre cen, from its position
+// p, attitude q and body velocity nu; returns |p - p_r(t)|.
+__device__ __forceinline__ float observe(const TaskView &tv, const float4 cen, float t, float px,
                                          float py, float pz, float qw, float qx, float qy,
                                          float qz, const float (&nu)[6], float *__restrict__ obs) {
   const float sp = fminf(1.f, fmaxf(-1.f, 2.f * (qw * qy - qz * qx)));
@@ -53,7 +53,6 @@ __device__ __forceinline__ float observe(const TaskView &tv, int64_t e, float t,
   const float theta = asinf(sp);
   const float psi = wrap_pi(atan2f(2.f * (qw * qz + qx * qy), 1.f - 2.f * (qy * qy + qz * qz)) -
                             tv.psi_r);
-  const float4 cen = tv.centre[e];
   const int m = tv.task == MG_TASK_STATION ? 1 : tv.m;
   for (int i = 0; i < m; ++i) {
     float x, y, z;
@@ -77,7 +76,22 @@ __device__ __forceinline__ float observe_planes(const TaskView &tv, const StateP
                                                 int64_t e, float t, float *__restrict__ obs) {
   const float4 a = st.s0[e], b = st.s1[e], c = st.s2[e], d = st.s3[e];
   const float nu[6] = {b.w, c.x, c.y, c.z, c.w, d.x};
-  return observe(tv, e, t, a.x, a.y, a.z, a.w, b.x, b.y, b.z, nu, obs);
+  return observe(tv, tv.centre[e], t, a.x, a.y, a.z, a.w, b.x, b.y, b.z, nu, obs);
+}
+
+// Room kept for a fused task kernel's static shared memory (thruster geometry, counters: under
+// 512 B) beside its dynamic staging of observation rows.
+constexpr size_t kStaticSmemReserve = 1024;
+// Dynamic shared memory a block may opt in to on GB300 (227 KB per block).
+constexpr size_t kMaxDynSmem = 227 * 1024;
+
+// Observation rows of `bytes` are staged in shared memory when they fit the opt-in limit.
+inline bool stage_fits(size_t bytes) { return bytes + kStaticSmemReserve <= kMaxDynSmem; }
+
+// Raise a kernel's dynamic shared-memory limit when a launch needs more than the default 48 KB.
+inline cudaError_t allow_dynamic_smem(const void *kernel, size_t bytes) {
+  if (bytes + kStaticSmemReserve <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 // Envs per block; the block's observations are staged in shared memory and written out as one
@@ -140,10 +154,97 @@ __global__ void __launch_bounds__(kTaskThreads)
 }
 
 // ---------------------------------------------------------------- fused task step
-// The last launch of a task step: the env's final sub-steps as in k_fleet, then, from the state
-// still in registers, the Eq. 4 error, the Eq. 2 observation, the episode bookkeeping and the
-// auto-reset, so the state is stored once and never re-read.  Each warp stages its 32 rows of
-// the observation in shared memory (when they fit) and writes them out as one contiguous run.
+// Per-env inputs of the task epilogue, loaded before any of its stores.
+struct TaskIn {
+  float4 centre;
+  int32_t clock;
+  uint32_t flag, episode;
+  float err_sum;
+};
+
+__device__ __forceinline__ TaskIn task_in(const FleetView &fv, const TaskView &tv,
+                                          const TaskOut &to, int64_t e) {
+  TaskIn in;
+  in.centre = tv.centre[e];
+  in.clock = tv.clock[e];
+  in.flag = fv.flags[e];
+  in.episode = to.episode[e];
+  in.err_sum = tv.err_sum[e];
+  return in;
+}
+
+// The task epilogue of env e from its state s after the task step's sub-steps (still in
+// registers): the Eq. 4 error, the episode bookkeeping, the auto-reset (the new episode is built
+// in s, so it is observed without a re-read), the state store and the Eq. 2 observation into row.
+template <int MT>
+__device__ __forceinline__ void task_epilogue(const FleetView &fv, const TaskView &tv,
+                                              const TaskOut &to, int32_t k_task, int64_t e,
+                                              const TaskIn &in, St<MT> &s, float *row) {
+  const int32_t clock = in.clock + k_task;
+  float t = (float)clock * fv.dt;
+  float rx, ry, rz;
+  reference(tv, in.centre, t, rx, ry, rz);
+  const float e0 = sqrtf((s.p[0] - rx) * (s.p[0] - rx) + (s.p[1] - ry) * (s.p[1] - ry) +
+                         (s.p[2] - rz) * (s.p[2] - rz));
+  const uint32_t flag = in.flag;
+  const bool bad = !all_finite<MT>(s) || (flag & 1u) || !(e0 == e0) || isinf(e0);
+  const bool over = (tv.max_err > 0.f && e0 > tv.max_err) ||
+                    (tv.episode_steps > 0 && clock >= tv.episode_steps);
+  const float sum = in.err_sum + e0;
+  to.err[e] = e0;
+  float nu[6] = {s.v[0], s.v[1], s.v[2], s.w[0], s.w[1], s.w[2]};
+  if (bad || over) {
+    // new episode (as reset_env)
+    const uint32_t ep = in.episode;
+    reset_nu(to.seed, (uint64_t)(fv.gid0 + e), ep, to.sigma, nu);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      s.p[i] = 0.f;
+      s.v[i] = nu[i];
+      s.w[i] = nu[3 + i];
+    }
+    s.q[0] = 1.f;
+    s.q[1] = s.q[2] = s.q[3] = 0.f;
+#pragma unroll
+    for (int i = 0; i < MT; ++i) s.n[i] = 0.f;
+    if (MT == 6) fv.st.s5[e] = 0.f;
+    to.episode[e] = ep + 1u;
+    if (flag & 1u) atomicAdd(fv.counters, ~0ull);  // decrement
+    fv.flags[e] = 0u;
+    to.done[e] = 1;
+    if (to.ep_err) to.ep_err[e] = sum;
+    tv.clock[e] = 0;
+    tv.err_sum[e] = 0.f;
+    t = 0.f;
+  } else {
+    to.done[e] = 0;
+    if (to.ep_err) to.ep_err[e] = 0.f;
+    tv.clock[e] = clock;
+    tv.err_sum[e] = sum;
+  }
+  store_state<MT>(fv.st, e, s);
+  observe(tv, in.centre, t, s.p[0], s.p[1], s.p[2], s.q[0], s.q[1], s.q[2], s.q[3], nu, row);
+}
+
+// Copy n_rows staged observation rows (src, in shared memory) to dst, by the warp's n_act live
+// lanes (its low lanes); 16-byte stores when both ends allow.
+__device__ __forceinline__ void copy_rows(const float *src, float *dst, int n_rows, int obs_dim,
+                                          int lane, int n_act) {
+  const int total = n_rows * obs_dim;
+  int i0 = 0;
+  if (((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15) == 0) {
+    const int n4 = total >> 2;
+    for (int i = lane; i < n4; i += n_act)
+      reinterpret_cast<float4 *>(dst)[i] = reinterpret_cast<const float4 *>(src)[i];
+    i0 = n4 << 2;
+  }
+  for (int i = i0 + lane; i < total; i += n_act) dst[i] = src[i];
+}
+
+// The last launch of a task step: the env's final sub-steps as in k_fleet, then the task
+// epilogue from the state still in registers, so the state is stored once and never re-read.
+// Each warp stages its 32 rows of the observation in shared memory (when they fit) and writes
+// them out as one contiguous run.
 template <int NTV, bool DIAG, int NH, bool XH>
 __global__ void __maxnreg__(XH ? kRegsXH : DIAG ? kRegsDiag : kRegsGeneral)
     k_fleet_task(const FleetView fv, const BlockDesc *__restrict__ blocks, const int32_t k_launch,
@@ -180,51 +281,8 @@ __global__ void __maxnreg__(XH ? kRegsXH : DIAG ? kRegsDiag : kRegsGeneral)
       XH ? sxh + threadIdx.x * MG_NXPARAM : nullptr);
 
   const int obs_dim = to.obs_dim;
-  float *row = to.stage ? sobs + threadIdx.x * obs_dim : to.obs + e * obs_dim;
-  const int32_t clock = tv.clock[e] + k_task;
-  float t = (float)clock * fv.dt;
-  float rx, ry, rz;
-  reference(tv, tv.centre[e], t, rx, ry, rz);
-  const float e0 = sqrtf((s.p[0] - rx) * (s.p[0] - rx) + (s.p[1] - ry) * (s.p[1] - ry) +
-                         (s.p[2] - rz) * (s.p[2] - rz));
-  const uint32_t flag = fv.flags[e];
-  const bool bad = !all_finite<MT>(s) || (flag & 1u) || !(e0 == e0) || isinf(e0);
-  const bool over = (tv.max_err > 0.f && e0 > tv.max_err) ||
-                    (tv.episode_steps > 0 && clock >= tv.episode_steps);
-  const float sum = tv.err_sum[e] + e0;
-  to.err[e] = e0;
-  float nu[6] = {s.v[0], s.v[1], s.v[2], s.w[0], s.w[1], s.w[2]};
-  if (bad || over) {
-    // new episode (as reset_env), built in registers so it is observed without a re-read
-    const uint32_t ep = to.episode[e];
-    reset_nu(to.seed, (uint64_t)(fv.gid0 + e), ep, to.sigma, nu);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      s.p[i] = 0.f;
-      s.v[i] = nu[i];
-      s.w[i] = nu[3 + i];
-    }
-    s.q[0] = 1.f;
-    s.q[1] = s.q[2] = s.q[3] = 0.f;
-#pragma unroll
-    for (int i = 0; i < MT; ++i) s.n[i] = 0.f;
-    if (MT == 6) fv.st.s5[e] = 0.f;
-    to.episode[e] = ep + 1u;
-    if (flag & 1u) atomicAdd(fv.counters, ~0ull);  // decrement
-    fv.flags[e] = 0u;
-    to.done[e] = 1;
-    if (to.ep_err) to.ep_err[e] = sum;
-    tv.clock[e] = 0;
-    tv.err_sum[e] = 0.f;
-    t = 0.f;
-  } else {
-    to.done[e] = 0;
-    if (to.ep_err) to.ep_err[e] = 0.f;
-    tv.clock[e] = clock;
-    tv.err_sum[e] = sum;
-  }
-  store_state<MT>(fv.st, e, s);
-  observe(tv, e, t, s.p[0], s.p[1], s.p[2], s.q[0], s.q[1], s.q[2], s.q[3], nu, row);
+  task_epilogue<MT>(fv, tv, to, k_task, e, task_in(fv, tv, to, e), s,
+                    to.stage ? sobs + threadIdx.x * obs_dim : to.obs + e * obs_dim);
   if (fv.cursor_adv) finish_envs(fv, &s_done, bd.count, fv.cursor_adv);
   if (!to.stage) return;
   // Warp copy-out: the warp's live lanes are its low lanes (threads below bd.count).
@@ -232,27 +290,22 @@ __global__ void __maxnreg__(XH ? kRegsXH : DIAG ? kRegsDiag : kRegsGeneral)
   const int wbase = threadIdx.x & ~31;
   const int n_act = min(32, bd.count - wbase);
   __syncwarp(n_act == 32 ? 0xffffffffu : ((1u << n_act) - 1u));
-  const int total = n_act * obs_dim;
-  const float *src = sobs + wbase * obs_dim;
-  float *dst = to.obs + ((int64_t)bd.env0 + wbase) * obs_dim;
-  int i0 = 0;
-  if (((reinterpret_cast<uintptr_t>(dst) | (uintptr_t)(wbase * obs_dim * 4)) & 15) == 0) {
-    const int n4 = total >> 2;
-    for (int i = lane; i < n4; i += n_act)
-      reinterpret_cast<float4 *>(dst)[i] = reinterpret_cast<const float4 *>(src)[i];
-    i0 = n4 << 2;
-  }
-  for (int i = i0 + lane; i < total; i += n_act) dst[i] = src[i];
+  copy_rows(sobs + wbase * obs_dim, to.obs + ((int64_t)bd.env0 + wbase) * obs_dim, n_act, obs_dim,
+            lane, n_act);
 }
 
 template <int NTV, bool DIAG, int NH, bool XH = false>
 cudaError_t fleet_task_t(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
                          int32_t k_launch, int32_t k_task, const TaskView &tv, const TaskOut &to,
                          size_t smem, cudaStream_t stream) {
+  const cudaError_t e = allow_dynamic_smem(
+      reinterpret_cast<const void *>(&k_fleet_task<NTV, DIAG, NH, XH>), smem);
+  if (e != cudaSuccess) return e;
   k_fleet_task<NTV, DIAG, NH, XH><<<n_blocks, threads, smem, stream>>>(fv, blocks, k_launch,
                                                                        k_task, tv, to);
   return cudaGetLastError();
 }
+
 
 template <int NTV>
 cudaError_t fleet_task_d(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
@@ -302,10 +355,10 @@ cudaError_t launch_fleet_task(const FleetView &fv, const BlockDesc *blocks, int 
       k_task < k_launch || (fv.xh && diag))
     return cudaErrorInvalidValue;
   // The off-diagonal hydrodynamics (if any) come first; the observation rows are staged in
-  // shared memory when both fit in 48 KB.
+  // shared memory when both fit beside the static shared memory (above 48 KB by opt-in).
   const size_t xh_bytes = fv.xh ? sizeof(float) * threads * MG_NXPARAM : 0;
   const size_t smem = sizeof(float) * threads * to.obs_dim;
-  to.stage = xh_bytes + smem <= 48 * 1024 ? 1 : 0;
+  to.stage = stage_fits(xh_bytes + smem) ? 1 : 0;
   const size_t dyn = xh_bytes + (to.stage ? smem : 0);
   switch (ntv) {
     case NT_6:

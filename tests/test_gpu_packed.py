@@ -172,3 +172,4 @@ def test_packed_kernel_info_and_fallbacks():
         out.append(sim.get_state().cpu().numpy())
         sim.close()
     np.testing.assert_array_equal(out[1], out[0])
+

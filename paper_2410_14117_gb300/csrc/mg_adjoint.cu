@@ -412,13 +412,22 @@ cudaError_t launch_adjoint(const FleetView &fv, const int32_t *types, bool eight
                            int64_t step0, float *dcoef, float *dact, float *dstate0,
                            cudaStream_t stream) {
   if (C < 1 || C > kMaxSeg || T < 1) return cudaErrorInvalidValue;
-  const int grid = (int)((fv.n + kAdjThreads - 1) / kAdjThreads);
+  // One warp per block while the fleet has fewer warps than the GPU has SMs x 4 (the backward
+  // pass is latency-bound, so its warps should be spread over all SMs, each with its own L1 for
+  // the threads' recompute buffers), larger blocks beyond.
+  int n_sm = 0, dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int64_t warps = (fv.n + 31) / 32;
+  const int threads = warps <= 4 * (int64_t)n_sm ? 32 : kAdjThreads;
+  const int grid = (int)((fv.n + threads - 1) / threads);
   if (eight)
-    k_adjoint<8><<<grid, kAdjThreads, 0, stream>>>(fv, types, ckpt, dtraj, T, C, step0, dcoef,
-                                                  dact, dstate0);
+    k_adjoint<8><<<grid, threads, 0, stream>>>(fv, types, ckpt, dtraj, T, C, step0, dcoef, dact,
+                                              dstate0);
   else
-    k_adjoint<6><<<grid, kAdjThreads, 0, stream>>>(fv, types, ckpt, dtraj, T, C, step0, dcoef,
-                                                  dact, dstate0);
+    k_adjoint<6><<<grid, threads, 0, stream>>>(fv, types, ckpt, dtraj, T, C, step0, dcoef, dact,
+                                              dstate0);
   return cudaGetLastError();
 }
 

@@ -324,7 +324,6 @@ def run_ours(args):
     acts_host = torch.from_numpy(acts_np).pin_memory()
     acts_dev = acts_host.to(dev)
     out_dev = torch.empty((n, 21), dtype=torch.float32, device=dev)
-    out_host = torch.empty((n, 21), dtype=torch.float32).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     launches_per_episode = (math.ceil(horizon / cfg.steps_per_launch)
                             if cfg.schedule == "static" else 1)
@@ -402,49 +401,24 @@ def run_ours(args):
             "clocks": clk,
             "gpu_launches": args.steps * (launches_per_episode + 3)}
 
-    # ---- end to end through the public API with host buffers: every episode's throttle
-    # schedule is copied from pinned host memory (on a side stream, into one of two device
-    # buffers, so that episode i+1's copy overlaps episode i's compute) and every episode's
-    # final state is read back to pinned host memory (exported to one of two device buffers,
-    # copied on another side stream, overlapping the next episode); parameters are randomised
-    # without a host wait (MG_RANDOMIZE_ASYNC: the fleet's mass matrices are diagonal).  All
-    # copies have completed when the clock stops.
+    # ---- end to end through the C ABI with host buffers: every episode's throttle schedule
+    # goes in from page-locked host memory (mg_set_actions_async: the library's copy stream,
+    # one of two device buffers, overlapping the previous episode's steps) and every episode's
+    # final state comes back to page-locked host memory (mg_get_state_async: the library's
+    # read-back stream, overlapping the next episode); parameters are randomised without a host
+    # wait (MG_RANDOMIZE_ASYNC: the fleet's mass matrices are diagonal).  All copies have
+    # completed when the clock stops (mg_sync).
     if not args.no_e2e:
         ke = min(args.steps, 10)
-        copy_stream, d2h_stream = torch.cuda.Stream(), torch.cuda.Stream()
-        bufs = [acts_dev, torch.empty_like(acts_dev)]
-        copied = [torch.cuda.Event(), torch.cuda.Event()]
-        free = [torch.cuda.Event(), torch.cuda.Event()]
-        outs_dev = [torch.empty((n, 21), dtype=torch.float32, device=dev) for _ in range(2)]
         outs_host = [torch.empty((n, 21), dtype=torch.float32).pin_memory() for _ in range(2)]
-        exported = [torch.cuda.Event(), torch.cuda.Event()]
-        read = [torch.cuda.Event(), torch.cuda.Event()]
-
-        def prefetch(i):
-            with torch.cuda.stream(copy_stream):
-                copy_stream.wait_event(free[i % 2])
-                bufs[i % 2].copy_(acts_host, non_blocking=True)
-                copied[i % 2].record(copy_stream)
 
         def e2e_episodes(count, seed0):
-            prefetch(0)
             for i in range(count):
-                if i + 1 < count:
-                    prefetch(i + 1)
-                stream.wait_event(copied[i % 2])
+                sim.set_actions_async(acts_host, hold)
                 sim.randomize(seed0 + i, 0.8, 1.2, 0.2, 0.3, wait=False)
                 sim.reset()
-                sim.set_actions_borrowed(bufs[i % 2], hold)
                 sim.step(horizon)
-                free[i % 2].record(stream)
-                stream.wait_event(read[i % 2])        # the buffer's previous read-back is done
-                sim.get_state(outs_dev[i % 2])
-                exported[i % 2].record(stream)
-                with torch.cuda.stream(d2h_stream):
-                    d2h_stream.wait_event(exported[i % 2])
-                    outs_host[i % 2].copy_(outs_dev[i % 2], non_blocking=True)
-                    read[i % 2].record(d2h_stream)
-            torch.cuda.synchronize()
+                sim.get_state_async(outs_host[i % 2])
             assert sim.sync() == 0
 
         e2e_episodes(2, 1)
@@ -455,10 +429,11 @@ def run_ours(args):
         line["e2e"] = {"value": world * n * horizon * ke / el, "unit": "env-steps/s",
                        "h2d_bytes_per_step": acts_np.nbytes,
                        "d2h_bytes_per_step": n * 21 * 4,
-                       "note": "per episode: throttle schedule H2D from pinned host (side stream, "
-                               "double-buffered, overlapping the previous episode), parameters "
-                               "randomised without a host wait, final state D2H to pinned host "
-                               "(side stream, double-buffered), all inside the wall-clock timed "
+                       "note": "per episode, through the C ABI: throttle schedule H2D from "
+                               "page-locked host memory (mg_set_actions_async, overlapping the "
+                               "previous episode), parameters randomised without a host wait, "
+                               "final state D2H to page-locked host memory (mg_get_state_async, "
+                               "overlapping the next episode), all inside the wall-clock timed "
                                "region"}
 
     # ---- the plain per-step form on the same GPU (one launch per sub-step)

@@ -288,13 +288,31 @@ mg_status mg_rollout_backward(mg_sim *sim, int32_t T, int32_t C, const float *ck
 mg_status mg_get_state(mg_sim *sim, float *out);
 mg_status mg_set_state(mg_sim *sim, const float *in);
 
+/* Asynchronous transfers with page-locked host memory (cudaHostAlloc / cudaHostRegister), for
+ * pipelines in which one episode's copies overlap the neighbouring episodes' steps.  Neither
+ * call waits: each copy runs on a stream of the library's own, into or out of one of two device
+ * buffers used alternately, ordered after the work that last used that buffer; mg_sync waits
+ * for these copies too.  Results are those of the synchronous calls.
+ *   mg_set_actions_async: as mg_set_actions (a: host [n_seg][n_envs][MG_MAX_THR], n_seg >= 1);
+ *     the steps queued after the call read the copy once it has landed.  The caller keeps a
+ *     unchanged until mg_sync returns, or until a second later call of mg_set_actions_async has
+ *     returned (which reuses this call's device buffer only after this call's steps).
+ *   mg_get_state_async: as mg_get_state into out (host [n_envs][MG_NSTATE]) of the state the
+ *     steps queued so far leave; out is complete once mg_sync returns.  A third call reuses the
+ *     first call's device buffer only after its copy has finished.
+ * Errors: MG_EINVAL (NULL, pageable or device memory, n_seg < 1, hold_steps < 1), MG_ENOMEM,
+ * MG_ECUDA. */
+mg_status mg_set_actions_async(mg_sim *sim, const float *a, int32_t n_seg, int32_t hold_steps);
+mg_status mg_get_state_async(mg_sim *sim, float *out);
+
 /* Start a new episode for every env whose mask byte is non-zero (mask: host or device
  * [n_envs]; NULL = all): p = 0, q = identity, n = 0, nu ~ N(0, nu0_sigma) drawn from Philox
  * keyed by (seed, env id + offset, the env's episode counter; Box-Muller evaluated in FP32),
  * then the counter is incremented and the env's non-finite flag cleared. */
 mg_status mg_reset(mg_sim *sim, const uint8_t *mask);
 
-/* Wait for the stream; *nonfinite_count (may be NULL) receives how many envs are flagged
+/* Wait for the stream (and the asynchronous host copies, if any have been issued);
+ * *nonfinite_count (may be NULL) receives how many envs are flagged
  * non-finite.  Returns MG_ETIMEOUT if a work-queue wait ever gave up (results since then are
  * unreliable; this is not expected to happen), else MG_ENOTSPD if the current parameters hold a
  * mass matrix that is not positive definite, else MG_ENONFINITE when that count is non-zero. */

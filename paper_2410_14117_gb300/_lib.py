@@ -82,6 +82,8 @@ SIGNATURES = {
     "mg_get_params": [_P, _P],
     "mg_set_actions": [_P, _P, _I32, _I32],
     "mg_set_actions_borrowed": [_P, _P, _I32, _I32],
+    "mg_set_actions_async": [_P, _P, _I32, _I32],
+    "mg_get_state_async": [_P, _P],
     "mg_set_procedural_actions": [_P, _U64, _I32],
     "mg_step": [_P, _I32],
     "mg_step_noalloc": [_P, _I32],

@@ -69,8 +69,15 @@ bool is_device_ptr(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// A captured mg_step launch sequence.  Besides k it bakes in the action source the kernels read
+// (buffer, segment count, hold, procedural seed), so those are part of the key: alternating
+// between action buffers replays cached graphs instead of capturing new ones.  Every other
+// setting a capture depends on drops the cache when it changes.
 struct GraphEntry {
   int32_t k;
+  const float *act_src;
+  int32_t n_seg, hold, proc;
+  uint64_t cmd_seed;
   cudaGraphExec_t exec;
   uint64_t last_use;
 };
@@ -146,6 +153,19 @@ struct mg_sim {
   // staging for host I/O
   void *stage = nullptr;
   size_t stage_cap = 0;
+
+  // asynchronous transfers from / to page-locked host memory (mg_set_actions_async,
+  // mg_get_state_async): two device buffers each way, used alternately, with their own copy
+  // streams; events order each copy after the last reader of its buffer and the sim's work after
+  // the copy it needs.  Created on first use.
+  cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr;
+  float *abuf[2] = {nullptr, nullptr};
+  size_t abuf_cap[2] = {0, 0};  // floats
+  cudaEvent_t a_copied[2] = {nullptr, nullptr}, a_released[2] = {nullptr, nullptr};
+  int a_next = 0, a_active = -1;  // a_active: the slot the kernels read, or -1
+  float *obuf[2] = {nullptr, nullptr};
+  cudaEvent_t o_exported[2] = {nullptr, nullptr}, o_read[2] = {nullptr, nullptr};
+  int o_next = 0;
 
   // task layer
   bool has_task = false;
@@ -317,6 +337,37 @@ mg_status launch_chunks(mg_sim *s, int32_t k, float *traj, cudaStream_t stream) 
     done += kk;
   }
   return MG_OK;
+}
+
+// Streams and events of the asynchronous host transfers.
+mg_status ensure_async(mg_sim *s) {
+  if (s->h2d_stream) return MG_OK;
+  MG_CK(cudaStreamCreateWithFlags(&s->h2d_stream, cudaStreamNonBlocking));
+  MG_CK(cudaStreamCreateWithFlags(&s->d2h_stream, cudaStreamNonBlocking));
+  for (int i = 0; i < 2; ++i) {
+    MG_CK(cudaEventCreateWithFlags(&s->a_copied[i], cudaEventDisableTiming));
+    MG_CK(cudaEventCreateWithFlags(&s->a_released[i], cudaEventDisableTiming));
+    MG_CK(cudaEventCreateWithFlags(&s->o_exported[i], cudaEventDisableTiming));
+    MG_CK(cudaEventCreateWithFlags(&s->o_read[i], cudaEventDisableTiming));
+  }
+  return MG_OK;
+}
+
+// The asynchronous action buffer the kernels read (if any) stops being read: everything queued
+// on the sim's stream so far is its last use.
+mg_status release_async_actions(mg_sim *s) {
+  if (s->a_active >= 0) MG_CK(cudaEventRecord(s->a_released[s->a_active], s->stream));
+  s->a_active = -1;
+  return MG_OK;
+}
+
+bool is_pinned_host(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
 }
 
 mg_status read_counter(mg_sim *s, int idx, unsigned long long *out) {
@@ -594,6 +645,20 @@ mg_status mg_destroy(mg_sim *s) {
   cudaDeviceSynchronize();
   s->drop_graphs();
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  if (s->h2d_stream) {
+    cudaStreamSynchronize(s->h2d_stream);
+    cudaStreamSynchronize(s->d2h_stream);
+    cudaStreamDestroy(s->h2d_stream);
+    cudaStreamDestroy(s->d2h_stream);
+    for (int i = 0; i < 2; ++i) {
+      cudaEventDestroy(s->a_copied[i]);
+      cudaEventDestroy(s->a_released[i]);
+      cudaEventDestroy(s->o_exported[i]);
+      cudaEventDestroy(s->o_read[i]);
+      cudaFree(s->abuf[i]);
+      cudaFree(s->obuf[i]);
+    }
+  }
   cudaFree(s->blocks_d);
   cudaFree(s->task_buf);
   cudaFree(s->act);
@@ -785,14 +850,14 @@ mg_status mg_set_actions(mg_sim *s, const float *a, int32_t n_seg, int32_t hold_
     s->act_cap = floats;
     s->drop_graphs();
   }
+  mg_status rs = release_async_actions(s);
+  if (rs != MG_OK) return rs;
   if (n_seg > 0) {
     const bool dev = is_device_ptr(a);
     MG_CK(cudaMemcpyAsync(s->act, a, floats * 4,
                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->stream));
     if (!dev) MG_CK(cudaStreamSynchronize(s->stream));
   }
-  if (s->proc || s->n_seg != n_seg || s->hold != hold_steps || s->act_src != s->act)
-    s->drop_graphs();
   s->act_src = s->act;
   s->proc = 0;
   s->n_seg = n_seg;
@@ -807,8 +872,44 @@ mg_status mg_set_actions_borrowed(mg_sim *s, const float *a, int32_t n_seg, int3
   if (!is_device_ptr(a)) return fail(MG_EINVAL, "borrowed actions must be device memory");
   if ((reinterpret_cast<uintptr_t>(a) & 15) != 0)
     return fail(MG_EINVAL, "borrowed actions must be 16-byte aligned");
-  if (s->proc || s->n_seg != n_seg || s->hold != hold_steps || s->act_src != a) s->drop_graphs();
+  mg_status rs = release_async_actions(s);
+  if (rs != MG_OK) return rs;
   s->act_src = a;
+  s->proc = 0;
+  s->n_seg = n_seg;
+  s->hold = hold_steps;
+  return rewind_cursor(s);
+}
+
+mg_status mg_set_actions_async(mg_sim *s, const float *a, int32_t n_seg, int32_t hold_steps) {
+  MG_NONNULL(s);
+  NvtxRange nvtx("mg_set_actions_async");
+  MG_NONNULL(a);
+  if (n_seg < 1 || hold_steps < 1) return fail(MG_EINVAL, "need n_seg >= 1 and hold_steps >= 1");
+  if (!is_pinned_host(a))
+    return fail(MG_EINVAL, "mg_set_actions_async needs page-locked host memory");
+  mg_status st = ensure_async(s);
+  if (st != MG_OK) return st;
+  const int slot = s->a_next;
+  const size_t floats = (size_t)n_seg * s->n * MG_MAX_THR;
+  if (floats > s->abuf_cap[slot]) {
+    MG_CK(cudaStreamSynchronize(s->stream));
+    MG_CK(cudaStreamSynchronize(s->h2d_stream));
+    cudaFree(s->abuf[slot]);
+    s->abuf[slot] = nullptr;
+    s->abuf_cap[slot] = 0;
+    MG_CK(cudaMalloc(&s->abuf[slot], floats * 4));
+    s->abuf_cap[slot] = floats;
+  }
+  s->a_next ^= 1;
+  // the copy waits for the last steps that read this buffer, the sim's later work for the copy
+  MG_CK(cudaStreamWaitEvent(s->h2d_stream, s->a_released[slot], 0));
+  MG_CK(cudaMemcpyAsync(s->abuf[slot], a, floats * 4, cudaMemcpyHostToDevice, s->h2d_stream));
+  MG_CK(cudaEventRecord(s->a_copied[slot], s->h2d_stream));
+  if ((st = release_async_actions(s)) != MG_OK) return st;
+  MG_CK(cudaStreamWaitEvent(s->stream, s->a_copied[slot], 0));
+  s->a_active = slot;
+  s->act_src = s->abuf[slot];
   s->proc = 0;
   s->n_seg = n_seg;
   s->hold = hold_steps;
@@ -818,7 +919,8 @@ mg_status mg_set_actions_borrowed(mg_sim *s, const float *a, int32_t n_seg, int3
 mg_status mg_set_procedural_actions(mg_sim *s, uint64_t cmd_seed, int32_t hold_steps) {
   MG_NONNULL(s);
   if (hold_steps < 1) return fail(MG_EINVAL, "hold_steps must be >= 1");
-  s->drop_graphs();
+  mg_status rs = release_async_actions(s);
+  if (rs != MG_OK) return rs;
   s->proc = 1;
   s->cmd_seed = cmd_seed;
   s->hold = hold_steps;
@@ -837,8 +939,12 @@ mg_status mg_step(mg_sim *s, int32_t k) {
     return MG_OK;
   }
   GraphEntry *hit = nullptr;
+  const float *src = s->proc ? nullptr : s->act_src;
+  const uint64_t seed = s->proc ? s->cmd_seed : 0;
   for (auto &g : s->graphs)
-    if (g.k == k) hit = &g;
+    if (g.k == k && g.act_src == src && g.n_seg == s->n_seg && g.hold == s->hold &&
+        g.proc == s->proc && g.cmd_seed == seed)
+      hit = &g;
   if (!hit) {
     if (s->graphs.size() >= 16) {
       auto lru = std::min_element(s->graphs.begin(), s->graphs.end(),
@@ -857,7 +963,7 @@ mg_status mg_step(mg_sim *s, int32_t k) {
       return st;
     }
     MG_CK(ce);
-    GraphEntry g{k, nullptr, 0};
+    GraphEntry g{k, src, s->n_seg, s->hold, s->proc, seed, nullptr, 0};
     ce = cudaGraphInstantiate(&g.exec, graph, 0);
     cudaGraphDestroy(graph);
     MG_CK(ce);
@@ -1032,6 +1138,28 @@ mg_status mg_get_state(mg_sim *s, float *out) {
   return MG_OK;
 }
 
+mg_status mg_get_state_async(mg_sim *s, float *out) {
+  MG_NONNULL(s);
+  NvtxRange nvtx("mg_get_state_async");
+  MG_NONNULL(out);
+  if (!is_pinned_host(out))
+    return fail(MG_EINVAL, "mg_get_state_async needs page-locked host memory");
+  mg_status st = ensure_async(s);
+  if (st != MG_OK) return st;
+  const int slot = s->o_next;
+  const size_t bytes = (size_t)s->n * MG_NSTATE * 4;
+  if (!s->obuf[slot]) MG_CK(cudaMalloc(&s->obuf[slot], bytes));
+  s->o_next ^= 1;
+  // the export waits for the previous read-back from this buffer, the read-back for the export
+  MG_CK(cudaStreamWaitEvent(s->stream, s->o_read[slot], 0));
+  MG_CK(launch_export_state(s->st, s->n, s->obuf[slot], s->stream));
+  MG_CK(cudaEventRecord(s->o_exported[slot], s->stream));
+  MG_CK(cudaStreamWaitEvent(s->d2h_stream, s->o_exported[slot], 0));
+  MG_CK(cudaMemcpyAsync(out, s->obuf[slot], bytes, cudaMemcpyDeviceToHost, s->d2h_stream));
+  MG_CK(cudaEventRecord(s->o_read[slot], s->d2h_stream));
+  return MG_OK;
+}
+
 mg_status mg_set_state(mg_sim *s, const float *in) {
   MG_NONNULL(s);
   NvtxRange nvtx("mg_set_state");
@@ -1061,6 +1189,10 @@ mg_status mg_reset(mg_sim *s, const uint8_t *mask) {
 mg_status mg_sync(mg_sim *s, int64_t *nonfinite_count) {
   MG_NONNULL(s);
   NvtxRange nvtx("mg_sync");
+  if (s->h2d_stream) {
+    MG_CK(cudaStreamSynchronize(s->h2d_stream));
+    MG_CK(cudaStreamSynchronize(s->d2h_stream));
+  }
   unsigned long long c = 0, to = 0;
   mg_status st = read_counter(s, 2, &to);
   if (st != MG_OK) return st;

@@ -161,6 +161,15 @@ class Sim:
         _check(actions, actions.shape, torch.float32)
         call("mg_set_actions", self._h, _ptr(actions), int(actions.shape[0]), int(hold_steps))
 
+    def set_actions_async(self, actions, hold_steps: int = 1):
+        """As set_actions from a page-locked host tensor, without waiting (mg_set_actions_async):
+        keep ``actions`` unchanged until ``sync()`` or the next-but-one call of this method."""
+        if actions.ndim != 3 or actions.shape[1:] != (self.n, MG_MAX_THR):
+            raise ValueError(f"actions must be [n_seg, {self.n}, {MG_MAX_THR}]")
+        _check(actions, actions.shape, torch.float32)
+        call("mg_set_actions_async", self._h, _ptr(actions), int(actions.shape[0]),
+             int(hold_steps))
+
     def set_actions_borrowed(self, actions, hold_steps: int = 1):
         """Read ``actions`` (float32 device tensor [n_seg, n_envs, 8]) in place, without a copy;
         keep it alive and unchanged until the steps using it have run (mg_set_actions_borrowed).
@@ -226,6 +235,13 @@ class Sim:
             out = torch.empty((self.n, MG_NSTATE), dtype=torch.float32, device=self.device)
         _check(out, (self.n, MG_NSTATE), torch.float32)
         call("mg_get_state", self._h, _ptr(out))
+        return out
+
+    def get_state_async(self, out):
+        """Read the state into a page-locked host tensor ``out`` [n, 21] without waiting
+        (mg_get_state_async); ``out`` is complete once ``sync()`` returns."""
+        _check(out, (self.n, MG_NSTATE), torch.float32)
+        call("mg_get_state_async", self._h, _ptr(out))
         return out
 
     def set_state(self, state):

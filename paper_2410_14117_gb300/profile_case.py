@@ -8,8 +8,10 @@ after a few warm-up calls: with ``--static`` each is one launch of the static-gr
 ``k`` sub-steps; otherwise each is one work-queue launch covering ``k`` sub-steps in chunks of
 ``--chunk``; with ``--task`` each is one circle-tracking task step (``k`` sub-steps and the fused
 observation / error / auto-reset epilogue, static grid); ``--split`` runs the split-integration
-comparison kernel, ``--full`` the general path with off-diagonal hydrodynamics.  Holds well under a GB of device memory
-at 65,536 envs.
+comparison kernel, ``--full`` the general path with off-diagonal hydrodynamics; ``--adjoint`` runs
+``launches`` forward and backward passes of the differentiable rollout (``k`` sub-steps,
+checkpoints every ``--chunk``, MSE loss on the trajectory).  Holds well under a GB of device
+memory at 65,536 envs.
 """
 from __future__ import annotations
 
@@ -47,7 +49,11 @@ def main():
     ap.add_argument("--full", action="store_true",
                     help="off-diagonal added mass and damping, r_g ~ U[-2, 2] cm (general path, "
                          "static grid)")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="forward + backward passes of the differentiable rollout instead")
     args = ap.parse_args()
+    if args.adjoint:
+        return adjoint_case(args)
 
     n = args.n_envs
     vs = I.fleet_vehicles()
@@ -87,6 +93,27 @@ def main():
     bad = sim.sync()
     sim.close()
     print(f"profile_case: {n} envs, {args.launches} launches of k={args.k}, non-finite {bad}")
+
+
+def adjoint_case(args):
+    from .adjoint import COEF_SLICE, rollout
+
+    n, T, C = args.n_envs, args.k, args.chunk
+    vs = I.fleet_vehicles()
+    sim = Sim(n, np.full(n, args.vehicle, dtype=np.int32), vs)
+    sim.set_launch(args.epb, 1000, True)
+    sim.randomize(1234, 0.8, 1.2, 0.2, 0.3)
+    coeffs = sim.get_params()[:, COEF_SLICE].clone().requires_grad_(True)
+    acts = torch.tensor(I.commands(5678, math.ceil(T / 10), n, vs[args.vehicle].n_thr),
+                        device="cuda", requires_grad=True)
+    s0 = torch.tensor(I.initial_states(21, n), dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup + args.launches):
+        traj = rollout(sim, coeffs, acts, s0, 10, T, C)
+        grads = torch.autograd.grad((traj ** 2).mean(), (coeffs, acts))
+    torch.cuda.synchronize()
+    sim.close()
+    print(f"profile_case: adjoint, {n} envs, T={T}, C={C}, |dL/dcoef|_1 "
+          f"{float(grads[0].abs().sum()):.4e}")
 
 
 if __name__ == "__main__":

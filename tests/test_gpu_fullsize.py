@@ -1,7 +1,9 @@
-"""Parity at the benchmark's full sizes, in the launch configuration the benchmark times, on
+"""Parity at the benchmark's full sizes, in the launch configurations the benchmark times, on
 sampled envs the oracle computes one by one: the 65,536-env headline fleet (work-queue kernel,
-168 registers, 8 warps/SM, chunk 100, actions read in place, CUDA graph) over a whole 1,000
-sub-step episode, and the 262,144-env mixed fleet over 500 sub-steps."""
+200-register cap, 8 warps/SM, chunk 100, actions read in place, CUDA graph) over a whole 1,000
+sub-step episode, the 262,144-env mixed fleet over 500 sub-steps and the 1,048,576-env top of
+the size sweep (each also on the packed static grid, two envs per thread, which the autotuner
+picks for them)."""
 import numpy as np
 import pytest
 import torch
@@ -63,12 +65,14 @@ def test_headline_fleet_sampled_matches_oracle():
     assert err_end.max() <= 2 * TOL_ROLLOUT, err_end.max(axis=0)
 
 
-def test_mixed_fleet_262144_sampled_matches_oracle():
+@pytest.mark.parametrize("launch", [LaunchConfig("queue", 128, 50, True, 12),
+                                    LaunchConfig("static", 32, 1000, packed=True)])
+def test_mixed_fleet_262144_sampled_matches_oracle(launch):
     vs = vehicles()
     n, hold = 262144, 10
     types = I.mixed_fleet(3, n)
     sim = Sim(n, types, vs)
-    LaunchConfig("queue", 128, 50, True, 12).apply(sim)
+    launch.apply(sim)
     sim.randomize(4321, 0.8, 1.2, 0.2, 0.3)
     sim.reset()
     nt = np.array([vs[t].n_thr for t in types])
@@ -84,13 +88,15 @@ def test_mixed_fleet_262144_sampled_matches_oracle():
     assert err.max() <= TOL_ROLLOUT, err.max(axis=0)
 
 
-def test_largest_sweep_fleet_sampled_matches_oracle():
+@pytest.mark.parametrize("launch", [LaunchConfig("static", 128, 200),
+                                    LaunchConfig("static", 64, 1000, packed=True)])
+def test_largest_sweep_fleet_sampled_matches_oracle(launch):
     """1,048,576 envs (the top of the fleet-size sweep), static grid, 200 sub-steps."""
     vs = vehicles()
     n, hold = 1 << 20, 10
     types = np.zeros(n, dtype=np.int32)
     sim = Sim(n, types, vs)
-    LaunchConfig("static", 128, 200).apply(sim)
+    launch.apply(sim)
     sim.randomize(99, 0.8, 1.2, 0.2, 0.3)
     sim.reset()
     cmds = I.commands(98, 20, n, 6)

@@ -228,11 +228,21 @@ def cpu_baseline(n_envs, horizon, hold, target_s=12.0):
               nthreads=1)
     single = 512 * 100 / (time.perf_counter() - t1)
     O.rollout(par[:8], geo, types[:8], s0[:8], cmd[:, :8], hold, 1, h=0.01, nthreads=cores)
+    # the small parity fleet: 1,024 nominal BlueROV2 envs, no current, 500 sub-steps
+    n1 = 1024
+    p1 = np.broadcast_to(nominal[0], (n1, nominal.shape[1])).copy()
+    s1 = I.initial_states(21, n1)
+    c1 = I.commands(5678, 50, n1, 6).astype(np.float64)
+    t1 = time.perf_counter()
+    O.rollout(p1, geo, np.zeros(n1, np.int32), s1, c1, hold, 500, h=0.01)
+    small = n1 * 500 / (time.perf_counter() - t1)
     return {"value": ns * steps * reps / dt, "unit": "env-steps/s", "cores": cores,
             "kind": "oracle", "single_core_value": single,
+            "small_fleet_value": small,
             "sample": f"{reps} x ({ns} envs x {steps} sub-steps) of the same randomised BlueROV2 "
                       f"workload (FP64 oracle, OpenMP over envs), {dt:.1f} s; single core: "
-                      "512 envs x 100 sub-steps"}
+                      "512 envs x 100 sub-steps; small_fleet_value: 1,024 nominal BlueROV2 envs "
+                      "x 500 sub-steps, no current, all cores"}
 
 
 def run_reference(args):
@@ -509,6 +519,7 @@ def run_ours(args):
 
     sim.close()
     if not args.no_extra and world == 1:
+        line["small_fleet"] = bench_small_fleet(vs)
         line["size_sweep"] = bench_size_sweep(vs)
         line["mixed_fleet"] = bench_mixed_fleet(vs)
         line["adjoint"] = bench_adjoint(vs)
@@ -539,6 +550,33 @@ def _time_episodes(fn, reps):
     b.record()
     torch.cuda.synchronize()
     return a.elapsed_time(b) / reps
+
+
+def bench_small_fleet(vs, n=1024, horizon=500, reps=5):
+    """The small parity fleet: 1,024 nominal BlueROV2 envs, no current, commands U[-1,1] held
+    10 sub-steps, 500 sub-steps of 0.01 s (parity against the oracle is in the tests)."""
+    import numpy as np
+    import torch
+    from paper_2410_14117_gb300 import inputs as I
+    from paper_2410_14117_gb300.autotune import Autotuner
+    from paper_2410_14117_gb300.sim import Sim
+
+    types = np.zeros(n, np.int32)
+    sim = Sim(n, types, vs)
+    launch = Autotuner(horizon=horizon, reps=2).tune(sim, vs)
+    acts = torch.tensor(I.commands(5678, horizon // 10, n, 6), device="cuda")
+    s0 = torch.tensor(I.initial_states(21, n), dtype=torch.float32, device="cuda")
+
+    def episode():
+        sim.set_state(s0)
+        sim.set_actions_borrowed(acts, 10)
+        sim.step(horizon)
+
+    ms = _time_episodes(episode, reps)
+    sim.close()
+    return {"workload": f"{n:,} nominal BlueROV2 envs, no current, {horizon} RK4 sub-steps",
+            "launch": dataclasses.asdict(launch),
+            "env_steps_per_s": n * horizon / (ms / 1e3)}
 
 
 def bench_size_sweep(vs, sizes=(4096, 16384, 65536, 262144, 1048576), horizon=1000, reps=3):

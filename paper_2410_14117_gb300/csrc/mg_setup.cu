@@ -16,13 +16,64 @@ constexpr int kThreads = 256;
 
 inline int blocks_for(int64_t n) { return (int)((n + kThreads - 1) / kThreads); }
 
-// Indices of the 27 randomised scalars in the parameter record, in draw order.
-__constant__ int c_rand_idx[27] = {
-    MG_P_M, MG_P_IG, MG_P_IG + 1, MG_P_IG + 2,
-    MG_P_MA, MG_P_MA + 1, MG_P_MA + 2, MG_P_MA + 3, MG_P_MA + 4, MG_P_MA + 5,
-    MG_P_DL, MG_P_DL + 1, MG_P_DL + 2, MG_P_DL + 3, MG_P_DL + 4, MG_P_DL + 5,
-    MG_P_DQ, MG_P_DQ + 1, MG_P_DQ + 2, MG_P_DQ + 3, MG_P_DQ + 4, MG_P_DQ + 5,
-    MG_P_W, MG_P_B, MG_P_RB + 2, MG_P_KT, MG_P_TAU};
+// Index of the j-th of the 27 randomised scalars in the parameter record, in draw order: m,
+// I_g (3), M_A (6), D_l (6), D_q (6), W, B (record entries 0..23 in order), then r_b,z, k_T,
+// tau_m.  A compile-time function, so that the unrolled draw loop addresses the record in
+// registers.
+static_assert(MG_P_M == 0 && MG_P_IG == 1 && MG_P_MA == 4 && MG_P_DL == 10 && MG_P_DQ == 16 &&
+                  MG_P_W == 22 && MG_P_B == 23 && MG_P_TAU == MG_P_KT + 1,
+              "randomised-scalar order assumes the record layout of mg.h");
+__host__ __device__ constexpr int rand_idx(int j) {
+  return j < 24 ? j : j == 24 ? MG_P_RB + 2 : j == 25 ? MG_P_KT : MG_P_TAU;
+}
+// Block size of the randomisation kernel: at ~150 registers two or three 128-thread blocks fit
+// per SM, where one 256-thread block leaves 65,536 envs 1.7 waves.
+constexpr int kRandThreads = 128;
+
+// derive() for an env whose mass matrix is diagonal (r_g = 0, no off-diagonal added mass): the
+// same values derive() stores, without building the 6 x 6 matrices (FP64 runs at a 64th of the
+// FP32 rate on this GPU).  I_o = I_g exactly and every off-diagonal entry is +0 when r_g = 0.
+__device__ void derive_diag(const SetupView &v, int64_t e, const double *p) {
+  const double m = p[MG_P_M];
+  const double *ma = p + MG_P_MA;
+  const double rg[3] = {p[MG_P_RG], p[MG_P_RG + 1], p[MG_P_RG + 2]};
+  double Mjj[6], mi[6];
+  bool spd = true;
+  for (int i = 0; i < 3; ++i) {
+    Mjj[i] = m + ma[i];
+    Mjj[3 + i] = p[MG_P_IG + i] + ma[3 + i];
+  }
+  for (int j = 0; j < 6; ++j) {
+    if (!(Mjj[j] > 0.0)) spd = false;
+    mi[j] = Mjj[j] > 0.0 ? 1.0 / Mjj[j] : 0.0;
+  }
+  if (!spd) atomicAdd(v.n_not_spd, 1ull);
+  const double W = p[MG_P_W], B = p[MG_P_B];
+  const double G[3] = {W * rg[0] - B * p[MG_P_RB], W * rg[1] - B * p[MG_P_RB + 1],
+                       W * rg[2] - B * p[MG_P_RB + 2]};
+  const ParamPlanes &pa = v.pa;
+  auto f = [](double x) { return (float)x; };
+  pa.d0[e] = make_float4(f(m), f(ma[0]), f(ma[1]), f(ma[2]));
+  pa.d1[e] = make_float4(f(Mjj[3]), f(Mjj[4]), f(Mjj[5]), f(W - B));
+  pa.d2[e] = make_float4(f(p[MG_P_DL]), f(p[MG_P_DL + 1]), f(p[MG_P_DL + 2]),
+                         f(p[MG_P_DL + 3]));
+  pa.d3[e] = make_float4(f(p[MG_P_DL + 4]), f(p[MG_P_DL + 5]), f(p[MG_P_DQ]),
+                         f(p[MG_P_DQ + 1]));
+  pa.d4[e] = make_float4(f(p[MG_P_DQ + 2]), f(p[MG_P_DQ + 3]), f(p[MG_P_DQ + 4]),
+                         f(p[MG_P_DQ + 5]));
+  pa.d5[e] = make_float4(f(G[0]), f(G[1]), f(G[2]), f(p[MG_P_KT]));
+  pa.d6[e] = make_float4(f(p[MG_P_VC]), f(p[MG_P_VC + 1]), f(p[MG_P_VC + 2]),
+                         f(1.0 / p[MG_P_TAU]));
+  pa.d7[e] = make_float4(f(mi[0]), f(mi[1]), f(mi[2]), f(mi[3]));
+  pa.d8[e] = make_float2(f(mi[4]), f(mi[5]));
+  pa.g0[e] = make_float4(f(m * rg[0]), f(m * rg[1]), f(m * rg[2]), 0.f);
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  pa.g1[e] = z;
+  pa.g2[e] = z;
+  pa.g3[e] = z;
+  pa.g4[e] = z;
+  pa.g5[e] = 0.f;
+}
 
 // Derive the step's parameter planes for env e from its FP64 record p[MG_NPARAM].
 __device__ void derive(const SetupView &v, int64_t e, const double *p) {
@@ -30,6 +81,15 @@ __device__ void derive(const SetupView &v, int64_t e, const double *p) {
   const double rg[3] = {p[MG_P_RG], p[MG_P_RG + 1], p[MG_P_RG + 2]};
   const double *ma = p + MG_P_MA;
   const double r2 = rg[0] * rg[0] + rg[1] * rg[1] + rg[2] * rg[2];
+  if (r2 == 0.0) {
+    bool xh_zero = true;
+    if (v.xh)
+      for (int t = 0; t < 15; ++t) xh_zero = xh_zero && v.xh[(int64_t)t * v.n + e] == 0.f;
+    if (xh_zero) {
+      derive_diag(v, e, p);
+      return;
+    }
+  }
   // I_o = I_g - m S(r_g)^2 = I_g + m (|r_g|^2 I - r_g r_g^T)  (inertia about the body origin)
   double Io[3][3];
   for (int i = 0; i < 3; ++i)
@@ -128,7 +188,8 @@ __device__ void derive(const SetupView &v, int64_t e, const double *p) {
   pa.g5[e] = f(Mi[4][5]);
 }
 
-__global__ void k_randomize(const SetupView v, const float *__restrict__ nominal, uint64_t seed,
+__global__ void __launch_bounds__(kRandThreads)
+    k_randomize(const SetupView v, const float *__restrict__ nominal, uint64_t seed,
                             double lo, double hi, double current_sigma, double rg_halfwidth) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= v.n) return;
@@ -137,10 +198,11 @@ __global__ void k_randomize(const SetupView v, const float *__restrict__ nominal
   double p[MG_NPARAM];
   for (int j = 0; j < MG_NPARAM; ++j) p[j] = (double)nom[j];
   uint4 x = make_uint4(0, 0, 0, 0);
+#pragma unroll
   for (int j = 0; j < 27; ++j) {
     if (j % 4 == 0) x = draw4(seed, gid, STREAM_PARAMS, (uint32_t)(j / 4));
     const uint32_t w = (j % 4 == 0) ? x.x : (j % 4 == 1) ? x.y : (j % 4 == 2) ? x.z : x.w;
-    const int idx = c_rand_idx[j];
+    const int idx = rand_idx(j);
     p[idx] = (double)nom[idx] * (lo + (hi - lo) * u01d(w));
   }
   const uint4 c = draw4(seed, gid, STREAM_CURRENT, 0u);
@@ -253,8 +315,8 @@ __global__ void k_philox(const uint32_t *__restrict__ ctr, const uint32_t *__res
 cudaError_t launch_randomize(const SetupView &v, const float *nominal, uint64_t seed, double lo,
                              double hi, double current_sigma, double rg_halfwidth,
                              cudaStream_t stream) {
-  k_randomize<<<blocks_for(v.n), kThreads, 0, stream>>>(v, nominal, seed, lo, hi,
-                                                        current_sigma, rg_halfwidth);
+  k_randomize<<<(int)((v.n + kRandThreads - 1) / kRandThreads), kRandThreads, 0, stream>>>(
+      v, nominal, seed, lo, hi, current_sigma, rg_halfwidth);
   return cudaGetLastError();
 }
 

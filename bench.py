@@ -848,6 +848,11 @@ def bench_full_hydro(vs, n=65536, horizon=1000, reps=3):
     return out
 
 
+# Sub-steps per serving tick: at 200 req/s p50 / p99 were 0.73 / 2.06 ms with 50, 0.67 / 2.08
+# with 100 and 0.64 / 2.01 with 200; at 2,000 req/s 100 cut p99 from 6.5 to 6.0 ms.
+SERVE_K = 100
+
+
 def bench_serve(vs, seconds, rate=200.0):
     """Poisson arrivals of rollout jobs (envs log-uniform [64, 65536], horizon U[50, 1000],
     type 50/50, randomised parameters and currents) served with continuous batching under a
@@ -860,7 +865,7 @@ def bench_serve(vs, seconds, rate=200.0):
                        "log-uniform [64, 65536], horizon U[50, 1000], 50/50 BlueROV2/Heavy, "
                        "trajectory recorded (13 floats per env-step), 120 GB budget"}
     for mode in ("batched", "serial"):
-        srv = Server(vs, budget_bytes=120e9, capacity_envs=8 << 20, k=50)
+        srv = Server(vs, budget_bytes=120e9, capacity_envs=8 << 20, k=SERVE_K)
         warm = requests_from_specs(I.serving_jobs(7, 0.05, rate_hz=rate))
         srv.run(warm, mode=mode)
         _, st = srv.run(requests_from_specs(specs), mode=mode)
@@ -870,7 +875,7 @@ def bench_serve(vs, seconds, rate=200.0):
     hot = I.serving_jobs(43, seconds / 4, rate_hz=10 * rate)
     out["stress"] = {"rate_hz": 10 * rate, "jobs": len(hot)}
     for mode in ("batched", "serial"):
-        srv = Server(vs, budget_bytes=120e9, capacity_envs=8 << 20, k=50)
+        srv = Server(vs, budget_bytes=120e9, capacity_envs=8 << 20, k=SERVE_K)
         _, st = srv.run(requests_from_specs(hot), mode=mode)
         srv.close()
         out["stress"][mode] = {k: st[k] for k in ("p50_ms", "p99_ms", "env_steps_per_s",

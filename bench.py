@@ -849,33 +849,45 @@ def bench_full_hydro(vs, n=65536, horizon=1000, reps=3):
 
 
 # Sub-steps per serving tick: at 200 req/s p50 / p99 were 0.73 / 2.06 ms with 50, 0.67 / 2.08
-# with 100 and 0.64 / 2.01 with 200; at 2,000 req/s 100 cut p99 from 6.5 to 6.0 ms.
+# with 100 and 0.64 / 2.01 with 200 (Python request loop); at 2,000 req/s 100 cut p99 from 6.5
+# to 6.0 ms.
 SERVE_K = 100
 
 
 def bench_serve(vs, seconds, rate=200.0):
     """Poisson arrivals of rollout jobs (envs log-uniform [64, 65536], horizon U[50, 1000],
     type 50/50, randomised parameters and currents) served with continuous batching under a
-    120 GB budget, and the same stream served one job at a time."""
+    120 GB budget by the native request loop (mg_server_*), and the same stream served one job
+    at a time; each server first serves one second of the same job mix (its record memory pool
+    warm), as the measured stream's own arrivals would after a while."""
     from paper_2410_14117_gb300 import inputs as I
-    from paper_2410_14117_gb300.serve import Server, requests_from_specs
+    from paper_2410_14117_gb300.serve import NativeServer, Server, requests_from_specs
 
     specs = I.serving_jobs(42, seconds, rate_hz=rate)
     out = {"workload": f"Poisson {rate:.0f} req/s for {seconds:.1f} s ({len(specs)} jobs), envs "
                        "log-uniform [64, 65536], horizon U[50, 1000], 50/50 BlueROV2/Heavy, "
-                       "trajectory recorded (13 floats per env-step), 120 GB budget"}
+                       "trajectory recorded (13 floats per env-step), 120 GB budget, "
+                       f"{SERVE_K} sub-steps per tick",
+           "loop": "native (mg_server_*)"}
     for mode in ("batched", "serial"):
-        srv = Server(vs, budget_bytes=120e9, capacity_envs=8 << 20, k=SERVE_K)
-        warm = requests_from_specs(I.serving_jobs(7, 0.05, rate_hz=rate))
-        srv.run(warm, mode=mode)
+        srv = NativeServer(vs, budget_bytes=120e9, capacity_envs=8 << 20, k=SERVE_K)
+        srv.run(requests_from_specs(I.serving_jobs(7, 1.0, rate_hz=rate)), mode=mode)
         _, st = srv.run(requests_from_specs(specs), mode=mode)
         srv.close()
         out[mode] = st
+    # the same stream through the Python request loop (Server), batched
+    srv = Server(vs, budget_bytes=120e9, capacity_envs=8 << 20, k=SERVE_K)
+    srv.run(requests_from_specs(I.serving_jobs(7, 1.0, rate_hz=rate)), mode="batched")
+    _, st = srv.run(requests_from_specs(specs), mode="batched")
+    srv.close()
+    out["python_loop_batched"] = {k: st[k] for k in ("p50_ms", "p99_ms", "env_steps_per_s")}
     # the same job mix at 10x the arrival rate: continuous batching against one job at a time
     hot = I.serving_jobs(43, seconds / 4, rate_hz=10 * rate)
     out["stress"] = {"rate_hz": 10 * rate, "jobs": len(hot)}
     for mode in ("batched", "serial"):
-        srv = Server(vs, budget_bytes=120e9, capacity_envs=8 << 20, k=SERVE_K)
+        srv = NativeServer(vs, budget_bytes=120e9, capacity_envs=8 << 20, k=SERVE_K)
+        srv.run(requests_from_specs(I.serving_jobs(8, seconds / 8, rate_hz=10 * rate)),
+                mode=mode)
         _, st = srv.run(requests_from_specs(hot), mode=mode)
         srv.close()
         out["stress"][mode] = {k: st[k] for k in ("p50_ms", "p99_ms", "env_steps_per_s",

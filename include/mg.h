@@ -295,8 +295,9 @@ mg_status mg_set_state(mg_sim *sim, const float *in);
  * for these copies too.  Results are those of the synchronous calls.
  *   mg_set_actions_async: as mg_set_actions (a: host [n_seg][n_envs][MG_MAX_THR], n_seg >= 1);
  *     the steps queued after the call read the copy once it has landed.  The caller keeps a
- *     unchanged until mg_sync returns, or until a second later call of mg_set_actions_async has
- *     returned (which reuses this call's device buffer only after this call's steps).
+ *     unchanged until mg_sync returns, or until the second later call of mg_set_actions_async
+ *     has returned (that call reuses this call's device buffer: it first waits on the host for
+ *     this call's copy, and its own copy waits on the device for this call's steps).
  *   mg_get_state_async: as mg_get_state into out (host [n_envs][MG_NSTATE]) of the state the
  *     steps queued so far leave; out is complete once mg_sync returns.  A third call reuses the
  *     first call's device buffer only after its copy has finished.
@@ -421,6 +422,66 @@ mg_status mg_pool_info(mg_pool *pool, int64_t *free_envs, int64_t *largest_free_
 
 /* Wait for the pool's stream. */
 mg_status mg_pool_sync(mg_pool *pool);
+
+/* Native request loop over a pool (continuous batching; the paper has no serving layer).  Jobs are submitted as specs and wait in a FIFO queue; each mg_server_poll admits
+ * queued jobs in order while the trajectory budget and a free arena range allow, issues one
+ * mg_pool_tick (every running job advances min(k, horizon - done) sub-steps in one launch),
+ * records an event after it and hands back the jobs whose last tick has completed.  At most
+ * max_inflight ticks stay queued beyond the oldest incomplete one; a poll that would exceed that,
+ * or that has nothing left to advance, waits for the oldest by polling its event (spinning for
+ * the first millisecond, never longer than wait_timeout_s: then MG_ETIMEOUT, and the server
+ * stays usable).  Trajectory records ([horizon][MG_NTRAJ][n_envs] floats each, when record != 0)
+ * are stream-ordered allocations of the server's own memory pool on the pool's stream, freed
+ * when a job leaves.  A job's result is the one it gets alone or on any other pool (its draws
+ * are keyed by its own seeds).  The server uses the pool's stream as set when it is created. */
+typedef struct mg_server mg_server;
+
+typedef struct {
+  double budget_bytes;     /* device bytes the resident jobs' trajectory records may take */
+  int32_t k;               /* sub-steps per tick, >= 1 */
+  int32_t max_inflight;    /* ticks queued beyond the oldest incomplete one, >= 1 */
+  int32_t record;          /* != 0: every job records its trajectory */
+  int32_t serial;          /* != 0: one job at a time (admitted only into an empty server) */
+  int32_t keep_done;       /* != 0: a finished job stays admitted until mg_server_release */
+  int32_t pad;
+  double wait_timeout_s;   /* longest a poll waits for a tick, > 0 */
+} mg_server_config;
+
+/* Create a server over pool (which it does not own; destroy the server first).  Errors:
+ * MG_EINVAL (NULL, k < 1, max_inflight < 1, negative budget, wait_timeout_s <= 0), MG_ECUDA. */
+mg_status mg_server_create(mg_pool *pool, const mg_server_config *cfg, mg_server **out);
+
+/* Wait for the device, release every job still admitted and free all records. NULL: no-op. */
+mg_status mg_server_destroy(mg_server *srv);
+
+/* Queue a job; *ticket (0, 1, 2, ... in submission order) names it in the calls below.  Errors:
+ * MG_EINVAL (n_envs outside [1, the pool's capacity], horizon or hold < 1, a record larger than
+ * the whole budget). */
+mg_status mg_server_submit(mg_server *srv, const mg_job_spec *spec, int64_t *ticket);
+
+/* One round of the loop (above); the counts (any may be NULL) are those after it: jobs queued,
+ * admitted and not yet handed back, ticks in flight.  Errors: MG_ETIMEOUT, MG_ECUDA, and those of
+ * the pool calls. */
+mg_status mg_server_poll(mg_server *srv, int32_t *n_queued, int32_t *n_running,
+                         int32_t *n_inflight);
+
+/* A job's submission, admission and completion times in seconds on the server's clock (from
+ * mg_server_create; monotonic), -1 while not yet admitted / done. */
+mg_status mg_server_job(mg_server *srv, int64_t ticket, double *submit_s, double *admit_s,
+                        double *done_s);
+
+/* A finished job kept by keep_done: its final state into state ([n_envs][MG_NSTATE], host or
+ * device, may be NULL) and its record into traj ([horizon][MG_NTRAJ][n_envs], host or device,
+ * may be NULL).  Synchronous.  Errors: MG_EINVAL, MG_ESTATE (not finished, not kept, released,
+ * or no record). */
+mg_status mg_server_job_result(mg_server *srv, int64_t ticket, float *state, float *traj);
+
+/* Release a finished job kept by keep_done (its envs and record).  Errors: MG_EINVAL, MG_ESTATE. */
+mg_status mg_server_release(mg_server *srv, int64_t ticket);
+
+/* The server's clock now, and the bytes of records held now and at most so far (any may be
+ * NULL). */
+mg_status mg_server_info(mg_server *srv, double *now_s, double *used_bytes, double *peak_bytes);
 
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char *mg_last_error(void);

@@ -62,9 +62,17 @@ class JobSpec(ctypes.Structure):
                 ("cmd_seed", ctypes.c_uint64), ("ranges", Ranges)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_double), ("k", ctypes.c_int32),
+                ("max_inflight", ctypes.c_int32), ("record", ctypes.c_int32),
+                ("serial", ctypes.c_int32), ("keep_done", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("wait_timeout_s", ctypes.c_double)]
+
+
 _P = ctypes.c_void_p
 _I32, _I64, _U32, _U64, _F = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64,
                               ctypes.c_float)
+_D = ctypes.c_double
 
 # name -> argtypes (every entry point returns mg_status except mg_last_error)
 SIGNATURES = {
@@ -113,6 +121,14 @@ SIGNATURES = {
     "mg_pool_release": [_P, _I32],
     "mg_pool_info": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I32)],
     "mg_pool_sync": [_P],
+    "mg_server_create": [_P, ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)],
+    "mg_server_destroy": [_P],
+    "mg_server_submit": [_P, ctypes.POINTER(JobSpec), ctypes.POINTER(_I64)],
+    "mg_server_poll": [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)],
+    "mg_server_job": [_P, _I64, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D)],
+    "mg_server_job_result": [_P, _I64, _P, _P],
+    "mg_server_release": [_P, _I64],
+    "mg_server_info": [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D)],
 }
 
 _lock = threading.Lock()

@@ -891,6 +891,9 @@ mg_status mg_set_actions_async(mg_sim *s, const float *a, int32_t n_seg, int32_t
   mg_status st = ensure_async(s);
   if (st != MG_OK) return st;
   const int slot = s->a_next;
+  // This slot's previous copy (two calls ago) read its host buffer; once it has finished, that
+  // buffer is the caller's again.
+  MG_CK(cudaEventSynchronize(s->a_copied[slot]));
   const size_t floats = (size_t)n_seg * s->n * MG_MAX_THR;
   if (floats > s->abuf_cap[slot]) {
     MG_CK(cudaStreamSynchronize(s->stream));

@@ -176,6 +176,11 @@ cudaError_t launch_flags_to_bytes(const uint32_t *flags, int64_t n, uint8_t *out
 cudaError_t launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,
                           cudaStream_t stream);
 
+// ---------------------------------------------------------------- job pool (mg_pool.cu)
+// The pool's stream and arena capacity, for the native request loop (mg_serve.cu).
+cudaStream_t pool_stream(const mg_pool *p);
+int64_t pool_capacity(const mg_pool *p);
+
 // ---------------------------------------------------------------- launchers (mg_adjoint.cu)
 cudaError_t launch_checkpoint(const StatePlanes &st, int64_t n, float *ck, cudaStream_t stream);
 cudaError_t launch_adjoint(const FleetView &fv, const int32_t *types, bool eight,

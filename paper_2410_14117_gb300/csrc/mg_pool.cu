@@ -363,6 +363,13 @@ mg_status mg_pool_destroy(mg_pool *p) {
   return MG_OK;
 }
 
+}  // extern "C"
+
+cudaStream_t mg::pool_stream(const mg_pool *p) { return p->stream; }
+int64_t mg::pool_capacity(const mg_pool *p) { return p->cap; }
+
+extern "C" {
+
 mg_status mg_pool_set_stream(mg_pool *p, void *stream) {
   if (!p) return pfail(MG_EINVAL, "NULL pool");
   p->stream = static_cast<cudaStream_t>(stream);

@@ -17,7 +17,8 @@ import time
 import numpy as np
 import torch
 
-from ._lib import MG_NSTATE, MG_NTRAJ, JobSpec, MGError, Ranges, VehicleParams, call
+from ._lib import (MG_NSTATE, MG_NTRAJ, JobSpec, MGError, Ranges, ServerConfig, VehicleParams,
+                   call)
 from .sim import _ptr, vehicle_struct
 
 # Device bytes per env held by the pool arena (state planes, parameter planes and records,
@@ -248,3 +249,112 @@ def requests_from_specs(specs, hold: int = 10):
     return [Request(arrival_s=s.arrival_s, n_envs=s.n_envs, horizon=s.horizon,
                     vehicle=s.vehicle, param_seed=s.param_seed, cmd_seed=s.cmd_seed, hold=hold)
             for s in specs]
+
+
+class NativeServer:
+    """The request loop of ``Server`` run natively (mg_server_*): admission, ticks and
+    completion handling happen inside the library; the host submits requests when they arrive
+    and calls one poll per round.  Same arguments, results and statistics as ``Server``."""
+
+    def __init__(self, vehicles, budget_bytes: float = 120e9, capacity_envs: int = 4 << 20,
+                 k: int = 50, record: bool = True, keep_results: bool = False,
+                 wait_timeout_s: float = 30.0, max_inflight: int = 2):
+        self.vehicles = vehicles
+        self.budget = float(budget_bytes)
+        self.k = int(k)
+        self.record = record
+        self.keep_results = keep_results
+        self.wait_timeout_s = float(wait_timeout_s)
+        self.max_inflight = int(max_inflight)
+        self.pool = Pool(capacity_envs, vehicles)
+        self.arena_bytes = self.pool.capacity * ARENA_BYTES_PER_ENV
+        if self.arena_bytes > self.budget:
+            raise ValueError("the arena alone exceeds the budget")
+        self.peak_used = self.arena_bytes
+        self._servers = {}  # mode -> native server, kept so its record memory pool stays warm
+
+    def _server(self, mode):
+        if mode not in self._servers:
+            cfg = ServerConfig(self.budget - self.arena_bytes, self.k, self.max_inflight,
+                               1 if self.record else 0, 1 if mode == "serial" else 0,
+                               1 if self.keep_results else 0, 0, self.wait_timeout_s)
+            h = ctypes.c_void_p()
+            call("mg_server_create", self.pool._h, ctypes.byref(cfg), ctypes.byref(h))
+            self._servers[mode] = h
+        return self._servers[mode]
+
+    def close(self):
+        for h in self._servers.values():
+            call("mg_server_destroy", h)
+        self._servers = {}
+        self.pool.close()
+
+    def run(self, requests, mode: str = "batched", realtime: bool = True):
+        """Serve ``requests`` (sorted by arrival_s); returns (served requests, stats)."""
+        reqs = sorted(requests, key=lambda r: r.arrival_s)
+        room = self.budget - self.arena_bytes
+        for r in reqs:
+            if r.n_envs > self.pool.capacity or (self.record and traj_bytes(r) > room):
+                raise ValueError(f"request of {r.n_envs} envs x {r.horizon} sub-steps can never "
+                                 "be admitted (arena capacity or budget too small)")
+        h = self._server(mode)
+        d = [ctypes.c_double() for _ in range(3)]
+
+        def clock():
+            call("mg_server_info", h, ctypes.byref(d[0]), None, None)
+            return d[0].value
+
+        tickets = {}
+        counts = [ctypes.c_int32() for _ in range(3)]
+        queue_depth = []
+        nxt = 0
+        t_start = clock()
+        while True:
+            t = clock() - t_start
+            while nxt < len(reqs) and (not realtime or reqs[nxt].arrival_s <= t):
+                r = reqs[nxt]
+                if not realtime:
+                    r.arrival_s = t
+                spec = JobSpec(int(r.n_envs), int(r.vehicle), int(r.hold), int(r.horizon), 0,
+                               int(r.param_seed), int(r.cmd_seed),
+                               Ranges(0.8, 1.2, 0.2, 0.3, 0))
+                tk = ctypes.c_int64()
+                call("mg_server_submit", h, ctypes.byref(spec), ctypes.byref(tk))
+                tickets[tk.value] = r
+                nxt += 1
+            call("mg_server_poll", h, *[ctypes.byref(c) for c in counts])
+            queued, running, inflight = (c.value for c in counts)
+            queue_depth.append(queued)
+            if queued or running or inflight:
+                continue
+            if nxt == len(reqs):
+                break
+            wait = reqs[nxt].arrival_s - (clock() - t_start)
+            if wait > 3e-4:
+                time.sleep(wait - 2e-4)  # then spin to the arrival
+        done = []
+        for tk, r in tickets.items():
+            call("mg_server_job", h, tk, None, ctypes.byref(d[1]), ctypes.byref(d[2]))
+            r.job_id = tk
+            r.admitted_s, r.done_s = d[1].value - t_start, d[2].value - t_start
+            if self.keep_results:
+                r.final_state = torch.empty((r.n_envs, MG_NSTATE), dtype=torch.float32,
+                                            device=self.pool.device)
+                r.traj = (torch.empty((r.horizon, MG_NTRAJ, r.n_envs), dtype=torch.float32,
+                                      device=self.pool.device) if self.record else None)
+                call("mg_server_job_result", h, tk, _ptr(r.final_state),
+                     _ptr(r.traj) if r.traj is not None else None)
+                call("mg_server_release", h, tk)
+            done.append(r)
+        call("mg_server_info", h, None, None, ctypes.byref(d[0]))
+        self.peak_used = max(self.peak_used, self.arena_bytes + d[0].value)
+        makespan = max(r.done_s for r in done) - min(r.arrival_s for r in done)
+        lat = np.array([r.latency_s for r in done])
+        steps = float(sum(r.n_envs * r.horizon for r in done))
+        stats = {"mode": mode, "jobs": len(done), "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                 "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                 "mean_ms": 1e3 * float(lat.mean()), "env_steps_per_s": steps / makespan,
+                 "makespan_s": makespan, "env_steps": steps,
+                 "max_queue_depth": int(max(queue_depth) if queue_depth else 0),
+                 "k": self.k}
+        return done, stats

@@ -8,7 +8,8 @@ import torch
 
 from oracle import oracle as O
 from paper_2410_14117_gb300 import inputs as I
-from paper_2410_14117_gb300.serve import Pool, Request, Server
+from paper_2410_14117_gb300._lib import MGError
+from paper_2410_14117_gb300.serve import NativeServer, Pool, Request, Server
 from paper_2410_14117_gb300.sim import Sim
 
 from _helpers import TOL_ROLLOUT, f32, oracle_geo, oracle_nominal, rel_err, vehicles
@@ -113,3 +114,68 @@ def test_pool_ranges_coalesce_and_reject():
     pool.sync()
     assert pool.progress(d) == (10, 10) and pool.progress(c) == (10, 10)
     pool.close()
+
+
+def _copy(reqs):
+    keys = ("arrival_s", "n_envs", "horizon", "vehicle", "param_seed", "cmd_seed", "hold")
+    return [Request(**{k: getattr(r, k) for k in keys}) for r in reqs]
+
+
+def test_native_server_alone_equals_mix_and_python_loop():
+    """The native request loop (mg_server_*): every job's final state and trajectory record is
+    the same in the mix, served one at a time, and through the Python loop, bit for bit."""
+    vs = vehicles()
+    reqs = _requests(seed=7, n_jobs=12)
+    out = {}
+    for name, cls, mode in [("mix", NativeServer, "batched"), ("alone", NativeServer, "serial"),
+                            ("python", Server, "batched")]:
+        srv = cls(vs, budget_bytes=8e9, capacity_envs=1 << 16, k=25, keep_results=True)
+        done, stats = srv.run(_copy(reqs), mode=mode)
+        srv.close()
+        assert stats["jobs"] == len(reqs)
+        assert all(r.admitted_s >= r.arrival_s - 1e-9 and r.done_s >= r.admitted_s for r in done)
+        out[name] = _by_key(done)
+    for key, r in out["alone"].items():
+        for other in ("mix", "python"):
+            torch.testing.assert_close(out[other][key].final_state, r.final_state, rtol=0, atol=0)
+            torch.testing.assert_close(out[other][key].traj, r.traj, rtol=0, atol=0)
+
+
+def test_native_server_budget_capacity_and_rejections():
+    vs = vehicles()
+    reqs = _requests(seed=5, n_jobs=12)
+    per = max(r.horizon * 13 * 4 * r.n_envs for r in reqs)
+    srv = NativeServer(vs, budget_bytes=4096 * 500 + 2.5 * per, capacity_envs=4096, k=40)
+    done, stats = srv.run(_copy(reqs), mode="batched")
+    assert stats["jobs"] == len(reqs)
+    assert srv.arena_bytes < srv.peak_used <= srv.budget
+    info = srv.pool.info()
+    assert info["free_envs"] == 4096 and info["largest_free_range"] == 4096 and info["jobs"] == 0
+    # FIFO: admission order follows arrival order
+    order = sorted(done, key=lambda r: r.admitted_s)
+    assert [r.arrival_s for r in order] == sorted(r.arrival_s for r in order)
+    with pytest.raises(ValueError):
+        srv.run([Request(0.0, 5000, 10, 0, 1, 2)])  # larger than the arena
+    srv.close()
+    # the ABI itself rejects what can never run
+    from paper_2410_14117_gb300._lib import ServerConfig, JobSpec, Ranges, call
+    import ctypes
+    pool = Pool(1000, vs)
+    h = ctypes.c_void_p()
+    with pytest.raises(MGError):
+        call("mg_server_create", pool._h, ctypes.byref(ServerConfig(1e9, 0, 2, 1, 0, 0, 0, 1.0)),
+             ctypes.byref(h))
+    call("mg_server_create", pool._h, ctypes.byref(ServerConfig(1e6, 10, 2, 1, 0, 0, 0, 1.0)),
+         ctypes.byref(h))
+    tk = ctypes.c_int64()
+    for spec in (JobSpec(2000, 0, 10, 10, 0, 1, 2, Ranges(0.8, 1.2, 0.2, 0.3, 0)),   # > arena
+                 JobSpec(100, 0, 10, 1000, 0, 1, 2, Ranges(0.8, 1.2, 0.2, 0.3, 0))):  # > budget
+        with pytest.raises(MGError) as ei:
+            call("mg_server_submit", h, ctypes.byref(spec), ctypes.byref(tk))
+        assert ei.value.code == "MG_EINVAL"
+    with pytest.raises(MGError) as ei:
+        call("mg_server_job_result", h, 0, None, None)
+    assert ei.value.code == "MG_EINVAL"
+    call("mg_server_destroy", h)
+    pool.close()
+

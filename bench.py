@@ -886,7 +886,7 @@ def bench_serve(vs, seconds, rate=200.0):
     out["stress"] = {"rate_hz": 10 * rate, "jobs": len(hot)}
     for mode in ("batched", "serial"):
         srv = NativeServer(vs, budget_bytes=120e9, capacity_envs=8 << 20, k=SERVE_K)
-        srv.run(requests_from_specs(I.serving_jobs(8, seconds / 8, rate_hz=10 * rate)),
+        srv.run(requests_from_specs(I.serving_jobs(8, seconds / 4, rate_hz=10 * rate)),
                 mode=mode)
         _, st = srv.run(requests_from_specs(hot), mode=mode)
         srv.close()

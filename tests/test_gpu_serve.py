@@ -179,3 +179,49 @@ def test_native_server_budget_capacity_and_rejections():
     call("mg_server_destroy", h)
     pool.close()
 
+
+
+def test_native_server_wait_times_out_and_stays_usable():
+    """A poll whose wait for a tick outlasts wait_timeout_s returns MG_ETIMEOUT and leaves the
+    server consistent: later polls pick the job up once the device has finished it, with the
+    result of an unhurried server (no fault is provoked: the tick simply takes longer than the
+    1-microsecond limit)."""
+    import ctypes
+    from paper_2410_14117_gb300._lib import JobSpec, Ranges, ServerConfig, call
+    vs = vehicles()
+    pool = Pool(1 << 16, vs)
+    spec = JobSpec(1 << 16, 0, 10, 600, 0, 11, 12, Ranges(0.8, 1.2, 0.2, 0.3, 0))
+    results = []
+    for timeout in (30.0, 1e-6):
+        h = ctypes.c_void_p()
+        call("mg_server_create", pool._h,
+             ctypes.byref(ServerConfig(1e10, 600, 1, 1, 0, 1, 0, timeout)), ctypes.byref(h))
+        tk = ctypes.c_int64()
+        call("mg_server_submit", h, ctypes.byref(spec), ctypes.byref(tk))
+        counts = [ctypes.c_int32() for _ in range(3)]
+        timeouts = 0
+        for _ in range(100000):
+            try:
+                call("mg_server_poll", h, *[ctypes.byref(c) for c in counts])
+            except MGError as e:
+                assert e.code == "MG_ETIMEOUT"
+                timeouts += 1
+                continue
+            if not any(c.value for c in counts):
+                break
+        done = ctypes.c_double()
+        call("mg_server_job", h, tk, None, None, ctypes.byref(done))
+        assert done.value > 0.0
+        state = torch.empty((1 << 16, 21), device="cuda")
+        call("mg_server_job_result", h, tk, _ptr_of(state), None)
+        call("mg_server_release", h, tk)
+        call("mg_server_destroy", h)
+        results.append((timeouts, state))
+    assert results[0][0] == 0 and results[1][0] > 0
+    torch.testing.assert_close(results[1][1], results[0][1], rtol=0, atol=0)
+    pool.close()
+
+
+def _ptr_of(t):
+    import ctypes
+    return ctypes.c_void_p(t.data_ptr())

@@ -338,6 +338,9 @@ def run_ours(args):
     launches_per_episode = (math.ceil(horizon / cfg.steps_per_launch)
                             if cfg.schedule == "static" else 1)
 
+    # Each episode's parameters are drawn while the previous episode steps
+    # (mg_randomize_prefetch on the library's own stream); the episode's mg_randomize installs
+    # them with one device copy.
     def episode(seed, a, out):
         sim.randomize(seed, 0.8, 1.2, 0.2, 0.3, wait=False)
         sim.reset()
@@ -346,8 +349,10 @@ def run_ours(args):
         else:
             sim.set_actions(a, hold)           # host schedule: copied in
         sim.step(horizon)
+        sim.randomize_prefetch(seed + 1)
         sim.get_state(out)
 
+    sim.randomize_prefetch(1000)
     for w in range(max(args.warmup, 3)):
         episode(1000 + w, acts_dev, out_dev)
     torch.cuda.synchronize()
@@ -363,12 +368,15 @@ def run_ours(args):
         flush.zero_()
         e0, e1, e2 = ev[i]
         e0.record(stream)
+        if i == 0:  # the first timed episode's draw is made inside the timed region too
+            sim.randomize_prefetch(2000)
         sim.randomize(2000 + i, 0.8, 1.2, 0.2, 0.3, wait=False)
         sim.reset()
         sim.set_actions_borrowed(acts_dev, hold)
         e1.record(stream)
         sim.step(horizon)
         e2.record(stream)
+        sim.randomize_prefetch(2000 + i + 1)
         sim.get_state(out_dev)
         ev[i].append(torch.cuda.Event(enable_timing=True))
         ev[i][3].record(stream)
@@ -409,14 +417,15 @@ def run_ours(args):
             "config": dict(workload_config(args), launch=dataclasses.asdict(cfg)),
             "roofline": roofline,
             "clocks": clk,
-            "gpu_launches": args.steps * (launches_per_episode + 3)}
+            "gpu_launches": args.steps * (launches_per_episode + 3) + 1}
 
     # ---- end to end through the C ABI with host buffers: every episode's throttle schedule
     # goes in from page-locked host memory (mg_set_actions_async: the library's copy stream,
     # one of two device buffers, overlapping the previous episode's steps) and every episode's
     # final state comes back to page-locked host memory (mg_get_state_async: the library's
-    # read-back stream, overlapping the next episode); parameters are randomised without a host
-    # wait (MG_RANDOMIZE_ASYNC: the fleet's mass matrices are diagonal).  All copies have
+    # read-back stream, overlapping the next episode); each episode's parameters are drawn
+    # while the previous episode steps (mg_randomize_prefetch) and installed without a host wait
+    # (MG_RANDOMIZE_ASYNC: the fleet's mass matrices are diagonal).  All copies and draws have
     # completed when the clock stops (mg_sync).
     if not args.no_e2e:
         # 50 pipelined episodes (0.1 s): the pipeline fills once (the first episode's schedule
@@ -425,11 +434,13 @@ def run_ours(args):
         outs_host = [torch.empty((n, 21), dtype=torch.float32).pin_memory() for _ in range(2)]
 
         def e2e_episodes(count, seed0):
+            sim.randomize_prefetch(seed0)
             for i in range(count):
                 sim.set_actions_async(acts_host, hold)
                 sim.randomize(seed0 + i, 0.8, 1.2, 0.2, 0.3, wait=False)
                 sim.reset()
                 sim.step(horizon)
+                sim.randomize_prefetch(seed0 + i + 1)
                 sim.get_state_async(outs_host[i % 2])
             assert sim.sync() == 0
 
@@ -443,7 +454,9 @@ def run_ours(args):
                        "d2h_bytes_per_step": n * 21 * 4,
                        "note": "per episode, through the C ABI: throttle schedule H2D from "
                                "page-locked host memory (mg_set_actions_async, overlapping the "
-                               "previous episode), parameters randomised without a host wait, "
+                               "previous episode), parameters drawn while the previous "
+                               "episode steps (mg_randomize_prefetch) and installed without a "
+                               "host wait, "
                                "final state D2H to page-locked host memory (mg_get_state_async, "
                                "overlapping the next episode), all inside the wall-clock timed "
                                "region; 50 episodes back to back, including the pipeline fill "

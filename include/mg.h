@@ -180,6 +180,23 @@ mg_status mg_set_packed(mg_sim *sim, int32_t packed);
  * matrix has a pivot <= 0), MG_ECUDA. */
 mg_status mg_randomize(mg_sim *sim, uint64_t seed, const mg_ranges *ranges);
 
+/* Background randomisation (§METHOD's per-episode domain randomisation, drawn ahead): draws the
+ * parameters mg_randomize(sim, seed, ranges) would draw into a second parameter buffer of the
+ * sim, on the library's own stream, so that the draw runs while the sim's stream is still
+ * stepping the current episode (a few 64-thread blocks striding over the fleet, leaving room on
+ * every SM for a step kernel).  The draw waits only for the previous install's copy, never for
+ * the sim's stream.  A later mg_randomize with the same seed, lo, hi and current_sigma, the same
+ * env-id offset and rg_halfwidth 0 installs the buffer with one device-to-device copy on the
+ * sim's stream (ordered after the draw) instead of drawing: the parameters are bit-identical to
+ * a direct draw, and the rest of mg_randomize (nu0_sigma and the seed recorded for mg_reset,
+ * episode counters zeroed, MG_RANDOMIZE_ASYNC) applies as usual.  Any other mg_randomize draws
+ * directly and leaves the buffer in place; a new prefetch replaces it.  ranges->nu0_sigma and
+ * ranges->flags are not used here.  The buffer (the sim's parameter planes and records, 360 B
+ * per env) is allocated on first use.  Errors: MG_EINVAL (ranges as mg_randomize, or mass matrices
+ * that may be full: some type with r_g != 0, rg_halfwidth != 0, or the off-diagonal extension
+ * set), MG_ENOMEM, MG_ECUDA. */
+mg_status mg_randomize_prefetch(mg_sim *sim, uint64_t seed, const mg_ranges *ranges);
+
 /* Set every env's parameters from a [n][MG_NPARAM] record (host or device); inverts the mass
  * matrices as mg_randomize does.  Synchronous.  Errors: MG_EINVAL, MG_ENOTSPD, MG_ECUDA. */
 mg_status mg_set_params(mg_sim *sim, const float *in);
@@ -312,8 +329,8 @@ mg_status mg_get_state_async(mg_sim *sim, float *out);
  * then the counter is incremented and the env's non-finite flag cleared. */
 mg_status mg_reset(mg_sim *sim, const uint8_t *mask);
 
-/* Wait for the stream (and the asynchronous host copies, if any have been issued);
- * *nonfinite_count (may be NULL) receives how many envs are flagged
+/* Wait for the stream (and the asynchronous host copies and background randomisation, if any
+ * have been issued); *nonfinite_count (may be NULL) receives how many envs are flagged
  * non-finite.  Returns MG_ETIMEOUT if a work-queue wait ever gave up (results since then are
  * unreliable; this is not expected to happen), else MG_ENOTSPD if the current parameters hold a
  * mass matrix that is not positive definite, else MG_ENONFINITE when that count is non-zero. */

@@ -114,6 +114,20 @@ struct mg_sim {
   // off-diagonal hydrodynamics, [MG_NXPARAM][n] planes (mg_set_hydro_offdiag), and whether set
   float *xh = nullptr;
   bool has_xh = false;
+  // the arena's parameter range (derived planes, then the raw records): one contiguous span
+  size_t par_off = 0, par_bytes = 0;
+
+  // background randomisation (mg_randomize_prefetch): a second parameter range of the same
+  // layout, followed by its own non-SPD count and off-diagonal word, drawn on the library's own
+  // stream; pf_done orders the install after the draw, pf_consumed the next draw after the
+  // install's copy.  Keyed by everything the draw depends on.  Created on first use.
+  cudaStream_t pf_stream = nullptr;
+  char *pf_buf = nullptr;
+  cudaEvent_t pf_done = nullptr, pf_consumed = nullptr;
+  bool pf_valid = false;
+  uint64_t pf_seed = 0;
+  float pf_lo = 0.f, pf_hi = 0.f, pf_current_sigma = 0.f;
+  int64_t pf_gid0 = 0;
 
   // static-schedule blocks
   BlockDesc *blocks_d = nullptr;
@@ -225,6 +239,24 @@ struct mg_sim {
     v.n_not_spd = counters + 1;
     v.any_offdiag = offdiag;
     v.xh = has_xh ? xh : nullptr;
+    return v;
+  }
+
+  // setup_view() with every parameter pointer moved into the background range
+  SetupView staged_setup_view() const {
+    SetupView v = setup_view();
+    const char *base = static_cast<const char *>(arena) + par_off;
+    auto move = [&](auto *ptr) {
+      return reinterpret_cast<decltype(ptr)>(pf_buf + (reinterpret_cast<const char *>(ptr) - base));
+    };
+    v.raw = move(v.raw);
+    v.pa.d0 = move(v.pa.d0); v.pa.d1 = move(v.pa.d1); v.pa.d2 = move(v.pa.d2);
+    v.pa.d3 = move(v.pa.d3); v.pa.d4 = move(v.pa.d4); v.pa.d5 = move(v.pa.d5);
+    v.pa.d6 = move(v.pa.d6); v.pa.d7 = move(v.pa.d7); v.pa.d8 = move(v.pa.d8);
+    v.pa.g0 = move(v.pa.g0); v.pa.g1 = move(v.pa.g1); v.pa.g2 = move(v.pa.g2);
+    v.pa.g3 = move(v.pa.g3); v.pa.g4 = move(v.pa.g4); v.pa.g5 = move(v.pa.g5);
+    v.n_not_spd = reinterpret_cast<unsigned long long *>(pf_buf + par_bytes);
+    v.any_offdiag = reinterpret_cast<unsigned int *>(pf_buf + par_bytes + 8);
     return v;
   }
 
@@ -554,6 +586,8 @@ mg_status mg_create(int64_t n_envs, const int32_t *vehicle_types,
   for (int i = 0; i < 5; ++i) *gp[i] = (float4 *)(a + o_g[i]);
   s->pa.g5 = (float *)(a + o_g5);
   s->raw = (float *)(a + o_raw);
+  s->par_off = o_d[0];
+  s->par_bytes = o_types - o_d[0];
   s->types_d = (int32_t *)(a + o_types);
   s->geo_d = (Geo *)(a + o_geo);
   s->nominal_d = (float *)(a + o_nom);
@@ -645,6 +679,13 @@ mg_status mg_destroy(mg_sim *s) {
   cudaDeviceSynchronize();
   s->drop_graphs();
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  if (s->pf_stream) {
+    cudaStreamSynchronize(s->pf_stream);
+    cudaStreamDestroy(s->pf_stream);
+    cudaEventDestroy(s->pf_done);
+    cudaEventDestroy(s->pf_consumed);
+    cudaFree(s->pf_buf);
+  }
   if (s->h2d_stream) {
     cudaStreamSynchronize(s->h2d_stream);
     cudaStreamSynchronize(s->d2h_stream);
@@ -732,23 +773,97 @@ mg_status mg_set_packed(mg_sim *s, int32_t packed) {
   return MG_OK;
 }
 
-mg_status mg_randomize(mg_sim *s, uint64_t seed, const mg_ranges *r) {
-  MG_NONNULL(s);
-  NvtxRange nvtx("mg_randomize");
-  MG_NONNULL(r);
+namespace {
+
+mg_status check_ranges(const mg_ranges *r) {
   if (!(r->lo > 0.f) || !(r->lo <= r->hi) || !(r->current_sigma >= 0.f) ||
       !(r->nu0_sigma >= 0.f) || (r->flags & ~MG_RANDOMIZE_ASYNC) != 0 ||
       !(r->rg_halfwidth >= 0.f))
     return fail(MG_EINVAL, "ranges: need 0 < lo <= hi, sigmas >= 0, rg_halfwidth >= 0, "
                            "flags 0 or MG_RANDOMIZE_ASYNC");
+  return MG_OK;
+}
+
+// Mass matrices known to be diagonal before any draw (what MG_RANDOMIZE_ASYNC and
+// mg_randomize_prefetch need).
+bool diagonal_by_construction(const mg_sim *s, const mg_ranges *r) {
+  return s->nominal_diag && r->rg_halfwidth == 0.f && !s->has_xh;
+}
+
+// Whether the background range holds exactly what mg_randomize(s, seed, r) would draw.
+bool staged_matches(const mg_sim *s, uint64_t seed, const mg_ranges *r) {
+  return s->pf_valid && diagonal_by_construction(s, r) && s->pf_seed == seed &&
+         s->pf_lo == r->lo && s->pf_hi == r->hi && s->pf_current_sigma == r->current_sigma &&
+         s->pf_gid0 == s->gid0;
+}
+
+}  // namespace
+
+mg_status mg_randomize_prefetch(mg_sim *s, uint64_t seed, const mg_ranges *r) {
+  MG_NONNULL(s);
+  NvtxRange nvtx("mg_randomize_prefetch");
+  MG_NONNULL(r);
+  mg_status st = check_ranges(r);
+  if (st != MG_OK) return st;
+  if (!diagonal_by_construction(s, r))
+    return fail(MG_EINVAL, "mg_randomize_prefetch needs mass matrices known to be diagonal "
+                           "(r_g = 0 for every type, rg_halfwidth = 0, no extension)");
+  if (!s->pf_stream) {
+    MG_CK(cudaStreamCreateWithFlags(&s->pf_stream, cudaStreamNonBlocking));
+    MG_CK(cudaEventCreateWithFlags(&s->pf_done, cudaEventDisableTiming));
+    MG_CK(cudaEventCreateWithFlags(&s->pf_consumed, cudaEventDisableTiming));
+    if (cudaMalloc(&s->pf_buf, s->par_bytes + 16) != cudaSuccess) {
+      cudaGetLastError();
+      s->pf_buf = nullptr;
+      cudaEventDestroy(s->pf_done);
+      cudaEventDestroy(s->pf_consumed);
+      cudaStreamDestroy(s->pf_stream);
+      s->pf_stream = nullptr;
+      return fail(MG_ENOMEM, "cudaMalloc(background parameter range)");
+    }
+  }
+  s->pf_valid = false;
+  // the last install's copy must have read the range (a never-recorded event is no wait)
+  MG_CK(cudaStreamWaitEvent(s->pf_stream, s->pf_consumed, 0));
+  const SetupView v = s->staged_setup_view();
+  MG_CK(cudaMemsetAsync(v.n_not_spd, 0, 16, s->pf_stream));
+  MG_CK(launch_randomize(v, s->nominal_d, seed, (double)r->lo, (double)r->hi,
+                         (double)r->current_sigma, 0.0, s->pf_stream, s->n_sm));
+  MG_CK(cudaEventRecord(s->pf_done, s->pf_stream));
+  s->pf_valid = true;
+  s->pf_seed = seed;
+  s->pf_lo = r->lo;
+  s->pf_hi = r->hi;
+  s->pf_current_sigma = r->current_sigma;
+  s->pf_gid0 = s->gid0;
+  return MG_OK;
+}
+
+mg_status mg_randomize(mg_sim *s, uint64_t seed, const mg_ranges *r) {
+  MG_NONNULL(s);
+  NvtxRange nvtx("mg_randomize");
+  MG_NONNULL(r);
+  mg_status st = check_ranges(r);
+  if (st != MG_OK) return st;
   const bool async = (r->flags & MG_RANDOMIZE_ASYNC) != 0;
-  if (async && !(s->nominal_diag && r->rg_halfwidth == 0.f && !s->has_xh))
+  if (async && !diagonal_by_construction(s, r))
     return fail(MG_EINVAL, "MG_RANDOMIZE_ASYNC needs mass matrices known to be diagonal "
                            "(r_g = 0 for every type, rg_halfwidth = 0, no extension)");
-  mg_status st = begin_params(s);
-  if (st != MG_OK) return st;
-  MG_CK(launch_randomize(s->setup_view(), s->nominal_d, seed, (double)r->lo, (double)r->hi,
-                         (double)r->current_sigma, (double)r->rg_halfwidth, s->stream));
+  if (staged_matches(s, seed, r)) {
+    // install the background draw: one copy of the parameter range and its two check words
+    char *live = static_cast<char *>(s->arena) + s->par_off;
+    MG_CK(cudaStreamWaitEvent(s->stream, s->pf_done, 0));
+    MG_CK(cudaMemcpyAsync(live, s->pf_buf, s->par_bytes, cudaMemcpyDeviceToDevice, s->stream));
+    MG_CK(cudaMemcpyAsync(s->counters + 1, s->pf_buf + s->par_bytes, 8,
+                          cudaMemcpyDeviceToDevice, s->stream));
+    MG_CK(cudaMemcpyAsync(s->offdiag, s->pf_buf + s->par_bytes + 8, 4,
+                          cudaMemcpyDeviceToDevice, s->stream));
+    MG_CK(cudaEventRecord(s->pf_consumed, s->stream));
+  } else {
+    if ((st = begin_params(s)) != MG_OK) return st;
+    MG_CK(launch_randomize(s->setup_view(), s->nominal_d, seed, (double)r->lo, (double)r->hi,
+                           (double)r->current_sigma, (double)r->rg_halfwidth, s->stream));
+  }
   MG_CK(cudaMemsetAsync(s->episode, 0, 4 * s->n, s->stream));
   s->reset_seed = seed;
   s->nu0_sigma = (double)r->nu0_sigma;
@@ -1192,6 +1307,7 @@ mg_status mg_reset(mg_sim *s, const uint8_t *mask) {
 mg_status mg_sync(mg_sim *s, int64_t *nonfinite_count) {
   MG_NONNULL(s);
   NvtxRange nvtx("mg_sync");
+  if (s->pf_stream) MG_CK(cudaStreamSynchronize(s->pf_stream));
   if (s->h2d_stream) {
     MG_CK(cudaStreamSynchronize(s->h2d_stream));
     MG_CK(cudaStreamSynchronize(s->d2h_stream));

@@ -154,9 +154,11 @@ struct SetupView {
   const float *xh;           // device [MG_NXPARAM][n] off-diagonal hydrodynamics, or null
 };
 
+// background_blocks > 0: at most that many 64-thread blocks striding over the fleet (leaves room
+// for a step kernel running concurrently on another stream); 0: one env per thread.
 cudaError_t launch_randomize(const SetupView &v, const float *nominal /*dev [n_types][35]*/,
                              uint64_t seed, double lo, double hi, double current_sigma,
-                             double rg_halfwidth, cudaStream_t stream);
+                             double rg_halfwidth, cudaStream_t stream, int background_blocks = 0);
 cudaError_t launch_import_params(const SetupView &v, const float *in /*dev [n][35]*/,
                                  cudaStream_t stream);
 // [n][MG_NXPARAM] records <-> [MG_NXPARAM][n] planes (to_planes: records -> planes).

@@ -4,6 +4,7 @@
 //     Eq. 1 by an FP64 Cholesky factorisation (M is symmetric positive definite for any
 //     physical vehicle; a non-positive pivot is counted and reported);
 //   - episode reset, and conversions between the SoA planes and the record layouts of mg.h.
+#include <algorithm>
 #include <type_traits>
 
 #include "mg_device.cuh"
@@ -29,6 +30,9 @@ __host__ __device__ constexpr int rand_idx(int j) {
 // Block size of the randomisation kernel: at ~150 registers two or three 128-thread blocks fit
 // per SM, where one 256-thread block leaves 65,536 envs 1.7 waves.
 constexpr int kRandThreads = 128;
+// Background form: 64-thread blocks (two warps, ~10 K registers) striding over the fleet, so
+// that one block fits beside a step kernel's resident blocks on every SM.
+constexpr int kRandBgThreads = 64;
 
 // derive() for an env whose mass matrix is diagonal (r_g = 0, no off-diagonal added mass): the
 // same values derive() stores, without building the 6 x 6 matrices (FP64 runs at a 64th of the
@@ -188,11 +192,10 @@ __device__ void derive(const SetupView &v, int64_t e, const double *p) {
   pa.g5[e] = f(Mi[4][5]);
 }
 
-__global__ void __launch_bounds__(kRandThreads)
-    k_randomize(const SetupView v, const float *__restrict__ nominal, uint64_t seed,
-                            double lo, double hi, double current_sigma, double rg_halfwidth) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= v.n) return;
+__device__ __forceinline__ void randomize_env(const SetupView &v, const float *__restrict__ nominal,
+                                              uint64_t seed, double lo, double hi,
+                                              double current_sigma, double rg_halfwidth,
+                                              int64_t e) {
   const uint64_t gid = (uint64_t)(v.gid0 + e);
   const float *nom = nominal + (int64_t)v.types[e] * MG_NPARAM;
   double p[MG_NPARAM];
@@ -226,6 +229,24 @@ __global__ void __launch_bounds__(kRandThreads)
     p[j] = (double)f;
   }
   derive(v, e, p);
+}
+
+// One env per thread.
+__global__ void __launch_bounds__(kRandThreads)
+    k_randomize(const SetupView v, const float *__restrict__ nominal, uint64_t seed,
+                            double lo, double hi, double current_sigma, double rg_halfwidth) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < v.n) randomize_env(v, nominal, seed, lo, hi, current_sigma, rg_halfwidth, e);
+}
+
+// Background form: a grid smaller than the fleet strides over it, leaving room on every SM for
+// a step kernel running concurrently on another stream.  Same per-env arithmetic.
+__global__ void __launch_bounds__(kRandBgThreads)
+    k_randomize_bg(const SetupView v, const float *__restrict__ nominal, uint64_t seed,
+                   double lo, double hi, double current_sigma, double rg_halfwidth) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < v.n; e += stride)
+    randomize_env(v, nominal, seed, lo, hi, current_sigma, rg_halfwidth, e);
 }
 
 __global__ void k_import_params(const SetupView v, const float *__restrict__ in) {
@@ -314,9 +335,16 @@ __global__ void k_philox(const uint32_t *__restrict__ ctr, const uint32_t *__res
 
 cudaError_t launch_randomize(const SetupView &v, const float *nominal, uint64_t seed, double lo,
                              double hi, double current_sigma, double rg_halfwidth,
-                             cudaStream_t stream) {
-  k_randomize<<<(int)((v.n + kRandThreads - 1) / kRandThreads), kRandThreads, 0, stream>>>(
-      v, nominal, seed, lo, hi, current_sigma, rg_halfwidth);
+                             cudaStream_t stream, int background_blocks) {
+  if (background_blocks > 0) {
+    const int64_t full = (v.n + kRandBgThreads - 1) / kRandBgThreads;
+    const int blocks = (int)std::min<int64_t>(full, background_blocks);
+    k_randomize_bg<<<blocks, kRandBgThreads, 0, stream>>>(v, nominal, seed, lo, hi,
+                                                          current_sigma, rg_halfwidth);
+  } else {
+    k_randomize<<<(int)((v.n + kRandThreads - 1) / kRandThreads), kRandThreads, 0, stream>>>(
+        v, nominal, seed, lo, hi, current_sigma, rg_halfwidth);
+  }
   return cudaGetLastError();
 }
 

@@ -123,6 +123,14 @@ class Sim:
                    rg_halfwidth)
         call("mg_randomize", self._h, ctypes.c_uint64(seed), ctypes.byref(r))
 
+    def randomize_prefetch(self, seed: int, lo: float = 0.8, hi: float = 1.2,
+                           current_sigma: float = 0.2):
+        """Draw randomize(seed, lo, hi, current_sigma) ahead, on the library's own stream, into a
+        second parameter buffer (mg_randomize_prefetch); the matching randomize() call installs
+        it with one device copy.  Diagonal-mass fleets."""
+        r = Ranges(lo, hi, current_sigma, 0.0, 0, 0.0)
+        call("mg_randomize_prefetch", self._h, ctypes.c_uint64(seed), ctypes.byref(r))
+
     def set_params(self, params):
         _check(params, (self.n, MG_NPARAM), torch.float32)
         call("mg_set_params", self._h, _ptr(params))

@@ -5,6 +5,7 @@
 //     physical vehicle; a non-positive pivot is counted and reported);
 //   - episode reset, and conversions between the SoA planes and the record layouts of mg.h.
 #include <algorithm>
+#include <cstdint>
 #include <type_traits>
 
 #include "mg_device.cuh"
@@ -290,20 +291,60 @@ __global__ void k_reset(const StatePlanes st, int64_t n, int64_t gid0,
   reset_env(st, e, (uint64_t)(gid0 + e), seed, sigma, episode, flags, nonfinite_count);
 }
 
-__global__ void k_export_state(const StatePlanes st, int64_t n, float *__restrict__ out) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n) return;
-  const float4 a = st.s0[e], b = st.s1[e], c = st.s2[e], d = st.s3[e], f = st.s4[e];
-  const float r[MG_NSTATE] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z,
-                              c.w, d.x, d.y, d.z, d.w, f.x, f.y, f.z, f.w, st.s5[e]};
-  float *o = out + e * MG_NSTATE;
-  for (int j = 0; j < MG_NSTATE; ++j) o[j] = r[j];
+// State rows ([n][MG_NSTATE], 84 B each) <-> planes, staged through shared memory so that a
+// block's rows move as one contiguous span (16-byte vectors when the row buffer is 16-byte
+// aligned: a block's span starts at a multiple of kRowThreads x 84 B = 10,752 B).
+constexpr int kRowThreads = 128;
+
+__device__ __forceinline__ bool aligned16(const void *p) {
+  return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
 }
 
-__global__ void k_import_state(const StatePlanes st, int64_t n, const float *__restrict__ in) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kRowThreads)
+    k_export_state(const StatePlanes st, int64_t n, float *__restrict__ out) {
+  __shared__ __align__(16) float rows[kRowThreads * MG_NSTATE];
+  const int64_t e0 = (int64_t)blockIdx.x * kRowThreads;
+  const int t = (int)threadIdx.x;
+  const int64_t e = e0 + t;
+  if (e < n) {
+    const float4 a = st.s0[e], b = st.s1[e], c = st.s2[e], d = st.s3[e], f = st.s4[e];
+    const float r[MG_NSTATE] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z,
+                                c.w, d.x, d.y, d.z, d.w, f.x, f.y, f.z, f.w, st.s5[e]};
+#pragma unroll
+    for (int j = 0; j < MG_NSTATE; ++j) rows[t * MG_NSTATE + j] = r[j];
+  }
+  __syncthreads();
+  const int total = (int)(n - e0 < kRowThreads ? n - e0 : kRowThreads) * MG_NSTATE;
+  float *o = out + e0 * MG_NSTATE;
+  int done = 0;
+  if (aligned16(out)) {
+    done = total & ~3;
+    float4 *o4 = reinterpret_cast<float4 *>(o);
+    const float4 *r4 = reinterpret_cast<const float4 *>(rows);
+    for (int i = t; i < done / 4; i += kRowThreads) o4[i] = r4[i];
+  }
+  for (int i = done + t; i < total; i += kRowThreads) o[i] = rows[i];
+}
+
+__global__ void __launch_bounds__(kRowThreads)
+    k_import_state(const StatePlanes st, int64_t n, const float *__restrict__ in) {
+  __shared__ __align__(16) float rows[kRowThreads * MG_NSTATE];
+  const int64_t e0 = (int64_t)blockIdx.x * kRowThreads;
+  const int t = (int)threadIdx.x;
+  const int total = (int)(n - e0 < kRowThreads ? n - e0 : kRowThreads) * MG_NSTATE;
+  const float *src = in + e0 * MG_NSTATE;
+  int done = 0;
+  if (aligned16(in)) {
+    done = total & ~3;
+    const float4 *i4 = reinterpret_cast<const float4 *>(src);
+    float4 *r4 = reinterpret_cast<float4 *>(rows);
+    for (int i = t; i < done / 4; i += kRowThreads) r4[i] = i4[i];
+  }
+  for (int i = done + t; i < total; i += kRowThreads) rows[i] = src[i];
+  __syncthreads();
+  const int64_t e = e0 + t;
   if (e >= n) return;
-  const float *r = in + e * MG_NSTATE;
+  const float *r = rows + t * MG_NSTATE;
   st.s0[e] = make_float4(r[0], r[1], r[2], r[3]);
   st.s1[e] = make_float4(r[4], r[5], r[6], r[7]);
   st.s2[e] = make_float4(r[8], r[9], r[10], r[11]);
@@ -374,13 +415,15 @@ cudaError_t launch_reset(const StatePlanes &st, int64_t n, int64_t gid0, const u
 
 cudaError_t launch_export_state(const StatePlanes &st, int64_t n, float *out,
                                 cudaStream_t stream) {
-  k_export_state<<<blocks_for(n), kThreads, 0, stream>>>(st, n, out);
+  k_export_state<<<(int)((n + kRowThreads - 1) / kRowThreads), kRowThreads, 0, stream>>>(st, n,
+                                                                                      out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_import_state(const StatePlanes &st, int64_t n, const float *in,
                                 cudaStream_t stream) {
-  k_import_state<<<blocks_for(n), kThreads, 0, stream>>>(st, n, in);
+  k_import_state<<<(int)((n + kRowThreads - 1) / kRowThreads), kRowThreads, 0, stream>>>(st, n,
+                                                                                      in);
   return cudaGetLastError();
 }
 

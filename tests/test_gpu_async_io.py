@@ -110,3 +110,25 @@ def test_alternating_action_buffers_replay_cached_graphs(queue):
         out.append(sim.get_state().cpu().numpy())
         sim.close()
     np.testing.assert_array_equal(out[1], out[0])
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 1000])
+@pytest.mark.parametrize("offset", [0, 1, 3])
+def test_state_rows_round_trip_any_alignment_and_ragged_tail(n, offset):
+    """mg_set_state / mg_get_state move [n][21] rows through shared memory in 128-row spans,
+    as 16-byte vectors when the buffer is 16-byte aligned: every fleet size (ragged last span)
+    and buffer offset (1 or 3 floats: misaligned) gives the rows back bit for bit."""
+    vs = vehicles()
+    sim = Sim(n, np.zeros(n, dtype=np.int32), vs)
+    rows = torch.from_numpy(I.random_states(7 + n, n, 6).astype(np.float32)).cuda()
+    src = torch.full((n * 21 + offset,), float("nan"), device="cuda")
+    src[offset:] = rows.reshape(-1)
+    sim.set_state(src[offset:].view(n, 21))
+    dst = torch.full((n * 21 + offset + 5,), -7.0, device="cuda")
+    sim.get_state(dst[offset:offset + n * 21].view(n, 21))
+    host = sim.get_state(torch.empty((n, 21), dtype=torch.float32))
+    assert sim.sync() == 0
+    sim.close()
+    torch.testing.assert_close(dst[offset:offset + n * 21].view(n, 21), rows, rtol=0, atol=0)
+    assert torch.all(dst[:offset] == -7.0) and torch.all(dst[offset + n * 21:] == -7.0)
+    torch.testing.assert_close(host, rows.cpu(), rtol=0, atol=0)

@@ -1,7 +1,8 @@
 """Parity at the benchmark's full sizes, in the launch configurations the benchmark times, on
 sampled envs the oracle computes one by one: the 65,536-env headline fleet (work-queue kernel,
 200-register cap, 8 warps/SM, chunk 100, actions read in place, CUDA graph) over a whole 1,000
-sub-step episode, the 262,144-env mixed fleet over 500 sub-steps and the 1,048,576-env top of
+sub-step episode, parameters drawn in the background and installed as the benchmark does them,
+the 262,144-env mixed fleet over 500 sub-steps and the 1,048,576-env top of
 the size sweep (each also on the packed static grid, two envs per thread, which the autotuner
 picks for them)."""
 import numpy as np
@@ -44,7 +45,9 @@ def test_headline_fleet_sampled_matches_oracle():
     types = np.zeros(n, dtype=np.int32)
     sim = Sim(n, types, vs)
     LaunchConfig("queue", 128, 100, True, 8).apply(sim)
-    sim.randomize(1234, 0.8, 1.2, 0.2, 0.3)
+    # the parameters reach the fleet as in the benchmark: drawn in the background, installed
+    sim.randomize_prefetch(1234, 0.8, 1.2, 0.2)
+    sim.randomize(1234, 0.8, 1.2, 0.2, 0.3, wait=False)
     sim.reset()
     cmds = I.commands(5678, 100, n, 6)
     acts = torch.tensor(cmds, device="cuda")

@@ -689,13 +689,21 @@ def bench_adjoint(vs, n=4096, T=200, C=20, reps=5):
         g = torch.autograd.grad(((tr - target) ** 2).mean(), (coeffs, acts))
         return g
 
-    fb_ms = _time_episodes(fb, reps)
+    fb_ms = _time_episodes(fb, reps)  # backward kernel chosen by fleet size
+    sim.set_adjoint_mode(1)            # one warp per 32 envs, for comparison
+    fb1_ms = _time_episodes(fb, reps)
+    sim.set_adjoint_mode(0)
     sim.close()
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    split = (n + 31) // 32 <= 2 * n_sm
     return {"workload": f"{n:,} BlueROV2 envs, {T} RK4 sub-steps, checkpoints every {C}, "
                         "MSE on the trajectory",
             "launch": dataclasses.asdict(launch),
+            "backward_kernel": ("two warps per 32 envs (segment re-run and stage records | "
+                                "transposes)" if split else "one warp per 32 envs"),
             "forward_ms": f_ms, "forward_backward_ms": fb_ms,
-            "backward_over_forward": (fb_ms - f_ms) / f_ms, "loss": float(loss.detach())}
+            "backward_over_forward": (fb_ms - f_ms) / f_ms,
+            "forward_backward_one_warp_ms": fb1_ms, "loss": float(loss.detach())}
 
 
 def bench_task(vs, n=65536, k=10, steps=100, reps=3):

@@ -300,6 +300,16 @@ mg_status mg_rollout_backward(mg_sim *sim, int32_t T, int32_t C, const float *ck
                               const float *dtraj, int64_t step0, float *dcoef, float *dact,
                               float *dstate0);
 
+/* Backward kernel of mg_rollout_backward.  mode 1: one thread per env, each re-running a
+ * checkpoint segment and then walking it backwards.  mode 2: two warps per 32 envs, one
+ * re-running the segments and recording every sub-step's RK4 stage states in a workspace
+ * (2 x C x (4 (10 + N) + 4) floats per env, N = 6 or 8 thrusters; allocated by
+ * mg_rollout_backward on first use), the other applying the transposes from those records one
+ * segment behind, so that a small fleet keeps twice as many schedulers busy.  mode 0 (default):
+ * mode 2 while 2 x ceil(n_envs / 32) warps fit one per scheduler of the GPU, else mode 1.  The
+ * per-env arithmetic is the same in both.  MG_EINVAL unless 0 <= mode <= 2. */
+mg_status mg_set_adjoint_mode(mg_sim *sim, int32_t mode);
+
 /* State in the record layout [n][MG_NSTATE] = p(3) q(4: w,x,y,z) nu(6) n(8, zero past n_thr);
  * host or device. */
 mg_status mg_get_state(mg_sim *sim, float *out);

@@ -87,6 +87,7 @@ SIGNATURES = {
     "mg_set_packed": [_P, _I32],
     "mg_randomize": [_P, _U64, ctypes.POINTER(Ranges)],
     "mg_randomize_prefetch": [_P, _U64, ctypes.POINTER(Ranges)],
+    "mg_set_adjoint_mode": [_P, _I32],
     "mg_set_params": [_P, _P],
     "mg_get_params": [_P, _P],
     "mg_set_actions": [_P, _P, _I32, _I32],

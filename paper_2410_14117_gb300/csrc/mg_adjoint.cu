@@ -27,19 +27,23 @@ struct Grad {
   float ma[3], J[3], mi[6], dl[6], dq[6];
 };
 
+// Every multiply-add of the adjoint code below is written as an explicit fmaf, so the compiler
+// forms no fused operation of its own: the results do not depend on the surrounding code the
+// functions are inlined into (the one-warp and two-warp backward kernels agree bit for bit).
+
 __device__ __forceinline__ void cross_vjp(const float a[3], const float b[3], const float gc[3],
                                           float ga[3], float gb[3]) {
   // c = a x b:  ga += b x gc,  gb += gc x a.
-  ga[0] += b[1] * gc[2] - b[2] * gc[1];
-  ga[1] += b[2] * gc[0] - b[0] * gc[2];
-  ga[2] += b[0] * gc[1] - b[1] * gc[0];
-  gb[0] += gc[1] * a[2] - gc[2] * a[1];
-  gb[1] += gc[2] * a[0] - gc[0] * a[2];
-  gb[2] += gc[0] * a[1] - gc[1] * a[0];
+  ga[0] = fmaf(b[1], gc[2], fmaf(-b[2], gc[1], ga[0]));
+  ga[1] = fmaf(b[2], gc[0], fmaf(-b[0], gc[2], ga[1]));
+  ga[2] = fmaf(b[0], gc[1], fmaf(-b[1], gc[0], ga[2]));
+  gb[0] = fmaf(gc[1], a[2], fmaf(-gc[2], a[1], gb[0]));
+  gb[1] = fmaf(gc[2], a[0], fmaf(-gc[0], a[2], gb[1]));
+  gb[2] = fmaf(gc[0], a[1], fmaf(-gc[1], a[0], gb[2]));
 }
 
 // gs += (d rhs / d s)^T gd; parameter and command adjoints accumulated into G and gcs.  The
-// forward quantities are recomputed with the formulas of rhs() (diagonal mass); gd.q is the
+// forward quantities are recomputed from the formulas of rhs() (diagonal mass); gd.q is the
 // adjoint of d.q = q (x) (0, w) (the doubled quaternion rate rhs() stores).
 template <int MT>
 __device__ void rhs_vjp(const St<MT> &s, const float (&cs)[MT], const ParDiag &P,
@@ -47,66 +51,74 @@ __device__ void rhs_vjp(const St<MT> &s, const float (&cs)[MT], const ParDiag &P
                         const St<MT> &gd, St<MT> &gs, Grad &G, float (&gcs)[MT]) {
   // ---------------- forward recomputation
   float t[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int i = 0; i < nt; ++i) {
+#pragma unroll
+  for (int i = 0; i < MT; ++i) {
+    if (i >= nt) continue;  // compile-time indices keep the arrays in registers
     const float f = s.n[i] * fabsf(s.n[i]);
     const float4 dd = gdir[i], aa = garm[i];
-    t[0] += f * dd.x; t[1] += f * dd.y; t[2] += f * dd.z;
-    t[3] += f * aa.x; t[4] += f * aa.y; t[5] += f * aa.z;
+    t[0] = fmaf(f, dd.x, t[0]); t[1] = fmaf(f, dd.y, t[1]); t[2] = fmaf(f, dd.z, t[2]);
+    t[3] = fmaf(f, aa.x, t[3]); t[4] = fmaf(f, aa.y, t[4]); t[5] = fmaf(f, aa.z, t[5]);
   }
   const float qw = s.q[0], qx = s.q[1], qy = s.q[2], qz = s.q[3];
   float R[3][3];
-  R[0][0] = 1.f - 2.f * (qy * qy + qz * qz);
-  R[0][1] = 2.f * (qx * qy - qw * qz);
-  R[0][2] = 2.f * (qx * qz + qw * qy);
-  R[1][0] = 2.f * (qx * qy + qw * qz);
-  R[1][1] = 1.f - 2.f * (qx * qx + qz * qz);
-  R[1][2] = 2.f * (qy * qz - qw * qx);
-  R[2][0] = 2.f * (qx * qz - qw * qy);
-  R[2][1] = 2.f * (qy * qz + qw * qx);
-  R[2][2] = 1.f - 2.f * (qx * qx + qy * qy);
+  R[0][0] = fmaf(-2.f, fmaf(qy, qy, qz * qz), 1.f);
+  R[0][1] = 2.f * fmaf(qx, qy, -qw * qz);
+  R[0][2] = 2.f * fmaf(qx, qz, qw * qy);
+  R[1][0] = 2.f * fmaf(qx, qy, qw * qz);
+  R[1][1] = fmaf(-2.f, fmaf(qx, qx, qz * qz), 1.f);
+  R[1][2] = 2.f * fmaf(qy, qz, -qw * qx);
+  R[2][0] = 2.f * fmaf(qx, qz, -qw * qy);
+  R[2][1] = 2.f * fmaf(qy, qz, qw * qx);
+  R[2][2] = fmaf(-2.f, fmaf(qx, qx, qy * qy), 1.f);
   const float v[3] = {s.v[0], s.v[1], s.v[2]}, w[3] = {s.w[0], s.w[1], s.w[2]};
   const float vc[3] = {P.vc0, P.vc1, P.vc2}, ma[3] = {P.ma0, P.ma1, P.ma2};
   const float J[3] = {P.J0, P.J1, P.J2}, G3[3] = {P.G0, P.G1, P.G2};
   float cb[3], r[3], qm[3], h[3], k[3], a[3];
-  for (int i = 0; i < 3; ++i) cb[i] = R[0][i] * vc[0] + R[1][i] * vc[1] + R[2][i] * vc[2];
+  for (int i = 0; i < 3; ++i)
+    cb[i] = fmaf(R[2][i], vc[2], fmaf(R[1][i], vc[1], R[0][i] * vc[0]));
   for (int i = 0; i < 3; ++i) {
     r[i] = v[i] - cb[i];
     qm[i] = ma[i] * r[i];
-    h[i] = P.m * v[i] + qm[i];
+    h[i] = fmaf(P.m, v[i], qm[i]);
     k[i] = J[i] * w[i];
   }
-  a[0] = w[1] * cb[2] - w[2] * cb[1];
-  a[1] = w[2] * cb[0] - w[0] * cb[2];
-  a[2] = w[0] * cb[1] - w[1] * cb[0];
+  a[0] = fmaf(w[1], cb[2], -w[2] * cb[1]);
+  a[1] = fmaf(w[2], cb[0], -w[0] * cb[2]);
+  a[2] = fmaf(w[0], cb[1], -w[1] * cb[0]);
   const float e[3] = {R[2][0], R[2][1], R[2][2]};
+  // translational: kT t + (W - B) e - w x h - (Dl + Dq |r|) r [- M_A (w x v_c^b)]
   float f[6];
-  f[0] = P.kT * t[0] + P.wb * e[0] - (w[1] * h[2] - w[2] * h[1]) -
-         (P.dl[0] + P.dq[0] * fabsf(r[0])) * r[0];
-  f[1] = P.kT * t[1] + P.wb * e[1] - (w[2] * h[0] - w[0] * h[2]) -
-         (P.dl[1] + P.dq[1] * fabsf(r[1])) * r[1];
-  f[2] = P.kT * t[2] + P.wb * e[2] - (w[0] * h[1] - w[1] * h[0]) -
-         (P.dl[2] + P.dq[2] * fabsf(r[2])) * r[2];
+  for (int i = 0; i < 3; ++i) {
+    const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+    float x = fmaf(P.kT, t[i], P.wb * e[i]);
+    x = fmaf(-w[i1], h[i2], fmaf(w[i2], h[i1], x));
+    f[i] = fmaf(-fmaf(P.dq[i], fabsf(r[i]), P.dl[i]), r[i], x);
+  }
   if (current_accel)
-    for (int i = 0; i < 3; ++i) f[i] -= ma[i] * a[i];
-  f[3] = P.kT * t[3] - (r[1] * qm[2] - r[2] * qm[1]) - (w[1] * k[2] - w[2] * k[1]) -
-         (P.dl[3] + P.dq[3] * fabsf(w[0])) * w[0] + (G3[1] * e[2] - G3[2] * e[1]);
-  f[4] = P.kT * t[4] - (r[2] * qm[0] - r[0] * qm[2]) - (w[2] * k[0] - w[0] * k[2]) -
-         (P.dl[4] + P.dq[4] * fabsf(w[1])) * w[1] + (G3[2] * e[0] - G3[0] * e[2]);
-  f[5] = P.kT * t[5] - (r[0] * qm[1] - r[1] * qm[0]) - (w[0] * k[1] - w[1] * k[0]) -
-         (P.dl[5] + P.dq[5] * fabsf(w[2])) * w[2] + (G3[0] * e[1] - G3[1] * e[0]);
+    for (int i = 0; i < 3; ++i) f[i] = fmaf(-ma[i], a[i], f[i]);
+  // rotational: kT t' - r x Q1 - w x k - (Dl + Dq |w|) w + G x e
+  for (int i = 0; i < 3; ++i) {
+    const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+    float x = fmaf(P.kT, t[3 + i], fmaf(-r[i1], qm[i2], r[i2] * qm[i1]));
+    x = fmaf(-w[i1], k[i2], fmaf(w[i2], k[i1], x));
+    x = fmaf(-fmaf(P.dq[3 + i], fabsf(w[i]), P.dl[3 + i]), w[i], x);
+    f[3 + i] = fmaf(G3[i1], e[i2], fmaf(-G3[i2], e[i1], x));
+  }
 
   // ---------------- reverse
   // lag: d.n_i = cs_i - n_i / tau_m
-  for (int i = 0; i < nt; ++i) {
+#pragma unroll
+  for (int i = 0; i < MT; ++i) {
+    if (i >= nt) continue;
     gcs[i] += gd.n[i];
-    gs.n[i] -= P.itau * gd.n[i];
+    gs.n[i] = fmaf(-P.itau, gd.n[i], gs.n[i]);
   }
   // nu' = M^-1 f
   const float gnu[6] = {gd.v[0], gd.v[1], gd.v[2], gd.w[0], gd.w[1], gd.w[2]};
   float gf[6], gt[6];
   for (int j = 0; j < 6; ++j) {
     gf[j] = P.mi[j] * gnu[j];
-    G.mi[j] += f[j] * gnu[j];
+    G.mi[j] = fmaf(f[j], gnu[j], G.mi[j]);
     gt[j] = P.kT * gf[j];
   }
   float gw[3] = {0.f, 0.f, 0.f}, gv[3] = {0.f, 0.f, 0.f}, gr[3] = {0.f, 0.f, 0.f};
@@ -119,9 +131,9 @@ __device__ void rhs_vjp(const St<MT> &s, const float (&cs)[MT], const ParDiag &P
   cross_vjp(w, k, ngfr, gw, gk);     // - w x k
   for (int j = 0; j < 3; ++j) {
     const float aw = fabsf(w[j]);
-    gw[j] -= (P.dl[3 + j] + 2.f * P.dq[3 + j] * aw) * gfr[j];
-    G.dl[3 + j] -= w[j] * gfr[j];
-    G.dq[3 + j] -= aw * w[j] * gfr[j];
+    gw[j] = fmaf(-fmaf(2.f * P.dq[3 + j], aw, P.dl[3 + j]), gfr[j], gw[j]);
+    G.dl[3 + j] = fmaf(-w[j], gfr[j], G.dl[3 + j]);
+    G.dq[3 + j] = fmaf(-aw * w[j], gfr[j], G.dq[3 + j]);
   }
   {
     float gG[3] = {0.f, 0.f, 0.f};
@@ -130,69 +142,74 @@ __device__ void rhs_vjp(const St<MT> &s, const float (&cs)[MT], const ParDiag &P
   // translational force
   const float gfl[3] = {gf[0], gf[1], gf[2]};
   const float ngfl[3] = {-gf[0], -gf[1], -gf[2]};
-  for (int j = 0; j < 3; ++j) ge[j] += P.wb * gfl[j];
+  for (int j = 0; j < 3; ++j) ge[j] = fmaf(P.wb, gfl[j], ge[j]);
   cross_vjp(w, h, ngfl, gw, gh);     // - w x h
   for (int j = 0; j < 3; ++j) {
     const float ar = fabsf(r[j]);
-    gr[j] -= (P.dl[j] + 2.f * P.dq[j] * ar) * gfl[j];
-    G.dl[j] -= r[j] * gfl[j];
-    G.dq[j] -= ar * r[j] * gfl[j];
+    gr[j] = fmaf(-fmaf(2.f * P.dq[j], ar, P.dl[j]), gfl[j], gr[j]);
+    G.dl[j] = fmaf(-r[j], gfl[j], G.dl[j]);
+    G.dq[j] = fmaf(-ar * r[j], gfl[j], G.dq[j]);
   }
   if (current_accel) {
     float ga[3];
     for (int j = 0; j < 3; ++j) {
-      G.ma[j] -= a[j] * gfl[j];
+      G.ma[j] = fmaf(-a[j], gfl[j], G.ma[j]);
       ga[j] = -ma[j] * gfl[j];
     }
     cross_vjp(w, cb, ga, gw, gcb);   // - M_A (w x v_c^b)
   }
   // k = J w, h = m v + Q1, Q1 = M_A r, r = v - v_c^b
   for (int j = 0; j < 3; ++j) {
-    gw[j] += J[j] * gk[j];
-    G.J[j] += w[j] * gk[j];
-    gv[j] += P.m * gh[j];
+    gw[j] = fmaf(J[j], gk[j], gw[j]);
+    G.J[j] = fmaf(w[j], gk[j], G.J[j]);
+    gv[j] = fmaf(P.m, gh[j], gv[j]);
     gqm[j] += gh[j];
-    gr[j] += ma[j] * gqm[j];
-    G.ma[j] += r[j] * gqm[j];
+    gr[j] = fmaf(ma[j], gqm[j], gr[j]);
+    G.ma[j] = fmaf(r[j], gqm[j], G.ma[j]);
     gv[j] += gr[j];
     gcb[j] -= gr[j];
   }
   // R entries: v_c^b = R^T v_c, e = third row of R, p' = R v
   float gR[3][3];
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) gR[i][j] = vc[i] * gcb[j] + gd.p[i] * v[j];
+    for (int j = 0; j < 3; ++j) gR[i][j] = fmaf(vc[i], gcb[j], gd.p[i] * v[j]);
   for (int j = 0; j < 3; ++j) {
     gR[2][j] += ge[j];
-    gv[j] += R[0][j] * gd.p[0] + R[1][j] * gd.p[1] + R[2][j] * gd.p[2];
+    gv[j] = fmaf(R[0][j], gd.p[0], fmaf(R[1][j], gd.p[1], fmaf(R[2][j], gd.p[2], gv[j])));
   }
   // d.q = q (x) (0, w)
   const float g0 = gd.q[0], g1 = gd.q[1], g2 = gd.q[2], g3 = gd.q[3];
-  gw[0] += -qx * g0 + qw * g1 + qz * g2 - qy * g3;
-  gw[1] += -qy * g0 - qz * g1 + qw * g2 + qx * g3;
-  gw[2] += -qz * g0 + qy * g1 - qx * g2 + qw * g3;
+  gw[0] = fmaf(-qx, g0, fmaf(qw, g1, fmaf(qz, g2, fmaf(-qy, g3, gw[0]))));
+  gw[1] = fmaf(-qy, g0, fmaf(-qz, g1, fmaf(qw, g2, fmaf(qx, g3, gw[1]))));
+  gw[2] = fmaf(-qz, g0, fmaf(qy, g1, fmaf(-qx, g2, fmaf(qw, g3, gw[2]))));
   float gq[4];
-  gq[0] = w[0] * g1 + w[1] * g2 + w[2] * g3;
-  gq[1] = -w[0] * g0 - w[2] * g2 + w[1] * g3;
-  gq[2] = -w[1] * g0 + w[2] * g1 - w[0] * g3;
-  gq[3] = -w[2] * g0 - w[1] * g1 + w[0] * g2;
+  gq[0] = fmaf(w[0], g1, fmaf(w[1], g2, w[2] * g3));
+  gq[1] = fmaf(-w[0], g0, fmaf(-w[2], g2, w[1] * g3));
+  gq[2] = fmaf(-w[1], g0, fmaf(w[2], g1, -w[0] * g3));
+  gq[3] = fmaf(-w[2], g0, fmaf(-w[1], g1, w[0] * g2));
   // R(q) -> q
-  gq[0] += 2.f * (-qz * gR[0][1] + qz * gR[1][0] + qy * gR[0][2] - qy * gR[2][0] -
-                  qx * gR[1][2] + qx * gR[2][1]);
-  gq[1] += 2.f * (qy * gR[0][1] + qy * gR[1][0] + qz * gR[0][2] + qz * gR[2][0] -
-                  qw * gR[1][2] + qw * gR[2][1]) -
-           4.f * qx * (gR[1][1] + gR[2][2]);
-  gq[2] += 2.f * (qx * gR[0][1] + qx * gR[1][0] + qw * gR[0][2] - qw * gR[2][0] +
-                  qz * gR[1][2] + qz * gR[2][1]) -
-           4.f * qy * (gR[0][0] + gR[2][2]);
-  gq[3] += 2.f * (-qw * gR[0][1] + qw * gR[1][0] + qx * gR[0][2] + qx * gR[2][0] +
-                  qy * gR[1][2] + qy * gR[2][1]) -
-           4.f * qz * (gR[0][0] + gR[1][1]);
+  {
+    const float s0 = fmaf(-qz, gR[0][1], fmaf(qz, gR[1][0], fmaf(qy, gR[0][2],
+                     fmaf(-qy, gR[2][0], fmaf(-qx, gR[1][2], qx * gR[2][1])))));
+    const float s1 = fmaf(qy, gR[0][1], fmaf(qy, gR[1][0], fmaf(qz, gR[0][2],
+                     fmaf(qz, gR[2][0], fmaf(-qw, gR[1][2], qw * gR[2][1])))));
+    const float s2 = fmaf(qx, gR[0][1], fmaf(qx, gR[1][0], fmaf(qw, gR[0][2],
+                     fmaf(-qw, gR[2][0], fmaf(qz, gR[1][2], qz * gR[2][1])))));
+    const float s3 = fmaf(-qw, gR[0][1], fmaf(qw, gR[1][0], fmaf(qx, gR[0][2],
+                     fmaf(qx, gR[2][0], fmaf(qy, gR[1][2], qy * gR[2][1])))));
+    gq[0] = fmaf(2.f, s0, gq[0]);
+    gq[1] = fmaf(2.f, s1, fmaf(-4.f * qx, gR[1][1] + gR[2][2], gq[1]));
+    gq[2] = fmaf(2.f, s2, fmaf(-4.f * qy, gR[0][0] + gR[2][2], gq[2]));
+    gq[3] = fmaf(2.f, s3, fmaf(-4.f * qz, gR[0][0] + gR[1][1], gq[3]));
+  }
   // thrust: t = sum_i n_i|n_i| b_i
-  for (int i = 0; i < nt; ++i) {
+#pragma unroll
+  for (int i = 0; i < MT; ++i) {
+    if (i >= nt) continue;
     const float4 dd = gdir[i], aa = garm[i];
-    const float gfi = dd.x * gt[0] + dd.y * gt[1] + dd.z * gt[2] + aa.x * gt[3] +
-                      aa.y * gt[4] + aa.z * gt[5];
-    gs.n[i] += 2.f * fabsf(s.n[i]) * gfi;
+    const float gfi = fmaf(dd.x, gt[0], fmaf(dd.y, gt[1], fmaf(dd.z, gt[2],
+                      fmaf(aa.x, gt[3], fmaf(aa.y, gt[4], aa.z * gt[5])))));
+    gs.n[i] = fmaf(2.f * fabsf(s.n[i]), gfi, gs.n[i]);
   }
   for (int i = 0; i < 4; ++i) gs.q[i] += gq[i];
   for (int i = 0; i < 3; ++i) {
@@ -206,11 +223,11 @@ __device__ void rhs_vjp(const St<MT> &s, const float (&cs)[MT], const ParDiag &P
 template <int MT>
 __device__ __forceinline__ void wscale(St<MT> &out, const St<MT> &x, float a, bool add) {
   const float aq = 0.5f * a;
-  for (int i = 0; i < 3; ++i) out.p[i] = (add ? out.p[i] : 0.f) + a * x.p[i];
-  for (int i = 0; i < 4; ++i) out.q[i] = (add ? out.q[i] : 0.f) + aq * x.q[i];
-  for (int i = 0; i < 3; ++i) out.v[i] = (add ? out.v[i] : 0.f) + a * x.v[i];
-  for (int i = 0; i < 3; ++i) out.w[i] = (add ? out.w[i] : 0.f) + a * x.w[i];
-  for (int i = 0; i < MT; ++i) out.n[i] = (add ? out.n[i] : 0.f) + a * x.n[i];
+  for (int i = 0; i < 3; ++i) out.p[i] = add ? fmaf(a, x.p[i], out.p[i]) : a * x.p[i];
+  for (int i = 0; i < 4; ++i) out.q[i] = add ? fmaf(aq, x.q[i], out.q[i]) : aq * x.q[i];
+  for (int i = 0; i < 3; ++i) out.v[i] = add ? fmaf(a, x.v[i], out.v[i]) : a * x.v[i];
+  for (int i = 0; i < 3; ++i) out.w[i] = add ? fmaf(a, x.w[i], out.w[i]) : a * x.w[i];
+  for (int i = 0; i < MT; ++i) out.n[i] = add ? fmaf(a, x.n[i], out.n[i]) : a * x.n[i];
 }
 
 template <int MT>
@@ -220,20 +237,17 @@ __device__ __forceinline__ void st_zero(St<MT> &x) {
   for (int i = 0; i < MT; ++i) x.n[i] = 0.f;
 }
 
-// lam: in, the adjoint of the sub-step's output s+; out, the adjoint of its input s.
-//   z  = s + h/6 W k1 + h/3 W k2 + h/3 W k3 + h/6 W k4,  s+ = N(z)
-//   y2 = s + h/2 W k1,  y3 = s + h/2 W k2,  y4 = s + h W k3,  k_i = rhs(y_i), y1 = s
-// reverse:  lk4 = h/6 W lz,            ly4 = J(y4)^T lk4
-//           lk3 = h/3 W lz + h W ly4,   ly3 = J(y3)^T lk3
-//           lk2 = h/3 W lz + h/2 W ly3, ly2 = J(y2)^T lk2
-//           lk1 = h/6 W lz + h/2 W ly2
-//           ls  = lz + ly4 + ly3 + ly2 + J(s)^T lk1
+// The RK4 stage states of one sub-step from its start state s (y1 = s):
+//   y2 = s + h/2 W k1,  y3 = s + h/2 W k2,  y4 = s + h W k3,  k_i = rhs(y_i),
+//   z  = s + h/6 W k1 + h/3 W k2 + h/3 W k3 + h/6 W k4  (before renormalisation).
 template <int MT>
-__device__ void step_vjp(const St<MT> &s, const float (&cs)[MT], const ParDiag &P,
-                         const float4 *gdir, const float4 *garm, int nt, bool current_accel,
-                         float h, St<MT> &lam, Grad &G, float (&gcs)[MT]) {
+__device__ __forceinline__ void stage_states(const St<MT> &s, const float (&cs)[MT],
+                                             const ParDiag &P, const float4 *gdir,
+                                             const float4 *garm, int nt, bool current_accel,
+                                             float h, St<MT> &y2, St<MT> &y3, St<MT> &y4,
+                                             St<MT> &z) {
   const float hh = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f);
-  St<MT> k, y2, y3, y4, z;
+  St<MT> k;
   rhs<MT, true, true>(s, cs, P, gdir, garm, nt, current_accel, k);
   axpy(z, s, h6, k);
   axpy(y2, s, hh, k);
@@ -245,16 +259,32 @@ __device__ void step_vjp(const St<MT> &s, const float (&cs)[MT], const ParDiag &
   axpy(y4, s, h, k);
   rhs<MT, true, true>(y4, cs, P, gdir, garm, nt, current_accel, k);
   axpy(z, z, h6, k);
+}
 
+// lam: in, the adjoint of the sub-step's output s+; out, the adjoint of its input s, given the
+// stage states (stage_states) and the pre-normalisation quaternion zq.
+//   s+ = N(z)
+// reverse:  lk4 = h/6 W lz,            ly4 = J(y4)^T lk4
+//           lk3 = h/3 W lz + h W ly4,   ly3 = J(y3)^T lk3
+//           lk2 = h/3 W lz + h/2 W ly3, ly2 = J(y2)^T lk2
+//           lk1 = h/6 W lz + h/2 W ly2
+//           ls  = lz + ly4 + ly3 + ly2 + J(s)^T lk1
+template <int MT>
+__device__ void step_vjp_stages(const St<MT> &s, const St<MT> &y2, const St<MT> &y3,
+                                const St<MT> &y4, const float (&zq)[4], const float (&cs)[MT],
+                                const ParDiag &P, const float4 *gdir, const float4 *garm, int nt,
+                                bool current_accel, float h, St<MT> &lam, Grad &G,
+                                float (&gcs)[MT]) {
+  const float hh = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f);
   // renormalisation q+ = z_q / |z_q|:  lz_q = (lam_q - q+ (q+ . lam_q)) / |z_q|
-  const float nq = sqrtf(z.q[0] * z.q[0] + z.q[1] * z.q[1] + z.q[2] * z.q[2] + z.q[3] * z.q[3]);
+  const float nq = sqrtf(fmaf(zq[0], zq[0], fmaf(zq[1], zq[1], fmaf(zq[2], zq[2], zq[3] * zq[3]))));
   float qn[4], dot = 0.f;
   for (int i = 0; i < 4; ++i) {
-    qn[i] = z.q[i] / nq;
-    dot += qn[i] * lam.q[i];
+    qn[i] = zq[i] / nq;
+    dot = fmaf(qn[i], lam.q[i], dot);
   }
   St<MT> lz = lam;
-  for (int i = 0; i < 4; ++i) lz.q[i] = (lam.q[i] - qn[i] * dot) / nq;
+  for (int i = 0; i < 4; ++i) lz.q[i] = fmaf(-qn[i], dot, lam.q[i]) / nq;
 
   St<MT> lk, ly;
   St<MT> &ls = lam;
@@ -264,25 +294,36 @@ __device__ void step_vjp(const St<MT> &s, const float (&cs)[MT], const ParDiag &
   st_zero(ly);
   rhs_vjp<MT>(y4, cs, P, gdir, garm, nt, current_accel, lk, ly, G, gcs);
   wscale(ls, ly, 1.f, true);
-  for (int i = 0; i < 4; ++i) ls.q[i] += 0.5f * ly.q[i];  // wscale halved the q part
+  for (int i = 0; i < 4; ++i) ls.q[i] = fmaf(0.5f, ly.q[i], ls.q[i]);  // wscale halved the q part
   // stage 3
   wscale(lk, lz, h3, false);
   wscale(lk, ly, h, true);
   st_zero(ly);
   rhs_vjp<MT>(y3, cs, P, gdir, garm, nt, current_accel, lk, ly, G, gcs);
   wscale(ls, ly, 1.f, true);
-  for (int i = 0; i < 4; ++i) ls.q[i] += 0.5f * ly.q[i];
+  for (int i = 0; i < 4; ++i) ls.q[i] = fmaf(0.5f, ly.q[i], ls.q[i]);
   // stage 2
   wscale(lk, lz, h3, false);
   wscale(lk, ly, hh, true);
   st_zero(ly);
   rhs_vjp<MT>(y2, cs, P, gdir, garm, nt, current_accel, lk, ly, G, gcs);
   wscale(ls, ly, 1.f, true);
-  for (int i = 0; i < 4; ++i) ls.q[i] += 0.5f * ly.q[i];
+  for (int i = 0; i < 4; ++i) ls.q[i] = fmaf(0.5f, ly.q[i], ls.q[i]);
   // stage 1
   wscale(lk, lz, h6, false);
   wscale(lk, ly, hh, true);
   rhs_vjp<MT>(s, cs, P, gdir, garm, nt, current_accel, lk, ls, G, gcs);
+}
+
+// The whole sub-step: stage states recomputed, then their transposes.
+template <int MT>
+__device__ void step_vjp(const St<MT> &s, const float (&cs)[MT], const ParDiag &P,
+                         const float4 *gdir, const float4 *garm, int nt, bool current_accel,
+                         float h, St<MT> &lam, Grad &G, float (&gcs)[MT]) {
+  St<MT> y2, y3, y4, z;
+  stage_states<MT>(s, cs, P, gdir, garm, nt, current_accel, h, y2, y3, y4, z);
+  const float zq[4] = {z.q[0], z.q[1], z.q[2], z.q[3]};
+  step_vjp_stages<MT>(s, y2, y3, y4, zq, cs, P, gdir, garm, nt, current_accel, h, lam, G, gcs);
 }
 
 constexpr int kMaxSeg = 32;  // largest checkpoint interval
@@ -296,7 +337,9 @@ __device__ __forceinline__ void commands_at(const FleetView &fv, int64_t e, int6
   for (int i = 0; i < MT; ++i) c[i] = 0.f;
   if (fv.n_seg > 0) {
     const float *a = reinterpret_cast<const float *>(fv.act) + (seg * fv.n + e) * MG_MAX_THR;
-    for (int i = 0; i < nt; ++i) c[i] = a[i] * itau;
+    #pragma unroll
+    for (int i = 0; i < MT; ++i)
+      if (i < nt) c[i] = a[i] * itau;
   }
 }
 
@@ -309,82 +352,52 @@ __global__ void k_checkpoint(const StatePlanes st, int64_t n, float *__restrict_
   for (int j = 0; j < MG_NSTATE; ++j) ck[(int64_t)j * n + e] = r[j];
 }
 
-// One thread per env.  ckpt [n_ck][MG_NSTATE][n] (state at sub-steps 0, C, 2C, ...),
-// dtraj [T][MG_NTRAJ][n] (loss adjoint of the state after each sub-step).  Outputs: dcoef
-// [n][18] (M_A, Dl, Dq diagonals), dact [n_seg][n][8] accumulated, dstate0 [n][21] or null.
 template <int MT>
-__global__ void __launch_bounds__(kAdjThreads)
-    k_adjoint(const FleetView fv, const int32_t *__restrict__ types, const float *__restrict__ ckpt,
-              const float *__restrict__ dtraj, int32_t T, int32_t C, int64_t step0,
-              float *__restrict__ dcoef, float *__restrict__ dact, float *__restrict__ dstate0) {
-  __shared__ float4 sgeo[MG_MAX_TYPES][2 * MG_MAX_THR];
-  for (int i = threadIdx.x; i < fv.n_types * 2 * MG_MAX_THR; i += blockDim.x) {
-    const int t = i / (2 * MG_MAX_THR), j = i % (2 * MG_MAX_THR);
-    sgeo[t][j] = j < MG_MAX_THR ? fv.geo[t].dir[j] : fv.geo[t].arm[j - MG_MAX_THR];
-  }
-  __syncthreads();
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= fv.n) return;
-  const int type = types[e];
-  const float4 *gdir = sgeo[type], *garm = sgeo[type] + MG_MAX_THR;
-  const int nt = fv.geo[type].n_thr;
-  const bool ca = !(fv.model_flags & MG_MODEL_NO_CURRENT_ACCEL);
-  const float h = fv.dt;
-  const int64_t n = fv.n;
-  ParDiag P;
-  load_par<true>(fv.pa, e, P);
-  const LagEnv L = lag_env(P.itau, h);  // the forward's throttle-lag update (checkpoint replay)
+__device__ __forceinline__ void load_checkpoint(const float *__restrict__ ckpt, int32_t sg,
+                                                int64_t n, int64_t e, St<MT> &S) {
+  const float *ck = ckpt + (int64_t)sg * MG_NSTATE * n + e;
+  for (int i = 0; i < 3; ++i) S.p[i] = ck[(int64_t)(i)*n];
+  for (int i = 0; i < 4; ++i) S.q[i] = ck[(int64_t)(3 + i) * n];
+  for (int i = 0; i < 3; ++i) S.v[i] = ck[(int64_t)(7 + i) * n];
+  for (int i = 0; i < 3; ++i) S.w[i] = ck[(int64_t)(10 + i) * n];
+  for (int i = 0; i < MT; ++i) S.n[i] = ck[(int64_t)(13 + i) * n];
+}
 
-  Grad G;
-  for (int i = 0; i < 3; ++i) G.ma[i] = G.J[i] = 0.f;
-  for (int i = 0; i < 6; ++i) G.mi[i] = G.dl[i] = G.dq[i] = 0.f;
-  St<MT> lam;
-  st_zero(lam);
-  St<MT> S[kMaxSeg];
-  float c[MT], gcs[MT];
+// lam += the loss adjoint of the state after sub-step t.
+template <int MT>
+__device__ __forceinline__ void add_traj_adjoint(const float *__restrict__ dtraj, int64_t t,
+                                                 int64_t n, int64_t e, St<MT> &lam) {
+  const float *g = dtraj + t * MG_NTRAJ * n + e;
+  for (int i = 0; i < 3; ++i) lam.p[i] += g[(int64_t)i * n];
+  for (int i = 0; i < 4; ++i) lam.q[i] += g[(int64_t)(3 + i) * n];
+  for (int i = 0; i < 3; ++i) lam.v[i] += g[(int64_t)(7 + i) * n];
+  for (int i = 0; i < 3; ++i) lam.w[i] += g[(int64_t)(10 + i) * n];
+}
 
-  const int32_t n_ck = (T + C - 1) / C;
-  for (int32_t sg = n_ck - 1; sg >= 0; --sg) {
-    const int32_t t0 = sg * C, len = min(C, T - t0);
-    // re-run the segment from its checkpoint
-    const float *ck = ckpt + (int64_t)sg * MG_NSTATE * n + e;
-    for (int i = 0; i < 3; ++i) S[0].p[i] = ck[(int64_t)(i)*n];
-    for (int i = 0; i < 4; ++i) S[0].q[i] = ck[(int64_t)(3 + i) * n];
-    for (int i = 0; i < 3; ++i) S[0].v[i] = ck[(int64_t)(7 + i) * n];
-    for (int i = 0; i < 3; ++i) S[0].w[i] = ck[(int64_t)(10 + i) * n];
-    for (int i = 0; i < MT; ++i) S[0].n[i] = ck[(int64_t)(13 + i) * n];
-    for (int32_t j = 1; j < len; ++j) {
-      S[j] = S[j - 1];
-      commands_at<MT>(fv, e, step0 + t0 + j - 1, nt, P.itau, c);
-      float b[MT];
-      lag_segment<MT>(c, L, b);
-      rk4_step_lag<MT, true, true>(S[j], b, L, P, gdir, garm, nt, ca, h);
-    }
-    // walk it backwards
-    for (int32_t j = len - 1; j >= 0; --j) {
-      const int64_t t = t0 + j;
-      const float *g = dtraj + t * MG_NTRAJ * n + e;
-      for (int i = 0; i < 3; ++i) lam.p[i] += g[(int64_t)i * n];
-      for (int i = 0; i < 4; ++i) lam.q[i] += g[(int64_t)(3 + i) * n];
-      for (int i = 0; i < 3; ++i) lam.v[i] += g[(int64_t)(7 + i) * n];
-      for (int i = 0; i < 3; ++i) lam.w[i] += g[(int64_t)(10 + i) * n];
-      commands_at<MT>(fv, e, step0 + t, nt, P.itau, c);
-      for (int i = 0; i < MT; ++i) gcs[i] = 0.f;
-      step_vjp<MT>(S[j], c, P, gdir, garm, nt, ca, h, lam, G, gcs);
-      if (dact && fv.n_seg > 0) {
-        int64_t seg = (step0 + t) / fv.hold;
-        if (seg > fv.n_seg - 1) seg = fv.n_seg - 1;
-        float *da = dact + (seg * n + e) * MG_MAX_THR;
-        for (int i = 0; i < nt; ++i) da[i] += P.itau * gcs[i];
-      }
-    }
-  }
-  // coefficients: M_A enters through Q1 (translational), J = diag(I_o) + M_A,rot and
-  // M^-1 = diag(1 / (m + M_A,lin), 1 / (I + M_A,rot)): d mi / d M_A = -mi^2.
+// Command adjoint of sub-step t into its action segment.
+template <int MT>
+__device__ __forceinline__ void add_action_adjoint(const FleetView &fv, int64_t t, int64_t e,
+                                                   int nt, float itau, const float (&gcs)[MT],
+                                                   float *__restrict__ dact) {
+  if (!dact || fv.n_seg <= 0) return;
+  int64_t seg = t / fv.hold;
+  if (seg > fv.n_seg - 1) seg = fv.n_seg - 1;
+  float *da = dact + (seg * fv.n + e) * MG_MAX_THR;
+  #pragma unroll
+  for (int i = 0; i < MT; ++i)
+    if (i < nt) da[i] = fmaf(itau, gcs[i], da[i]);
+}
+
+// Coefficients: M_A enters through Q1 (translational), J = diag(I_o) + M_A,rot and
+// M^-1 = diag(1 / (m + M_A,lin), 1 / (I + M_A,rot)): d mi / d M_A = -mi^2.
+template <int MT>
+__device__ __forceinline__ void write_gradients(const ParDiag &P, const Grad &G, const St<MT> &lam,
+                                                int64_t e, float *__restrict__ dcoef,
+                                                float *__restrict__ dstate0) {
   float *dc = dcoef + e * 18;
   for (int j = 0; j < 3; ++j) {
-    dc[j] = G.ma[j] - P.mi[j] * P.mi[j] * G.mi[j];
-    dc[3 + j] = G.J[j] - P.mi[3 + j] * P.mi[3 + j] * G.mi[3 + j];
+    dc[j] = fmaf(-P.mi[j] * P.mi[j], G.mi[j], G.ma[j]);
+    dc[3 + j] = fmaf(-P.mi[3 + j] * P.mi[3 + j], G.mi[3 + j], G.J[j]);
   }
   for (int j = 0; j < 6; ++j) {
     dc[6 + j] = G.dl[j];
@@ -400,6 +413,265 @@ __global__ void __launch_bounds__(kAdjThreads)
   }
 }
 
+__device__ __forceinline__ void zero_grad(Grad &G) {
+  for (int i = 0; i < 3; ++i) G.ma[i] = G.J[i] = 0.f;
+  for (int i = 0; i < 6; ++i) G.mi[i] = G.dl[i] = G.dq[i] = 0.f;
+}
+
+__device__ __forceinline__ void stage_geometry(const FleetView &fv,
+                                               float4 (*sgeo)[2 * MG_MAX_THR]) {
+  for (int i = threadIdx.x; i < fv.n_types * 2 * MG_MAX_THR; i += blockDim.x) {
+    const int t = i / (2 * MG_MAX_THR), j = i % (2 * MG_MAX_THR);
+    sgeo[t][j] = j < MG_MAX_THR ? fv.geo[t].dir[j] : fv.geo[t].arm[j - MG_MAX_THR];
+  }
+}
+
+// One thread per env.  ckpt [n_ck][MG_NSTATE][n] (state at sub-steps 0, C, 2C, ...),
+// dtraj [T][MG_NTRAJ][n] (loss adjoint of the state after each sub-step).  Outputs: dcoef
+// [n][18] (M_A, Dl, Dq diagonals), dact [n_seg][n][8] accumulated, dstate0 [n][21] or null.
+template <int MT>
+__global__ void __launch_bounds__(kAdjThreads)
+    k_adjoint(const FleetView fv, const int32_t *__restrict__ types, const float *__restrict__ ckpt,
+              const float *__restrict__ dtraj, int32_t T, int32_t C, int64_t step0,
+              float *__restrict__ dcoef, float *__restrict__ dact, float *__restrict__ dstate0) {
+  __shared__ float4 sgeo[MG_MAX_TYPES][2 * MG_MAX_THR];
+  stage_geometry(fv, sgeo);
+  __syncthreads();
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= fv.n) return;
+  const int type = types[e];
+  const float4 *gdir = sgeo[type], *garm = sgeo[type] + MG_MAX_THR;
+  const int nt = fv.geo[type].n_thr;
+  const bool ca = !(fv.model_flags & MG_MODEL_NO_CURRENT_ACCEL);
+  const float h = fv.dt;
+  const int64_t n = fv.n;
+  ParDiag P;
+  load_par<true>(fv.pa, e, P);
+  const LagEnv L = lag_env(P.itau, h);  // the forward's throttle-lag update (checkpoint replay)
+
+  Grad G;
+  zero_grad(G);
+  St<MT> lam;
+  st_zero(lam);
+  St<MT> S[kMaxSeg];
+  float c[MT], gcs[MT];
+
+  const int32_t n_ck = (T + C - 1) / C;
+  for (int32_t sg = n_ck - 1; sg >= 0; --sg) {
+    const int32_t t0 = sg * C, len = min(C, T - t0);
+    // re-run the segment from its checkpoint
+    load_checkpoint<MT>(ckpt, sg, n, e, S[0]);
+    for (int32_t j = 1; j < len; ++j) {
+      S[j] = S[j - 1];
+      commands_at<MT>(fv, e, step0 + t0 + j - 1, nt, P.itau, c);
+      float b[MT];
+      lag_segment<MT>(c, L, b);
+      rk4_step_lag<MT, true, true>(S[j], b, L, P, gdir, garm, nt, ca, h);
+    }
+    // walk it backwards
+    for (int32_t j = len - 1; j >= 0; --j) {
+      const int64_t t = t0 + j;
+      add_traj_adjoint<MT>(dtraj, t, n, e, lam);
+      commands_at<MT>(fv, e, step0 + t, nt, P.itau, c);
+      for (int i = 0; i < MT; ++i) gcs[i] = 0.f;
+      step_vjp<MT>(S[j], c, P, gdir, garm, nt, ca, h, lam, G, gcs);
+      add_action_adjoint<MT>(fv, step0 + t, e, nt, P.itau, gcs, dact);
+    }
+  }
+  write_gradients<MT>(P, G, lam, e, dcoef, dstate0);
+}
+
+// ---------------------------------------------------------------- two-warp form
+// For fleets with fewer 32-env warps than the GPU has schedulers, where the one-warp kernel
+// above leaves most of them idle and runs on instruction latency: blocks of two warps over the
+// same 32 envs.  Warp 0 re-runs each checkpoint segment and writes, for every sub-step, the
+// stage states the transposes need (q, nu and n of y1..y4, and the quaternion before
+// renormalisation) to a workspace; warp 1 applies step_vjp_stages from those records, one
+// segment behind.  The workspace holds two segments, used alternately; a block barrier at each
+// segment boundary hands one over.  The per-env arithmetic is k_adjoint's: stage_states and
+// step_vjp_stages are the two halves of step_vjp.
+constexpr int kWsThreads = 64;
+
+template <int MT>
+__host__ __device__ constexpr int rec_words() { return 4 * (10 + MT) + 4; }
+
+template <int MT>
+__device__ __forceinline__ void put_stage(float *__restrict__ r, int64_t n, int f,
+                                          const St<MT> &y) {
+  for (int i = 0; i < 4; ++i) r[(int64_t)(f + i) * n] = y.q[i];
+  for (int i = 0; i < 3; ++i) r[(int64_t)(f + 4 + i) * n] = y.v[i];
+  for (int i = 0; i < 3; ++i) r[(int64_t)(f + 7 + i) * n] = y.w[i];
+  for (int i = 0; i < MT; ++i) r[(int64_t)(f + 10 + i) * n] = y.n[i];
+}
+
+// Warp 0: segment sg re-run from its checkpoint; record j of `rec` gets sub-step t0 + j.
+template <int MT>
+__device__ __forceinline__ void produce_segment(const FleetView &fv, int64_t e, const ParDiag &P,
+                                                const LagEnv &L, const float4 *gdir,
+                                                const float4 *garm, int nt, bool ca, float h,
+                                                const float *__restrict__ ckpt, int32_t sg,
+                                                int32_t C, int32_t T, int64_t step0,
+                                                float *__restrict__ rec) {
+  constexpr int W = rec_words<MT>(), Y = 10 + MT;
+  const int64_t n = fv.n;
+  const int32_t t0 = sg * C, len = min(C, T - t0);
+  St<MT> S;
+  load_checkpoint<MT>(ckpt, sg, n, e, S);
+  float c[MT];
+  for (int32_t j = 0; j < len; ++j) {
+    commands_at<MT>(fv, e, step0 + t0 + j, nt, P.itau, c);
+    St<MT> y2, y3, y4, z;
+    stage_states<MT>(S, c, P, gdir, garm, nt, ca, h, y2, y3, y4, z);
+    float *r = rec + (int64_t)j * W * n;
+    put_stage<MT>(r, n, 0, S);
+    put_stage<MT>(r, n, Y, y2);
+    put_stage<MT>(r, n, 2 * Y, y3);
+    put_stage<MT>(r, n, 3 * Y, y4);
+    for (int i = 0; i < 4; ++i) r[(int64_t)(4 * Y + i) * n] = z.q[i];
+    if (j + 1 < len) {  // the next start state, as the forward computed it
+      float b[MT];
+      lag_segment<MT>(c, L, b);
+      rk4_step_lag<MT, true, true>(S, b, L, P, gdir, garm, nt, ca, h);
+    }
+  }
+}
+
+// Per-lane asynchronous 4-byte copies global -> shared (sm_80+ cp.async), so that the consumer
+// warp's next record is in flight while it works on the current one.
+__device__ __forceinline__ void cp_async4(float *smem, const float *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all_but_one() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+
+// What the consumer reads per sub-step: the stage record, the loss adjoint of the sub-step's
+// output and the sub-step's buffered command.
+template <int MT>
+__host__ __device__ constexpr int fetch_words() { return rec_words<MT>() + MG_NTRAJ + MT; }
+
+// Queue the copies of sub-step t0 + j's inputs into buf [fetch_words][32] (this lane's column).
+template <int MT>
+__device__ __forceinline__ void fetch_substep(const FleetView &fv, int64_t e,
+                                              const float *__restrict__ rec,
+                                              const float *__restrict__ dtraj, int64_t t0,
+                                              int32_t j, int64_t step0, float *buf) {
+  constexpr int W = rec_words<MT>();
+  const int64_t n = fv.n;
+  const float *r = rec + (int64_t)j * W * n;
+  for (int f = 0; f < W; ++f) cp_async4(buf + f * 32, r + (int64_t)f * n);
+  const float *g = dtraj + (t0 + j) * MG_NTRAJ * n + e;
+  for (int f = 0; f < MG_NTRAJ; ++f) cp_async4(buf + (W + f) * 32, g + (int64_t)f * n);
+  if (fv.n_seg > 0) {
+    int64_t seg = (step0 + t0 + j) / fv.hold;
+    if (seg > fv.n_seg - 1) seg = fv.n_seg - 1;
+    const float *a = reinterpret_cast<const float *>(fv.act) + (seg * n + e) * MG_MAX_THR;
+    for (int i = 0; i < MT; ++i) cp_async4(buf + (W + MG_NTRAJ + i) * 32, a + i);
+  }
+  cp_async_commit();
+}
+
+template <int MT>
+__device__ __forceinline__ void read_stage(const float *buf, int f, St<MT> &y) {
+  for (int i = 0; i < 3; ++i) y.p[i] = 0.f;  // p does not enter the right-hand side
+  for (int i = 0; i < 4; ++i) y.q[i] = buf[(f + i) * 32];
+  for (int i = 0; i < 3; ++i) y.v[i] = buf[(f + 4 + i) * 32];
+  for (int i = 0; i < 3; ++i) y.w[i] = buf[(f + 7 + i) * 32];
+  for (int i = 0; i < MT; ++i) y.n[i] = buf[(f + 10 + i) * 32];
+}
+
+// Warp 1: segment sg walked backwards from its records, each sub-step's inputs copied into
+// shared memory (double buffer sbuf [2][fetch_words][32]) while the previous one is processed.
+template <int MT>
+__device__ __forceinline__ void consume_segment(const FleetView &fv, int64_t e, int lane,
+                                                const ParDiag &P, const float4 *gdir,
+                                                const float4 *garm, int nt, bool ca, float h,
+                                                const float *__restrict__ dtraj, int32_t sg,
+                                                int32_t C, int32_t T, int64_t step0,
+                                                const float *__restrict__ rec, float *sbuf,
+                                                float *__restrict__ dact, St<MT> &lam, Grad &G) {
+  constexpr int W = rec_words<MT>(), Y = 10 + MT, F = fetch_words<MT>();
+  const int32_t t0 = sg * C, len = min(C, T - t0);
+  float c[MT], gcs[MT];
+  fetch_substep<MT>(fv, e, rec, dtraj, t0, len - 1, step0, sbuf + ((len - 1) & 1) * F * 32 + lane);
+  for (int32_t j = len - 1; j >= 0; --j) {
+    if (j > 0)
+      fetch_substep<MT>(fv, e, rec, dtraj, t0, j - 1, step0, sbuf + ((j - 1) & 1) * F * 32 + lane);
+    else
+      cp_async_commit();  // an empty group keeps "all but the newest" meaning sub-step j
+    cp_async_wait_all_but_one();
+    const float *b = sbuf + (j & 1) * F * 32 + lane;
+    const int64_t t = t0 + j;
+    for (int i = 0; i < 3; ++i) lam.p[i] += b[(W + i) * 32];
+    for (int i = 0; i < 4; ++i) lam.q[i] += b[(W + 3 + i) * 32];
+    for (int i = 0; i < 3; ++i) lam.v[i] += b[(W + 7 + i) * 32];
+    for (int i = 0; i < 3; ++i) lam.w[i] += b[(W + 10 + i) * 32];
+    for (int i = 0; i < MT; ++i)
+      c[i] = (fv.n_seg > 0 && i < nt) ? b[(W + MG_NTRAJ + i) * 32] * P.itau : 0.f;
+    for (int i = 0; i < MT; ++i) gcs[i] = 0.f;
+    St<MT> s, y2, y3, y4;
+    read_stage<MT>(b, 0, s);
+    read_stage<MT>(b, Y, y2);
+    read_stage<MT>(b, 2 * Y, y3);
+    read_stage<MT>(b, 3 * Y, y4);
+    float zq[4];
+    for (int i = 0; i < 4; ++i) zq[i] = b[(4 * Y + i) * 32];
+    step_vjp_stages<MT>(s, y2, y3, y4, zq, c, P, gdir, garm, nt, ca, h, lam, G, gcs);
+    add_action_adjoint<MT>(fv, step0 + t, e, nt, P.itau, gcs, dact);
+  }
+}
+
+// ws: [2][C][rec_words<MT>()][n] floats.  Grid: one block per 32 envs.
+template <int MT>
+__global__ void __launch_bounds__(kWsThreads)
+    k_adjoint_ws(const FleetView fv, const int32_t *__restrict__ types,
+                 const float *__restrict__ ckpt, const float *__restrict__ dtraj, int32_t T,
+                 int32_t C, int64_t step0, float *__restrict__ dcoef, float *__restrict__ dact,
+                 float *__restrict__ dstate0, float *__restrict__ ws) {
+  __shared__ float4 sgeo[MG_MAX_TYPES][2 * MG_MAX_THR];
+  __shared__ float sbuf[2 * fetch_words<MT>() * 32];
+  stage_geometry(fv, sgeo);
+  __syncthreads();
+  const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+  const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+  const bool live = e < fv.n;  // lanes past the fleet only take part in the barriers
+  const int64_t el = live ? e : 0;
+  const int type = types[el];
+  const float4 *gdir = sgeo[type], *garm = sgeo[type] + MG_MAX_THR;
+  const int nt = fv.geo[type].n_thr;
+  const bool ca = !(fv.model_flags & MG_MODEL_NO_CURRENT_ACCEL);
+  const float h = fv.dt;
+  ParDiag P;
+  load_par<true>(fv.pa, el, P);
+  const int64_t slot = (int64_t)C * rec_words<MT>() * fv.n;
+
+  const int32_t n_ck = (T + C - 1) / C;
+  if (warp == 0 && live)
+    produce_segment<MT>(fv, e, P, lag_env(P.itau, h), gdir, garm, nt, ca, h, ckpt, n_ck - 1, C,
+                        T, step0, ws + ((n_ck - 1) & 1) * slot + e);
+  __syncthreads();
+  Grad G;
+  zero_grad(G);
+  St<MT> lam;
+  st_zero(lam);
+  for (int32_t sg = n_ck - 1; sg >= 0; --sg) {
+    if (warp == 0) {
+      if (live && sg > 0)
+        produce_segment<MT>(fv, e, P, lag_env(P.itau, h), gdir, garm, nt, ca, h, ckpt, sg - 1,
+                            C, T, step0, ws + ((sg - 1) & 1) * slot + e);
+    } else if (live) {
+      consume_segment<MT>(fv, e, lane, P, gdir, garm, nt, ca, h, dtraj, sg, C, T, step0,
+                          ws + (sg & 1) * slot + e, sbuf, dact, lam, G);
+    }
+    __syncthreads();
+  }
+  if (warp == 1 && live) write_gradients<MT>(P, G, lam, e, dcoef, dstate0);
+}
+
 }  // namespace
 
 cudaError_t launch_checkpoint(const StatePlanes &st, int64_t n, float *ck, cudaStream_t stream) {
@@ -407,17 +679,55 @@ cudaError_t launch_checkpoint(const StatePlanes &st, int64_t n, float *ck, cudaS
   return cudaGetLastError();
 }
 
+namespace {
+
+cudaError_t sm_count(int *n_sm) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(n_sm, cudaDevAttrMultiProcessorCount, dev);
+  return e;
+}
+
+}  // namespace
+
+cudaError_t adjoint_split(int64_t n, int mode, bool *split) {
+  if (mode == 1 || mode == 2) {
+    *split = mode == 2;
+    return cudaSuccess;
+  }
+  // by fleet size: the two-warp form while its 2 x ceil(n / 32) warps fit one per scheduler
+  int n_sm = 0;
+  cudaError_t e = sm_count(&n_sm);
+  if (e != cudaSuccess) return e;
+  *split = (n + 31) / 32 <= 2 * (int64_t)n_sm;
+  return cudaSuccess;
+}
+
+size_t adjoint_workspace_bytes(bool eight, int64_t n, int32_t C) {
+  return 2 * (size_t)C * (size_t)(eight ? rec_words<8>() : rec_words<6>()) * (size_t)n *
+         sizeof(float);
+}
+
 cudaError_t launch_adjoint(const FleetView &fv, const int32_t *types, bool eight,
                            const float *ckpt, const float *dtraj, int32_t T, int32_t C,
-                           int64_t step0, float *dcoef, float *dact, float *dstate0,
-                           cudaStream_t stream) {
-  if (C < 1 || C > kMaxSeg || T < 1) return cudaErrorInvalidValue;
+                           int64_t step0, float *dcoef, float *dact, float *dstate0, bool split,
+                           float *ws, cudaStream_t stream) {
+  if (C < 1 || C > kMaxSeg || T < 1 || (split && !ws)) return cudaErrorInvalidValue;
+  if (split) {
+    const int grid = (int)((fv.n + 31) / 32);
+    if (eight)
+      k_adjoint_ws<8><<<grid, kWsThreads, 0, stream>>>(fv, types, ckpt, dtraj, T, C, step0,
+                                                       dcoef, dact, dstate0, ws);
+    else
+      k_adjoint_ws<6><<<grid, kWsThreads, 0, stream>>>(fv, types, ckpt, dtraj, T, C, step0,
+                                                       dcoef, dact, dstate0, ws);
+    return cudaGetLastError();
+  }
   // One warp per block while the fleet has fewer warps than the GPU has SMs x 4 (the backward
   // pass is latency-bound, so its warps should be spread over all SMs, each with its own L1 for
   // the threads' recompute buffers), larger blocks beyond.
-  int n_sm = 0, dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  int n_sm = 0;
+  cudaError_t e = sm_count(&n_sm);
   if (e != cudaSuccess) return e;
   const int64_t warps = (fv.n + 31) / 32;
   const int threads = warps <= 4 * (int64_t)n_sm ? 32 : kAdjThreads;

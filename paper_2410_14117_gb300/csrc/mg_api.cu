@@ -114,6 +114,10 @@ struct mg_sim {
   // off-diagonal hydrodynamics, [MG_NXPARAM][n] planes (mg_set_hydro_offdiag), and whether set
   float *xh = nullptr;
   bool has_xh = false;
+  // backward kernel (mg_set_adjoint_mode) and the two-warp form's workspace
+  int32_t adj_mode = 0;
+  float *adj_ws = nullptr;
+  size_t adj_ws_cap = 0;
   // the arena's parameter range (derived planes, then the raw records): one contiguous span
   size_t par_off = 0, par_bytes = 0;
 
@@ -705,6 +709,7 @@ mg_status mg_destroy(mg_sim *s) {
   cudaFree(s->act);
   cudaFree(s->stage);
   cudaFree(s->xh);
+  cudaFree(s->adj_ws);
   cudaFree(s->arena);
   delete s;
   return MG_OK;
@@ -1170,8 +1175,33 @@ mg_status mg_rollout_backward(mg_sim *s, int32_t T, int32_t C, const float *ckpt
     if (!is_device_ptr(p)) return fail(MG_EINVAL, "adjoint buffers must be device memory");
   if ((dact && !is_device_ptr(dact)) || (dstate0 && !is_device_ptr(dstate0)))
     return fail(MG_EINVAL, "adjoint buffers must be device memory");
-  MG_CK(launch_adjoint(s->view(), s->types_d, s->ntv != NT_6, ckpt, dtraj, T, C, step0, dcoef,
-                       dact, dstate0, s->stream));
+  const bool eight = s->ntv != NT_6;
+  bool split = false;
+  MG_CK(adjoint_split(s->n, s->adj_mode, &split));
+  if (split) {
+    const size_t bytes = adjoint_workspace_bytes(eight, s->n, C);
+    if (s->adj_ws_cap < bytes) {
+      MG_CK(cudaStreamSynchronize(s->stream));
+      cudaFree(s->adj_ws);
+      s->adj_ws = nullptr;
+      s->adj_ws_cap = 0;
+      if (cudaMalloc(&s->adj_ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        s->adj_ws = nullptr;
+        return fail(MG_ENOMEM, "cudaMalloc(adjoint workspace)");
+      }
+      s->adj_ws_cap = bytes;
+    }
+  }
+  MG_CK(launch_adjoint(s->view(), s->types_d, eight, ckpt, dtraj, T, C, step0, dcoef, dact,
+                       dstate0, split, s->adj_ws, s->stream));
+  return MG_OK;
+}
+
+mg_status mg_set_adjoint_mode(mg_sim *s, int32_t mode) {
+  MG_NONNULL(s);
+  if (mode < 0 || mode > 2) return fail(MG_EINVAL, "adjoint mode must be 0, 1 or 2");
+  s->adj_mode = mode;
   return MG_OK;
 }
 

@@ -185,10 +185,14 @@ int64_t pool_capacity(const mg_pool *p);
 
 // ---------------------------------------------------------------- launchers (mg_adjoint.cu)
 cudaError_t launch_checkpoint(const StatePlanes &st, int64_t n, float *ck, cudaStream_t stream);
+// Backward kernel: mode 1 one warp per 32 envs, 2 the two-warp form (producer and consumer warps
+// per 32 envs, through a workspace of adjoint_workspace_bytes), 0 chosen by fleet size.
+cudaError_t adjoint_split(int64_t n, int mode, bool *split);
+size_t adjoint_workspace_bytes(bool eight, int64_t n, int32_t C);
 cudaError_t launch_adjoint(const FleetView &fv, const int32_t *types, bool eight,
                            const float *ckpt, const float *dtraj, int32_t T, int32_t C,
-                           int64_t step0, float *dcoef, float *dact, float *dstate0,
-                           cudaStream_t stream);
+                           int64_t step0, float *dcoef, float *dact, float *dstate0, bool split,
+                           float *ws, cudaStream_t stream);
 int adjoint_max_interval();
 
 // ---------------------------------------------------------------- launchers (mg_task.cu)

@@ -108,6 +108,11 @@ class Sim:
         """Two envs per thread with packed FP32x2 arithmetic (see mg_set_packed)."""
         call("mg_set_packed", self._h, 1 if packed else 0)
 
+    def set_adjoint_mode(self, mode: int = 0):
+        """Backward kernel of the adjoint: 0 by fleet size, 1 one warp per 32 envs, 2 a
+        producer and a consumer warp per 32 envs (see mg_set_adjoint_mode)."""
+        call("mg_set_adjoint_mode", self._h, int(mode))
+
     def kernel_info(self) -> dict:
         r, t, l = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         call("mg_kernel_info", self._h, ctypes.byref(r), ctypes.byref(t), ctypes.byref(l))

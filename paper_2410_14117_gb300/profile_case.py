@@ -10,7 +10,8 @@ after a few warm-up calls: with ``--static`` each is one launch of the static-gr
 observation / error / auto-reset epilogue, static grid); ``--split`` runs the split-integration
 comparison kernel, ``--full`` the general path with off-diagonal hydrodynamics; ``--adjoint`` runs
 ``launches`` forward and backward passes of the differentiable rollout (``k`` sub-steps,
-checkpoints every ``--chunk``, MSE loss on the trajectory).  Holds well under a GB of device
+checkpoints every ``--chunk``, MSE loss on the trajectory; ``--adjoint-mode`` picks the backward
+kernel).  Holds well under a GB of device
 memory at 65,536 envs.
 """
 from __future__ import annotations
@@ -51,6 +52,8 @@ def main():
                          "static grid)")
     ap.add_argument("--adjoint", action="store_true",
                     help="forward + backward passes of the differentiable rollout instead")
+    ap.add_argument("--adjoint-mode", type=int, default=0,
+                    help="backward kernel (mg_set_adjoint_mode): 0 by size, 1 one warp, 2 two warps")
     args = ap.parse_args()
     if args.adjoint:
         return adjoint_case(args)
@@ -102,6 +105,7 @@ def adjoint_case(args):
     vs = I.fleet_vehicles()
     sim = Sim(n, np.full(n, args.vehicle, dtype=np.int32), vs)
     sim.set_launch(args.epb, 1000, True)
+    sim.set_adjoint_mode(args.adjoint_mode)
     sim.randomize(1234, 0.8, 1.2, 0.2, 0.3)
     coeffs = sim.get_params()[:, COEF_SLICE].clone().requires_grad_(True)
     acts = torch.tensor(I.commands(5678, math.ceil(T / 10), n, vs[args.vehicle].n_thr),

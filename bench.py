@@ -465,7 +465,7 @@ def run_ours(args):
     # ---- the plain per-step form on the same GPU (one launch per sub-step)
     if not args.no_per_step:
         sim.set_actions_borrowed(acts_dev, hold)
-        sim.set_schedule(False)
+        sim.set_schedule(False, False)  # static grid, 128-register kernel (16 warps/SM)
         sim.set_packed(False)
         sim.set_launch(args.epb, 1, False)
         sim.randomize(7, 0.8, 1.2, 0.2, 0.3)

@@ -154,9 +154,12 @@ mg_status mg_set_launch(mg_sim *sim, int32_t envs_per_block, int32_t steps_per_l
  * warps claim (32-env slice, steps_per_launch-chunk) units from a queue in chunk-major order,
  * each unit waiting (bounded, see MG_ETIMEOUT in mg_sync) for its slice's previous chunk; faster
  * warps take more units, which balances the SMs when the fleet has more 32-env slices than
- * resident warps.  wide != 0 gives that kernel up to 200 registers per thread instead of
- * 128 (diagonal-mass fleets; the general kernel always has 168); warps_per_sm > 0 caps its
- * resident warps per SM (0 = as many as fit).  work_queue = 0 (default) launches a static grid of
+ * resident warps.  wide != 0 (default) gives that kernel, and the static grid's kernel
+ * outside mg_step_record, up to 200 registers per thread instead of 128 (diagonal-mass fleets;
+ * the general kernels always have 168): the queue at 8 warps/SM runs best with it, and a static
+ * grid of few envs (a warp per scheduler or fewer) gains 6-7 %, while a large static grid
+ * keeps more warps resident at 128; warps_per_sm > 0 caps the queue kernel's resident warps
+ * per SM (0 = as many as fit).  work_queue = 0 (default) launches a static grid of
  * envs_per_block-env blocks per steps_per_launch sub-steps (steps_per_launch = 1: the plain
  * per-step form).  All choices give bit-identical results.  mg_step_record always uses the
  * static grid.  MG_EINVAL unless 0 <= warps_per_sm <= 64. */

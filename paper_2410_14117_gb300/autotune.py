@@ -24,7 +24,7 @@ class LaunchConfig:
     schedule: str          # "static" or "queue"
     envs_per_block: int    # static grid block size
     steps_per_launch: int  # static: sub-steps per launch; queue: sub-steps per unit (chunk)
-    wide: bool = True      # queue: 200-register kernel (diagonal mass)
+    wide: bool = True      # 200-register diagonal-mass kernel (queue; static grid)
     warps_per_sm: int = 0  # queue: resident-warp cap (0 = as many as fit)
     packed: bool = False   # static: two envs per thread, packed FP32x2 arithmetic (diag. mass)
 
@@ -35,7 +35,9 @@ class LaunchConfig:
 
 
 DEFAULT_CANDIDATES = (
-    [LaunchConfig("static", epb, spl) for epb in (32, 64, 128, 256) for spl in (50, 1000)]
+    [LaunchConfig("static", epb, spl, False) for epb in (32, 64, 128, 256) for spl in (50, 1000)]
+    # the 200-register static kernel: for small fleets (a warp per scheduler or fewer)
+    + [LaunchConfig("static", epb, spl, True) for epb in (32, 64) for spl in (50, 1000)]
     + [LaunchConfig("queue", 128, ch, wide, wps)
        for wide, wps in ((False, 16), (False, 12), (True, 12), (True, 8))
        for ch in (25, 50, 100)]

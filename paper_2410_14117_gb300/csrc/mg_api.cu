@@ -147,7 +147,7 @@ struct mg_sim {
   uint32_t *sched = nullptr;
   int n_sm = 1;
   bool queue = false;
-  bool queue_wide = true;
+  bool wide = true;
   int32_t queue_warps_per_sm = 0;
 
   // actions (act_src: what the kernels read — the sim's copy, or a caller's borrowed buffer)
@@ -359,7 +359,7 @@ mg_status launch_chunks(mg_sim *s, int32_t k, float *traj, cudaStream_t stream) 
   if (s->queue && !traj && !s->has_xh) {
     v.cursor_adv = k;
     MG_CK(launch_fleet_queue(v, s->slices_d, s->n_slices, s->ntv, s->diag, s->structured,
-                             s->queue_wide, s->queue_warps_per_sm, k, s->spl, s->sched, s->n_sm,
+                             s->wide, s->queue_warps_per_sm, k, s->spl, s->sched, s->n_sm,
                              stream));
     return MG_OK;
   }
@@ -369,7 +369,7 @@ mg_status launch_chunks(mg_sim *s, int32_t k, float *traj, cudaStream_t stream) 
     v.cursor_off = done;
     v.cursor_adv = (done + kk == k) ? k : 0;
     MG_CK(launch_fleet(v, s->blocks_d, s->n_blocks, s->threads, s->ntv, s->diag, s->structured,
-                       kk, t, stream));
+                       s->wide, kk, t, stream));
     done += kk;
   }
   return MG_OK;
@@ -500,7 +500,7 @@ mg_status mg_step_noalloc(mg_sim *s, int32_t k) {
   FleetView v = s->view();
   v.cursor_adv = k;
   MG_CK(launch_fleet_queue(v, s->slices_d, s->n_slices, s->ntv, s->diag, s->structured,
-                           s->queue_wide, s->queue_warps_per_sm, k, s->spl, sched, s->n_sm,
+                           s->wide, s->queue_warps_per_sm, k, s->spl, sched, s->n_sm,
                            s->stream));
   s->cursor += k;
   return MG_OK;
@@ -765,7 +765,7 @@ mg_status mg_set_schedule(mg_sim *s, int32_t work_queue, int32_t wide, int32_t w
   MG_NONNULL(s);
   if (warps_per_sm < 0 || warps_per_sm > 64) return fail(MG_EINVAL, "warps_per_sm in [0, 64]");
   s->queue = work_queue != 0;
-  s->queue_wide = wide != 0;
+  s->wide = wide != 0;
   s->queue_warps_per_sm = warps_per_sm;
   s->drop_graphs();
   return MG_OK;
@@ -1152,7 +1152,7 @@ mg_status mg_rollout_forward(mg_sim *s, int32_t T, int32_t C, float *traj, float
     v.cursor_off = t0;
     v.cursor_adv = (t0 + len == T) ? T : 0;
     MG_CK(launch_fleet(v, s->blocks_d, s->n_blocks, s->threads, s->ntv, s->diag, s->structured,
-                       len, traj + (int64_t)t0 * MG_NTRAJ * s->n, s->stream));
+                       false, len, traj + (int64_t)t0 * MG_NTRAJ * s->n, s->stream));
   }
   s->cursor += T;
   if (step0_out) *step0_out = step0;
@@ -1405,9 +1405,9 @@ mg_status mg_kernel_info(mg_sim *s, int32_t *regs, int32_t *max_threads, int32_t
   if (s->packed && !s->queue && s->diag && !s->has_xh)
     MG_CK(pair_kernel_attributes(s->ntv, s->structured, &a));
   else if (s->queue)
-    MG_CK(queue_kernel_attributes(s->ntv, s->diag, s->queue_wide, s->structured, &a, &per_sm));
+    MG_CK(queue_kernel_attributes(s->ntv, s->diag, s->wide, s->structured, &a, &per_sm));
   else
-    MG_CK(fleet_kernel_attributes(s->ntv, s->diag, s->structured, false, &a));
+    MG_CK(fleet_kernel_attributes(s->ntv, s->diag, s->structured, false, s->wide, &a));
   if (regs) *regs = a.numRegs;
   if (max_threads) *max_threads = a.maxThreadsPerBlock;
   if (local_bytes) *local_bytes = (int32_t)a.localSizeBytes;

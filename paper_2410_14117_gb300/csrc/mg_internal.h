@@ -110,11 +110,12 @@ enum NtVariant { NT_6 = 0, NT_8 = 1, NT_MIXED = 2 };
 // Static schedule: one block per BlockDesc, k sub-steps per launch.
 // structured: every vehicle type present has the vectored layout (thrusters 0..3 with d_z = 0,
 // the rest with d_x = d_y = 0), so the allocation skips its exact zeros (diagonal mass only).
+// wide: the diagonal-mass kernel without recording gets 200 registers instead of 128.
 cudaError_t launch_fleet(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
-                         NtVariant ntv, bool diag, bool structured, int32_t k, float *traj,
-                         cudaStream_t stream);
+                         NtVariant ntv, bool diag, bool structured, bool wide, int32_t k,
+                         float *traj, cudaStream_t stream);
 cudaError_t fleet_kernel_attributes(NtVariant ntv, bool diag, bool structured, bool record,
-                                    cudaFuncAttributes *attr);
+                                    bool wide, cudaFuncAttributes *attr);
 
 // Work-queue schedule: warps claim (32-env slice, chunk of sub-steps) units in chunk-major
 // order.  sched: device words, zeroed by the launcher: [0] next unit, [1..3] unused,

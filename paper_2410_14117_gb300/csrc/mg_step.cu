@@ -41,9 +41,9 @@ __device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
 }
 
 // XH: off-diagonal hydrodynamics (general path), the block's coefficients staged in dynamic
-// shared memory [blockDim.x][MG_NXPARAM].
-template <int NTV, bool DIAG, bool REC, int NH, bool XH = false>
-__global__ void __maxnreg__(XH ? kRegsXH : DIAG ? kRegsDiag : kRegsGeneral)
+// shared memory [blockDim.x][MG_NXPARAM].  WIDE (diagonal mass, no recording): 200 registers.
+template <int NTV, bool DIAG, bool REC, int NH, bool XH = false, bool WIDE = false>
+__global__ void __maxnreg__(XH ? kRegsXH : !DIAG ? kRegsGeneral : WIDE ? kRegsWide : kRegsDiag)
     k_fleet(const FleetView fv, const BlockDesc *__restrict__ blocks, const int32_t k,
             float *__restrict__ traj) {
   constexpr int MT = (NTV == NT_6) ? 6 : 8;
@@ -81,7 +81,7 @@ __global__ void __maxnreg__(XH ? kRegsXH : DIAG ? kRegsDiag : kRegsGeneral)
 }
 
 template <int NTV, bool DIAG, bool WIDE, int NH>
-__global__ void __maxnreg__(!DIAG ? kRegsGeneral : WIDE ? kRegsQueueWide : kRegsDiag)
+__global__ void __maxnreg__(!DIAG ? kRegsGeneral : WIDE ? kRegsWide : kRegsDiag)
     k_fleet_queue(const FleetView fv, const BlockDesc *__restrict__ slices, const int32_t n_slices,
                   const int32_t k_total, const int32_t chunk, uint32_t *__restrict__ sched) {
   constexpr int MT = (NTV == NT_6) ? 6 : 8;
@@ -157,41 +157,50 @@ cudaError_t launch_pdl(Kernel kernel, int n_blocks, int threads, size_t smem, cu
 }
 
 // Structured allocation (NH = 4) is only instantiated for the diagonal-mass step, the
-// off-diagonal hydrodynamics (XH) only for the general one.
-template <int NTV, bool DIAG, bool REC>
+// off-diagonal hydrodynamics (XH) only for the general one, the wide register budget only for
+// the diagonal-mass step without recording.
+template <int NTV, bool DIAG, bool REC, bool WIDE>
 cudaError_t launch_t(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
                      bool structured, int32_t k, float *traj, cudaStream_t stream) {
   if constexpr (!DIAG) if (fv.xh)
     return launch_pdl(k_fleet<NTV, false, REC, 0, true>, n_blocks, threads,
                       sizeof(float) * MG_NXPARAM * threads, stream, fv, blocks, k, traj);
   if (DIAG && structured)
-    return launch_pdl(k_fleet<NTV, DIAG, REC, (DIAG ? 4 : 0)>, n_blocks, threads, 0, stream, fv,
-                      blocks, k, traj);
-  return launch_pdl(k_fleet<NTV, DIAG, REC, 0>, n_blocks, threads, 0, stream, fv, blocks, k,
-                    traj);
+    return launch_pdl(k_fleet<NTV, DIAG, REC, (DIAG ? 4 : 0), false, WIDE>, n_blocks, threads,
+                      0, stream, fv, blocks, k, traj);
+  return launch_pdl(k_fleet<NTV, DIAG, REC, 0, false, WIDE>, n_blocks, threads, 0, stream, fv,
+                    blocks, k, traj);
 }
 
 template <int NTV, bool DIAG>
 cudaError_t launch_r(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
-                     bool structured, int32_t k, float *traj, cudaStream_t stream) {
-  return traj ? launch_t<NTV, DIAG, true>(fv, blocks, n_blocks, threads, structured, k, traj,
-                                          stream)
-              : launch_t<NTV, DIAG, false>(fv, blocks, n_blocks, threads, structured, k, traj,
+                     bool structured, bool wide, int32_t k, float *traj, cudaStream_t stream) {
+  if (traj)
+    return launch_t<NTV, DIAG, true, false>(fv, blocks, n_blocks, threads, structured, k, traj,
+                                            stream);
+  if constexpr (DIAG)
+    if (wide)
+      return launch_t<NTV, true, false, true>(fv, blocks, n_blocks, threads, structured, k,
+                                              traj, stream);
+  return launch_t<NTV, DIAG, false, false>(fv, blocks, n_blocks, threads, structured, k, traj,
                                            stream);
 }
 
 template <int NTV>
 cudaError_t launch_d(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
-                     bool diag, bool structured, int32_t k, float *traj, cudaStream_t stream) {
-  return diag ? launch_r<NTV, true>(fv, blocks, n_blocks, threads, structured, k, traj, stream)
-              : launch_r<NTV, false>(fv, blocks, n_blocks, threads, structured, k, traj, stream);
+                     bool diag, bool structured, bool wide, int32_t k, float *traj,
+                     cudaStream_t stream) {
+  return diag ? launch_r<NTV, true>(fv, blocks, n_blocks, threads, structured, wide, k, traj,
+                                    stream)
+              : launch_r<NTV, false>(fv, blocks, n_blocks, threads, structured, wide, k, traj,
+                                     stream);
 }
 
-template <int NTV, bool DIAG, bool REC>
+template <int NTV, bool DIAG, bool REC, bool WIDE = false>
 const void *kernel_ptr(bool structured) {
   if (DIAG && structured)
-    return reinterpret_cast<const void *>(&k_fleet<NTV, DIAG, REC, (DIAG ? 4 : 0)>);
-  return reinterpret_cast<const void *>(&k_fleet<NTV, DIAG, REC, 0>);
+    return reinterpret_cast<const void *>(&k_fleet<NTV, DIAG, REC, (DIAG ? 4 : 0), false, WIDE>);
+  return reinterpret_cast<const void *>(&k_fleet<NTV, DIAG, REC, 0, false, WIDE>);
 }
 
 template <int NTV, bool DIAG>
@@ -243,28 +252,31 @@ void queue_launch(bool diag, bool wide, bool structured, int grid, const FleetVi
 }  // namespace
 
 cudaError_t launch_fleet(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
-                         NtVariant ntv, bool diag, bool structured, int32_t k, float *traj,
-                         cudaStream_t stream) {
+                         NtVariant ntv, bool diag, bool structured, bool wide, int32_t k,
+                         float *traj, cudaStream_t stream) {
   if (threads < 32 || threads > kMaxThreads || threads % 32 || n_blocks < 1 || k < 1 ||
       (fv.xh && diag))
     return cudaErrorInvalidValue;
   switch (ntv) {
     case NT_6:
-      return launch_d<NT_6>(fv, blocks, n_blocks, threads, diag, structured, k, traj, stream);
+      return launch_d<NT_6>(fv, blocks, n_blocks, threads, diag, structured, wide, k, traj,
+                            stream);
     case NT_8:
-      return launch_d<NT_8>(fv, blocks, n_blocks, threads, diag, structured, k, traj, stream);
+      return launch_d<NT_8>(fv, blocks, n_blocks, threads, diag, structured, wide, k, traj,
+                            stream);
     default:
-      return launch_d<NT_MIXED>(fv, blocks, n_blocks, threads, diag, structured, k, traj,
+      return launch_d<NT_MIXED>(fv, blocks, n_blocks, threads, diag, structured, wide, k, traj,
                                 stream);
   }
 }
 
 cudaError_t fleet_kernel_attributes(NtVariant ntv, bool diag, bool structured, bool rec,
-                                    cudaFuncAttributes *attr) {
+                                    bool wide, cudaFuncAttributes *attr) {
   const void *f = nullptr;
 #define MG_PICK(N)                                                                      \
   f = diag ? (rec ? kernel_ptr<N, true, true>(structured)                               \
-                  : kernel_ptr<N, true, false>(structured))                             \
+                  : wide ? kernel_ptr<N, true, false, true>(structured)                 \
+                         : kernel_ptr<N, true, false>(structured))                      \
            : (rec ? kernel_ptr<N, false, true>(false) : kernel_ptr<N, false, false>(false));
   switch (ntv) {
     case NT_6: MG_PICK(NT_6) break;

@@ -38,7 +38,8 @@ def main():
     ap.add_argument("--static", action="store_true",
                     help="static grid (one launch per k sub-steps) instead of the work queue")
     ap.add_argument("--narrow", action="store_true",
-                    help="work queue with the 128-register kernel instead of the 200-register one")
+                    help="the 128-register diagonal-mass kernel instead of the 200-register one "
+                         "(work queue; static grid)")
     ap.add_argument("--wps", type=int, default=8, help="work queue: resident warps per SM cap")
     ap.add_argument("--packed", action="store_true",
                     help="two envs per thread with packed FP32x2 arithmetic (mg_set_packed)")

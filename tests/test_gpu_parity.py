@@ -17,11 +17,11 @@ pytestmark = pytest.mark.gpu
 H = 0.01
 
 
-def make_sim(types, vs=None, epb=128, spl=50, graph=True, queue=True):
+def make_sim(types, vs=None, epb=128, spl=50, graph=True, queue=True, wide=True):
     vs = vs or vehicles()
     sim = Sim(len(types), types, vs)
     sim.set_launch(epb, spl, graph)
-    sim.set_schedule(queue)
+    sim.set_schedule(queue, wide)
     return sim
 
 
@@ -208,8 +208,8 @@ def test_ragged_sizes_and_launch_shapes(n, epb, spl, graph):
 
 @pytest.mark.parametrize("general", [False, True])
 def test_schedule_and_launch_shape_do_not_change_results(general):
-    """Same arithmetic per env whatever the schedule (work queue or static grid), block size,
-    chunking or graph replay: bitwise equal final states."""
+    """Same arithmetic per env whatever the schedule (work queue or static grid), register budget
+    (128 or 200), block size, chunking or graph replay: bitwise equal final states."""
     vs = vehicles()
     n = 3000
     types = I.mixed_fleet(4, n, max_group=500)
@@ -219,10 +219,11 @@ def test_schedule_and_launch_shape_do_not_change_results(general):
         params[:, I.P_RG:I.P_RG + 3] = I.round_f32(
             np.random.default_rng(2).uniform(-0.02, 0.02, (n, 3)))
     out = []
-    for epb, spl, graph, queue in [(128, 50, True, True), (64, 1, False, False),
-                                   (256, 17, True, False), (32, 300, False, True),
-                                   (96, 7, False, True), (128, 1, True, True)]:
-        sim = make_sim(types, vs, epb=epb, spl=spl, graph=graph, queue=queue)
+    for epb, spl, graph, queue, wide in [(128, 50, True, True, True), (64, 1, False, False, False),
+                                         (256, 17, True, False, True), (32, 300, False, True, False),
+                                         (96, 7, False, True, True), (128, 1, True, True, True),
+                                         (32, 300, True, False, True), (64, 50, False, False, False)]:
+        sim = make_sim(types, vs, epb=epb, spl=spl, graph=graph, queue=queue, wide=wide)
         if general:
             sim.set_params(torch.tensor(params, dtype=torch.float32, device="cuda"))
             sim.set_state(torch.tensor(I.random_states(5, n, [vs[t].n_thr for t in types]),

@@ -58,7 +58,8 @@ def _signature(types: np.ndarray, vehicles, general: bool) -> str:
 
 class Autotuner:
     def __init__(self, cache_path: str | None = None, candidates=DEFAULT_CANDIDATES,
-                 horizon: int = 300, reps: int = 3, k_per_call: int | None = None):
+                 horizon: int = 300, reps: int = 3, k_per_call: int | None = None,
+                 refine_rounds: int = 3):
         """``horizon`` sub-steps are timed per repetition, as one ``step(horizon)`` call, or as
         ``horizon // k_per_call`` calls of ``step(k_per_call)`` when the caller steps in small
         pieces (a policy loop): the best launch shape differs between the two."""
@@ -66,6 +67,7 @@ class Autotuner:
         self.candidates = list(candidates)
         self.horizon = horizon
         self.reps = reps
+        self.refine_rounds = refine_rounds
         self.k_per_call = k_per_call if k_per_call else horizon
         if not 1 <= self.k_per_call <= horizon:
             raise ValueError("need 1 <= k_per_call <= horizon")
@@ -79,8 +81,22 @@ class Autotuner:
         sig = _signature(np.asarray(types, dtype=np.int32), vehicles, general)
         return f"{dev}|{n_envs}|{sig}|k{self.k_per_call}"
 
+    def _time_ms(self, sim: Sim, cfg: LaunchConfig, calls: int, start, end) -> float:
+        cfg.apply(sim)
+        sim.step(self.k_per_call)  # warm-up (and graph capture)
+        torch.cuda.synchronize()
+        start.record(sim.stream)
+        for _ in range(self.reps * calls):
+            sim.step(self.k_per_call)
+        end.record(sim.stream)
+        torch.cuda.synchronize()
+        return start.elapsed_time(end) / self.reps
+
     def measure(self, n_envs: int, types, vehicles, general: bool = False):
-        """Time every candidate; returns [(config, env-steps/s)] sorted fastest first."""
+        """Time every candidate; returns [(config, env-steps/s)] sorted fastest first.  The
+        candidates within 3 % of the fastest are timed again, in turn, ``refine_rounds`` times,
+        and ranked by their best time: one short timing each leaves neighbours such as chunks
+        of 50 and 100 sub-steps in an order that changes from run to run."""
         types = np.asarray(types, dtype=np.int32)
         sim = Sim(n_envs, types, vehicles)
         try:
@@ -91,23 +107,20 @@ class Autotuner:
                 sim.set_params(p)
             sim.reset()
             sim.set_procedural_actions(11, 10)
-            out = []
             start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             calls = self.horizon // self.k_per_call
-            for cfg in self.candidates:
-                cfg.apply(sim)
-                sim.step(self.k_per_call)  # warm-up (and graph capture)
-                torch.cuda.synchronize()
-                start.record(sim.stream)
-                for _ in range(self.reps * calls):
-                    sim.step(self.k_per_call)
-                end.record(sim.stream)
-                torch.cuda.synchronize()
-                ms = start.elapsed_time(end) / self.reps
-                out.append((cfg, n_envs * calls * self.k_per_call / (ms / 1e3)))
+            steps = n_envs * calls * self.k_per_call
+            ms = {cfg: self._time_ms(sim, cfg, calls, start, end) for cfg in self.candidates}
+            best = min(ms.values())
+            finalists = sorted((c for c in ms if ms[c] <= 1.03 * best), key=ms.get)[:4]
+            if len(finalists) > 1:
+                for _ in range(self.refine_rounds):
+                    for cfg in finalists:
+                        ms[cfg] = min(ms[cfg], self._time_ms(sim, cfg, calls, start, end))
             sim.sync()
         finally:
             sim.close()
+        out = [(cfg, steps / (t / 1e3)) for cfg, t in ms.items()]
         out.sort(key=lambda t: -t[1])
         return out
 

@@ -61,6 +61,33 @@ def test_alone_equals_mix_and_plain_fleet():
         sim.close()
 
 
+def test_tick_register_budget_does_not_change_results():
+    """Ticks of at most 2 x SMs blocks run the 200-register kernel, larger ones the 128-register
+    kernel: a 45,000-env job (352 blocks) served with three small jobs, then each job alone,
+    gives the same final states and trajectories bit for bit, whichever budget its ticks got."""
+    vs = vehicles()
+    reqs = [Request(arrival_s=0.0, n_envs=45000, horizon=120, vehicle=0, param_seed=5,
+                    cmd_seed=6, hold=10)]
+    g = np.random.default_rng(11)
+    for i in range(3):
+        reqs.append(Request(arrival_s=0.0, n_envs=int(g.integers(100, 2000)), horizon=180,
+                            vehicle=i % 2, param_seed=int(g.integers(1, 2**40)),
+                            cmd_seed=int(g.integers(1, 2**40)), hold=7))
+    keys = ("arrival_s", "n_envs", "horizon", "vehicle", "param_seed", "cmd_seed", "hold")
+    srv = Server(vs, budget_bytes=8e9, capacity_envs=1 << 16, k=25, keep_results=True)
+    mix, stats = srv.run([Request(**{k: getattr(r, k) for k in keys}) for r in reqs],
+                         mode="batched")
+    srv.close()
+    assert stats["jobs"] == len(reqs)
+    srv = Server(vs, budget_bytes=8e9, capacity_envs=1 << 16, k=25, keep_results=True)
+    alone, _ = srv.run(reqs, mode="serial")
+    srv.close()
+    a, m = _by_key(alone), _by_key(mix)
+    for key, r in a.items():
+        torch.testing.assert_close(m[key].final_state, r.final_state, rtol=0, atol=0)
+        torch.testing.assert_close(m[key].traj, r.traj, rtol=0, atol=0)
+
+
 def test_served_job_matches_oracle():
     vs = vehicles()
     r = Request(arrival_s=0.0, n_envs=700, horizon=300, vehicle=1, param_seed=77, cmd_seed=88,

@@ -11,7 +11,8 @@ observation / error / auto-reset epilogue, static grid); ``--split`` runs the sp
 comparison kernel, ``--full`` the general path with off-diagonal hydrodynamics; ``--adjoint`` runs
 ``launches`` forward and backward passes of the differentiable rollout (``k`` sub-steps,
 checkpoints every ``--chunk``, MSE loss on the trajectory; ``--adjoint-mode`` picks the backward
-kernel).  Holds well under a GB of device
+kernel); ``--serve JOBS`` runs ``launches`` serving ticks of ``k`` sub-steps over JOBS jobs in a
+job pool.  Holds well under a GB of device
 memory at 65,536 envs.
 """
 from __future__ import annotations
@@ -53,11 +54,17 @@ def main():
                          "static grid)")
     ap.add_argument("--adjoint", action="store_true",
                     help="forward + backward passes of the differentiable rollout instead")
+    ap.add_argument("--serve", type=int, default=0, metavar="JOBS",
+                    help="serving ticks instead: JOBS jobs of n_envs / JOBS envs each (types "
+                         "alternating BlueROV2 / Heavy) in a job pool, each launch one tick of k "
+                         "sub-steps over all of them")
     ap.add_argument("--adjoint-mode", type=int, default=0,
                     help="backward kernel (mg_set_adjoint_mode): 0 by size, 1 one warp, 2 two warps")
     args = ap.parse_args()
     if args.adjoint:
         return adjoint_case(args)
+    if args.serve:
+        return serve_case(args)
 
     n = args.n_envs
     vs = I.fleet_vehicles()
@@ -119,6 +126,23 @@ def adjoint_case(args):
     sim.close()
     print(f"profile_case: adjoint, {n} envs, T={T}, C={C}, |dL/dcoef|_1 "
           f"{float(grads[0].abs().sum()):.4e}")
+
+
+def serve_case(args):
+    from .serve import Pool
+
+    vs = I.fleet_vehicles()
+    per = args.n_envs // args.serve
+    pool = Pool(per * args.serve, vs)
+    horizon = args.k * (args.warmup + args.launches)
+    for j in range(args.serve):
+        jid = pool.admit(per, j % 2, horizon, 100 + j, 200 + j, hold=10)
+        assert jid is not None
+    for _ in range(args.warmup + args.launches):
+        pool.tick(args.k)
+    pool.sync()
+    print(f"profile_case: serve, {args.serve} jobs x {per} envs, "
+          f"{args.warmup + args.launches} ticks of k={args.k}")
 
 
 if __name__ == "__main__":

@@ -187,6 +187,7 @@ struct mg_sim {
 
   // task layer
   bool has_task = false;
+  const void *task_out_ok[4] = {nullptr, nullptr, nullptr, nullptr};  // last validated outputs
   mg_task_spec task{};
   void *task_buf = nullptr;  // centre [n] float4, clock [n] int32, err_sum [n] float
   TaskView task_view() const {
@@ -1242,10 +1243,16 @@ mg_status mg_task_step(mg_sim *s, int32_t k, float *obs, float *err, uint8_t *do
   MG_NONNULL(done);
   if (!s->has_task) return fail(MG_ESTATE, "no task set");
   if (k < 0) return fail(MG_EINVAL, "k must be >= 0");
-  for (const void *p : {(const void *)obs, (const void *)err, (const void *)done})
-    if (!is_device_ptr(p)) return fail(MG_EINVAL, "task outputs must be device memory");
-  if (episode_err && !is_device_ptr(episode_err))
-    return fail(MG_EINVAL, "task outputs must be device memory");
+  // a policy loop passes the same output buffers every call: check them once (a pointer query
+  // costs microseconds, more than the host budget of a task step)
+  const void *outs[4] = {obs, err, done, episode_err};
+  if (!std::equal(outs, outs + 4, s->task_out_ok)) {
+    for (const void *p : {(const void *)obs, (const void *)err, (const void *)done})
+      if (!is_device_ptr(p)) return fail(MG_EINVAL, "task outputs must be device memory");
+    if (episode_err && !is_device_ptr(episode_err))
+      return fail(MG_EINVAL, "task outputs must be device memory");
+    std::copy(outs, outs + 4, s->task_out_ok);
+  }
   if (k == 0) {  // observe only
     MG_CK(launch_task(s->st, s->task_view(), s->n, s->gid0, 0, s->dt, obs, err, done,
                       episode_err, s->reset_seed, s->nu0_sigma, s->episode, s->flags,

@@ -165,6 +165,15 @@ mg_status mg_set_launch(mg_sim *sim, int32_t envs_per_block, int32_t steps_per_l
  * static grid.  MG_EINVAL unless 0 <= warps_per_sm <= 64. */
 mg_status mg_set_schedule(mg_sim *sim, int32_t work_queue, int32_t wide, int32_t warps_per_sm);
 
+/* Bound on each wait of the work-queue schedule (a unit waiting for its slice's previous chunk):
+ * at most `polls` polls of about 128 ns each (0 restores the default MG_WAIT_POLLS_DEFAULT,
+ * about half a second).  A wait that runs out is counted, the unit goes on without the chunk it
+ * waited for (its results are then unreliable, but every access stays in bounds and the launch
+ * ends), and the next mg_sync returns MG_ETIMEOUT.  A failure-detection knob: a limit far below
+ * a chunk's run time makes waits give up on purpose.  MG_EINVAL if polls > 2^30. */
+#define MG_WAIT_POLLS_DEFAULT 4194304u
+mg_status mg_set_wait_limit(mg_sim *sim, uint32_t polls);
+
 /* Packed arithmetic for the static-grid diagonal-mass step (every env with r_g = 0 and no
  * off-diagonal extension; other fleets, the work-queue schedule, mg_step_record, the fused last
  * launch of mg_task_step, the adjoint, the split step and the pool use the one-env-per-thread
@@ -220,15 +229,24 @@ mg_status mg_set_hydro_offdiag(mg_sim *sim, const float *x);
  * none is set). */
 mg_status mg_get_hydro_offdiag(mg_sim *sim, float *out);
 
+/* Width w of every action buffer below: floats per env and segment.  w = MG_MAX_THR (default:
+ * rows padded to 8, entries past a vehicle's thruster count ignored) or w = 6 (24-byte rows
+ * without padding: fleets whose vehicle types all have 6 thrusters, where padding would be a
+ * quarter of the schedule's bytes).  Changing the width clears the current action schedule
+ * (commands are zero until the next mg_set_actions*, cursor rewound).  Errors: MG_EINVAL (w not 6
+ * or MG_MAX_THR; w = 6 with a type of another thruster count). */
+mg_status mg_set_action_width(mg_sim *sim, int32_t w);
+
 /* Throttle actions (Eq. 3: one throttle setting per thruster).  a: host or device
- * [n_seg][n_envs][MG_MAX_THR], entries past a vehicle's thruster count ignored.  The library
+ * [n_seg][n_envs][w] (w from mg_set_action_width), entries past a vehicle's thruster count
+ * ignored.  The library
  * copies it.  Sub-step j counted from this call (across later mg_step calls) uses segment
  * min(j / hold_steps, n_seg - 1).  n_seg = 0 (a may be NULL) sets all commands to zero.
  * Errors: MG_EINVAL (n_seg < 0, hold_steps < 1), MG_ENOMEM, MG_ECUDA. */
 mg_status mg_set_actions(mg_sim *sim, const float *a, int32_t n_seg, int32_t hold_steps);
 
 /* As mg_set_actions, but without a copy: the kernels read a (device, 16-byte aligned,
- * [n_seg][n_envs][MG_MAX_THR]) in place.  The caller keeps the buffer alive and unchanged until
+ * [n_seg][n_envs][w]) in place.  The caller keeps the buffer alive and unchanged until
  * the stream has passed every mg_step that uses it (e.g. a policy's output tensor consumed by the
  * next step).  Errors: MG_EINVAL (NULL or host pointer, misaligned, n_seg < 1, hold_steps < 1). */
 mg_status mg_set_actions_borrowed(mg_sim *sim, const float *a, int32_t n_seg, int32_t hold_steps);
@@ -266,8 +284,9 @@ mg_status mg_step_split(mg_sim *sim, int32_t k, float *accel);
  * CUDA graph is instantiated, nothing is staged) and keeps the queue's scheduler words in a
  * fixed 256 KB device array compiled into the library instead of the sim's own buffers.  The
  * paper has no counterpart; it is an interface convenience around the same kernel.
- *   - The first call on a device looks up that array's device address (once per device, with
- *     the device current); make that first call before any stream capture.
+ *   - The first call for a sim on a device looks up that array's address on the sim's device
+ *     (once per device; the sim's device is made current for the look-up and the caller's
+ *     current device restored); make that first call before any stream capture.
  *   - Fleets of at most 65,536 32-env slices (2,097,152 envs of one vehicle type) are accepted;
  *     larger ones get MG_EINVAL with a message saying so.
  *   - All calls, from every sim on the device, share the one array and it keeps the last call's
@@ -295,8 +314,9 @@ mg_status mg_rollout_forward(mg_sim *sim, int32_t T, int32_t C, float *traj, flo
  * [T][MG_NTRAJ][n], the loss gradient with respect to traj.  Writes dcoef, device [n][18], the
  * gradient with respect to each env's added-mass, linear-damping and quadratic-damping diagonals
  * (record entries 4..21, §METHOD Eq. 1 hydrodynamic term); adds the gradient with respect to the
- * buffered actions (Eq. 3) into dact, device [n_seg][n][MG_MAX_THR] (may be NULL); writes the
- * gradient with respect to the start state into dstate0, device [n][MG_NSTATE] (may be NULL).
+ * buffered actions (Eq. 3) into dact, device [n_seg][n][w] (w the action width; may be NULL);
+ * writes the gradient with respect to the start state into dstate0, device [n][MG_NSTATE] (may
+ * be NULL).
  * Parameters and actions must be those of the forward; the sim's state is not read or changed.
  * Errors: MG_EINVAL (bad sizes, host buffers, a fleet with r_g != 0, procedural actions). */
 mg_status mg_rollout_backward(mg_sim *sim, int32_t T, int32_t C, const float *ckpt,
@@ -323,7 +343,7 @@ mg_status mg_set_state(mg_sim *sim, const float *in);
  * call waits: each copy runs on a stream of the library's own, into or out of one of two device
  * buffers used alternately, ordered after the work that last used that buffer; mg_sync waits
  * for these copies too.  Results are those of the synchronous calls.
- *   mg_set_actions_async: as mg_set_actions (a: host [n_seg][n_envs][MG_MAX_THR], n_seg >= 1);
+ *   mg_set_actions_async: as mg_set_actions (a: host [n_seg][n_envs][w], n_seg >= 1);
  *     the steps queued after the call read the copy once it has landed.  The caller keeps a
  *     unchanged until mg_sync returns, or until the second later call of mg_set_actions_async
  *     has returned (that call reuses this call's device buffer: it first waits on the host for
@@ -344,9 +364,11 @@ mg_status mg_reset(mg_sim *sim, const uint8_t *mask);
 
 /* Wait for the stream (and the asynchronous host copies and background randomisation, if any
  * have been issued); *nonfinite_count (may be NULL) receives how many envs are flagged
- * non-finite.  Returns MG_ETIMEOUT if a work-queue wait ever gave up (results since then are
- * unreliable; this is not expected to happen), else MG_ENOTSPD if the current parameters hold a
- * mass matrix that is not positive definite, else MG_ENONFINITE when that count is non-zero. */
+ * non-finite.  Returns MG_ETIMEOUT if a work-queue wait gave up since the last mg_sync (results
+ * of those steps are unreliable: restore the state with mg_set_state or mg_reset; not expected
+ * with the default limit of mg_set_wait_limit) and clears that count, else MG_ENOTSPD if the
+ * current parameters hold a mass matrix that is not positive definite, else MG_ENONFINITE when
+ * that count is non-zero. */
 mg_status mg_sync(mg_sim *sim, int64_t *nonfinite_count);
 
 /* Per-env non-finite flags into out [n_envs] (host or device), 1 = flagged. */
@@ -453,10 +475,11 @@ mg_status mg_pool_info(mg_pool *pool, int64_t *free_envs, int64_t *largest_free_
 /* Wait for the pool's stream. */
 mg_status mg_pool_sync(mg_pool *pool);
 
-/* Native request loop over a pool (continuous batching; the paper has no serving layer).  Jobs are submitted as specs and wait in a FIFO queue; each mg_server_poll admits
- * queued jobs in order while the trajectory budget and a free arena range allow, issues one
- * mg_pool_tick (every running job advances min(k, horizon - done) sub-steps in one launch),
- * records an event after it and hands back the jobs whose last tick has completed.  At most
+/* Native request loop over a pool (continuous batching; the paper has no serving layer).  Jobs
+ * are submitted as specs and wait in a FIFO queue; each mg_server_poll admits queued jobs in
+ * order while the trajectory budget and a free arena range allow, issues one mg_pool_tick
+ * (every running job advances min(k, horizon - done) sub-steps in one launch), records an event
+ * after it and hands back the jobs whose last tick has completed.  At most
  * max_inflight ticks stay queued beyond the oldest incomplete one; a poll that would exceed that,
  * or that has nothing left to advance, waits for the oldest by polling its event (spinning for
  * the first millisecond, never longer than wait_timeout_s: then MG_ETIMEOUT, and the server

@@ -84,6 +84,7 @@ SIGNATURES = {
     "mg_set_timestep": [_P, _F],
     "mg_set_launch": [_P, _I32, _I32, _I32],
     "mg_set_schedule": [_P, _I32, _I32, _I32],
+    "mg_set_wait_limit": [_P, ctypes.c_uint32],
     "mg_set_packed": [_P, _I32],
     "mg_randomize": [_P, _U64, ctypes.POINTER(Ranges)],
     "mg_randomize_prefetch": [_P, _U64, ctypes.POINTER(Ranges)],
@@ -93,6 +94,7 @@ SIGNATURES = {
     "mg_set_actions": [_P, _P, _I32, _I32],
     "mg_set_actions_borrowed": [_P, _P, _I32, _I32],
     "mg_set_actions_async": [_P, _P, _I32, _I32],
+    "mg_set_action_width": [_P, _I32],
     "mg_get_state_async": [_P, _P],
     "mg_set_procedural_actions": [_P, _U64, _I32],
     "mg_step": [_P, _I32],

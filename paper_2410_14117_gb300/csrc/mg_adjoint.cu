@@ -345,7 +345,7 @@ __device__ __forceinline__ void commands_at(const FleetView &fv, int64_t e, int6
   if (seg > fv.n_seg - 1) seg = fv.n_seg - 1;
   for (int i = 0; i < MT; ++i) c[i] = 0.f;
   if (fv.n_seg > 0) {
-    const float *a = reinterpret_cast<const float *>(fv.act) + (seg * fv.n + e) * MG_MAX_THR;
+    const float *a = fv.act + (seg * fv.n + e) * fv.act_w;
     #pragma unroll
     for (int i = 0; i < MT; ++i)
       if (i < nt) c[i] = a[i] * itau;
@@ -391,7 +391,7 @@ __device__ __forceinline__ void add_action_adjoint(const FleetView &fv, int64_t 
   if (!dact || fv.n_seg <= 0) return;
   int64_t seg = t / fv.hold;
   if (seg > fv.n_seg - 1) seg = fv.n_seg - 1;
-  float *da = dact + (seg * fv.n + e) * MG_MAX_THR;
+  float *da = dact + (seg * fv.n + e) * fv.act_w;
   #pragma unroll
   for (int i = 0; i < MT; ++i)
     if (i < nt) da[i] = fmaf(itau, gcs[i], da[i]);
@@ -578,7 +578,7 @@ __device__ __forceinline__ void fetch_substep(const FleetView &fv, int64_t e,
   if (fv.n_seg > 0) {
     int64_t seg = (step0 + t0 + j) / fv.hold;
     if (seg > fv.n_seg - 1) seg = fv.n_seg - 1;
-    const float *a = reinterpret_cast<const float *>(fv.act) + (seg * n + e) * MG_MAX_THR;
+    const float *a = fv.act + (seg * n + e) * fv.act_w;
     for (int i = 0; i < MT; ++i) cp_async4(buf + (W + MG_NTRAJ + i) * 32, a + i);
   }
   cp_async_commit();

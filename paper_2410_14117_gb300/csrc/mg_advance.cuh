@@ -80,12 +80,19 @@ __device__ __forceinline__ void load_commands(const FleetView &fv, int64_t e, in
     procedural_commands<MT>(fv.cmd_seed, (uint64_t)(fv.gid0 + e), seg, c);
   } else if (fv.n_seg > 0) {
     const int64_t sg = seg < fv.n_seg - 1 ? seg : fv.n_seg - 1;
-    const float4 *a = fv.act + (sg * fv.n + e) * 2;
-    const float4 lo = __ldg(a), hi = __ldg(a + 1);
-    c[0] = lo.x; c[1] = lo.y; c[2] = lo.z; c[3] = lo.w; c[4] = hi.x; c[5] = hi.y;
-    if constexpr (MT > 6) {
-      c[6] = hi.z;
-      c[7] = hi.w;
+    if (MT == 6 && fv.act_w == 6) {
+      // 24-byte rows (no padding): three 8-byte loads; a warp's rows are 768 contiguous bytes
+      const float2 *a = reinterpret_cast<const float2 *>(fv.act + (sg * fv.n + e) * 6);
+      const float2 x = __ldg(a), y = __ldg(a + 1), z = __ldg(a + 2);
+      c[0] = x.x; c[1] = x.y; c[2] = y.x; c[3] = y.y; c[4] = z.x; c[5] = z.y;
+    } else {
+      const float4 *a = reinterpret_cast<const float4 *>(fv.act + (sg * fv.n + e) * MG_MAX_THR);
+      const float4 lo = __ldg(a), hi = __ldg(a + 1);
+      c[0] = lo.x; c[1] = lo.y; c[2] = lo.z; c[3] = lo.w; c[4] = hi.x; c[5] = hi.y;
+      if constexpr (MT > 6) {
+        c[6] = hi.z;
+        c[7] = hi.w;
+      }
     }
   } else {
 #pragma unroll

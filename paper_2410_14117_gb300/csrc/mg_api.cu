@@ -149,11 +149,13 @@ struct mg_sim {
   bool queue = false;
   bool wide = true;
   int32_t queue_warps_per_sm = 0;
+  uint32_t wait_limit = MG_WAIT_POLLS_DEFAULT;  // bound on a work-queue wait (mg_set_wait_limit)
 
   // actions (act_src: what the kernels read — the sim's copy, or a caller's borrowed buffer)
   float *act = nullptr;
   const float *act_src = nullptr;
   size_t act_cap = 0;  // floats
+  int32_t act_w = MG_MAX_THR;  // floats per env and segment of every action buffer
   int32_t n_seg = 0, hold = 1;
   int32_t proc = 0;
   uint64_t cmd_seed = 0;
@@ -219,7 +221,8 @@ struct mg_sim {
     v.n_types = n_types;
     v.n = n;
     v.gid0 = gid0;
-    v.act = reinterpret_cast<const float4 *>(act_src);
+    v.act = act_src;
+    v.act_w = act_w;
     v.n_seg = proc ? 0 : n_seg;
     v.hold = hold;
     v.cmd_seed = cmd_seed;
@@ -229,6 +232,7 @@ struct mg_sim {
     v.flags = flags;
     v.counters = counters;
     v.xh = has_xh ? xh : nullptr;
+    v.spin_limit = wait_limit;
     v.cursor = reinterpret_cast<int64_t *>(counters + 3);
     v.done_blocks = reinterpret_cast<unsigned int *>(counters + 4);
     return v;
@@ -460,16 +464,21 @@ constexpr int kMaxDevices = 64;
 uint32_t *g_noalloc_ptr[kMaxDevices] = {};
 std::mutex g_noalloc_mu;
 
-// Device address of g_noalloc_sched on the current device, looked up once per device.  In host
-// code the array's name is only a host-side stand-in, so kernels must be given this address.
-mg_status noalloc_scratch(uint32_t **out) {
-  int dev = 0;
-  MG_CK(cudaGetDevice(&dev));
+// Device address of g_noalloc_sched on device dev (the sim's), looked up once per device with
+// that device current: the array has one copy per device, and in host code its name is only a
+// host-side stand-in, so kernels must be given this address.  The caller's current device is
+// restored before returning.
+mg_status noalloc_scratch(int dev, uint32_t **out) {
   if (dev < 0 || dev >= kMaxDevices) return fail(MG_EINVAL, "device index out of range");
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
+    int cur = 0;
+    MG_CK(cudaGetDevice(&cur));
+    if (cur != dev) MG_CK(cudaSetDevice(dev));
     void *p = nullptr;
-    MG_CK(cudaGetSymbolAddress(&p, g_noalloc_sched));
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_sched);
+    if (cur != dev) MG_CK(cudaSetDevice(cur));
+    MG_CK(e);
     g_noalloc_ptr[dev] = static_cast<uint32_t *>(p);
   }
   *out = g_noalloc_ptr[dev];
@@ -496,7 +505,7 @@ mg_status mg_step_noalloc(mg_sim *s, int32_t k) {
     return fail(MG_EINVAL, buf);
   }
   uint32_t *sched = nullptr;
-  mg_status st = noalloc_scratch(&sched);
+  mg_status st = noalloc_scratch(s->dev, &sched);
   if (st != MG_OK) return st;
   FleetView v = s->view();
   v.cursor_adv = k;
@@ -772,6 +781,15 @@ mg_status mg_set_schedule(mg_sim *s, int32_t work_queue, int32_t wide, int32_t w
   return MG_OK;
 }
 
+mg_status mg_set_wait_limit(mg_sim *s, uint32_t polls) {
+  MG_NONNULL(s);
+  if (polls > (1u << 30)) return fail(MG_EINVAL, "polls must be <= 2^30");
+  const uint32_t v = polls ? polls : (uint32_t)MG_WAIT_POLLS_DEFAULT;
+  if (v != s->wait_limit) s->drop_graphs();
+  s->wait_limit = v;
+  return MG_OK;
+}
+
 mg_status mg_set_packed(mg_sim *s, int32_t packed) {
   MG_NONNULL(s);
   s->packed = packed != 0;
@@ -961,7 +979,7 @@ mg_status mg_set_actions(mg_sim *s, const float *a, int32_t n_seg, int32_t hold_
   MG_NONNULL(s);
   if (n_seg < 0 || hold_steps < 1) return fail(MG_EINVAL, "need n_seg >= 0 and hold_steps >= 1");
   if (n_seg > 0 && !a) return fail(MG_EINVAL, "a is NULL with n_seg > 0");
-  const size_t floats = (size_t)n_seg * s->n * MG_MAX_THR;
+  const size_t floats = (size_t)n_seg * s->n * s->act_w;
   if (floats > s->act_cap) {
     MG_CK(cudaStreamSynchronize(s->stream));
     cudaFree(s->act);
@@ -1015,7 +1033,7 @@ mg_status mg_set_actions_async(mg_sim *s, const float *a, int32_t n_seg, int32_t
   // This slot's previous copy (two calls ago) read its host buffer; once it has finished, that
   // buffer is the caller's again.
   MG_CK(cudaEventSynchronize(s->a_copied[slot]));
-  const size_t floats = (size_t)n_seg * s->n * MG_MAX_THR;
+  const size_t floats = (size_t)n_seg * s->n * s->act_w;
   if (floats > s->abuf_cap[slot]) {
     MG_CK(cudaStreamSynchronize(s->stream));
     MG_CK(cudaStreamSynchronize(s->h2d_stream));
@@ -1037,6 +1055,25 @@ mg_status mg_set_actions_async(mg_sim *s, const float *a, int32_t n_seg, int32_t
   s->proc = 0;
   s->n_seg = n_seg;
   s->hold = hold_steps;
+  return rewind_cursor(s);
+}
+
+mg_status mg_set_action_width(mg_sim *s, int32_t width) {
+  MG_NONNULL(s);
+  if (width != MG_MAX_THR && width != 6)
+    return fail(MG_EINVAL, "the action width must be 6 or MG_MAX_THR");
+  if (width < MG_MAX_THR && s->ntv != NT_6)
+    return fail(MG_EINVAL, "a 6-float action width needs a fleet of 6-thruster vehicles only");
+  if (width == s->act_w) return MG_OK;
+  mg_status rs = release_async_actions(s);
+  if (rs != MG_OK) return rs;
+  // the buffered schedule was laid out for the old width: the commands become zero until the
+  // next mg_set_actions* call
+  s->act_w = width;
+  s->act_src = nullptr;
+  s->proc = 0;
+  s->n_seg = 0;
+  s->drop_graphs();
   return rewind_cursor(s);
 }
 
@@ -1355,6 +1392,9 @@ mg_status mg_sync(mg_sim *s, int64_t *nonfinite_count) {
   if ((st = read_counter(s, 0, &c)) != MG_OK) return st;
   if (nonfinite_count) *nonfinite_count = (int64_t)c;
   if (to) {
+    // reported once: the count restarts from zero for the steps after this call
+    MG_CK(cudaMemsetAsync(s->counters + 2, 0, sizeof(unsigned long long), s->stream));
+    MG_CK(cudaStreamSynchronize(s->stream));
     char buf[128];
     snprintf(buf, sizeof buf, "%llu work-queue waits timed out", to);
     return fail(MG_ETIMEOUT, buf);

@@ -78,7 +78,8 @@ struct FleetView {
   int32_t n_types;
   int64_t n;                 // envs
   int64_t gid0;              // env id offset for counter-based draws
-  const float4 *act;         // [n_seg][n][8] as float4 pairs, or null
+  const float *act;          // [n_seg][n][act_w] (16-byte aligned), or null
+  int32_t act_w;             // floats per env and segment: MG_MAX_THR, or 6 (mg_set_action_width)
   int32_t n_seg;
   int32_t hold;
   uint64_t cmd_seed;         // procedural actions when proc != 0
@@ -97,6 +98,9 @@ struct FleetView {
   // cursor_adv once all its blocks are done.  Only that launch pays for the completion count.
   int32_t cursor_off;
   int32_t cursor_adv;
+  // Work-queue schedule: polls of ~128 ns a unit's wait for its slice's previous chunk may take
+  // before it gives up (counted in counters[2] and reported by mg_sync as MG_ETIMEOUT).
+  uint32_t spin_limit;
   // Off-diagonal hydrodynamics, device [MG_NXPARAM][n] (component-major), or null: the static
   // and task kernels then run their XH variants (general path), staging each block's
   // coefficients in shared memory.

@@ -197,6 +197,7 @@ FleetView pool_view(const mg_pool *p) {
   v.flags = p->flags;
   v.counters = p->counters;
   v.hold = 1;
+  v.spin_limit = MG_WAIT_POLLS_DEFAULT;
   return v;
 }
 

@@ -26,9 +26,6 @@ namespace mg {
 namespace {
 
 constexpr int kMaxThreads = 256;
-// Bound on a work-queue wait (polls of ~128 ns each, ~0.5 s); on expiry the wait is counted as a
-// time-out and the unit proceeds.
-constexpr uint32_t kSpinLimit = 1u << 22;
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
   uint32_t v;
@@ -107,10 +104,12 @@ __global__ void __maxnreg__(!DIAG ? kRegsGeneral : WIDE ? kRegsWide : kRegsDiag)
     const int32_t c = (int32_t)(u / (uint32_t)n_slices);
     const int32_t d = (int32_t)(u % (uint32_t)n_slices);
     if (c > 0 && lane == 0) {
-      // The slice's previous chunk was claimed earlier by a running warp, so it completes.
+      // The slice's previous chunk was claimed earlier by a running warp, so it completes.  The
+      // wait is bounded (fv.spin_limit polls of ~128 ns, MG_WAIT_POLLS_DEFAULT unless set by
+      // mg_set_wait_limit): on expiry it is counted as a time-out and the unit proceeds.
       uint32_t polls = 0;
       while (ld_acquire(sched + 4 + d) < (uint32_t)c) {
-        if (++polls > kSpinLimit) {
+        if (++polls > fv.spin_limit) {
           atomicAdd(fv.counters + 2, 1ull);
           break;
         }

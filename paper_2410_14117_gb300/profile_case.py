@@ -42,6 +42,9 @@ def main():
                     help="the 128-register diagonal-mass kernel instead of the 200-register one "
                          "(work queue; static grid)")
     ap.add_argument("--wps", type=int, default=8, help="work queue: resident warps per SM cap")
+    ap.add_argument("--width6", action="store_true",
+                    help="unpadded throttle schedule, 6 floats per env and segment "
+                         "(mg_set_action_width; 6-thruster vehicle)")
     ap.add_argument("--packed", action="store_true",
                     help="two envs per thread with packed FP32x2 arithmetic (mg_set_packed)")
     ap.add_argument("--task", action="store_true",
@@ -85,6 +88,9 @@ def main():
     acc = torch.zeros((6, n), device="cuda") if args.split else None
     total = (args.warmup + args.launches) * args.k
     cmds = I.commands(5678, math.ceil(total / 10), n, vs[args.vehicle].n_thr)
+    if args.width6:
+        sim.set_action_width(6)
+        cmds = np.ascontiguousarray(cmds[:, :, :6])
     sim.set_actions(torch.tensor(cmds, device="cuda"), 10)
     if args.task:
         sim.set_schedule(False)

@@ -78,6 +78,7 @@ class Sim:
         self.types = types
         self.n_thr = np.array([int(vehicles[t].n_thr) for t in types], dtype=np.int32)
         self.device = torch.device("cuda", torch.cuda.current_device())
+        self.act_w = MG_MAX_THR
         self.set_stream(stream if stream is not None else torch.cuda.current_stream())
 
     # ------------------------------------------------------------------ configuration
@@ -103,6 +104,11 @@ class Sim:
         """Static grid (default) or the work-queue schedule (see mg_set_schedule)."""
         call("mg_set_schedule", self._h, 1 if work_queue else 0, 1 if wide else 0,
              int(warps_per_sm))
+
+    def set_wait_limit(self, polls: int = 0):
+        """Bound on each work-queue wait in polls of ~128 ns (0: the default; see
+        mg_set_wait_limit)."""
+        call("mg_set_wait_limit", self._h, int(polls))
 
     def set_packed(self, packed: bool = True):
         """Two envs per thread with packed FP32x2 arithmetic (see mg_set_packed)."""
@@ -165,36 +171,44 @@ class Sim:
 
     # ------------------------------------------------------------------ actions and stepping
     def set_actions(self, actions, hold_steps: int = 1):
-        """``actions``: float32 [n_seg, n_envs, 8] (device tensor, or host tensor/array)."""
+        """``actions``: float32 [n_seg, n_envs, w] (device tensor, or host tensor/array), w the
+        action width (8 unless set_action_width(6))."""
         if actions is None:
             call("mg_set_actions", self._h, None, 0, int(hold_steps))
             return
-        if actions.ndim != 3 or actions.shape[1:] != (self.n, MG_MAX_THR):
-            raise ValueError(f"actions must be [n_seg, {self.n}, {MG_MAX_THR}]")
+        if actions.ndim != 3 or actions.shape[1:] != (self.n, self.act_w):
+            raise ValueError(f"actions must be [n_seg, {self.n}, {self.act_w}]")
         _check(actions, actions.shape, torch.float32)
         call("mg_set_actions", self._h, _ptr(actions), int(actions.shape[0]), int(hold_steps))
 
     def set_actions_async(self, actions, hold_steps: int = 1):
         """As set_actions from a page-locked host tensor, without waiting (mg_set_actions_async):
         keep ``actions`` unchanged until ``sync()`` or the next-but-one call of this method."""
-        if actions.ndim != 3 or actions.shape[1:] != (self.n, MG_MAX_THR):
-            raise ValueError(f"actions must be [n_seg, {self.n}, {MG_MAX_THR}]")
+        if actions.ndim != 3 or actions.shape[1:] != (self.n, self.act_w):
+            raise ValueError(f"actions must be [n_seg, {self.n}, {self.act_w}]")
         _check(actions, actions.shape, torch.float32)
         call("mg_set_actions_async", self._h, _ptr(actions), int(actions.shape[0]),
              int(hold_steps))
 
     def set_actions_borrowed(self, actions, hold_steps: int = 1):
-        """Read ``actions`` (float32 device tensor [n_seg, n_envs, 8]) in place, without a copy;
+        """Read ``actions`` (float32 device tensor [n_seg, n_envs, w]) in place, without a copy;
         keep it alive and unchanged until the steps using it have run (mg_set_actions_borrowed).
         """
         if not (isinstance(actions, torch.Tensor) and actions.is_cuda):
             raise ValueError("borrowed actions must be a CUDA tensor")
-        if actions.ndim != 3 or actions.shape[1:] != (self.n, MG_MAX_THR):
-            raise ValueError(f"actions must be [n_seg, {self.n}, {MG_MAX_THR}]")
+        if actions.ndim != 3 or actions.shape[1:] != (self.n, self.act_w):
+            raise ValueError(f"actions must be [n_seg, {self.n}, {self.act_w}]")
         _check(actions, actions.shape, torch.float32)
         self._borrowed = actions  # keeps the storage alive while the sim may read it
         call("mg_set_actions_borrowed", self._h, _ptr(actions), int(actions.shape[0]),
              int(hold_steps))
+
+    def set_action_width(self, width: int):
+        """Floats per env and segment of later action buffers: 8 (default, zero-padded past a
+        vehicle's thruster count) or 6 (fleets of 6-thruster vehicles; no padding).  Clears the
+        current schedule (see mg_set_action_width)."""
+        call("mg_set_action_width", self._h, int(width))
+        self.act_w = int(width)
 
     def set_procedural_actions(self, cmd_seed: int, hold_steps: int):
         call("mg_set_procedural_actions", self._h, ctypes.c_uint64(cmd_seed), int(hold_steps))

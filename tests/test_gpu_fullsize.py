@@ -1,10 +1,10 @@
 """Parity at the benchmark's full sizes, in the launch configurations the benchmark times, on
 sampled envs the oracle computes one by one: the 65,536-env headline fleet (work-queue kernel,
-200-register cap, 8 warps/SM, chunk 100, actions read in place, CUDA graph) over a whole 1,000
-sub-step episode, parameters drawn in the background and installed as the benchmark does them,
-the 262,144-env mixed fleet over 500 sub-steps and the 1,048,576-env top of
-the size sweep (each also on the packed static grid, two envs per thread, which the autotuner
-picks for them)."""
+200-register cap, 8 warps/SM, chunk 100, the unpadded 6-float throttle schedule read in place,
+CUDA graph) over a whole 1,000 sub-step episode, parameters drawn in the background and
+installed as the benchmark does them; the 262,144-env mixed fleet over 500 sub-steps and the
+1,048,576-env top of the size sweep (each also on the packed static grid, two envs per thread,
+which the autotuner picks for them)."""
 import numpy as np
 import pytest
 import torch
@@ -45,12 +45,13 @@ def test_headline_fleet_sampled_matches_oracle():
     types = np.zeros(n, dtype=np.int32)
     sim = Sim(n, types, vs)
     LaunchConfig("queue", 128, 100, True, 8).apply(sim)
+    sim.set_action_width(6)  # the benchmark's unpadded schedule
     # the parameters reach the fleet as in the benchmark: drawn in the background, installed
     sim.randomize_prefetch(1234, 0.8, 1.2, 0.2)
     sim.randomize(1234, 0.8, 1.2, 0.2, 0.3, wait=False)
     sim.reset()
     cmds = I.commands(5678, 100, n, 6)
-    acts = torch.tensor(cmds, device="cuda")
+    acts = torch.tensor(np.ascontiguousarray(cmds[:, :, :6]), device="cuda")
     sim.set_actions_borrowed(acts, hold)
     sample = _sample(n, 600, 3)
     sim.step(500)
@@ -61,11 +62,15 @@ def test_headline_fleet_sampled_matches_oracle():
     sim.close()
     ref_mid = _oracle_rollout(vs, types, sample, 1234, cmds, hold, 500)
     err_mid = rel_err(mid, ref_mid)
-    assert err_mid.max() <= TOL_ROLLOUT, err_mid.max(axis=0)
-    # a whole episode: the 500-sub-step bar scaled by the horizon (errors grow about linearly)
     ref_end = _oracle_rollout(vs, types, sample, 1234, cmds, hold, 1000)
     err_end = rel_err(end, ref_end)
-    assert err_end.max() <= 2 * TOL_ROLLOUT, err_end.max(axis=0)
+    msg = (f"max per-block error after 500 sub-steps {err_mid.max():.3e} "
+           f"(p, q, v, w, n: {np.array2string(err_mid.max(axis=0), precision=3)}), after 1,000 "
+           f"{err_end.max():.3e} ({np.array2string(err_end.max(axis=0), precision=3)})")
+    print(msg)
+    assert err_mid.max() <= TOL_ROLLOUT, msg
+    # the whole episode is held to the same bar as 500 sub-steps
+    assert err_end.max() <= TOL_ROLLOUT, msg
 
 
 @pytest.mark.parametrize("launch", [LaunchConfig("queue", 128, 50, True, 12),

@@ -29,6 +29,7 @@ def _fleet(n, types, vs):
 
 
 def test_noalloc_step_matches_mg_step_on_two_calls():
+    """Same work-queue kernel, same schedule: the two entry points agree bit for bit."""
     vs = I.fleet_vehicles()
     n = 20000
     types = I.mixed_fleet(5, n, max_group=3000)
@@ -36,11 +37,33 @@ def test_noalloc_step_matches_mg_step_on_two_calls():
     for _ in range(2):
         ref.step(300)
         call("mg_step_noalloc", nal._h, 300)
+        a = ref.get_state()
+        b = nal.get_state()
+        assert torch.isfinite(b).all()
+        assert torch.equal(b, a)
+    assert nal.sync() == 0
+    ref.close()
+    nal.close()
+
+
+def test_noalloc_step_matches_static_grid_mg_step():
+    """A sim whose own schedule is the static grid still gets the work-queue kernel from
+    mg_step_noalloc; the two schedules round the same arithmetic alike, so the results agree
+    within the rollout tolerance (and in practice exactly)."""
+    vs = I.fleet_vehicles()
+    n = 5000
+    types = I.mixed_fleet(6, n, max_group=1500)
+    ref, nal = _fleet(n, types, vs), _fleet(n, types, vs)
+    ref.set_schedule(False, False)
+    ref.set_launch(64, 100, True)
+    for _ in range(2):
+        ref.step(250)
+        call("mg_step_noalloc", nal._h, 250)
         a = ref.get_state().double().cpu().numpy()
         b = nal.get_state().double().cpu().numpy()
         assert np.isfinite(b).all()
         assert rel_err(b, a).max() <= TOL_ROLLOUT
-    assert nal.sync() == 0
+    assert nal.sync() == 0 and ref.sync() == 0
     ref.close()
     nal.close()
 

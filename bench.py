@@ -37,7 +37,8 @@ METRIC = "env-steps/s at 64K envs (fused vs per-step, same GPU); p50/p99 serve l
 # in its closed form (12 per thruster) + quaternion renormalisation (15).
 FLOPS_PER_ENV_STEP = {6: 4 * 256 + 164 + 6 * 12 + 15, 8: 4 * 270 + 164 + 8 * 12 + 15}
 # Algorithmic HBM bytes per env of one launch: state read + written ((13 + n_thr) floats each),
-# the 34 parameter floats of the diagonal-mass step, and one command vector per segment.
+# the 34 parameter floats of the diagonal-mass step, and one command row (unpadded for a fleet of
+# 6-thruster vehicles: mg_set_action_width 6).
 STATE_BYTES = {6: 19 * 4, 8: 21 * 4}
 PARAM_BYTES = 34 * 4
 CMD_BYTES = {6: 6 * 4, 8: 8 * 4}
@@ -138,8 +139,6 @@ KERNEL_SOURCES = {
     "k_fleet": ("paper_2410_14117_gb300/csrc/mg_step.cu",) + _COMMON_SOURCES,
     "k_fleet_queue": ("paper_2410_14117_gb300/csrc/mg_step.cu",) + _COMMON_SOURCES,
     "k_fleet_step1": ("paper_2410_14117_gb300/csrc/mg_step.cu",) + _COMMON_SOURCES,
-    "k_fleet_pair": ("paper_2410_14117_gb300/csrc/mg_pair.cu",
-                     "paper_2410_14117_gb300/csrc/mg_pair.cuh") + _COMMON_SOURCES,
 }
 
 
@@ -158,15 +157,17 @@ def kernel_sources_sha(files) -> str:
 def profiled_traffic(kernel: str, n_envs: int, k: int):
     """DRAM bytes (read + write) of one launch of `k` sub-steps over `n_envs` envs, from
     profiles/dram_traffic.txt: a capture of the current sources with the same sub-steps per
-    launch, scaled by the env count (traffic is per env at a fixed k), else None."""
+    launch and fleet size (whether the working set stays in the L2 depends on the size), else
+    None."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path) or kernel not in KERNEL_SOURCES:
         return None
     sha = kernel_sources_sha(KERNEL_SOURCES[kernel])
     for line in open(path):
         f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
-        if f.get("kernel") == kernel and f.get("sources_sha") == sha and int(f["k"]) == k:
-            return float(f["dram_bytes"]) * n_envs / float(f["n_envs"])
+        if (f.get("kernel") == kernel and f.get("sources_sha") == sha and int(f["k"]) == k
+                and int(f["n_envs"]) == n_envs):
+            return float(f["dram_bytes"])
     return None
 
 
@@ -237,12 +238,8 @@ def cpu_baseline(n_envs, horizon, hold, target_s=12.0):
     O.rollout(p1, geo, np.zeros(n1, np.int32), s1, c1, hold, 500, h=0.01)
     small = n1 * 500 / (time.perf_counter() - t1)
     return {"value": ns * steps * reps / dt, "unit": "env-steps/s", "cores": cores,
-            "kind": "oracle", "single_core_value": single,
-            "small_fleet_value": small,
-            "sample": f"{reps} x ({ns} envs x {steps} sub-steps) of the same randomised BlueROV2 "
-                      f"workload (FP64 oracle, OpenMP over envs), {dt:.1f} s; single core: "
-                      "512 envs x 100 sub-steps; small_fleet_value: 1,024 nominal BlueROV2 envs "
-                      "x 500 sub-steps, no current, all cores"}
+            "kind": "oracle", "single_core_value": single, "small_fleet_value": small,
+            "sample": f"{reps}x({ns} envs x {steps} sub-steps), {dt:.1f} s"}
 
 
 def run_reference(args):
@@ -277,8 +274,7 @@ def run_reference(args):
         times.append(time.perf_counter() - t)
     total = sum(times)
     value = ns * steps * args.steps / total
-    sample = (f"{ns} envs x {steps} sub-steps per step of the 65,536-env randomised BlueROV2 "
-              f"workload (FP64 oracle, OpenMP over envs)")
+    sample = f"{ns} envs x {steps} sub-steps of the headline workload per step"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "env-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
@@ -293,14 +289,55 @@ def run_reference(args):
 
 
 def workload_config(args):
-    return {"workload": f"{args.n_envs:,} domain-randomised BlueROV2 envs (params U[0.8,1.2]"
-                        f"x nominal, NED current N(0,0.2)), {args.horizon:,} RK4 sub-steps of "
-                        f"0.01 s per episode, commands U[-1,1] held {args.hold} sub-steps",
-            "n_envs": args.n_envs, "horizon": args.horizon,
-            "l2": "flushed between timed steps (256 MB write, outside the events)"}
+    """The headline workload: randomised BlueROV2 envs (parameters U[0.8,1.2] x nominal, NED
+    current N(0,0.2)), whole episodes of `horizon` RK4 sub-steps of 0.01 s, commands U[-1,1] held
+    `hold` sub-steps; the L2 is flushed (256 MB write, outside the events) between timed
+    episodes."""
+    return {"workload": f"{args.n_envs} randomised BlueROV2, {args.horizon} RK4 sub-steps",
+            "n_envs": args.n_envs, "horizon": args.horizon, "l2": "flushed"}
 
 
 # ----------------------------------------------------------------------------- our arm
+
+def sig(x, digits=4):
+    """x with every float rounded to `digits` significant digits (keeps the JSON line short)."""
+    if isinstance(x, float):
+        return float(f"{x:.{digits}g}") if math.isfinite(x) else None
+    if isinstance(x, dict):
+        return {k: sig(v, digits) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [sig(v, digits) for v in x]
+    return x
+
+
+def launch_tag(cfg) -> str:
+    """Short name of a launch configuration: schedule/block or chunk/flags."""
+    if cfg.schedule == "queue":
+        return f"q{cfg.steps_per_launch}w{cfg.warps_per_sm}{'W' if cfg.wide else ''}"
+    return f"s{cfg.envs_per_block}k{cfg.steps_per_launch}{'W' if cfg.wide else ''}"
+
+
+def l2_copy_gbs(mb=10, reps=1000):
+    """Bandwidth of back-to-back device copies of an L2-resident buffer pair moving about the
+    per-step kernel's bytes per launch (2 x 10 MiB against its 20.4 MB): read + write bytes over
+    the time per copy, best of 5 runs of `reps` copies.  The ceiling of a launch-per-sub-step
+    kernel whose working set stays in the L2, launch gaps included as for that kernel."""
+    import torch
+    a = torch.empty(mb << 20, dtype=torch.uint8, device="cuda")
+    b = torch.empty_like(a)
+    b.copy_(a)
+    best = float("inf")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(5):
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / reps)
+    return 2 * a.numel() / (best / 1e3) / 1e9
+
 
 def run_ours(args):
     import numpy as np
@@ -329,8 +366,11 @@ def run_ours(args):
     sim = Sim(n, types0, vs)
     sim.set_env_id_offset(rank_env_offset(rank, n))
     cfg.apply(sim)
+    # the fleet is all 6-thruster BlueROV2s: the throttle schedule is stored unpadded,
+    # [n_seg][n][6] (24 B per env and segment)
+    sim.set_action_width(6)
     n_seg = math.ceil(horizon / hold)
-    acts_np = I.commands(5678 + rank, n_seg, n, 6)
+    acts_np = np.ascontiguousarray(I.commands(5678 + rank, n_seg, n, 6)[:, :, :6])
     acts_host = torch.from_numpy(acts_np).pin_memory()
     acts_dev = acts_host.to(dev)
     out_dev = torch.empty((n, 21), dtype=torch.float32, device=dev)
@@ -344,10 +384,7 @@ def run_ours(args):
     def episode(seed, a, out):
         sim.randomize(seed, 0.8, 1.2, 0.2, 0.3, wait=False)
         sim.reset()
-        if a.is_cuda:
-            sim.set_actions_borrowed(a, hold)  # already resident: read in place
-        else:
-            sim.set_actions(a, hold)           # host schedule: copied in
+        sim.set_actions_borrowed(a, hold)  # already resident: read in place
         sim.step(horizon)
         sim.randomize_prefetch(seed + 1)
         sim.get_state(out)
@@ -357,7 +394,7 @@ def run_ours(args):
         episode(1000 + w, acts_dev, out_dev)
     torch.cuda.synchronize()
 
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     barrier = (lambda: torch.distributed.barrier()) if world > 1 else (lambda: None)
     clocks = Clocks(local)
     barrier()
@@ -366,7 +403,7 @@ def run_ours(args):
     torch.cuda.nvtx.range_push("timed")
     for i in range(args.steps):
         flush.zero_()
-        e0, e1, e2 = ev[i]
+        e0, e1, e2, e3 = ev[i]
         e0.record(stream)
         if i == 0:  # the first timed episode's draw is made inside the timed region too
             sim.randomize_prefetch(2000)
@@ -378,8 +415,7 @@ def run_ours(args):
         e2.record(stream)
         sim.randomize_prefetch(2000 + i + 1)
         sim.get_state(out_dev)
-        ev[i].append(torch.cuda.Event(enable_timing=True))
-        ev[i][3].record(stream)
+        e3.record(stream)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     barrier()
@@ -396,25 +432,18 @@ def run_ours(args):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = fp32_alu_peak_tflops(sm_max)
     achieved = flops / launch_s / 1e12
-    kname = ("k_fleet_queue" if cfg.schedule == "queue" else
-             "k_fleet_pair" if cfg.packed else "k_fleet")
+    kname = "k_fleet_queue" if cfg.schedule == "queue" else "k_fleet"
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak,
                 "traffic": profiled_traffic(kname, n, horizon // launches_per_episode),
-                "kernel": ("k_fleet_queue (persistent, work queue" if cfg.schedule == "queue"
-                           else "k_fleet_pair (persistent, static grid, two envs per thread"
-                           if cfg.packed else "k_fleet (persistent, static grid") +
-                          ", 6 thrusters, diagonal mass)",
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 flops x {sm_max:.0f} MHz "
-                               f"({peak_kind} max SM clock)",
-                "flops_per_env_step": FLOPS_PER_ENV_STEP[6],
-                "launch_ms": launch_s * 1e3}
+                "kernel": kname, "peak_kind": f"derived ({peak_kind} max SM clock)",
+                "flops_per_env_step": FLOPS_PER_ENV_STEP[6], "launch_ms": launch_s * 1e3}
 
     line = {"metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": dict(workload_config(args), launch=dataclasses.asdict(cfg)),
+            "config": dict(workload_config(args), launch=launch_tag(cfg)),
             "roofline": roofline,
             "clocks": clk,
             "gpu_launches": args.steps * (launches_per_episode + 3) + 1}
@@ -426,10 +455,9 @@ def run_ours(args):
     # read-back stream, overlapping the next episode); each episode's parameters are drawn
     # while the previous episode steps (mg_randomize_prefetch) and installed without a host wait
     # (MG_RANDOMIZE_ASYNC: the fleet's mass matrices are diagonal).  All copies and draws have
-    # completed when the clock stops (mg_sync).
+    # completed when the clock stops (mg_sync).  50 episodes back to back, pipeline fill
+    # included.
     if not args.no_e2e:
-        # 50 pipelined episodes (0.1 s): the pipeline fills once (the first episode's schedule
-        # copy overlaps nothing) and then runs at its steady-state rate
         ke = min(args.steps, 50)
         outs_host = [torch.empty((n, 21), dtype=torch.float32).pin_memory() for _ in range(2)]
 
@@ -451,86 +479,24 @@ def run_ours(args):
         el = reduce_max(time.perf_counter() - t, dev)
         line["e2e"] = {"value": world * n * horizon * ke / el, "unit": "env-steps/s",
                        "h2d_bytes_per_step": acts_np.nbytes,
-                       "d2h_bytes_per_step": n * 21 * 4,
-                       "note": "per episode, through the C ABI: throttle schedule H2D from "
-                               "page-locked host memory (mg_set_actions_async, overlapping the "
-                               "previous episode), parameters drawn while the previous "
-                               "episode steps (mg_randomize_prefetch) and installed without a "
-                               "host wait, "
-                               "final state D2H to page-locked host memory (mg_get_state_async, "
-                               "overlapping the next episode), all inside the wall-clock timed "
-                               "region; 50 episodes back to back, including the pipeline fill "
-                               "(one copy that overlaps nothing)"}
+                       "d2h_bytes_per_step": n * 21 * 4}
 
     # ---- the plain per-step form on the same GPU (one launch per sub-step)
     if not args.no_per_step:
-        sim.set_actions_borrowed(acts_dev, hold)
-        sim.set_schedule(False, False)  # static grid, 128-register kernel (16 warps/SM)
-        sim.set_packed(False)
-        sim.set_launch(args.epb, 1, False)
-        sim.randomize(7, 0.8, 1.2, 0.2, 0.3)
-        sim.reset()
-        for _ in range(50):
-            sim.step(1)
-        reps = 2
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        a.record(stream)
-        for _ in range(reps):
-            sim.set_actions_borrowed(acts_dev, hold)
-            for _ in range(horizon):
-                sim.step(1)
-        b.record(stream)
-        torch.cuda.synchronize()
-        host_ms = a.elapsed_time(b) / reps
-        sim.set_launch(args.epb, 1, True)
-        sim.set_actions_borrowed(acts_dev, hold)
-        sim.step(horizon)  # capture
-        torch.cuda.synchronize()
-        a.record(stream)
-        for _ in range(reps):
-            sim.set_actions_borrowed(acts_dev, hold)
-            sim.step(horizon)
-        b.record(stream)
-        torch.cuda.synchronize()
-        graph_ms_ps = a.elapsed_time(b) / reps
-        per_launch_s = graph_ms_ps / 1e3 / horizon
-        bytes_per_launch = n * (2 * STATE_BYTES[6] + PARAM_BYTES + CMD_BYTES[6])
-        hbm = float(peaks.get("hbm_gbs", 6800.0))
-        ach = bytes_per_launch / per_launch_s / 1e9
-        fused_ms_episode = statistics.mean(graph_ms)
-        ps_traffic = profiled_traffic("k_fleet_step1", n, 1)
-        # the persistent form exactly as the scale configuration names it: static grid, 50
-        # sub-steps per launch (20 launches per episode), all in one captured CUDA graph
-        sim.set_launch(args.epb, 50, True)
-        sim.set_actions_borrowed(acts_dev, hold)
-        sim.step(horizon)  # capture
-        torch.cuda.synchronize()
-        a.record(stream)
-        for _ in range(reps):
-            sim.set_actions_borrowed(acts_dev, hold)
-            sim.step(horizon)
-        b.record(stream)
-        torch.cuda.synchronize()
-        k50_ms = a.elapsed_time(b) / reps
-        line["per_step"] = {
-            "host_launched": n * horizon / (host_ms / 1e3),
-            "graph": n * horizon / (graph_ms_ps / 1e3),
-            "fused_sub_steps_only": n * horizon / (fused_ms_episode / 1e3),
-            "fused_over_host_launched": host_ms / fused_ms_episode,
-            "fused_over_graph": graph_ms_ps / fused_ms_episode,
-            "persistent_k50_graph": {
-                "env_steps_per_s": n * horizon / (k50_ms / 1e3),
-                "over_host_launched": host_ms / k50_ms, "over_graph": graph_ms_ps / k50_ms,
-                "launch": f"static grid, {args.epb} envs/block, 50 sub-steps per launch, "
-                          "one CUDA graph per episode"},
-            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                         "frac": ach / hbm, "bytes_per_env_step": bytes_per_launch // n,
-                         "launch_us": per_launch_s * 1e6, "traffic": ps_traffic,
-                         "peak_source": f"{peak_kind} hbm_gbs"}}
+        fused_ms = statistics.mean(graph_ms)
+        ps = bench_per_step(sim, acts_dev, args, peaks, peak_kind)
+        host_ms, ps_ms, k50_ms = ps.pop("host_ms"), ps.pop("graph_ms"), ps.pop("k50_ms")
+        # the autotuned persistent form, and the static k = 50 form in one CUDA graph, over the
+        # per-step form launched from the host and replayed from a graph
+        line["fused_over_per_step"] = {"host": host_ms / fused_ms, "graph": ps_ms / fused_ms,
+                                       "k50_over_host": host_ms / k50_ms,
+                                       "k50_over_graph": ps_ms / k50_ms}
+        line["per_step"] = ps
         cfg.apply(sim)
 
     sim.close()
+    if not args.no_per_step and world == 1:
+        line["per_step"]["1M"] = bench_per_step_large(vs, args, peaks, peak_kind)
     if not args.no_extra and world == 1:
         line["small_fleet"] = bench_small_fleet(vs)
         line["size_sweep"] = bench_size_sweep(vs)
@@ -545,7 +511,7 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_baseline(n, horizon, hold)
 
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        print(json.dumps(sig(line), separators=(",", ":")), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -563,6 +529,108 @@ def _time_episodes(fn, reps):
     b.record()
     torch.cuda.synchronize()
     return a.elapsed_time(b) / reps
+
+
+def _per_step_roofline(bytes_per_launch, launch_s, n, bound, peak, peak_kind, traffic):
+    ach = bytes_per_launch / launch_s / 1e9
+    return {"bound": bound, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_kind": peak_kind, "bytes_per_env_step": bytes_per_launch // n,
+            "launch_us": launch_s * 1e6, "traffic": traffic}
+
+
+def bench_per_step(sim, acts_dev, args, peaks, peak_kind):
+    """The headline fleet (65,536 envs) in the plain per-step form: one static-grid launch per
+    sub-step (128-register kernel, 16 warps/SM), host-launched and replayed from one CUDA graph,
+    and the persistent form as the scale configuration names it (static grid, 50 sub-steps per
+    launch, one graph).  Its working set (state, parameters, one command: 20 MB) stays in the
+    129 MB L2 from launch to launch (ncu, steady state: no DRAM reads, ~40 KB of DRAM writes
+    against 24.8 MB of L2 traffic per launch), so its roofline is the L2-resident copy measured
+    here, not HBM."""
+    import torch
+    n, horizon, hold = args.n_envs, args.horizon, args.hold
+    stream = torch.cuda.current_stream()
+    sim.set_actions_borrowed(acts_dev, hold)
+    sim.set_schedule(False, False)
+    sim.set_launch(args.epb, 1, False)
+    sim.randomize(7, 0.8, 1.2, 0.2, 0.3)
+    sim.reset()
+    for _ in range(50):
+        sim.step(1)
+    reps = 2
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def host_loop():
+        sim.set_actions_borrowed(acts_dev, hold)
+        for _ in range(horizon):
+            sim.step(1)
+
+    def graph_episode():
+        sim.set_actions_borrowed(acts_dev, hold)
+        sim.step(horizon)
+
+    host_ms = timed(host_loop)
+    sim.set_launch(args.epb, 1, True)
+    graph_episode()  # capture
+    graph_ms = timed(graph_episode)
+    sim.set_launch(args.epb, 50, True)
+    graph_episode()  # capture
+    k50_ms = timed(graph_episode)
+    launch_s = graph_ms / 1e3 / horizon
+    bytes_per_launch = n * (2 * STATE_BYTES[6] + PARAM_BYTES + CMD_BYTES[6])
+    l2 = l2_copy_gbs()
+    return {"host": n * horizon / (host_ms / 1e3), "graph": n * horizon / (graph_ms / 1e3),
+            "k50_graph": n * horizon / (k50_ms / 1e3),
+            "roofline": _per_step_roofline(bytes_per_launch, launch_s, n, "l2", l2,
+                                           "measured here (L2-resident copy)",
+                                           profiled_traffic("k_fleet_step1", n, 1)),
+            "host_ms": host_ms, "graph_ms": graph_ms, "k50_ms": k50_ms}
+
+
+def bench_per_step_large(vs, args, peaks, peak_kind, n=1 << 20, steps=200):
+    """The per-step form where its working set (312 MB per launch) is well past the L2: a
+    1,048,576-env randomised BlueROV2 fleet, one launch per sub-step replayed from a CUDA graph,
+    unpadded buffered commands; bounded by HBM bandwidth."""
+    import numpy as np
+    import torch
+    from paper_2410_14117_gb300 import inputs as I
+    from paper_2410_14117_gb300.sim import Sim
+
+    sim = Sim(n, np.zeros(n, np.int32), vs)
+    sim.set_schedule(False, False)
+    sim.set_launch(args.epb, 1, True)
+    sim.set_action_width(6)
+    sim.randomize(8, 0.8, 1.2, 0.2, 0.3)
+    sim.reset()
+    acts = torch.tensor(np.ascontiguousarray(I.commands(9, steps // args.hold, n, 6)[:, :, :6]),
+                        device="cuda")
+
+    def episode():
+        sim.set_actions_borrowed(acts, args.hold)
+        sim.step(steps)
+
+    ms = _time_episodes(episode, 3)
+    assert sim.sync() == 0
+    # the persistent form on the same fleet, for the ratio at this size (200-register static grid)
+    sim.set_schedule(False, True)
+    sim.set_launch(64, 1000, True)
+    fused_ms = _time_episodes(episode, 3)
+    sim.close()
+    launch_s = ms / 1e3 / steps
+    bytes_per_launch = n * (2 * STATE_BYTES[6] + PARAM_BYTES + CMD_BYTES[6])
+    return {"graph": n * steps / (ms / 1e3), "fused_over_graph": ms / fused_ms,
+            "roofline": _per_step_roofline(bytes_per_launch, launch_s, n, "hbm",
+                                           float(peaks.get("hbm_gbs", 6800.0)),
+                                           f"{peak_kind} hbm_gbs",
+                                           profiled_traffic("k_fleet_step1", n, 1))}
 
 
 def bench_small_fleet(vs, n=1024, horizon=500, reps=5):
@@ -587,24 +655,20 @@ def bench_small_fleet(vs, n=1024, horizon=500, reps=5):
 
     ms = _time_episodes(episode, reps)
     sim.close()
-    return {"workload": f"{n:,} nominal BlueROV2 envs, no current, {horizon} RK4 sub-steps",
-            "launch": dataclasses.asdict(launch),
-            "env_steps_per_s": n * horizon / (ms / 1e3)}
+    return {"rate": n * horizon / (ms / 1e3), "launch": launch_tag(launch)}
 
 
 def bench_size_sweep(vs, sizes=(4096, 16384, 65536, 262144, 1048576), horizon=1000, reps=3):
     """Config-2 sweep: the headline workload's sub-steps (randomised BlueROV2, current,
     procedural commands held 10) at each fleet size, with the launch the autotuner picks for
-    that size; per-sub-step time and the fraction of the FP32 ALU peak."""
+    that size.  Rows [envs, env-sub-steps/s, fraction of the FP32 ALU peak, launch]."""
     import numpy as np
     from paper_2410_14117_gb300.autotune import Autotuner
     from paper_2410_14117_gb300.sim import Sim
 
     peak = fp32_alu_peak_tflops(2070.0)
     tuner = Autotuner(horizon=horizon, reps=2)
-    out = {"workload": f"BlueROV2, parameters x U[0.8,1.2], current N(0,0.2), {horizon:,} "
-                       "sub-steps per call, procedural commands held 10; autotuned per size",
-           "sizes": []}
+    rows = []
     for n in sizes:
         types = np.zeros(n, np.int32)
         cfg = tuner.pick(n, types, vs)
@@ -617,49 +681,42 @@ def bench_size_sweep(vs, sizes=(4096, 16384, 65536, 262144, 1048576), horizon=10
         assert sim.sync() == 0
         sim.close()
         rate = n * horizon / (ms / 1e3)
-        out["sizes"].append({"n_envs": n, "env_substeps_per_s": rate,
-                             "us_per_substep": ms * 1e3 / horizon,
-                             "alu_frac": rate * FLOPS_PER_ENV_STEP[6] / (peak * 1e12),
-                             "launch": dataclasses.asdict(cfg)})
-    return out
+        rows.append([n, rate, rate * FLOPS_PER_ENV_STEP[6] / (peak * 1e12), launch_tag(cfg)])
+    return rows
 
 
 def bench_mixed_fleet(vs, n=262144, horizon=500, reps=5):
     """Mixed BlueROV2 / BlueROV2-Heavy fleet, groups log-uniform in [1, 32768] (60/40 types),
     randomised; autotuned launch; against a homogeneous BlueROV2 fleet of the same size."""
     import numpy as np
-    import torch
     from paper_2410_14117_gb300 import inputs as I
     from paper_2410_14117_gb300.autotune import Autotuner
     from paper_2410_14117_gb300.sim import Sim
 
     out = {}
     tuner = Autotuner(horizon=horizon, reps=2)
-    for name, types in (("mixed", I.mixed_fleet(3, n)), ("homogeneous", np.zeros(n, np.int32))):
+    for name, types in (("mixed", I.mixed_fleet(3, n)), ("homog", np.zeros(n, np.int32))):
         cfg = tuner.pick(n, types, vs)
         sim = Sim(n, types, vs)
         cfg.apply(sim)
         sim.randomize(1234, 0.8, 1.2, 0.2, 0.3)
         sim.reset()
         sim.set_procedural_actions(5678, 10)
-
         ms = _time_episodes(lambda: sim.step(horizon), reps)
         assert sim.sync() == 0
-        out[name] = {"env_steps_per_s": n * horizon / (ms / 1e3), "launch": dataclasses.asdict(cfg)}
+        out[name] = n * horizon / (ms / 1e3)
+        out[name + "_launch"] = launch_tag(cfg)
         if name == "mixed":
-            runs = np.flatnonzero(np.diff(types)) + 1
-            out[name]["groups"] = int(runs.size + 1)
-            out[name]["heavy_fraction"] = float((types == 1).mean())
+            out["groups"] = int(np.count_nonzero(np.diff(types)) + 1)
+            out["heavy_frac"] = float((types == 1).mean())
         sim.close()
-    out["workload"] = (f"{n:,} envs, {horizon} RK4 sub-steps, procedural commands held 10 "
-                       "sub-steps; groups log-uniform in [1, 32768], 60% BlueROV2 / 40% Heavy")
-    out["mixed_over_homogeneous"] = (out["mixed"]["env_steps_per_s"] /
-                                     out["homogeneous"]["env_steps_per_s"])
+    out["ratio"] = out["mixed"] / out["homog"]
     return out
 
 
 def bench_adjoint(vs, n=4096, T=200, C=20, reps=5):
-    """Differentiable rollout: forward (recording + checkpoints) and hand-written adjoint."""
+    """Differentiable rollout: forward (recording + checkpoints) and hand-written adjoint,
+    4,096 BlueROV2 envs, 200 sub-steps, checkpoints every 20, MSE on the trajectory."""
     import numpy as np
     import torch
     from paper_2410_14117_gb300 import inputs as I
@@ -669,7 +726,7 @@ def bench_adjoint(vs, n=4096, T=200, C=20, reps=5):
 
     sim = Sim(n, np.zeros(n, np.int32), vs)
     # the forward's checkpoint segments are launches of C sub-steps: tune for that call size
-    launch = Autotuner(horizon=T, reps=2, k_per_call=C).tune(sim, vs)
+    Autotuner(horizon=T, reps=2, k_per_call=C).tune(sim, vs)
     sim.randomize(1234, 0.8, 1.2, 0.2, 0.3)
     params = sim.get_params()
     coeffs = params[:, COEF_SLICE].clone().requires_grad_(True)
@@ -681,29 +738,18 @@ def bench_adjoint(vs, n=4096, T=200, C=20, reps=5):
         return rollout(sim, coeffs, acts, s0, 10, T, C)
 
     f_ms = _time_episodes(fwd, reps)
-    traj = fwd()
-    loss = ((traj - target) ** 2).mean()
 
     def fb():
         tr = rollout(sim, coeffs, acts, s0, 10, T, C)
-        g = torch.autograd.grad(((tr - target) ** 2).mean(), (coeffs, acts))
-        return g
+        return torch.autograd.grad(((tr - target) ** 2).mean(), (coeffs, acts))
 
     fb_ms = _time_episodes(fb, reps)  # backward kernel chosen by fleet size
     sim.set_adjoint_mode(1)            # one warp per 32 envs, for comparison
     fb1_ms = _time_episodes(fb, reps)
     sim.set_adjoint_mode(0)
     sim.close()
-    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
-    split = (n + 31) // 32 <= 2 * n_sm
-    return {"workload": f"{n:,} BlueROV2 envs, {T} RK4 sub-steps, checkpoints every {C}, "
-                        "MSE on the trajectory",
-            "launch": dataclasses.asdict(launch),
-            "backward_kernel": ("two warps per 32 envs (segment re-run and stage records | "
-                                "transposes)" if split else "one warp per 32 envs"),
-            "forward_ms": f_ms, "forward_backward_ms": fb_ms,
-            "backward_over_forward": (fb_ms - f_ms) / f_ms,
-            "forward_backward_one_warp_ms": fb1_ms, "loss": float(loss.detach())}
+    return {"fwd_ms": f_ms, "fwd_bwd_ms": fb_ms, "bwd_over_fwd": (fb_ms - f_ms) / f_ms,
+            "fwd_bwd_1warp_ms": fb1_ms}
 
 
 def bench_task(vs, n=65536, k=10, steps=100, reps=3):
@@ -716,7 +762,7 @@ def bench_task(vs, n=65536, k=10, steps=100, reps=3):
 
     types = np.zeros(n, np.int32)
     sim = Sim(n, types, vs)
-    launch = Autotuner(horizon=k * 10, reps=2, k_per_call=k).tune(sim, vs)
+    Autotuner(horizon=k * 10, reps=2, k_per_call=k).tune(sim, vs)
     sim.randomize(11, 0.8, 1.2, 0.2, 0.3)
     sim.reset()
     sim.set_procedural_actions(12, k)
@@ -745,16 +791,9 @@ def bench_task(vs, n=65536, k=10, steps=100, reps=3):
     plain_ms = _time_episodes(plain, reps)
     observe_ms = _time_episodes(lambda: [sim.task_step(0) for _ in range(steps)], reps)
     sim.close()
-    return {"workload": f"{n:,} BlueROV2 envs, circle tracking (3 look-ahead points, auto-reset"
-                        " after 1000 sub-steps or 3 m error), spawn within 0.5 m of the "
-                        f"reference, {steps} task steps of {k} sub-steps",
-            "launch": dataclasses.asdict(launch),
-            "resets_per_task_step": resets,
-            "observe_only_us": observe_ms / steps * 1e3,
-            "env_substeps_per_s": n * k * steps / (task_ms / 1e3),
-            "task_steps_per_s": n * steps / (task_ms / 1e3),
-            "plain_env_substeps_per_s": n * k * steps / (plain_ms / 1e3),
-            "task_overhead": task_ms / plain_ms - 1.0}
+    return {"rate": n * k * steps / (task_ms / 1e3), "plain": n * k * steps / (plain_ms / 1e3),
+            "step_us": task_ms / steps * 1e3, "observe_us": observe_ms / steps * 1e3,
+            "resets": resets}
 
 
 def _count_resets(sim, k, steps):
@@ -768,7 +807,8 @@ def bench_split(vs, n=65536, horizon=1000, n_acc=4096, reps=3):
     """The paper's split integration (§METHOD: engine-integrated rigid body, hydrodynamic term
     as an external force with the previous sub-step's acceleration in its added-mass part)
     against the coupled RK4 step: throughput, accuracy at h = 0.01 against the coupled equation
-    at h = 0.001, and how many randomised envs the lagged added mass destabilises."""
+    at h = 0.001 (4,096 envs, added mass halved so that it is stable, 1 s), and the share of
+    randomised envs the lagged added mass destabilises."""
     import numpy as np
     import torch
     from paper_2410_14117_gb300 import inputs as I
@@ -784,9 +824,7 @@ def bench_split(vs, n=65536, horizon=1000, n_acc=4096, reps=3):
         sim.reset()
         return sim
 
-    out = {"workload": f"{n:,} BlueROV2 envs (parameters x U[0.8,1.2], current N(0,0.2)), "
-                       "procedural commands held 0.1 s; accuracy on 4,096 envs with added mass "
-                       "halved (stable), 1 s against coupled RK4 at h = 0.001"}
+    out = {}
     # throughput, added mass halved so that every env stays finite
     sim = fleet(n, 1234, 0.5)
     sim.set_launch(128, horizon, False)
@@ -796,8 +834,8 @@ def bench_split(vs, n=65536, horizon=1000, n_acc=4096, reps=3):
     sim.set_launch(128, 50, True)
     coupled_ms = _time_episodes(lambda: sim.step(horizon), reps)
     sim.close()
-    out["split_env_substeps_per_s"] = n * horizon / (split_ms / 1e3)
-    out["coupled_static_env_substeps_per_s"] = n * horizon / (coupled_ms / 1e3)
+    out["split"] = n * horizon / (split_ms / 1e3)
+    out["coupled"] = n * horizon / (coupled_ms / 1e3)
     # accuracy: the same commands in time (held 0.1 s) at h = 0.01 and the h = 0.001 reference
     res = {}
     for name, dt, hold, steps, split in (("ref", 0.001, 100, 1000, False),
@@ -814,9 +852,7 @@ def bench_split(vs, n=65536, horizon=1000, n_acc=4096, reps=3):
         sim.close()
     for name in ("coupled", "split"):
         dp = np.abs(res[name][:, 0:3] - res["ref"][:, 0:3]).max(axis=1)
-        dv = np.abs(res[name][:, 7:13] - res["ref"][:, 7:13]).max(axis=1)
-        out[f"{name}_pos_err_m"] = {"median": float(np.median(dp)), "max": float(dp.max())}
-        out[f"{name}_vel_err"] = {"median": float(np.median(dv)), "max": float(dv.max())}
+        out[f"{name}_pos_err_m"] = [float(np.median(dp)), float(dp.max())]
     # stability with the randomised nominal added mass
     sim = fleet(n_acc, 99, 1.0)
     p = sim.get_params().double().cpu().numpy()
@@ -827,29 +863,23 @@ def bench_split(vs, n=65536, horizon=1000, n_acc=4096, reps=3):
     st = sim.get_state().double().cpu().numpy()
     sim.close()
     blown = ~np.isfinite(st).all(axis=1) | (np.abs(st[:, 7:13]).max(axis=1) > 100.0)
-    predicted = ratio.max(axis=1) > 1.0
-    out["stability"] = {"envs": n_acc, "sub_steps": 1000,
-                        "predicted_unstable (added mass > rigid-body mass in some axis)":
-                            float(predicted.mean()),
-                        "diverged": float(blown.mean()),
-                        "diverged_among_predicted_stable": float(blown[~predicted].mean())
-                        if (~predicted).any() else None}
+    out["unstable_pred"] = float((ratio.max(axis=1) > 1.0).mean())
+    out["diverged"] = float(blown.mean())
     return out
 
 
 def bench_full_hydro(vs, n=65536, horizon=1000, reps=3):
-    """Full (non-diagonal) added mass and linear damping with randomised centres of gravity:
-    the general path with the off-diagonal coefficients staged per block, against the
-    diagonal-mass path, same fleet size and workload."""
+    """Full (non-diagonal) added mass and linear damping with randomised centres of gravity
+    (r_g ~ U[-2, 2] cm per axis, off-diagonal M_A and D_l at 15 % coupling): the general path
+    with the off-diagonal coefficients staged per block, against the diagonal-mass path, same
+    fleet size and workload."""
     import numpy as np
     import torch
     from paper_2410_14117_gb300 import inputs as I
     from paper_2410_14117_gb300.sim import Sim
 
-    out = {"workload": f"{n:,} BlueROV2 envs, parameters x U[0.8,1.2], current N(0,0.2), "
-                       f"{horizon:,} sub-steps, procedural commands held 10; full: r_g ~ "
-                       "U[-2, 2] cm per axis and off-diagonal M_A, D_l at 15 % coupling"}
-    for name in ("diagonal", "full"):
+    out = {}
+    for name in ("diag", "full"):
         sim = Sim(n, np.zeros(n, np.int32), vs)
         sim.set_launch(128, horizon, True)
         if name == "full":
@@ -864,8 +894,8 @@ def bench_full_hydro(vs, n=65536, horizon=1000, reps=3):
         ms = _time_episodes(lambda: sim.step(horizon), reps)
         assert sim.sync() == 0
         sim.close()
-        out[f"{name}_env_substeps_per_s"] = n * horizon / (ms / 1e3)
-    out["full_over_diagonal"] = out["full_env_substeps_per_s"] / out["diagonal_env_substeps_per_s"]
+        out[name] = n * horizon / (ms / 1e3)
+    out["ratio"] = out["full"] / out["diag"]
     return out
 
 
@@ -877,42 +907,38 @@ SERVE_K = 100
 
 def bench_serve(vs, seconds, rate=200.0):
     """Poisson arrivals of rollout jobs (envs log-uniform [64, 65536], horizon U[50, 1000],
-    type 50/50, randomised parameters and currents) served with continuous batching under a
-    120 GB budget by the native request loop (mg_server_*), and the same stream served one job
-    at a time; each server first serves one second of the same job mix (its record memory pool
-    warm), as the measured stream's own arrivals would after a while."""
+    type 50/50, randomised parameters and currents, trajectory recorded) served with continuous
+    batching under a 120 GB budget by the native request loop (mg_server_*), and the same stream
+    served one job at a time; each server first serves one second of the same job mix (its
+    record memory pool warm), as the measured stream's own arrivals would after a while.  Then
+    the same job mix at 10x the arrival rate."""
     from paper_2410_14117_gb300 import inputs as I
     from paper_2410_14117_gb300.serve import NativeServer, Server, requests_from_specs
 
     specs = I.serving_jobs(42, seconds, rate_hz=rate)
-    out = {"workload": f"Poisson {rate:.0f} req/s for {seconds:.1f} s ({len(specs)} jobs), envs "
-                       "log-uniform [64, 65536], horizon U[50, 1000], 50/50 BlueROV2/Heavy, "
-                       "trajectory recorded (13 floats per env-step), 120 GB budget, "
-                       f"{SERVE_K} sub-steps per tick",
-           "loop": "native (mg_server_*)"}
+    out = {"jobs": len(specs)}
+    keys = ("p50_ms", "p99_ms", "env_steps_per_s")
     for mode in ("batched", "serial"):
         srv = NativeServer(vs, budget_bytes=120e9, capacity_envs=8 << 20, k=SERVE_K)
         srv.run(requests_from_specs(I.serving_jobs(7, 1.0, rate_hz=rate)), mode=mode)
         _, st = srv.run(requests_from_specs(specs), mode=mode)
         srv.close()
-        out[mode] = st
+        out[mode] = [st[k] for k in keys]
     # the same stream through the Python request loop (Server), batched
     srv = Server(vs, budget_bytes=120e9, capacity_envs=8 << 20, k=SERVE_K)
     srv.run(requests_from_specs(I.serving_jobs(7, 1.0, rate_hz=rate)), mode="batched")
     _, st = srv.run(requests_from_specs(specs), mode="batched")
     srv.close()
-    out["python_loop_batched"] = {k: st[k] for k in ("p50_ms", "p99_ms", "env_steps_per_s")}
-    # the same job mix at 10x the arrival rate: continuous batching against one job at a time
+    out["python_batched"] = [st[k] for k in keys]
     hot = I.serving_jobs(43, seconds / 4, rate_hz=10 * rate)
-    out["stress"] = {"rate_hz": 10 * rate, "jobs": len(hot)}
+    out["stress_jobs"] = len(hot)
     for mode in ("batched", "serial"):
         srv = NativeServer(vs, budget_bytes=120e9, capacity_envs=8 << 20, k=SERVE_K)
         srv.run(requests_from_specs(I.serving_jobs(8, seconds / 4, rate_hz=10 * rate)),
                 mode=mode)
         _, st = srv.run(requests_from_specs(hot), mode=mode)
         srv.close()
-        out["stress"][mode] = {k: st[k] for k in ("p50_ms", "p99_ms", "env_steps_per_s",
-                                                  "max_queue_depth")}
+        out["stress_" + mode] = [st[k] for k in keys]
     return out
 
 

@@ -138,7 +138,9 @@ mg_status mg_set_stream(mg_sim *sim, void *cuda_stream);
  * would.  Default 0. */
 mg_status mg_set_env_id_offset(mg_sim *sim, int64_t offset);
 
-/* MG_MODEL_* bits.  Default 0 (full model). */
+/* MG_MODEL_* bits.  Default 0 (full model).  The diagonal-mass kernels fold the current term
+ * into their coefficients, so with MG_MODEL_NO_CURRENT_ACCEL every fleet steps on the general
+ * path (same results within rounding, more arithmetic per sub-step). */
 mg_status mg_set_model_flags(mg_sim *sim, uint32_t flags);
 
 /* Sub-step size dt in seconds (default 0.01).  MG_EINVAL unless 0 < dt <= 1. */
@@ -173,15 +175,6 @@ mg_status mg_set_schedule(mg_sim *sim, int32_t work_queue, int32_t wide, int32_t
  * a chunk's run time makes waits give up on purpose.  MG_EINVAL if polls > 2^30. */
 #define MG_WAIT_POLLS_DEFAULT 4194304u
 mg_status mg_set_wait_limit(mg_sim *sim, uint32_t polls);
-
-/* Packed arithmetic for the static-grid diagonal-mass step (every env with r_g = 0 and no
- * off-diagonal extension; other fleets, the work-queue schedule, mg_step_record, the fused last
- * launch of mg_task_step, the adjoint, the split step and the pool use the one-env-per-thread
- * kernels).  packed != 0: each thread advances two envs and issues every operation of the RK4
- * sub-step of Eq. 1 (§METHOD) as one FP32x2 instruction over the pair (sm_100+: a packed FMA is
- * two correctly rounded FMAs), so results are bit-identical to the one-env-per-thread kernels.
- * A block of envs_per_block threads covers up to 2 x envs_per_block envs.  Default 0. */
-mg_status mg_set_packed(mg_sim *sim, int32_t packed);
 
 /* Domain randomisation (§METHOD; §EXPERIMENTS "supports domain randomization"): per env, draws
  * from Philox4x32-10 keyed by (seed, env id + offset), then builds M = M_RB + M_A in FP64 and
@@ -220,7 +213,7 @@ mg_status mg_get_params(mg_sim *sim, float *out);
  * x [n][MG_NXPARAM] (host or device; layout above), or clear it (x = NULL: the diagonal model).
  * The mass matrices are re-inverted in FP64 with the off-diagonal added mass; a fleet with a
  * non-zero extension steps on the general path (static grid: mg_set_schedule's work queue is
- * not used for it; mg_step_split and mg_rollout_backward reject it).  mg_randomize and
+ * not used for it; mg_step_split rejects it).  mg_randomize and
  * mg_set_params keep the extension.  Synchronous.  Errors: MG_EINVAL, MG_ENOMEM, MG_ENOTSPD
  * (stored, but some M_RB + M_A is not positive definite), MG_ECUDA. */
 mg_status mg_set_hydro_offdiag(mg_sim *sim, const float *x);
@@ -316,9 +309,12 @@ mg_status mg_rollout_forward(mg_sim *sim, int32_t T, int32_t C, float *traj, flo
  * (record entries 4..21, §METHOD Eq. 1 hydrodynamic term); adds the gradient with respect to the
  * buffered actions (Eq. 3) into dact, device [n_seg][n][w] (w the action width; may be NULL);
  * writes the gradient with respect to the start state into dstate0, device [n][MG_NSTATE] (may
- * be NULL).
- * Parameters and actions must be those of the forward; the sim's state is not read or changed.
- * Errors: MG_EINVAL (bad sizes, host buffers, a fleet with r_g != 0, procedural actions). */
+ * be NULL).  Every fleet the step covers: diagonal-mass fleets, and on the general path fleets
+ * with off-centre gravity (r_g != 0) and / or the off-diagonal extension, where a diagonal
+ * coefficient M_A,jj also enters the full M = M_RB + M_A (its share of the gradient is
+ * -(M^-1 g)_j nu'_j for the loss adjoint g of nu').  Parameters, extension and actions must be
+ * those of the forward; the sim's state is not read or changed.
+ * Errors: MG_EINVAL (bad sizes, host buffers, procedural actions). */
 mg_status mg_rollout_backward(mg_sim *sim, int32_t T, int32_t C, const float *ckpt,
                               const float *dtraj, int64_t step0, float *dcoef, float *dact,
                               float *dstate0);

@@ -85,7 +85,6 @@ SIGNATURES = {
     "mg_set_launch": [_P, _I32, _I32, _I32],
     "mg_set_schedule": [_P, _I32, _I32, _I32],
     "mg_set_wait_limit": [_P, ctypes.c_uint32],
-    "mg_set_packed": [_P, _I32],
     "mg_randomize": [_P, _U64, ctypes.POINTER(Ranges)],
     "mg_randomize_prefetch": [_P, _U64, ctypes.POINTER(Ranges)],
     "mg_set_adjoint_mode": [_P, _I32],

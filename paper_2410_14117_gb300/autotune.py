@@ -26,23 +26,19 @@ class LaunchConfig:
     steps_per_launch: int  # static: sub-steps per launch; queue: sub-steps per unit (chunk)
     wide: bool = True      # 200-register diagonal-mass kernel (queue; static grid)
     warps_per_sm: int = 0  # queue: resident-warp cap (0 = as many as fit)
-    packed: bool = False   # static: two envs per thread, packed FP32x2 arithmetic (diag. mass)
 
     def apply(self, sim: Sim, use_graph: bool = True):
         sim.set_launch(self.envs_per_block, self.steps_per_launch, use_graph)
         sim.set_schedule(self.schedule == "queue", self.wide, self.warps_per_sm)
-        sim.set_packed(self.packed)
 
 
 DEFAULT_CANDIDATES = (
-    [LaunchConfig("static", epb, spl, False) for epb in (32, 64, 128, 256) for spl in (50, 1000)]
-    # the 200-register static kernel: for small fleets (a warp per scheduler or fewer)
-    + [LaunchConfig("static", epb, spl, True) for epb in (32, 64) for spl in (50, 1000)]
+    # the static grid with the 128-register and the 200-register diagonal-mass kernel
+    [LaunchConfig("static", epb, spl, wide) for wide in (False, True) for epb in (32, 64, 128, 256)
+     for spl in (50, 1000)]
     + [LaunchConfig("queue", 128, ch, wide, wps)
        for wide, wps in ((False, 16), (False, 12), (True, 12), (True, 8))
        for ch in (25, 50, 100)]
-    + [LaunchConfig("static", epb, spl, packed=True) for epb in (32, 64, 128)
-       for spl in (50, 1000)]
 )
 
 

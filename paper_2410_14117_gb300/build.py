@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libmg.so")
 
 SOURCES = ["mg_api.cu", "mg_step.cu", "mg_setup.cu", "mg_adjoint.cu", "mg_pool.cu", "mg_task.cu",
-           "mg_split.cu", "mg_pair.cu", "mg_serve.cu"]
+           "mg_split.cu", "mg_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-I" + INCLUDE, "-I" + CSRC]

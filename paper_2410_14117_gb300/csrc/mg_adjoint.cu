@@ -12,10 +12,16 @@
 // rhs(), written out below).  It is the adjoint of the discrete map the forward computes, so it
 // matches finite differences of the rollout itself, not of the continuous equations.
 //
-// Diagonal-mass fleets only (r_g = 0): the coefficient chain rule uses M^-1 = diag(1 / M_jj).
+// Two parameter paths, as the forward has:
+//   - diagonal mass (r_g = 0, no off-diagonal extension): M^-1 = diag(1 / M_jj);
+//   - general (GEN): off-centre gravity (the m r_g coupling of M_RB and C_RB, off-diagonal
+//     I_o) and the off-diagonal added mass and linear damping of the extension record (zeros
+//     when the fleet has none), with the full M^-1.  A diagonal coefficient theta = M_A,jj enters
+//     M = M_RB + M_A, so nu' = M^-1 f gets d nu'/d theta = -M^-1 e_j nu'_j, whose contribution to
+//     the gradient is -(M^-1 g)_j nu'_j for the loss adjoint g of nu' (M^-1 is symmetric).
 #include <type_traits>
 
-#include "mg_device.cuh"
+#include "mg_advance.cuh"
 
 namespace mg {
 
@@ -24,8 +30,29 @@ namespace {
 constexpr int kAdjThreads = 128;
 
 struct Grad {
-  float ma[3], J[3], mi[6], dl[6], dq[6];
+  float ma[3], J[3], mv[6], dl[6], dq[6];  // mv: the M_A,jj gradient through M^-1
 };
+
+// What the adjoint reads for one env: the loaded parameters (transposes), the coefficients the
+// forward step used (re-running it bit for bit) and, on the general path, the env's off-diagonal
+// hydrodynamic coefficients (a row of MG_NXPARAM floats in shared memory).
+template <bool GEN>
+struct AdjEnv {
+  Par<!GEN> P;
+  Coef<!GEN> F;
+  const float *xh;
+};
+
+// Off-diagonal entries of the extension record (layout of mg.h): M_A above its diagonal
+// (01 02 03 04 05 12 13 14 15 23 24 25 34 35 45, mirrored below), then D_l's off-diagonal
+// entries row by row (5 per row).
+__device__ __forceinline__ float xa(const float *xh, int i, int j) {
+  const int a = i < j ? i : j, b = i < j ? j : i;
+  return xh[5 * a - a * (a - 1) / 2 + (b - a - 1)];
+}
+__device__ __forceinline__ float xd(const float *xh, int i, int j) {
+  return xh[15 + 5 * i + (j < i ? j : j - 1)];
+}
 
 // Every multiply-add of the adjoint code below is written as an explicit fmaf, so the compiler
 // forms no fused operation of its own: the results do not depend on the surrounding code the
@@ -42,13 +69,33 @@ __device__ __forceinline__ void cross_vjp(const float a[3], const float b[3], co
   gb[2] = fmaf(gc[0], a[1], fmaf(-gc[1], a[0], gb[2]));
 }
 
+// Packed symmetric M^-1 (general path) times x.
+__device__ __forceinline__ void minv_apply(const ParGen &P, const float x[6], float y[6]) {
+  const float *o = P.mo;  // 01 02 03 04 05 12 13 14 15 23 24 25 34 35 45
+  y[0] = fmaf(P.mi[0], x[0], fmaf(o[0], x[1], fmaf(o[1], x[2], fmaf(o[2], x[3],
+         fmaf(o[3], x[4], o[4] * x[5])))));
+  y[1] = fmaf(o[0], x[0], fmaf(P.mi[1], x[1], fmaf(o[5], x[2], fmaf(o[6], x[3],
+         fmaf(o[7], x[4], o[8] * x[5])))));
+  y[2] = fmaf(o[1], x[0], fmaf(o[5], x[1], fmaf(P.mi[2], x[2], fmaf(o[9], x[3],
+         fmaf(o[10], x[4], o[11] * x[5])))));
+  y[3] = fmaf(o[2], x[0], fmaf(o[6], x[1], fmaf(o[9], x[2], fmaf(P.mi[3], x[3],
+         fmaf(o[12], x[4], o[13] * x[5])))));
+  y[4] = fmaf(o[3], x[0], fmaf(o[7], x[1], fmaf(o[10], x[2], fmaf(o[12], x[3],
+         fmaf(P.mi[4], x[4], o[14] * x[5])))));
+  y[5] = fmaf(o[4], x[0], fmaf(o[8], x[1], fmaf(o[11], x[2], fmaf(o[13], x[3],
+         fmaf(o[14], x[4], P.mi[5] * x[5])))));
+}
+
 // gs += (d rhs / d s)^T gd; parameter and command adjoints accumulated into G and gcs.  The
-// forward quantities are recomputed from the formulas of rhs() (diagonal mass); gd.q is the
-// adjoint of d.q = q (x) (0, w) (the doubled quaternion rate rhs() stores).
-template <int MT>
-__device__ void rhs_vjp(const St<MT> &s, const float (&cs)[MT], const ParDiag &P,
+// forward quantities are recomputed from Eq. 1 in the general path's Kirchhoff form (the
+// diagonal-mass path drops the terms that vanish with r_g = 0 and diagonal M_A, D_l); gd.q is
+// the adjoint of d.q = q (x) (0, w) (the doubled quaternion rate rhs() stores).
+template <int MT, bool GEN>
+__device__ void rhs_vjp(const St<MT> &s, const float (&cs)[MT], const AdjEnv<GEN> &A,
                         const float4 *gdir, const float4 *garm, int nt, bool current_accel,
                         const St<MT> &gd, St<MT> &gs, Grad &G, float (&gcs)[MT]) {
+  const auto &P = A.P;
+  const float *xh = A.xh;
   // ---------------- forward recomputation
   float t[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -73,37 +120,75 @@ __device__ void rhs_vjp(const St<MT> &s, const float (&cs)[MT], const ParDiag &P
   const float v[3] = {s.v[0], s.v[1], s.v[2]}, w[3] = {s.w[0], s.w[1], s.w[2]};
   const float vc[3] = {P.vc0, P.vc1, P.vc2}, ma[3] = {P.ma0, P.ma1, P.ma2};
   const float J[3] = {P.J0, P.J1, P.J2}, G3[3] = {P.G0, P.G1, P.G2};
-  float cb[3], r[3], qm[3], h[3], k[3], a[3];
+  float cb[3], r[3], qm[3], h[3], k[3], c[3] = {0.f, 0.f, 0.f}, am[3] = {0.f, 0.f, 0.f};
+  float mrg[3] = {0.f, 0.f, 0.f};
+  if constexpr (GEN) {
+    mrg[0] = P.mrg0; mrg[1] = P.mrg1; mrg[2] = P.mrg2;
+  }
   for (int i = 0; i < 3; ++i)
     cb[i] = fmaf(R[2][i], vc[2], fmaf(R[1][i], vc[1], R[0][i] * vc[0]));
   for (int i = 0; i < 3; ++i) {
     r[i] = v[i] - cb[i];
     qm[i] = ma[i] * r[i];
-    h[i] = fmaf(P.m, v[i], qm[i]);
     k[i] = J[i] * w[i];
   }
-  a[0] = fmaf(w[1], cb[2], -w[2] * cb[1]);
-  a[1] = fmaf(w[2], cb[0], -w[0] * cb[2]);
-  a[2] = fmaf(w[0], cb[1], -w[1] * cb[0]);
+  const float nur[6] = {r[0], r[1], r[2], w[0], w[1], w[2]};
+  if constexpr (GEN) {
+    // off-diagonal added mass in the momenta; w x m r_g; off-diagonal I_o w + m r_g x v
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        if (j != i) qm[i] = fmaf(xa(xh, i, j), nur[j], qm[i]);
+        if (j != 3 + i) k[i] = fmaf(xa(xh, 3 + i, j), nur[j], k[i]);
+      }
+    am[0] = fmaf(w[1], mrg[2], -w[2] * mrg[1]);
+    am[1] = fmaf(w[2], mrg[0], -w[0] * mrg[2]);
+    am[2] = fmaf(w[0], mrg[1], -w[1] * mrg[0]);
+    k[0] = fmaf(P.Ixy, w[1], fmaf(P.Ixz, w[2], fmaf(mrg[1], v[2], fmaf(-mrg[2], v[1], k[0]))));
+    k[1] = fmaf(P.Ixy, w[0], fmaf(P.Iyz, w[2], fmaf(mrg[2], v[0], fmaf(-mrg[0], v[2], k[1]))));
+    k[2] = fmaf(P.Ixz, w[0], fmaf(P.Iyz, w[1], fmaf(mrg[0], v[1], fmaf(-mrg[1], v[0], k[2]))));
+  }
+  for (int i = 0; i < 3; ++i) h[i] = fmaf(P.m, v[i], qm[i]) + am[i];
+  if (current_accel) {
+    c[0] = fmaf(w[1], cb[2], -w[2] * cb[1]);
+    c[1] = fmaf(w[2], cb[0], -w[0] * cb[2]);
+    c[2] = fmaf(w[0], cb[1], -w[1] * cb[0]);
+  }
   const float e[3] = {R[2][0], R[2][1], R[2][2]};
-  // translational: kT t + (W - B) e - w x h - (Dl + Dq |r|) r [- M_A (w x v_c^b)]
+  // translational: kT t + (W - B) e - w x h - (Dl + Dq |r|) r [- M_A [w x v_c^b; 0]]
+  //                [- off-diagonal D_l nu_r]
   float f[6];
   for (int i = 0; i < 3; ++i) {
     const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
     float x = fmaf(P.kT, t[i], P.wb * e[i]);
     x = fmaf(-w[i1], h[i2], fmaf(w[i2], h[i1], x));
-    f[i] = fmaf(-fmaf(P.dq[i], fabsf(r[i]), P.dl[i]), r[i], x);
+    x = fmaf(-fmaf(P.dq[i], fabsf(r[i]), P.dl[i]), r[i], x);
+    f[i] = fmaf(-ma[i], c[i], x);
   }
-  if (current_accel)
-    for (int i = 0; i < 3; ++i) f[i] = fmaf(-ma[i], a[i], f[i]);
-  // rotational: kT t' - r x Q1 - w x k - (Dl + Dq |w|) w + G x e
+  // rotational: kT t' - r x Q1 - w x k [- v x (w x m r_g)] - (Dl + Dq |w|) w + G x e
+  //             [- M_A [w x v_c^b; 0]] [- off-diagonal D_l nu_r]
   for (int i = 0; i < 3; ++i) {
     const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
     float x = fmaf(P.kT, t[3 + i], fmaf(-r[i1], qm[i2], r[i2] * qm[i1]));
     x = fmaf(-w[i1], k[i2], fmaf(w[i2], k[i1], x));
+    if constexpr (GEN) x = fmaf(-v[i1], am[i2], fmaf(v[i2], am[i1], x));
     x = fmaf(-fmaf(P.dq[3 + i], fabsf(w[i]), P.dl[3 + i]), w[i], x);
     f[3 + i] = fmaf(G3[i1], e[i2], fmaf(-G3[i2], e[i1], x));
   }
+  if constexpr (GEN) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        if (j < 3 && j != i) f[i] = fmaf(-xa(xh, i, j), c[j], f[i]);
+        if (j != i) f[i] = fmaf(-xd(xh, i, j), nur[j], f[i]);
+      }
+  }
+  float nud[6];  // nu' = M^-1 f
+  if constexpr (GEN) minv_apply(P, f, nud);
+  else
+    for (int j = 0; j < 6; ++j) nud[j] = P.mi[j] * f[j];
 
   // ---------------- reverse
   // lag: d.n_i = cs_i - n_i / tau_m
@@ -113,22 +198,36 @@ __device__ void rhs_vjp(const St<MT> &s, const float (&cs)[MT], const ParDiag &P
     gcs[i] += gd.n[i];
     gs.n[i] = fmaf(-P.itau, gd.n[i], gs.n[i]);
   }
-  // nu' = M^-1 f
+  // nu' = M^-1 f: gf = M^-1 g (symmetric), and M_jj's share -gf_j nu'_j
   const float gnu[6] = {gd.v[0], gd.v[1], gd.v[2], gd.w[0], gd.w[1], gd.w[2]};
   float gf[6], gt[6];
+  if constexpr (GEN) minv_apply(P, gnu, gf);
+  else
+    for (int j = 0; j < 6; ++j) gf[j] = P.mi[j] * gnu[j];
   for (int j = 0; j < 6; ++j) {
-    gf[j] = P.mi[j] * gnu[j];
-    G.mi[j] = fmaf(f[j], gnu[j], G.mi[j]);
+    G.mv[j] = fmaf(-gf[j], nud[j], G.mv[j]);
     gt[j] = P.kT * gf[j];
   }
   float gw[3] = {0.f, 0.f, 0.f}, gv[3] = {0.f, 0.f, 0.f}, gr[3] = {0.f, 0.f, 0.f};
   float gh[3] = {0.f, 0.f, 0.f}, gk[3] = {0.f, 0.f, 0.f}, gqm[3] = {0.f, 0.f, 0.f};
-  float gcb[3] = {0.f, 0.f, 0.f}, ge[3] = {0.f, 0.f, 0.f};
+  float gcb[3] = {0.f, 0.f, 0.f}, ge[3] = {0.f, 0.f, 0.f}, gc[3] = {0.f, 0.f, 0.f};
+  float gam[3] = {0.f, 0.f, 0.f}, gnur[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if constexpr (GEN) {
+    // off-diagonal current term and linear damping
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        if (j < 3 && j != i) gc[j] = fmaf(-xa(xh, i, j), gf[i], gc[j]);
+        if (j != i) gnur[j] = fmaf(-xd(xh, i, j), gf[i], gnur[j]);
+      }
+  }
   // rotational force
   const float gfr[3] = {gf[3], gf[4], gf[5]};
   const float ngfr[3] = {-gf[3], -gf[4], -gf[5]};
   cross_vjp(r, qm, ngfr, gr, gqm);   // - r x Q1
   cross_vjp(w, k, ngfr, gw, gk);     // - w x k
+  if constexpr (GEN) cross_vjp(v, am, ngfr, gv, gam);  // - v x (w x m r_g)
   for (int j = 0; j < 3; ++j) {
     const float aw = fabsf(w[j]);
     gw[j] = fmaf(-fmaf(2.f * P.dq[3 + j], aw, P.dl[3 + j]), gfr[j], gw[j]);
@@ -151,12 +250,31 @@ __device__ void rhs_vjp(const St<MT> &s, const float (&cs)[MT], const ParDiag &P
     G.dq[j] = fmaf(-ar * r[j], gfl[j], G.dq[j]);
   }
   if (current_accel) {
-    float ga[3];
     for (int j = 0; j < 3; ++j) {
-      G.ma[j] = fmaf(-a[j], gfl[j], G.ma[j]);
-      ga[j] = -ma[j] * gfl[j];
+      G.ma[j] = fmaf(-c[j], gfl[j], G.ma[j]);
+      gc[j] = fmaf(-ma[j], gfl[j], gc[j]);
     }
-    cross_vjp(w, cb, ga, gw, gcb);   // - M_A (w x v_c^b)
+    cross_vjp(w, cb, gc, gw, gcb);   // c = w x v_c^b
+  }
+  if constexpr (GEN) {
+    // k += off-diagonal I_o w + m r_g x v;  h += w x m r_g
+    gw[0] = fmaf(P.Ixy, gk[1], fmaf(P.Ixz, gk[2], gw[0]));
+    gw[1] = fmaf(P.Ixy, gk[0], fmaf(P.Iyz, gk[2], gw[1]));
+    gw[2] = fmaf(P.Ixz, gk[0], fmaf(P.Iyz, gk[1], gw[2]));
+    gv[0] = fmaf(gk[1], mrg[2], fmaf(-gk[2], mrg[1], gv[0]));
+    gv[1] = fmaf(gk[2], mrg[0], fmaf(-gk[0], mrg[2], gv[1]));
+    gv[2] = fmaf(gk[0], mrg[1], fmaf(-gk[1], mrg[0], gv[2]));
+    for (int j = 0; j < 3; ++j) gam[j] += gh[j];
+    float gmrg[3] = {0.f, 0.f, 0.f};
+    cross_vjp(w, mrg, gam, gw, gmrg);
+    // off-diagonal added mass in the momenta (Q1 enters through h and through r x Q1)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        if (j != i) gnur[j] = fmaf(xa(xh, i, j), gqm[i] + gh[i], gnur[j]);
+        if (j != 3 + i) gnur[j] = fmaf(xa(xh, 3 + i, j), gk[i], gnur[j]);
+      }
   }
   // k = J w, h = m v + Q1, Q1 = M_A r, r = v - v_c^b
   for (int j = 0; j < 3; ++j) {
@@ -166,6 +284,8 @@ __device__ void rhs_vjp(const St<MT> &s, const float (&cs)[MT], const ParDiag &P
     gqm[j] += gh[j];
     gr[j] = fmaf(ma[j], gqm[j], gr[j]);
     G.ma[j] = fmaf(r[j], gqm[j], G.ma[j]);
+    gr[j] += gnur[j];
+    gw[j] += gnur[3 + j];
     gv[j] += gr[j];
     gcb[j] -= gr[j];
   }
@@ -237,27 +357,44 @@ __device__ __forceinline__ void st_zero(St<MT> &x) {
   for (int i = 0; i < MT; ++i) x.n[i] = 0.f;
 }
 
+// The forward's right-hand side and closed-form-lag sub-step for this env (the step kernels'
+// own code: the diagonal-mass coefficients, or the general path with the staged off-diagonal
+// coefficients).
+template <int MT, bool GEN>
+__device__ __forceinline__ void fwd_rhs(const St<MT> &y, const float (&cs)[MT],
+                                        const AdjEnv<GEN> &A, const float4 *gdir,
+                                        const float4 *garm, int nt, bool ca, St<MT> &k) {
+  rhs<MT, !GEN, true, 0, GEN>(y, cs, A.F, gdir, garm, nt, ca, k, A.xh);
+}
+
+template <int MT, bool GEN>
+__device__ __forceinline__ void fwd_step(St<MT> &S, const float (&b)[MT], const LagEnv &L,
+                                         const AdjEnv<GEN> &A, const float4 *gdir,
+                                         const float4 *garm, int nt, bool ca, float h) {
+  rk4_step_lag<MT, !GEN, true, 0, GEN>(S, b, L, A.F, gdir, garm, nt, ca, h, A.xh);
+}
+
 // The RK4 stage states of one sub-step from its start state s (y1 = s):
 //   y2 = s + h/2 W k1,  y3 = s + h/2 W k2,  y4 = s + h W k3,  k_i = rhs(y_i),
 //   z  = s + h/6 W k1 + h/3 W k2 + h/3 W k3 + h/6 W k4  (before renormalisation).
-template <int MT>
+template <int MT, bool GEN>
 __device__ __forceinline__ void stage_states(const St<MT> &s, const float (&cs)[MT],
-                                             const ParDiag &P, const float4 *gdir,
+                                             const AdjEnv<GEN> &A, const float4 *gdir,
                                              const float4 *garm, int nt, bool current_accel,
                                              float h, St<MT> &y2, St<MT> &y3, St<MT> &y4,
                                              St<MT> &z) {
   const float hh = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f);
   St<MT> k;
-  rhs<MT, true, true>(s, cs, P, gdir, garm, nt, current_accel, k);
+  fwd_rhs<MT, GEN>(s, cs, A, gdir, garm, nt, current_accel, k);
   axpy(z, s, h6, k);
   axpy(y2, s, hh, k);
-  rhs<MT, true, true>(y2, cs, P, gdir, garm, nt, current_accel, k);
+  fwd_rhs<MT, GEN>(y2, cs, A, gdir, garm, nt, current_accel, k);
   axpy(z, z, h3, k);
   axpy(y3, s, hh, k);
-  rhs<MT, true, true>(y3, cs, P, gdir, garm, nt, current_accel, k);
+  fwd_rhs<MT, GEN>(y3, cs, A, gdir, garm, nt, current_accel, k);
   axpy(z, z, h3, k);
   axpy(y4, s, h, k);
-  rhs<MT, true, true>(y4, cs, P, gdir, garm, nt, current_accel, k);
+  fwd_rhs<MT, GEN>(y4, cs, A, gdir, garm, nt, current_accel, k);
   axpy(z, z, h6, k);
 }
 
@@ -284,9 +421,9 @@ __device__ __forceinline__ void st_add(St<MT> &y, const St<MT> &x) {
 // stalled mostly on instruction fetch: 1.41 / 1.29 ms against 1.11 / 1.04 ms rolled at 4,096
 // envs).  The stage states are then selected or read by a runtime index.  Same operations
 // either way.
-template <int MT, bool UNROLL, typename Stage>
+template <int MT, bool GEN, bool UNROLL, typename Stage>
 __device__ __forceinline__ void step_vjp_stages(Stage stage, const float (&zq)[4],
-                                                const float (&cs)[MT], const ParDiag &P,
+                                                const float (&cs)[MT], const AdjEnv<GEN> &A,
                                                 const float4 *gdir, const float4 *garm, int nt,
                                                 bool current_accel, float h, St<MT> &lam,
                                                 Grad &G, float (&gcs)[MT]) {
@@ -311,7 +448,7 @@ __device__ __forceinline__ void step_vjp_stages(Stage stage, const float (&zq)[4
     St<MT> y;
     stage(i, y);
     st_zero(ly);
-    rhs_vjp<MT>(y, cs, P, gdir, garm, nt, current_accel, lk, ly, G, gcs);
+    rhs_vjp<MT, GEN>(y, cs, A, gdir, garm, nt, current_accel, lk, ly, G, gcs);
     st_add(ls, ly);
   };
   if constexpr (UNROLL) {
@@ -324,15 +461,16 @@ __device__ __forceinline__ void step_vjp_stages(Stage stage, const float (&zq)[4
 }
 
 // The whole sub-step: stage states recomputed, then their transposes.
-template <int MT>
-__device__ void step_vjp(const St<MT> &s, const float (&cs)[MT], const ParDiag &P,
+template <int MT, bool GEN>
+__device__ void step_vjp(const St<MT> &s, const float (&cs)[MT], const AdjEnv<GEN> &A,
                          const float4 *gdir, const float4 *garm, int nt, bool current_accel,
                          float h, St<MT> &lam, Grad &G, float (&gcs)[MT]) {
   St<MT> y2, y3, y4, z;
-  stage_states<MT>(s, cs, P, gdir, garm, nt, current_accel, h, y2, y3, y4, z);
+  stage_states<MT, GEN>(s, cs, A, gdir, garm, nt, current_accel, h, y2, y3, y4, z);
   const float zq[4] = {z.q[0], z.q[1], z.q[2], z.q[3]};
   auto stage = [&](int i, St<MT> &y) { y = i == 0 ? s : i == 1 ? y2 : i == 2 ? y3 : y4; };
-  step_vjp_stages<MT, false>(stage, zq, cs, P, gdir, garm, nt, current_accel, h, lam, G, gcs);
+  step_vjp_stages<MT, GEN, false>(stage, zq, cs, A, gdir, garm, nt, current_accel, h, lam, G,
+                                  gcs);
 }
 
 constexpr int kMaxSeg = 32;  // largest checkpoint interval
@@ -397,16 +535,16 @@ __device__ __forceinline__ void add_action_adjoint(const FleetView &fv, int64_t 
     if (i < nt) da[i] = fmaf(itau, gcs[i], da[i]);
 }
 
-// Coefficients: M_A enters through Q1 (translational), J = diag(I_o) + M_A,rot and
-// M^-1 = diag(1 / (m + M_A,lin), 1 / (I + M_A,rot)): d mi / d M_A = -mi^2.
+// Coefficients: M_A,jj enters the momenta (Q1 for j < 3, J = diag(I_o) + M_A,rot for j >= 3),
+// the current term and M (G.mv); D_l and D_q their damping terms.
 template <int MT>
-__device__ __forceinline__ void write_gradients(const ParDiag &P, const Grad &G, const St<MT> &lam,
-                                                int64_t e, float *__restrict__ dcoef,
+__device__ __forceinline__ void write_gradients(const Grad &G, const St<MT> &lam, int64_t e,
+                                                float *__restrict__ dcoef,
                                                 float *__restrict__ dstate0) {
   float *dc = dcoef + e * 18;
   for (int j = 0; j < 3; ++j) {
-    dc[j] = fmaf(-P.mi[j] * P.mi[j], G.mi[j], G.ma[j]);
-    dc[3 + j] = fmaf(-P.mi[3 + j] * P.mi[3 + j], G.mi[3 + j], G.J[j]);
+    dc[j] = G.ma[j] + G.mv[j];
+    dc[3 + j] = G.J[j] + G.mv[3 + j];
   }
   for (int j = 0; j < 6; ++j) {
     dc[6 + j] = G.dl[j];
@@ -424,7 +562,7 @@ __device__ __forceinline__ void write_gradients(const ParDiag &P, const Grad &G,
 
 __device__ __forceinline__ void zero_grad(Grad &G) {
   for (int i = 0; i < 3; ++i) G.ma[i] = G.J[i] = 0.f;
-  for (int i = 0; i < 6; ++i) G.mi[i] = G.dl[i] = G.dq[i] = 0.f;
+  for (int i = 0; i < 6; ++i) G.mv[i] = G.dl[i] = G.dq[i] = 0.f;
 }
 
 __device__ __forceinline__ void stage_geometry(const FleetView &fv,
@@ -435,18 +573,42 @@ __device__ __forceinline__ void stage_geometry(const FleetView &fv,
   }
 }
 
+// General path: rows [0, count) of sx receive the off-diagonal coefficients of envs env0, ...,
+// or zeros when the fleet has no extension (off-centre gravity only).
+__device__ __forceinline__ void stage_xh_or_zero(const FleetView &fv, int64_t env0, int count,
+                                                 float *sx) {
+  if (fv.xh) {
+    stage_xh(fv.xh, fv.n, env0, count, sx);
+  } else {
+    for (int i = threadIdx.x; i < count * MG_NXPARAM; i += blockDim.x) sx[i] = 0.f;
+  }
+}
+
+template <bool GEN>
+__device__ __forceinline__ void load_env(const FleetView &fv, int64_t e, bool ca,
+                                         const float *sxh_row, AdjEnv<GEN> &A) {
+  load_par<!GEN>(fv.pa, e, A.P);
+  A.F = make_coef<!GEN>(A.P);
+  A.xh = GEN ? sxh_row : nullptr;
+}
+
 // One thread per env.  ckpt [n_ck][MG_NSTATE][n] (state at sub-steps 0, C, 2C, ...),
 // dtraj [T][MG_NTRAJ][n] (loss adjoint of the state after each sub-step).  Outputs: dcoef
-// [n][18] (M_A, Dl, Dq diagonals), dact [n_seg][n][8] accumulated, dstate0 [n][21] or null.
-template <int MT>
+// [n][18] (M_A, Dl, Dq diagonals), dact [n_seg][n][w] accumulated, dstate0 [n][21] or null.
+// GEN: dynamic shared memory [blockDim.x][MG_NXPARAM] for the block's off-diagonal coefficients.
+template <int MT, bool GEN>
 __global__ void __launch_bounds__(kAdjThreads)
     k_adjoint(const FleetView fv, const int32_t *__restrict__ types, const float *__restrict__ ckpt,
               const float *__restrict__ dtraj, int32_t T, int32_t C, int64_t step0,
               float *__restrict__ dcoef, float *__restrict__ dact, float *__restrict__ dstate0) {
   __shared__ float4 sgeo[MG_MAX_TYPES][2 * MG_MAX_THR];
+  extern __shared__ float sxh[];
   stage_geometry(fv, sgeo);
+  const int64_t env0 = (int64_t)blockIdx.x * blockDim.x;
+  if constexpr (GEN)
+    stage_xh_or_zero(fv, env0, (int)min((int64_t)blockDim.x, fv.n - env0), sxh);
   __syncthreads();
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t e = env0 + threadIdx.x;
   if (e >= fv.n) return;
   const int type = types[e];
   const float4 *gdir = sgeo[type], *garm = sgeo[type] + MG_MAX_THR;
@@ -454,9 +616,9 @@ __global__ void __launch_bounds__(kAdjThreads)
   const bool ca = !(fv.model_flags & MG_MODEL_NO_CURRENT_ACCEL);
   const float h = fv.dt;
   const int64_t n = fv.n;
-  ParDiag P;
-  load_par<true>(fv.pa, e, P);
-  const LagEnv L = lag_env(P.itau, h);  // the forward's throttle-lag update (checkpoint replay)
+  AdjEnv<GEN> A;
+  load_env<GEN>(fv, e, ca, sxh + threadIdx.x * MG_NXPARAM, A);
+  const LagEnv L = lag_env(A.P.itau, h);  // the forward's throttle-lag update (replay)
 
   Grad G;
   zero_grad(G);
@@ -472,22 +634,22 @@ __global__ void __launch_bounds__(kAdjThreads)
     load_checkpoint<MT>(ckpt, sg, n, e, S[0]);
     for (int32_t j = 1; j < len; ++j) {
       S[j] = S[j - 1];
-      commands_at<MT>(fv, e, step0 + t0 + j - 1, nt, P.itau, c);
+      commands_at<MT>(fv, e, step0 + t0 + j - 1, nt, A.P.itau, c);
       float b[MT];
       lag_segment<MT>(c, L, b);
-      rk4_step_lag<MT, true, true>(S[j], b, L, P, gdir, garm, nt, ca, h);
+      fwd_step<MT, GEN>(S[j], b, L, A, gdir, garm, nt, ca, h);
     }
     // walk it backwards
     for (int32_t j = len - 1; j >= 0; --j) {
       const int64_t t = t0 + j;
       add_traj_adjoint<MT>(dtraj, t, n, e, lam);
-      commands_at<MT>(fv, e, step0 + t, nt, P.itau, c);
+      commands_at<MT>(fv, e, step0 + t, nt, A.P.itau, c);
       for (int i = 0; i < MT; ++i) gcs[i] = 0.f;
-      step_vjp<MT>(S[j], c, P, gdir, garm, nt, ca, h, lam, G, gcs);
-      add_action_adjoint<MT>(fv, step0 + t, e, nt, P.itau, gcs, dact);
+      step_vjp<MT, GEN>(S[j], c, A, gdir, garm, nt, ca, h, lam, G, gcs);
+      add_action_adjoint<MT>(fv, step0 + t, e, nt, A.P.itau, gcs, dact);
     }
   }
-  write_gradients<MT>(P, G, lam, e, dcoef, dstate0);
+  write_gradients<MT>(G, lam, e, dcoef, dstate0);
 }
 
 // ---------------------------------------------------------------- two-warp form
@@ -514,12 +676,12 @@ __device__ __forceinline__ void put_stage(float *__restrict__ r, int64_t n, int 
 }
 
 // Warp 0: segment sg re-run from its checkpoint; record j of `rec` gets sub-step t0 + j.
-template <int MT>
-__device__ __forceinline__ void produce_segment(const FleetView &fv, int64_t e, const ParDiag &P,
-                                                const LagEnv &L, const float4 *gdir,
-                                                const float4 *garm, int nt, bool ca, float h,
-                                                const float *__restrict__ ckpt, int32_t sg,
-                                                int32_t C, int32_t T, int64_t step0,
+template <int MT, bool GEN>
+__device__ __forceinline__ void produce_segment(const FleetView &fv, int64_t e,
+                                                const AdjEnv<GEN> &A, const LagEnv &L,
+                                                const float4 *gdir, const float4 *garm, int nt,
+                                                bool ca, float h, const float *__restrict__ ckpt,
+                                                int32_t sg, int32_t C, int32_t T, int64_t step0,
                                                 float *__restrict__ rec) {
   constexpr int W = rec_words<MT>(), Y = 10 + MT;
   const int64_t n = fv.n;
@@ -528,9 +690,9 @@ __device__ __forceinline__ void produce_segment(const FleetView &fv, int64_t e, 
   load_checkpoint<MT>(ckpt, sg, n, e, S);
   float c[MT];
   for (int32_t j = 0; j < len; ++j) {
-    commands_at<MT>(fv, e, step0 + t0 + j, nt, P.itau, c);
+    commands_at<MT>(fv, e, step0 + t0 + j, nt, A.P.itau, c);
     St<MT> y2, y3, y4, z;
-    stage_states<MT>(S, c, P, gdir, garm, nt, ca, h, y2, y3, y4, z);
+    stage_states<MT, GEN>(S, c, A, gdir, garm, nt, ca, h, y2, y3, y4, z);
     float *r = rec + (int64_t)j * W * n;
     put_stage<MT>(r, n, 0, S);
     put_stage<MT>(r, n, Y, y2);
@@ -540,7 +702,7 @@ __device__ __forceinline__ void produce_segment(const FleetView &fv, int64_t e, 
     if (j + 1 < len) {  // the next start state, as the forward computed it
       float b[MT];
       lag_segment<MT>(c, L, b);
-      rk4_step_lag<MT, true, true>(S, b, L, P, gdir, garm, nt, ca, h);
+      fwd_step<MT, GEN>(S, b, L, A, gdir, garm, nt, ca, h);
     }
   }
 }
@@ -595,9 +757,9 @@ __device__ __forceinline__ void read_stage(const float *buf, int f, St<MT> &y) {
 
 // Warp 1: segment sg walked backwards from its records, each sub-step's inputs copied into
 // shared memory (double buffer sbuf [2][fetch_words][32]) while the previous one is processed.
-template <int MT>
+template <int MT, bool GEN>
 __device__ __forceinline__ void consume_segment(const FleetView &fv, int64_t e, int lane,
-                                                const ParDiag &P, const float4 *gdir,
+                                                const AdjEnv<GEN> &A, const float4 *gdir,
                                                 const float4 *garm, int nt, bool ca, float h,
                                                 const float *__restrict__ dtraj, int32_t sg,
                                                 int32_t C, int32_t T, int64_t step0,
@@ -620,18 +782,20 @@ __device__ __forceinline__ void consume_segment(const FleetView &fv, int64_t e, 
     for (int i = 0; i < 3; ++i) lam.v[i] += b[(W + 7 + i) * 32];
     for (int i = 0; i < 3; ++i) lam.w[i] += b[(W + 10 + i) * 32];
     for (int i = 0; i < MT; ++i)
-      c[i] = (fv.n_seg > 0 && i < nt) ? b[(W + MG_NTRAJ + i) * 32] * P.itau : 0.f;
+      c[i] = (fv.n_seg > 0 && i < nt) ? b[(W + MG_NTRAJ + i) * 32] * A.P.itau : 0.f;
     for (int i = 0; i < MT; ++i) gcs[i] = 0.f;
     float zq[4];
     for (int i = 0; i < 4; ++i) zq[i] = b[(4 * Y + i) * 32];
     auto stage = [&](int i, St<MT> &y) { read_stage<MT>(b, i * Y, y); };
-    step_vjp_stages<MT, false>(stage, zq, c, P, gdir, garm, nt, ca, h, lam, G, gcs);
-    add_action_adjoint<MT>(fv, step0 + t, e, nt, P.itau, gcs, dact);
+    step_vjp_stages<MT, GEN, false>(stage, zq, c, A, gdir, garm, nt, ca, h, lam, G, gcs);
+    add_action_adjoint<MT>(fv, step0 + t, e, nt, A.P.itau, gcs, dact);
   }
 }
 
-// ws: [2][C][rec_words<MT>()][n] floats.  Grid: one block per 32 envs.
-template <int MT>
+// ws: [2][C][rec_words<MT>()][n] floats.  Grid: one block per 32 envs.  GEN: dynamic shared
+// memory [32][MG_NXPARAM] for the block's off-diagonal coefficients (both warps read a lane's
+// row).
+template <int MT, bool GEN>
 __global__ void __launch_bounds__(kWsThreads)
     k_adjoint_ws(const FleetView fv, const int32_t *__restrict__ types,
                  const float *__restrict__ ckpt, const float *__restrict__ dtraj, int32_t T,
@@ -639,10 +803,13 @@ __global__ void __launch_bounds__(kWsThreads)
                  float *__restrict__ dstate0, float *__restrict__ ws) {
   __shared__ float4 sgeo[MG_MAX_TYPES][2 * MG_MAX_THR];
   __shared__ float sbuf[2 * fetch_words<MT>() * 32];
+  extern __shared__ float sxh[];
   stage_geometry(fv, sgeo);
+  const int64_t env0 = (int64_t)blockIdx.x * 32;
+  if constexpr (GEN) stage_xh_or_zero(fv, env0, (int)min((int64_t)32, fv.n - env0), sxh);
   __syncthreads();
   const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
-  const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+  const int64_t e = env0 + lane;
   const bool live = e < fv.n;  // lanes past the fleet only take part in the barriers
   const int64_t el = live ? e : 0;
   const int type = types[el];
@@ -650,14 +817,14 @@ __global__ void __launch_bounds__(kWsThreads)
   const int nt = fv.geo[type].n_thr;
   const bool ca = !(fv.model_flags & MG_MODEL_NO_CURRENT_ACCEL);
   const float h = fv.dt;
-  ParDiag P;
-  load_par<true>(fv.pa, el, P);
+  AdjEnv<GEN> A;
+  load_env<GEN>(fv, el, ca, sxh + lane * MG_NXPARAM, A);
   const int64_t slot = (int64_t)C * rec_words<MT>() * fv.n;
 
   const int32_t n_ck = (T + C - 1) / C;
   if (warp == 0 && live)
-    produce_segment<MT>(fv, e, P, lag_env(P.itau, h), gdir, garm, nt, ca, h, ckpt, n_ck - 1, C,
-                        T, step0, ws + ((n_ck - 1) & 1) * slot + e);
+    produce_segment<MT, GEN>(fv, e, A, lag_env(A.P.itau, h), gdir, garm, nt, ca, h, ckpt,
+                             n_ck - 1, C, T, step0, ws + ((n_ck - 1) & 1) * slot + e);
   __syncthreads();
   Grad G;
   zero_grad(G);
@@ -666,15 +833,39 @@ __global__ void __launch_bounds__(kWsThreads)
   for (int32_t sg = n_ck - 1; sg >= 0; --sg) {
     if (warp == 0) {
       if (live && sg > 0)
-        produce_segment<MT>(fv, e, P, lag_env(P.itau, h), gdir, garm, nt, ca, h, ckpt, sg - 1,
-                            C, T, step0, ws + ((sg - 1) & 1) * slot + e);
+        produce_segment<MT, GEN>(fv, e, A, lag_env(A.P.itau, h), gdir, garm, nt, ca, h, ckpt,
+                                 sg - 1, C, T, step0, ws + ((sg - 1) & 1) * slot + e);
     } else if (live) {
-      consume_segment<MT>(fv, e, lane, P, gdir, garm, nt, ca, h, dtraj, sg, C, T, step0,
-                          ws + (sg & 1) * slot + e, sbuf, dact, lam, G);
+      consume_segment<MT, GEN>(fv, e, lane, A, gdir, garm, nt, ca, h, dtraj, sg, C, T, step0,
+                               ws + (sg & 1) * slot + e, sbuf, dact, lam, G);
     }
     __syncthreads();
   }
-  if (warp == 1 && live) write_gradients<MT>(P, G, lam, e, dcoef, dstate0);
+  if (warp == 1 && live) write_gradients<MT>(G, lam, e, dcoef, dstate0);
+}
+
+template <int MT, bool GEN>
+cudaError_t launch_adjoint_t(const FleetView &fv, const int32_t *types, const float *ckpt,
+                             const float *dtraj, int32_t T, int32_t C, int64_t step0,
+                             float *dcoef, float *dact, float *dstate0, bool split, float *ws,
+                             int n_sm, cudaStream_t stream) {
+  if (split) {
+    const int grid = (int)((fv.n + 31) / 32);
+    const size_t smem = GEN ? sizeof(float) * 32 * MG_NXPARAM : 0;
+    k_adjoint_ws<MT, GEN><<<grid, kWsThreads, smem, stream>>>(fv, types, ckpt, dtraj, T, C,
+                                                               step0, dcoef, dact, dstate0, ws);
+    return cudaGetLastError();
+  }
+  // One warp per block while the fleet has fewer warps than the GPU has SMs x 4 (the backward
+  // pass is latency-bound, so its warps should be spread over all SMs, each with its own L1 for
+  // the threads' recompute buffers), larger blocks beyond.
+  const int64_t warps = (fv.n + 31) / 32;
+  const int threads = warps <= 4 * (int64_t)n_sm ? 32 : kAdjThreads;
+  const int grid = (int)((fv.n + threads - 1) / threads);
+  const size_t smem = GEN ? sizeof(float) * threads * MG_NXPARAM : 0;
+  k_adjoint<MT, GEN><<<grid, threads, smem, stream>>>(fv, types, ckpt, dtraj, T, C, step0, dcoef,
+                                                      dact, dstate0);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -713,37 +904,23 @@ size_t adjoint_workspace_bytes(bool eight, int64_t n, int32_t C) {
          sizeof(float);
 }
 
-cudaError_t launch_adjoint(const FleetView &fv, const int32_t *types, bool eight,
+cudaError_t launch_adjoint(const FleetView &fv, const int32_t *types, bool eight, bool general,
                            const float *ckpt, const float *dtraj, int32_t T, int32_t C,
                            int64_t step0, float *dcoef, float *dact, float *dstate0, bool split,
                            float *ws, cudaStream_t stream) {
   if (C < 1 || C > kMaxSeg || T < 1 || (split && !ws)) return cudaErrorInvalidValue;
-  if (split) {
-    const int grid = (int)((fv.n + 31) / 32);
-    if (eight)
-      k_adjoint_ws<8><<<grid, kWsThreads, 0, stream>>>(fv, types, ckpt, dtraj, T, C, step0,
-                                                       dcoef, dact, dstate0, ws);
-    else
-      k_adjoint_ws<6><<<grid, kWsThreads, 0, stream>>>(fv, types, ckpt, dtraj, T, C, step0,
-                                                       dcoef, dact, dstate0, ws);
-    return cudaGetLastError();
-  }
-  // One warp per block while the fleet has fewer warps than the GPU has SMs x 4 (the backward
-  // pass is latency-bound, so its warps should be spread over all SMs, each with its own L1 for
-  // the threads' recompute buffers), larger blocks beyond.
   int n_sm = 0;
   cudaError_t e = sm_count(&n_sm);
   if (e != cudaSuccess) return e;
-  const int64_t warps = (fv.n + 31) / 32;
-  const int threads = warps <= 4 * (int64_t)n_sm ? 32 : kAdjThreads;
-  const int grid = (int)((fv.n + threads - 1) / threads);
   if (eight)
-    k_adjoint<8><<<grid, threads, 0, stream>>>(fv, types, ckpt, dtraj, T, C, step0, dcoef, dact,
-                                              dstate0);
-  else
-    k_adjoint<6><<<grid, threads, 0, stream>>>(fv, types, ckpt, dtraj, T, C, step0, dcoef, dact,
-                                              dstate0);
-  return cudaGetLastError();
+    return general ? launch_adjoint_t<8, true>(fv, types, ckpt, dtraj, T, C, step0, dcoef, dact,
+                                               dstate0, split, ws, n_sm, stream)
+                   : launch_adjoint_t<8, false>(fv, types, ckpt, dtraj, T, C, step0, dcoef,
+                                                dact, dstate0, split, ws, n_sm, stream);
+  return general ? launch_adjoint_t<6, true>(fv, types, ckpt, dtraj, T, C, step0, dcoef, dact,
+                                             dstate0, split, ws, n_sm, stream)
+                 : launch_adjoint_t<6, false>(fv, types, ckpt, dtraj, T, C, step0, dcoef, dact,
+                                              dstate0, split, ws, n_sm, stream);
 }
 
 int adjoint_max_interval() { return kMaxSeg; }

@@ -145,8 +145,12 @@ __device__ __forceinline__ void advance_env(const FleetView &fv, int64_t e, int 
   const float h = fv.dt;
 
   load_state<MT, L2>(fv.st, e, s);
-  Par<DIAG> P;
-  load_par<DIAG>(fv.pa, e, P);
+  Coef<DIAG> P;
+  {
+    Par<DIAG> raw;
+    load_par<DIAG>(fv.pa, e, raw);
+    P = make_coef<DIAG>(raw);
+  }
 
   // Action cursor: sub-step j uses segment j / hold (clamped to the last buffered segment).
   int64_t seg = step0 / fv.hold;

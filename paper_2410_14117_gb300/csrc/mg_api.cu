@@ -91,6 +91,10 @@ struct mg_sim {
   std::vector<int32_t> types_h;
   std::vector<mg_vehicle_params> vp;
   NtVariant ntv = NT_6;
+  // mass_diag: every env's M_RB + M_A is diagonal (r_g = 0, no off-diagonal extension).  diag:
+  // the step kernels take the diagonal-mass path, whose coefficients also fold in the
+  // current-acceleration term, so a sim that switches that term off takes the general path.
+  bool mass_diag = true;
   bool diag = true;
   bool structured = false;  // every type present has the vectored thruster layout
   bool nominal_diag = true;  // every type has r_g = 0 (randomised M_RB + M_A stays diagonal)
@@ -137,10 +141,6 @@ struct mg_sim {
   BlockDesc *blocks_d = nullptr;
   int n_blocks = 0;
   int threads = 128;
-  // packed (two envs per thread) static blocks of at most 2 x threads envs
-  BlockDesc *pblocks_d = nullptr;
-  int n_pblocks = 0;
-  bool packed = false;
   // work-queue schedule: 32-env slices and the scheduler words
   BlockDesc *slices_d = nullptr;
   int n_slices = 0;
@@ -323,25 +323,18 @@ std::vector<BlockDesc> cut_runs(const mg_sim *s, int width) {
   return b;
 }
 
-// Build the static-schedule block lists: pieces of at most epb envs (one env per thread), and
-// pieces of at most 2 x threads envs for the packed kernel (two envs per thread).
+// Build the static-schedule block list: pieces of at most epb envs (one env per thread).
 mg_status build_blocks(mg_sim *s) {
   s->threads = (int)align_up((size_t)s->epb, 32);
   const std::vector<BlockDesc> b = cut_runs(s, s->epb);
-  const std::vector<BlockDesc> pb = cut_runs(s, 2 * s->threads);
   if (s->blocks_d) {
     MG_CK(cudaStreamSynchronize(s->stream));
     cudaFree(s->blocks_d);
     s->blocks_d = nullptr;
-    s->pblocks_d = nullptr;
   }
-  MG_CK(cudaMalloc(&s->blocks_d, (b.size() + pb.size()) * sizeof(BlockDesc)));
-  s->pblocks_d = s->blocks_d + b.size();
+  MG_CK(cudaMalloc(&s->blocks_d, b.size() * sizeof(BlockDesc)));
   MG_CK(cudaMemcpy(s->blocks_d, b.data(), b.size() * sizeof(BlockDesc), cudaMemcpyHostToDevice));
-  MG_CK(cudaMemcpy(s->pblocks_d, pb.data(), pb.size() * sizeof(BlockDesc),
-                   cudaMemcpyHostToDevice));
   s->n_blocks = (int)b.size();
-  s->n_pblocks = (int)pb.size();
   s->drop_graphs();
   return MG_OK;
 }
@@ -350,17 +343,6 @@ mg_status build_blocks(mg_sim *s) {
 // call, and the last advances the cursor by k.
 mg_status launch_chunks(mg_sim *s, int32_t k, float *traj, cudaStream_t stream) {
   FleetView v = s->view();
-  if (s->packed && !s->queue && s->diag && !traj && !s->has_xh) {
-    for (int32_t done = 0; done < k;) {
-      const int32_t kk = std::min(s->spl, k - done);
-      v.cursor_off = done;
-      v.cursor_adv = (done + kk == k) ? k : 0;
-      MG_CK(launch_fleet_pair(v, s->pblocks_d, s->n_pblocks, s->threads, s->ntv, s->structured,
-                              kk, stream));
-      done += kk;
-    }
-    return MG_OK;
-  }
   if (s->queue && !traj && !s->has_xh) {
     v.cursor_adv = k;
     MG_CK(launch_fleet_queue(v, s->slices_d, s->n_slices, s->ntv, s->diag, s->structured,
@@ -418,6 +400,14 @@ mg_status read_counter(mg_sim *s, int idx, unsigned long long *out) {
   return MG_OK;
 }
 
+// Record the fleet's mass structure and pick the kernel path (see mg_sim::diag).
+void set_mass_diag(mg_sim *s, bool mass_diag) {
+  s->mass_diag = mass_diag;
+  const bool diag = mass_diag && !(s->model_flags & MG_MODEL_NO_CURRENT_ACCEL);
+  if (diag != s->diag) s->drop_graphs();
+  s->diag = diag;
+}
+
 // After a parameter change: count non-SPD envs and pick the diagonal or general kernel.
 mg_status finish_params(mg_sim *s) {
   unsigned long long bad = 0;
@@ -425,9 +415,7 @@ mg_status finish_params(mg_sim *s) {
   MG_CK(cudaMemcpyAsync(&off, s->offdiag, sizeof off, cudaMemcpyDeviceToHost, s->stream));
   mg_status st = read_counter(s, 1, &bad);
   if (st != MG_OK) return st;
-  const bool diag = (off == 0) && !s->has_xh;  // the extension always takes the general path
-  if (diag != s->diag) s->drop_graphs();
-  s->diag = diag;
+  set_mass_diag(s, (off == 0) && !s->has_xh);  // the extension always takes the general path
   if (bad) {
     char buf[160];
     snprintf(buf, sizeof buf, "%llu envs have a mass matrix that is not positive definite", bad);
@@ -744,6 +732,7 @@ mg_status mg_set_model_flags(mg_sim *s, uint32_t flags) {
   if (flags & ~MG_MODEL_NO_CURRENT_ACCEL) return fail(MG_EINVAL, "unknown model flag");
   s->model_flags = flags;
   s->drop_graphs();
+  set_mass_diag(s, s->mass_diag);
   return MG_OK;
 }
 
@@ -787,13 +776,6 @@ mg_status mg_set_wait_limit(mg_sim *s, uint32_t polls) {
   const uint32_t v = polls ? polls : (uint32_t)MG_WAIT_POLLS_DEFAULT;
   if (v != s->wait_limit) s->drop_graphs();
   s->wait_limit = v;
-  return MG_OK;
-}
-
-mg_status mg_set_packed(mg_sim *s, int32_t packed) {
-  MG_NONNULL(s);
-  s->packed = packed != 0;
-  s->drop_graphs();
   return MG_OK;
 }
 
@@ -892,8 +874,7 @@ mg_status mg_randomize(mg_sim *s, uint64_t seed, const mg_ranges *r) {
   s->reset_seed = seed;
   s->nu0_sigma = (double)r->nu0_sigma;
   if (async) {  // diagonal by construction; a pivot <= 0 is left to mg_sync
-    if (!s->diag) s->drop_graphs();
-    s->diag = true;
+    set_mass_diag(s, true);
     return MG_OK;
   }
   return finish_params(s);
@@ -1143,7 +1124,7 @@ mg_status mg_step_split(mg_sim *s, int32_t k, float *accel) {
   MG_NONNULL(accel);
   if (k < 1) return fail(MG_EINVAL, "k must be >= 1");
   if (!is_device_ptr(accel)) return fail(MG_EINVAL, "accel must be device memory");
-  if (!s->diag)
+  if (!s->mass_diag)
     return fail(MG_EINVAL, "the split step covers diagonal-mass fleets (r_g = 0, no "
                            "off-diagonal hydrodynamics) only");
   FleetView v = s->view();
@@ -1207,7 +1188,6 @@ mg_status mg_rollout_backward(mg_sim *s, int32_t T, int32_t C, const float *ckpt
   MG_NONNULL(dcoef);
   if (T < 1 || C < 1 || C > adjoint_max_interval() || step0 < 0)
     return fail(MG_EINVAL, "need T >= 1, 1 <= C <= 32, step0 >= 0");
-  if (!s->diag) return fail(MG_EINVAL, "the adjoint needs a diagonal mass matrix (r_g = 0)");
   if (s->proc) return fail(MG_EINVAL, "the adjoint needs buffered actions (mg_set_actions)");
   for (const void *p : {(const void *)ckpt, (const void *)dtraj, (const void *)dcoef})
     if (!is_device_ptr(p)) return fail(MG_EINVAL, "adjoint buffers must be device memory");
@@ -1231,8 +1211,8 @@ mg_status mg_rollout_backward(mg_sim *s, int32_t T, int32_t C, const float *ckpt
       s->adj_ws_cap = bytes;
     }
   }
-  MG_CK(launch_adjoint(s->view(), s->types_d, eight, ckpt, dtraj, T, C, step0, dcoef, dact,
-                       dstate0, split, s->adj_ws, s->stream));
+  MG_CK(launch_adjoint(s->view(), s->types_d, eight, !s->diag || s->has_xh, ckpt, dtraj, T, C,
+                       step0, dcoef, dact, dstate0, split, s->adj_ws, s->stream));
   return MG_OK;
 }
 
@@ -1449,9 +1429,7 @@ mg_status mg_kernel_info(mg_sim *s, int32_t *regs, int32_t *max_threads, int32_t
   MG_NONNULL(s);
   cudaFuncAttributes a;
   int per_sm = 0;
-  if (s->packed && !s->queue && s->diag && !s->has_xh)
-    MG_CK(pair_kernel_attributes(s->ntv, s->structured, &a));
-  else if (s->queue)
+  if (s->queue)
     MG_CK(queue_kernel_attributes(s->ntv, s->diag, s->wide, s->structured, &a, &per_sm));
   else
     MG_CK(fleet_kernel_attributes(s->ntv, s->diag, s->structured, false, s->wide, &a));

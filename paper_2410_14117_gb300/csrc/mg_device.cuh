@@ -152,6 +152,65 @@ struct ParGen : ParDiag {
 template <bool DIAG>
 using Par = typename std::conditional<DIAG, ParDiag, ParGen>::type;
 
+// Diagonal-mass step coefficients, formed from ParDiag once per launch.  With r_g = 0 and
+// diagonal M_A, M = M_RB + M_A is diagonal, and Eq. 1's row i reads nu'_i = f_i / M_ii.  Every
+// parameter that multiplies a term of f_i is stored pre-multiplied by (M^-1)_ii, so each row's
+// chain of FMAs ends in nu'_i itself, and the Kirchhoff Coriolis terms are expanded into the
+// products they reduce to when M_RB and M_A are diagonal (row indices i, i1 = i+1, i2 = i+2 mod 3;
+// r = v - v_c^b):
+//   translational, -(w x (m v + M_A r)) - M_A (w x v_c^b) with v_c^b = v - r:
+//     w_i2 [(m + Ma_i) v_i1 + (Ma_i1 - Ma_i) r_i1] - w_i1 [(m + Ma_i) v_i2 + (Ma_i2 - Ma_i) r_i2],
+//     and (m + Ma_i) / M_ii = 1, so the v terms carry no coefficient;
+//   rotational, -(r x M_A r) - (w x J w):  (Ma_i1 - Ma_i2) r_i1 r_i2 + (J_i1 - J_i2) w_i1 w_i2.
+// The same mathematics as the general path (rhs with ParGen), in fewer operations.  It includes
+// the current-acceleration term M_A [w x v_c^b; 0] (the default model); a sim with that term
+// switched off (MG_MODEL_NO_CURRENT_ACCEL) runs the general path.
+struct StepDiag {
+  // translational rows: mi kT, mi (W - B), mi (Ma_i1 - Ma_i), mi (Ma_i2 - Ma_i), mi Dl_i, mi Dq_i
+  // (mi = 1 / M_ii)
+  float At[3], Wt[3], bp[3], bm[3], dlt[3], dqt[3];
+  // rotational rows: mi kT, mi (Ma_i1 - Ma_i2), mi (J_i1 - J_i2), mi Dl, mi Dq, mi G_i1, mi G_i2
+  float Ar[3], B[3], C[3], dlr[3], dqr[3], Gp[3], Gm[3];
+  float vc0, vc1, vc2, itau;  // NED current, 1 / tau_m
+};
+
+__device__ __forceinline__ StepDiag step_diag(const ParDiag &P) {
+  StepDiag C;
+  const float ma[3] = {P.ma0, P.ma1, P.ma2}, J[3] = {P.J0, P.J1, P.J2};
+  const float G[3] = {P.G0, P.G1, P.G2};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+    const float mt = P.mi[i], mr = P.mi[3 + i];
+    C.At[i] = mt * P.kT;
+    C.Wt[i] = mt * P.wb;
+    C.bp[i] = mt * (ma[i1] - ma[i]);
+    C.bm[i] = mt * (ma[i2] - ma[i]);
+    C.dlt[i] = mt * P.dl[i];
+    C.dqt[i] = mt * P.dq[i];
+    C.Ar[i] = mr * P.kT;
+    C.B[i] = mr * (ma[i1] - ma[i2]);
+    C.C[i] = mr * (J[i1] - J[i2]);
+    C.dlr[i] = mr * P.dl[3 + i];
+    C.dqr[i] = mr * P.dq[3 + i];
+    C.Gp[i] = mr * G[i1];
+    C.Gm[i] = mr * G[i2];
+  }
+  C.vc0 = P.vc0; C.vc1 = P.vc1; C.vc2 = P.vc2; C.itau = P.itau;
+  return C;
+}
+
+// What the step's right-hand side reads: the diagonal-mass coefficients above, or the general
+// parameters as loaded.
+template <bool DIAG>
+using Coef = typename std::conditional<DIAG, StepDiag, ParGen>::type;
+
+template <bool DIAG>
+__device__ __forceinline__ Coef<DIAG> make_coef(const Par<DIAG> &P) {
+  if constexpr (DIAG) return step_diag(P);
+  else return P;
+}
+
 __device__ __forceinline__ float4 ldg4(const float4 *p, int64_t e) { return __ldg(p + e); }
 
 template <bool DIAG>
@@ -217,8 +276,10 @@ __device__ __forceinline__ void store_state(const StatePlanes &sp, int64_t e, co
 //   - cs[i] = c_i / tau_m (the command pre-divided by the lag constant once per segment), so
 //     n_i' = cs_i - n_i / tau_m is a single FMA;
 //   - d.q holds 2 q' (the 1/2 of q' = 1/2 q (x) (0, w) is folded into the RK4 weights).
-// Every sum is written as a chain of FMAs into the generalised force (same terms as Eq. 1; only
-// the rounding order differs from a term-by-term evaluation).
+// Every sum is written as a chain of FMAs (same terms as Eq. 1; only the rounding order differs
+// from a term-by-term evaluation).  The diagonal-mass path reads the StepDiag coefficients (each
+// row's chain ends in nu'_i, no separate M^-1 multiply); the general path reads ParGen and
+// multiplies the generalised force by the full M^-1.
 // gdir/garm: the block's vehicle type's thruster directions and moment arms (shared memory),
 // zero past its thruster count; MIXED (fleets with several thruster counts) evaluates all MT
 // thrusters, the absent ones contributing exact zeros (their command is zeroed by the caller and
@@ -231,8 +292,9 @@ __device__ __forceinline__ void store_state(const StatePlanes &sp, int64_t e, co
 // (M_A above its diagonal, then D_l's off-diagonal entries, both row-major; mg.h) enter the
 // added-mass momenta Q = M_A nu_r, the current term M_A [w x v_c^b; 0] and the damping D_l nu_r.
 // LAGD = false leaves d.n unset (the caller integrates the linear throttle lag in closed form).
+// The diagonal-mass path always includes the current-acceleration term (current_accel unused).
 template <int MT, bool DIAG, bool MIXED, int NH = 0, bool XH = false, bool LAGD = true>
-__device__ __forceinline__ void rhs(const St<MT> &s, const float (&cs)[MT], const Par<DIAG> &P,
+__device__ __forceinline__ void rhs(const St<MT> &s, const float (&cs)[MT], const Coef<DIAG> &P,
                                     const float4 *gdir, const float4 *garm, int nt,
                                     bool current_accel, St<MT> &d,
                                     const float *__restrict__ xh = nullptr) {
@@ -272,109 +334,135 @@ __device__ __forceinline__ void rhs(const St<MT> &s, const float (&cs)[MT], cons
   const float v0 = s.v[0], v1 = s.v[1], v2 = s.v[2];
   const float w0 = s.w[0], w1 = s.w[1], w2 = s.w[2];
 
-  // Current constant in NED, seen from the body: v_c^b = R^T v_c; relative velocity v_r.
-  const float cb0 = fmaf(R20, P.vc2, fmaf(R10, P.vc1, R00 * P.vc0));
-  const float cb1 = fmaf(R21, P.vc2, fmaf(R11, P.vc1, R01 * P.vc0));
-  const float cb2 = fmaf(R22, P.vc2, fmaf(R12, P.vc1, R02 * P.vc0));
-  const float r0 = v0 - cb0, r1 = v1 - cb1, r2 = v2 - cb2;
+  if constexpr (DIAG) {
+    (void)current_accel;
+    // Velocity relative to the current (constant in NED): r = v - R^T v_c.
+    const float r0 = fmaf(-R20, P.vc2, fmaf(-R10, P.vc1, fmaf(-R00, P.vc0, v0)));
+    const float r1 = fmaf(-R21, P.vc2, fmaf(-R11, P.vc1, fmaf(-R01, P.vc0, v1)));
+    const float r2 = fmaf(-R22, P.vc2, fmaf(-R12, P.vc1, fmaf(-R02, P.vc0, v2)));
+    // Translational rows (StepDiag): thrust, (W - B) k_e with k_e = R^T e3 = (R20, R21, R22),
+    // the expanded Coriolis terms, damping.
+    {
+      const float u0 = fmaf(P.bp[0], r1, v1), x0 = fmaf(P.bm[0], r2, v2);
+      const float u1 = fmaf(P.bp[1], r2, v2), x1 = fmaf(P.bm[1], r0, v0);
+      const float u2 = fmaf(P.bp[2], r0, v0), x2 = fmaf(P.bm[2], r1, v1);
+      float a0 = fmaf(P.Wt[0], R20, P.At[0] * t0);
+      float a1 = fmaf(P.Wt[1], R21, P.At[1] * t1);
+      float a2 = fmaf(P.Wt[2], R22, P.At[2] * t2);
+      a0 = fmaf(-w1, x0, fmaf(w2, u0, a0));
+      a1 = fmaf(-w2, x1, fmaf(w0, u1, a1));
+      a2 = fmaf(-w0, x2, fmaf(w1, u2, a2));
+      d.v[0] = fmaf(-fmaf(P.dqt[0], fabsf(r0), P.dlt[0]), r0, a0);
+      d.v[1] = fmaf(-fmaf(P.dqt[1], fabsf(r1), P.dlt[1]), r1, a1);
+      d.v[2] = fmaf(-fmaf(P.dqt[2], fabsf(r2), P.dlt[2]), r2, a2);
+    }
+    // Rotational rows: thrust moment, G x k_e, Munk and gyroscopic products, damping.
+    {
+      float b0 = fmaf(-P.Gm[0], R21, fmaf(P.Gp[0], R22, P.Ar[0] * t3));
+      float b1 = fmaf(-P.Gm[1], R22, fmaf(P.Gp[1], R20, P.Ar[1] * t4));
+      float b2 = fmaf(-P.Gm[2], R20, fmaf(P.Gp[2], R21, P.Ar[2] * t5));
+      b0 = fmaf(P.C[0] * w1, w2, fmaf(P.B[0] * r1, r2, b0));
+      b1 = fmaf(P.C[1] * w2, w0, fmaf(P.B[1] * r2, r0, b1));
+      b2 = fmaf(P.C[2] * w0, w1, fmaf(P.B[2] * r0, r1, b2));
+      d.w[0] = fmaf(-fmaf(P.dqr[0], fabsf(w0), P.dlr[0]), w0, b0);
+      d.w[1] = fmaf(-fmaf(P.dqr[1], fabsf(w1), P.dlr[1]), w1, b1);
+      d.w[2] = fmaf(-fmaf(P.dqr[2], fabsf(w2), P.dlr[2]), w2, b2);
+    }
+  } else {
+    // Current constant in NED, seen from the body: v_c^b = R^T v_c; relative velocity v_r.
+    const float cb0 = fmaf(R20, P.vc2, fmaf(R10, P.vc1, R00 * P.vc0));
+    const float cb1 = fmaf(R21, P.vc2, fmaf(R11, P.vc1, R01 * P.vc0));
+    const float cb2 = fmaf(R22, P.vc2, fmaf(R12, P.vc1, R02 * P.vc0));
+    const float r0 = v0 - cb0, r1 = v1 - cb1, r2 = v2 - cb2;
 
-  // Momenta: Q1 = M_A,lin v_r; h = P1 + Q1 = m v + Q1 (+ w x m r_g);
-  //          k = P2 + Q2 = (diag(I_o) + M_A,rot) w (+ off-diagonal I_o w + m r_g x v).
-  float q0 = P.ma0 * r0, q1 = P.ma1 * r1, q2 = P.ma2 * r2;
-  float k0 = P.J0 * w0, k1 = P.J1 * w1, k2 = P.J2 * w2;
-  if constexpr (XH) {
-    // off-diagonal added mass: Q_i += sum_{j != i} M_A,ij nu_r,j (upper triangle, mirrored)
-    const float *A = xh;  // 01 02 03 04 05 12 13 14 15 23 24 25 34 35 45
-    q0 = fmaf(A[0], r1, fmaf(A[1], r2, fmaf(A[2], w0, fmaf(A[3], w1, fmaf(A[4], w2, q0)))));
-    q1 = fmaf(A[0], r0, fmaf(A[5], r2, fmaf(A[6], w0, fmaf(A[7], w1, fmaf(A[8], w2, q1)))));
-    q2 = fmaf(A[1], r0, fmaf(A[5], r1, fmaf(A[9], w0, fmaf(A[10], w1, fmaf(A[11], w2, q2)))));
-    k0 = fmaf(A[2], r0, fmaf(A[6], r1, fmaf(A[9], r2, fmaf(A[12], w1, fmaf(A[13], w2, k0)))));
-    k1 = fmaf(A[3], r0, fmaf(A[7], r1, fmaf(A[10], r2, fmaf(A[12], w0, fmaf(A[14], w2, k1)))));
-    k2 = fmaf(A[4], r0, fmaf(A[8], r1, fmaf(A[11], r2, fmaf(A[13], w0, fmaf(A[14], w1, k2)))));
-  }
-  float h0 = fmaf(P.m, v0, q0), h1 = fmaf(P.m, v1, q1), h2 = fmaf(P.m, v2, q2);
-  float a0 = 0.f, a1 = 0.f, a2 = 0.f;  // w x m r_g
-  if constexpr (!DIAG) {
-    a0 = fmaf(w1, P.mrg2, -w2 * P.mrg1);
-    a1 = fmaf(w2, P.mrg0, -w0 * P.mrg2);
-    a2 = fmaf(w0, P.mrg1, -w1 * P.mrg0);
+    // Momenta: Q1 = M_A,lin v_r; h = P1 + Q1 = m v + Q1 + w x m r_g;
+    //          k = P2 + Q2 = (diag(I_o) + M_A,rot) w + off-diagonal I_o w + m r_g x v.
+    float q0 = P.ma0 * r0, q1 = P.ma1 * r1, q2 = P.ma2 * r2;
+    float k0 = P.J0 * w0, k1 = P.J1 * w1, k2 = P.J2 * w2;
+    if constexpr (XH) {
+      // off-diagonal added mass: Q_i += sum_{j != i} M_A,ij nu_r,j (upper triangle, mirrored)
+      const float *A = xh;  // 01 02 03 04 05 12 13 14 15 23 24 25 34 35 45
+      q0 = fmaf(A[0], r1, fmaf(A[1], r2, fmaf(A[2], w0, fmaf(A[3], w1, fmaf(A[4], w2, q0)))));
+      q1 = fmaf(A[0], r0, fmaf(A[5], r2, fmaf(A[6], w0, fmaf(A[7], w1, fmaf(A[8], w2, q1)))));
+      q2 = fmaf(A[1], r0, fmaf(A[5], r1, fmaf(A[9], w0, fmaf(A[10], w1, fmaf(A[11], w2, q2)))));
+      k0 = fmaf(A[2], r0, fmaf(A[6], r1, fmaf(A[9], r2, fmaf(A[12], w1, fmaf(A[13], w2, k0)))));
+      k1 = fmaf(A[3], r0, fmaf(A[7], r1, fmaf(A[10], r2, fmaf(A[12], w0, fmaf(A[14], w2, k1)))));
+      k2 = fmaf(A[4], r0, fmaf(A[8], r1, fmaf(A[11], r2, fmaf(A[13], w0, fmaf(A[14], w1, k2)))));
+    }
+    float h0 = fmaf(P.m, v0, q0), h1 = fmaf(P.m, v1, q1), h2 = fmaf(P.m, v2, q2);
+    const float a0 = fmaf(w1, P.mrg2, -w2 * P.mrg1);  // w x m r_g
+    const float a1 = fmaf(w2, P.mrg0, -w0 * P.mrg2);
+    const float a2 = fmaf(w0, P.mrg1, -w1 * P.mrg0);
     h0 += a0; h1 += a1; h2 += a2;
     k0 = fmaf(P.Ixy, w1, fmaf(P.Ixz, w2, fmaf(P.mrg1, v2, fmaf(-P.mrg2, v1, k0))));
     k1 = fmaf(P.Ixy, w0, fmaf(P.Iyz, w2, fmaf(P.mrg2, v0, fmaf(-P.mrg0, v2, k1))));
     k2 = fmaf(P.Ixz, w0, fmaf(P.Iyz, w1, fmaf(P.mrg0, v1, fmaf(-P.mrg1, v0, k2))));
-  }
 
-  // Translational generalised force:
-  //   kT t + (W - B) k_e - w x h - (Dl + Dq |v_r|) v_r [- M_A,lin (w x v_c^b)],
-  // with k_e = R^T e3 = (R20, R21, R22) the restoring direction.
-  float f0 = fmaf(P.wb, R20, P.kT * t0);
-  float f1 = fmaf(P.wb, R21, P.kT * t1);
-  float f2 = fmaf(P.wb, R22, P.kT * t2);
-  f0 = fmaf(w2, h1, fmaf(-w1, h2, f0));
-  f1 = fmaf(w0, h2, fmaf(-w2, h0, f1));
-  f2 = fmaf(w1, h0, fmaf(-w0, h1, f2));
-  f0 = fmaf(-fmaf(P.dq[0], fabsf(r0), P.dl[0]), r0, f0);
-  f1 = fmaf(-fmaf(P.dq[1], fabsf(r1), P.dl[1]), r1, f1);
-  f2 = fmaf(-fmaf(P.dq[2], fabsf(r2), P.dl[2]), r2, f2);
-  float c0 = 0.f, c1 = 0.f, c2 = 0.f;  // w x v_c^b
-  if (current_accel) {
-    c0 = fmaf(w1, cb2, -w2 * cb1);
-    c1 = fmaf(w2, cb0, -w0 * cb2);
-    c2 = fmaf(w0, cb1, -w1 * cb0);
-    f0 = fmaf(-P.ma0, c0, f0);
-    f1 = fmaf(-P.ma1, c1, f1);
-    f2 = fmaf(-P.ma2, c2, f2);
-  }
-  if constexpr (XH) {
-    // off-diagonal current term and linear damping of the translational rows
-    const float *A = xh, *Dl = xh + 15;  // Dl: row-major off-diagonal, 5 per row
-    f0 = fmaf(-A[0], c1, fmaf(-A[1], c2, f0));
-    f1 = fmaf(-A[0], c0, fmaf(-A[5], c2, f1));
-    f2 = fmaf(-A[1], c0, fmaf(-A[5], c1, f2));
-    f0 = fmaf(-Dl[0], r1, fmaf(-Dl[1], r2, fmaf(-Dl[2], w0, fmaf(-Dl[3], w1,
-             fmaf(-Dl[4], w2, f0)))));
-    f1 = fmaf(-Dl[5], r0, fmaf(-Dl[6], r2, fmaf(-Dl[7], w0, fmaf(-Dl[8], w1,
-             fmaf(-Dl[9], w2, f1)))));
-    f2 = fmaf(-Dl[10], r0, fmaf(-Dl[11], r1, fmaf(-Dl[12], w0, fmaf(-Dl[13], w1,
-             fmaf(-Dl[14], w2, f2)))));
-  }
-  // Rotational: kT t' - v_r x Q1 - w x k [- v x (w x m r_g)] - (Dl + Dq|w|) w + G x k_e.
-  float f3 = fmaf(r2, q1, fmaf(-r1, q2, P.kT * t3));
-  float f4 = fmaf(r0, q2, fmaf(-r2, q0, P.kT * t4));
-  float f5 = fmaf(r1, q0, fmaf(-r0, q1, P.kT * t5));
-  f3 = fmaf(w2, k1, fmaf(-w1, k2, f3));
-  f4 = fmaf(w0, k2, fmaf(-w2, k0, f4));
-  f5 = fmaf(w1, k0, fmaf(-w0, k1, f5));
-  if constexpr (!DIAG) {
+    // Translational generalised force:
+    //   kT t + (W - B) k_e - w x h - (Dl + Dq |v_r|) v_r [- M_A,lin (w x v_c^b)],
+    // with k_e = R^T e3 = (R20, R21, R22) the restoring direction.
+    float f0 = fmaf(P.wb, R20, P.kT * t0);
+    float f1 = fmaf(P.wb, R21, P.kT * t1);
+    float f2 = fmaf(P.wb, R22, P.kT * t2);
+    f0 = fmaf(w2, h1, fmaf(-w1, h2, f0));
+    f1 = fmaf(w0, h2, fmaf(-w2, h0, f1));
+    f2 = fmaf(w1, h0, fmaf(-w0, h1, f2));
+    f0 = fmaf(-fmaf(P.dq[0], fabsf(r0), P.dl[0]), r0, f0);
+    f1 = fmaf(-fmaf(P.dq[1], fabsf(r1), P.dl[1]), r1, f1);
+    f2 = fmaf(-fmaf(P.dq[2], fabsf(r2), P.dl[2]), r2, f2);
+    float c0 = 0.f, c1 = 0.f, c2 = 0.f;  // w x v_c^b
+    if (current_accel) {
+      c0 = fmaf(w1, cb2, -w2 * cb1);
+      c1 = fmaf(w2, cb0, -w0 * cb2);
+      c2 = fmaf(w0, cb1, -w1 * cb0);
+      f0 = fmaf(-P.ma0, c0, f0);
+      f1 = fmaf(-P.ma1, c1, f1);
+      f2 = fmaf(-P.ma2, c2, f2);
+    }
+    if constexpr (XH) {
+      // off-diagonal current term and linear damping of the translational rows
+      const float *A = xh, *Dl = xh + 15;  // Dl: row-major off-diagonal, 5 per row
+      f0 = fmaf(-A[0], c1, fmaf(-A[1], c2, f0));
+      f1 = fmaf(-A[0], c0, fmaf(-A[5], c2, f1));
+      f2 = fmaf(-A[1], c0, fmaf(-A[5], c1, f2));
+      f0 = fmaf(-Dl[0], r1, fmaf(-Dl[1], r2, fmaf(-Dl[2], w0, fmaf(-Dl[3], w1,
+               fmaf(-Dl[4], w2, f0)))));
+      f1 = fmaf(-Dl[5], r0, fmaf(-Dl[6], r2, fmaf(-Dl[7], w0, fmaf(-Dl[8], w1,
+               fmaf(-Dl[9], w2, f1)))));
+      f2 = fmaf(-Dl[10], r0, fmaf(-Dl[11], r1, fmaf(-Dl[12], w0, fmaf(-Dl[13], w1,
+               fmaf(-Dl[14], w2, f2)))));
+    }
+    // Rotational: kT t' - v_r x Q1 - w x k - v x (w x m r_g) - (Dl + Dq|w|) w + G x k_e.
+    float f3 = fmaf(r2, q1, fmaf(-r1, q2, P.kT * t3));
+    float f4 = fmaf(r0, q2, fmaf(-r2, q0, P.kT * t4));
+    float f5 = fmaf(r1, q0, fmaf(-r0, q1, P.kT * t5));
+    f3 = fmaf(w2, k1, fmaf(-w1, k2, f3));
+    f4 = fmaf(w0, k2, fmaf(-w2, k0, f4));
+    f5 = fmaf(w1, k0, fmaf(-w0, k1, f5));
     f3 = fmaf(v2, a1, fmaf(-v1, a2, f3));
     f4 = fmaf(v0, a2, fmaf(-v2, a0, f4));
     f5 = fmaf(v1, a0, fmaf(-v0, a1, f5));
-  }
-  f3 = fmaf(-fmaf(P.dq[3], fabsf(w0), P.dl[3]), w0, f3);
-  f4 = fmaf(-fmaf(P.dq[4], fabsf(w1), P.dl[4]), w1, f4);
-  f5 = fmaf(-fmaf(P.dq[5], fabsf(w2), P.dl[5]), w2, f5);
-  f3 = fmaf(-P.G2, R21, fmaf(P.G1, R22, f3));
-  f4 = fmaf(-P.G0, R22, fmaf(P.G2, R20, f4));
-  f5 = fmaf(-P.G1, R20, fmaf(P.G0, R21, f5));
-  if constexpr (XH) {
-    // off-diagonal current term and linear damping of the rotational rows
-    const float *A = xh, *Dl = xh + 15;
-    f3 = fmaf(-A[2], c0, fmaf(-A[6], c1, fmaf(-A[9], c2, f3)));
-    f4 = fmaf(-A[3], c0, fmaf(-A[7], c1, fmaf(-A[10], c2, f4)));
-    f5 = fmaf(-A[4], c0, fmaf(-A[8], c1, fmaf(-A[11], c2, f5)));
-    f3 = fmaf(-Dl[15], r0, fmaf(-Dl[16], r1, fmaf(-Dl[17], r2, fmaf(-Dl[18], w1,
-             fmaf(-Dl[19], w2, f3)))));
-    f4 = fmaf(-Dl[20], r0, fmaf(-Dl[21], r1, fmaf(-Dl[22], r2, fmaf(-Dl[23], w0,
-             fmaf(-Dl[24], w2, f4)))));
-    f5 = fmaf(-Dl[25], r0, fmaf(-Dl[26], r1, fmaf(-Dl[27], r2, fmaf(-Dl[28], w0,
-             fmaf(-Dl[29], w1, f5)))));
-  }
+    f3 = fmaf(-fmaf(P.dq[3], fabsf(w0), P.dl[3]), w0, f3);
+    f4 = fmaf(-fmaf(P.dq[4], fabsf(w1), P.dl[4]), w1, f4);
+    f5 = fmaf(-fmaf(P.dq[5], fabsf(w2), P.dl[5]), w2, f5);
+    f3 = fmaf(-P.G2, R21, fmaf(P.G1, R22, f3));
+    f4 = fmaf(-P.G0, R22, fmaf(P.G2, R20, f4));
+    f5 = fmaf(-P.G1, R20, fmaf(P.G0, R21, f5));
+    if constexpr (XH) {
+      // off-diagonal current term and linear damping of the rotational rows
+      const float *A = xh, *Dl = xh + 15;
+      f3 = fmaf(-A[2], c0, fmaf(-A[6], c1, fmaf(-A[9], c2, f3)));
+      f4 = fmaf(-A[3], c0, fmaf(-A[7], c1, fmaf(-A[10], c2, f4)));
+      f5 = fmaf(-A[4], c0, fmaf(-A[8], c1, fmaf(-A[11], c2, f5)));
+      f3 = fmaf(-Dl[15], r0, fmaf(-Dl[16], r1, fmaf(-Dl[17], r2, fmaf(-Dl[18], w1,
+               fmaf(-Dl[19], w2, f3)))));
+      f4 = fmaf(-Dl[20], r0, fmaf(-Dl[21], r1, fmaf(-Dl[22], r2, fmaf(-Dl[23], w0,
+               fmaf(-Dl[24], w2, f4)))));
+      f5 = fmaf(-Dl[25], r0, fmaf(-Dl[26], r1, fmaf(-Dl[27], r2, fmaf(-Dl[28], w0,
+               fmaf(-Dl[29], w1, f5)))));
+    }
 
-  // nu' = M^-1 f.
-  if constexpr (DIAG) {
-    d.v[0] = P.mi[0] * f0; d.v[1] = P.mi[1] * f1; d.v[2] = P.mi[2] * f2;
-    d.w[0] = P.mi[3] * f3; d.w[1] = P.mi[4] * f4; d.w[2] = P.mi[5] * f5;
-  } else {
+    // nu' = M^-1 f.
     const float *o = P.mo;
     d.v[0] = P.mi[0] * f0 + o[0] * f1 + o[1] * f2 + o[2] * f3 + o[3] * f4 + o[4] * f5;
     d.v[1] = o[0] * f0 + P.mi[1] * f1 + o[5] * f2 + o[6] * f3 + o[7] * f4 + o[8] * f5;
@@ -467,7 +555,7 @@ __device__ __forceinline__ void lag_segment(const float (&cs)[MT], const LagEnv 
 // One sub-step (§METHOD): classical RK4 of size h, command held (cs = c / tau_m), then
 // q <- q / |q|.
 template <int MT, bool DIAG, bool MIXED, int NH = 0, bool XH = false>
-__device__ __forceinline__ void rk4_step(St<MT> &s, const float (&cs)[MT], const Par<DIAG> &P,
+__device__ __forceinline__ void rk4_step(St<MT> &s, const float (&cs)[MT], const Coef<DIAG> &P,
                                          const float4 *gdir, const float4 *garm, int nt,
                                          bool current_accel, float h,
                                          const float *__restrict__ xh = nullptr) {
@@ -495,7 +583,7 @@ __device__ __forceinline__ void rk4_step(St<MT> &s, const float (&cs)[MT], const
 // the lag state.
 template <int MT, bool DIAG, bool MIXED, int NH = 0, bool XH = false>
 __device__ __forceinline__ void rk4_step_lag(St<MT> &s, const float (&b)[MT], const LagEnv &L,
-                                             const Par<DIAG> &P, const float4 *gdir,
+                                             const Coef<DIAG> &P, const float4 *gdir,
                                              const float4 *garm, int nt, bool current_accel,
                                              float h, const float *__restrict__ xh = nullptr) {
   const float hh = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f);

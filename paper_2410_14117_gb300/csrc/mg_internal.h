@@ -136,14 +136,6 @@ cudaError_t launch_fleet_queue(const FleetView &fv, const BlockDesc *slices, int
 cudaError_t queue_kernel_attributes(NtVariant ntv, bool diag, bool wide, bool structured,
                                     cudaFuncAttributes *attr, int *blocks_per_sm);
 
-// Packed FP32x2 form of the diagonal-mass static-grid step (mg_pair.cu): two envs per thread,
-// results bit-identical to launch_fleet.  Block b of `threads` threads covers blocks[b] (at most
-// 2 x threads envs).
-cudaError_t launch_fleet_pair(const FleetView &fv, const BlockDesc *blocks, int n_blocks,
-                              int threads, NtVariant ntv, bool structured, int32_t k,
-                              cudaStream_t stream);
-cudaError_t pair_kernel_attributes(NtVariant ntv, bool structured, cudaFuncAttributes *attr);
-
 // True when thrusters [0, 4) of the geometry have d_z = 0 and the rest d_x = d_y = 0.
 bool vectored_layout(const Geo &g);
 
@@ -194,7 +186,8 @@ cudaError_t launch_checkpoint(const StatePlanes &st, int64_t n, float *ck, cudaS
 // per 32 envs, through a workspace of adjoint_workspace_bytes), 0 chosen by fleet size.
 cudaError_t adjoint_split(int64_t n, int mode, bool *split);
 size_t adjoint_workspace_bytes(bool eight, int64_t n, int32_t C);
-cudaError_t launch_adjoint(const FleetView &fv, const int32_t *types, bool eight,
+// general: the general-path kernels (off-centre gravity, off-diagonal extension, full M^-1).
+cudaError_t launch_adjoint(const FleetView &fv, const int32_t *types, bool eight, bool general,
                            const float *ckpt, const float *dtraj, int32_t T, int32_t C,
                            int64_t step0, float *dcoef, float *dact, float *dstate0, bool split,
                            float *ws, cudaStream_t stream);

@@ -68,8 +68,12 @@ __global__ void __maxnreg__(!DIAG ? kRegsGeneral : WIDE ? kRegsWide : kRegsDiag)
 
   St<MT> s;
   load_state<MT>(fv.st, e, s);
-  Par<DIAG> P;
-  load_par<DIAG>(fv.pa, e, P);
+  Coef<DIAG> P;
+  {
+    Par<DIAG> raw;
+    load_par<DIAG>(fv.pa, e, raw);
+    P = make_coef<DIAG>(raw);
+  }
   int64_t seg = jd.step0 / jd.hold;
   int32_t left = jd.hold - (int32_t)(jd.step0 - seg * jd.hold);
   const LagEnv L = lag_env(P.itau, fv.dt);

@@ -45,8 +45,6 @@ def main():
     ap.add_argument("--width6", action="store_true",
                     help="unpadded throttle schedule, 6 floats per env and segment "
                          "(mg_set_action_width; 6-thruster vehicle)")
-    ap.add_argument("--packed", action="store_true",
-                    help="two envs per thread with packed FP32x2 arithmetic (mg_set_packed)")
     ap.add_argument("--task", action="store_true",
                     help="circle-tracking task steps of k sub-steps (fused task epilogue) instead "
                          "of plain steps; static grid")
@@ -74,7 +72,6 @@ def main():
     sim = Sim(n, np.full(n, args.vehicle, dtype=np.int32), vs)
     sim.set_launch(args.epb, args.k if args.static else args.chunk, False)
     sim.set_schedule(not args.static, not args.narrow, args.wps)
-    sim.set_packed(args.packed)
     sim.randomize(1234, 0.8, 1.2, 0.2, 0.3, rg_halfwidth=0.02 if args.full else 0.0)
     if args.split:
         p = sim.get_params()

@@ -110,10 +110,6 @@ class Sim:
         mg_set_wait_limit)."""
         call("mg_set_wait_limit", self._h, int(polls))
 
-    def set_packed(self, packed: bool = True):
-        """Two envs per thread with packed FP32x2 arithmetic (see mg_set_packed)."""
-        call("mg_set_packed", self._h, 1 if packed else 0)
-
     def set_adjoint_mode(self, mode: int = 0):
         """Backward kernel of the adjoint: 0 by fleet size, 1 one warp per 32 envs, 2 a
         producer and a consumer warp per 32 envs (see mg_set_adjoint_mode)."""

@@ -21,15 +21,14 @@ def _fleet(vs, n, launch):
     sim = Sim(n, np.zeros(n, np.int32), vs)
     kind, epb, spl = launch
     sim.set_launch(epb, spl, True)
-    sim.set_schedule(kind == "queue", True, 8 if kind == "queue" else 0)
-    sim.set_packed(kind == "packed")
+    sim.set_schedule(kind == "queue", kind != "narrow", 8 if kind == "queue" else 0)
     sim.randomize(5, 0.8, 1.2, 0.2, 0.3)
     sim.reset()
     return sim
 
 
-@pytest.mark.parametrize("launch", [("static", 128, 50), ("static", 32, 1), ("queue", 128, 40),
-                                    ("packed", 64, 100)])
+@pytest.mark.parametrize("launch", [("static", 128, 50), ("narrow", 32, 1), ("queue", 128, 40),
+                                    ("narrow", 64, 100)])
 @pytest.mark.parametrize("how", ["copied", "borrowed", "async"])
 def test_six_wide_schedule_equals_padded_schedule(launch, how):
     vs = vehicles()

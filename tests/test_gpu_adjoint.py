@@ -129,32 +129,87 @@ def test_zero_loss_gradient_gives_zero_and_is_linear():
     sim.close()
 
 
-def test_adjoint_rejects_off_centre_gravity():
-    vs = vehicles()
-    n = 32
-    types = np.zeros(n, dtype=np.int32)
-    params = np.broadcast_to(oracle_nominal(vs)[0], (n, I.NPARAM)).copy()
-    params[:, I.P_RG] = 0.01
+def _general_problem(kind, n=64, T=200, hold=10, seed=11):
+    """The FD problem of _problem on the general path: kind "cg" randomises the centre of
+    gravity (r_g ~ U[-2, 2] cm per axis), "coupled" adds off-diagonal added mass and linear
+    damping at 15 % coupling as well; the target uses the same r_g and extension."""
+    vs, types, params, s0, cmds, _ = _problem(n=n, T=T, hold=hold, seed=seed)
+    g = np.random.default_rng(200 + seed)
+    params[:, I.P_RG:I.P_RG + 3] = I.round_f32(g.uniform(-0.02, 0.02, size=(n, 3)))
+    xpar = I.hydro_offdiag(300 + seed, params) if kind == "coupled" else None
+    pt = params.copy()
+    pt[:, COEF_SLICE] *= np.random.default_rng(99 + seed).uniform(0.9, 1.1, size=(n, 18))
+    pt = I.round_f32(pt)
+    _, target = O.rollout(pt, oracle_geo(vs), types, s0, cmds, hold, T, record=True, xpar=xpar)
+    return vs, types, params, xpar, s0, cmds, I.round_f32(target[:, :, :13])
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("kind", ["cg", "coupled"])
+def test_general_path_gradients_match_fd(kind, mode):
+    """Off-centre gravity (full M_RB, m r_g coupling in C_RB) and the off-diagonal extension
+    (full M_A and D_l): the adjoint's coefficient and action gradients against central finite
+    differences of the FP64 oracle, whose mass matrix and terms are built in full."""
+    T, hold = 200, 10
+    vs, types, params, xpar, s0, cmds, target = _general_problem(kind, T=T, hold=hold)
+    n = len(types)
     sim = Sim(n, types, vs)
+    sim.set_adjoint_mode(mode)
     sim.set_params(torch.tensor(params, dtype=torch.float32, device="cuda"))
+    if xpar is not None:
+        sim.set_hydro_offdiag(torch.tensor(xpar, dtype=torch.float32, device="cuda"))
     coeffs = torch.tensor(params[:, COEF_SLICE], dtype=torch.float32, device="cuda",
                           requires_grad=True)
-    acts = torch.zeros((2, n, 8), device="cuda", requires_grad=True)
-    traj = rollout(sim, coeffs, acts, torch.zeros((n, 21), device="cuda") +
-                   torch.tensor([0, 0, 0, 1] + [0] * 17, device="cuda"), 10, 20, 10)
-    with pytest.raises(MGError):
-        traj.sum().backward()
+    acts = torch.tensor(cmds, dtype=torch.float32, device="cuda", requires_grad=True)
+    st0 = torch.tensor(s0, dtype=torch.float32, device="cuda")
+    traj = rollout(sim, coeffs, acts, st0, hold, T, 20)
+    tgt = torch.tensor(target, dtype=torch.float32, device="cuda")
+    ((traj - tgt) ** 2).mean().backward()
+    gc = coeffs.grad.double().cpu().numpy()
+    ga = acts.grad.double().cpu().numpy()
     sim.close()
 
+    def losses(p, c):
+        _, tr = O.rollout(p, oracle_geo(vs), types, s0, c, hold, T, record=True, xpar=xpar)
+        d = tr[:, :, :13] - target
+        return (d * d).sum(axis=(0, 2)) / d.size
 
-@pytest.mark.parametrize("n,mixed,T,C", [(64, False, 200, 20), (1000, True, 93, 7),
-                                         (4096, False, 50, 32), (37, True, 5, 1)])
-def test_backward_kernels_agree(n, mixed, T, C):
+    fd = np.zeros((n, 18))
+    for j in range(18):
+        col = COEF_SLICE.start + j
+        d = FD_REL * np.abs(params[:, col])
+        p1, p2 = params.copy(), params.copy()
+        p1[:, col] += d
+        p2[:, col] -= d
+        fd[:, j] = (losses(p1, cmds) - losses(p2, cmds)) / (2 * d)
+    err = _rel(gc, fd)
+    assert err.max() <= TOL_GRAD, (kind, err.max(), np.argmax(err))
+    # the actions of one segment in the middle of the rollout, every thruster
+    sg = cmds.shape[0] // 2
+    fa = np.zeros((n, 6))
+    for i in range(6):
+        d = FD_REL * np.maximum(np.abs(cmds[sg, :, i]), 1e-3)
+        c1, c2 = cmds.copy(), cmds.copy()
+        c1[sg, :, i] += d
+        c2[sg, :, i] -= d
+        fa[:, i] = (losses(params, c1) - losses(params, c2)) / (2 * d)
+    err = _rel(ga[sg, :, :6], fa)
+    assert err.max() <= TOL_GRAD, (kind, err.max())
+
+
+@pytest.mark.parametrize("n,mixed,T,C,general", [(64, False, 200, 20, False),
+                                                 (1000, True, 93, 7, False),
+                                                 (4096, False, 50, 32, False),
+                                                 (37, True, 5, 1, False),
+                                                 (1000, True, 93, 7, True),
+                                                 (37, False, 45, 20, True)])
+def test_backward_kernels_agree(n, mixed, T, C, general):
     """The two backward kernels (one warp per 32 envs; producer and consumer warps through
     stage records and shared-memory prefetch) evaluate the same per-env operations, every
     multiply-add written as an explicit fmaf, so their coefficient, action and initial-state
     adjoints agree bit for bit: 6-thruster and mixed fleets (8-thruster records), ragged last
-    segments and blocks, one-sub-step segments."""
+    segments and blocks, one-sub-step segments, the diagonal-mass and the general path
+    (randomised centre of gravity with the off-diagonal extension)."""
     vs = vehicles()
     types = I.mixed_fleet(3, n, max_group=300) if mixed else np.zeros(n, dtype=np.int32)
     nt = np.array([vs[t].n_thr for t in types])
@@ -163,7 +218,11 @@ def test_backward_kernels_agree(n, mixed, T, C):
     for mode in (1, 2):
         sim = Sim(n, types, vs)
         sim.set_adjoint_mode(mode)
-        sim.randomize(77, 0.8, 1.2, 0.2, 0.3)
+        sim.randomize(77, 0.8, 1.2, 0.2, 0.3, rg_halfwidth=0.02 if general else 0.0)
+        if general:
+            p = sim.get_params().double().cpu().numpy()
+            sim.set_hydro_offdiag(torch.tensor(I.hydro_offdiag(8, p), dtype=torch.float32,
+                                               device="cuda"))
         coeffs = sim.get_params()[:, COEF_SLICE].clone().requires_grad_(True)
         acts = torch.tensor(I.commands(5, (T + hold - 1) // hold, n, nt), device="cuda",
                             requires_grad=True)

@@ -3,8 +3,8 @@ sampled envs the oracle computes one by one: the 65,536-env headline fleet (work
 200-register cap, 8 warps/SM, chunk 100, the unpadded 6-float throttle schedule read in place,
 CUDA graph) over a whole 1,000 sub-step episode, parameters drawn in the background and
 installed as the benchmark does them; the 262,144-env mixed fleet over 500 sub-steps and the
-1,048,576-env top of the size sweep (each also on the packed static grid, two envs per thread,
-which the autotuner picks for them)."""
+1,048,576-env top of the size sweep (each also on the 200-register static grid the autotuner picks
+for them)."""
 import numpy as np
 import pytest
 import torch
@@ -74,7 +74,7 @@ def test_headline_fleet_sampled_matches_oracle():
 
 
 @pytest.mark.parametrize("launch", [LaunchConfig("queue", 128, 50, True, 12),
-                                    LaunchConfig("static", 32, 1000, packed=True)])
+                                    LaunchConfig("static", 32, 1000, True)])
 def test_mixed_fleet_262144_sampled_matches_oracle(launch):
     vs = vehicles()
     n, hold = 262144, 10
@@ -97,7 +97,7 @@ def test_mixed_fleet_262144_sampled_matches_oracle(launch):
 
 
 @pytest.mark.parametrize("launch", [LaunchConfig("static", 128, 200),
-                                    LaunchConfig("static", 64, 1000, packed=True)])
+                                    LaunchConfig("static", 64, 1000, True)])
 def test_largest_sweep_fleet_sampled_matches_oracle(launch):
     """1,048,576 envs (the top of the fleet-size sweep), static grid, 200 sub-steps."""
     vs = vehicles()

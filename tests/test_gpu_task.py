@@ -28,23 +28,23 @@ def _centres(n, seed=1):
     return c
 
 
-# (task, look-ahead points, envs per block, sub-steps per launch, work queue, packed): the last
+# (task, look-ahead points, envs per block, sub-steps per launch, work queue, wide): the last
 # launch of a task step carries the fused epilogue; with 3 sub-steps per launch the first 9 of the
 # 10 run as plain step launches first.  Observation rows are staged in shared memory (above 48 KB
 # by opt-in) unless a block's rows exceed the 227 KB limit: 40 look-ahead points (246 floats per
-# row) at 256 envs per block take the direct-write path.  packed: the leading static launches
-# run two envs per thread (the fused last launch keeps one env per thread).
-@pytest.mark.parametrize("task,m,epb,spl,queue,packed", [
-    (O.TASK_STATION, 3, 64, 50, False, False), (O.TASK_CIRCLE, 3, 128, 50, False, False),
-    (O.TASK_HELIX, 40, 64, 50, False, False), (O.TASK_LEMNISCATE, 3, 96, 3, True, False),
-    (O.TASK_CIRCLE, 10, 128, 4, False, False),
-    (O.TASK_CIRCLE, 3, 64, 50, False, True), (O.TASK_HELIX, 40, 32, 50, False, True),
-    (O.TASK_LEMNISCATE, 3, 96, 3, False, True), (O.TASK_STATION, 3, 128, 4, True, True),
+# row) at 256 envs per block take the direct-write path.  wide: the leading plain launches run the
+# 200-register kernel (False: the 128-register one).
+@pytest.mark.parametrize("task,m,epb,spl,queue,wide", [
+    (O.TASK_STATION, 3, 64, 50, False, True), (O.TASK_CIRCLE, 3, 128, 50, False, True),
+    (O.TASK_HELIX, 40, 64, 50, False, True), (O.TASK_LEMNISCATE, 3, 96, 3, True, True),
+    (O.TASK_CIRCLE, 10, 128, 4, False, True),
+    (O.TASK_CIRCLE, 3, 64, 50, False, False), (O.TASK_HELIX, 40, 32, 50, False, False),
+    (O.TASK_LEMNISCATE, 3, 96, 3, False, False), (O.TASK_STATION, 3, 128, 4, True, False),
     # rows of exactly 48 KB per block (256 threads x 48 floats), staged by opt-in beside the
     # static shared memory
-    (O.TASK_CIRCLE, 7, 256, 50, False, False), (O.TASK_CIRCLE, 3, 256, 4, False, True),
-    (O.TASK_HELIX, 40, 256, 50, False, False)])
-def test_task_step_matches_oracle(task, m, epb, spl, queue, packed):
+    (O.TASK_CIRCLE, 7, 256, 50, False, True), (O.TASK_CIRCLE, 3, 256, 4, False, False),
+    (O.TASK_HELIX, 40, 256, 50, False, True)])
+def test_task_step_matches_oracle(task, m, epb, spl, queue, wide):
     vs = vehicles()
     n = 384
     types = I.mixed_fleet(task + 5, n, max_group=100)
@@ -53,8 +53,7 @@ def test_task_step_matches_oracle(task, m, epb, spl, queue, packed):
     centres = _centres(n, task)
     sim = Sim(n, types, vs)
     sim.set_launch(epb, spl, False)
-    sim.set_schedule(queue)
-    sim.set_packed(packed)
+    sim.set_schedule(queue, wide)
     sim.randomize(SEED, 0.8, 1.2, 0.2, SIGMA)
     sim.reset()
     sim.set_procedural_actions(CMD_SEED, K)

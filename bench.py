@@ -29,13 +29,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "env-steps/s at 64K envs (fused vs per-step, same GPU); p50/p99 serve latency"
 
-# Algorithmic FP32 work per env and sub-step of the diagonal-mass step (FMA = 2 flops), counted
-# from the arithmetic of Eq. 1 + RK4 as the kernel performs it for the vectored thruster layout
-# (the allocation's known zeros are not multiplied): 4 right-hand sides without the lag
-# derivative (6 thrusters: 256 flops each; 8 thrusters: 270) + RK4 stage updates and
-# combination of p, q, nu (164; the unused stage values of p are not formed) + the throttle lag
-# in its closed form (12 per thruster) + quaternion renormalisation (15).
-FLOPS_PER_ENV_STEP = {6: 4 * 256 + 164 + 6 * 12 + 15, 8: 4 * 270 + 164 + 8 * 12 + 15}
+# Algorithmic FP32 work per env and sub-step of the diagonal-mass step (FMA = 2 flops, a product
+# into a zero accumulator 1), counted from the arithmetic of Eq. 1 + RK4 as the kernel performs
+# it for the vectored thruster layout (the allocation's known zeros are not multiplied): 4
+# right-hand sides without the lag derivative (6 thrusters: 223 flops each = thrust 52, R(q) 28,
+# relative velocity 18, translational rows 45, rotational rows 45, kinematics 35; 8 thrusters:
+# 237) + RK4 stage updates and combination of p, q, nu (164; the unused stage values of p are
+# not formed) + the throttle lag in its closed form (12 per thruster) + quaternion
+# renormalisation (15).
+FLOPS_PER_ENV_STEP = {6: 4 * 223 + 164 + 6 * 12 + 15, 8: 4 * 237 + 164 + 8 * 12 + 15}
 # Algorithmic HBM bytes per env of one launch: state read + written ((13 + n_thr) floats each),
 # the 34 parameter floats of the diagonal-mass step, and one command row (unpadded for a fleet of
 # 6-thruster vehicles: mg_set_action_width 6).
@@ -317,26 +319,17 @@ def launch_tag(cfg) -> str:
     return f"s{cfg.envs_per_block}k{cfg.steps_per_launch}{'W' if cfg.wide else ''}"
 
 
-def l2_copy_gbs(mb=10, reps=1000):
-    """Bandwidth of back-to-back device copies of an L2-resident buffer pair moving about the
-    per-step kernel's bytes per launch (2 x 10 MiB against its 20.4 MB): read + write bytes over
-    the time per copy, best of 5 runs of `reps` copies.  The ceiling of a launch-per-sub-step
-    kernel whose working set stays in the L2, launch gaps included as for that kernel."""
-    import torch
-    a = torch.empty(mb << 20, dtype=torch.uint8, device="cuda")
-    b = torch.empty_like(a)
-    b.copy_(a)
-    best = float("inf")
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(5):
-        torch.cuda.synchronize()
-        e0.record()
-        for _ in range(reps):
-            b.copy_(a)
-        e1.record()
-        torch.cuda.synchronize()
-        best = min(best, e0.elapsed_time(e1) / reps)
-    return 2 * a.numel() / (best / 1e3) / 1e9
+def l2_peak_gbs():
+    """The L2's peak bandwidth from profiles/peaks_ncu.txt (ncu: lts__t_bytes.sum.peak_sustained
+    bytes per L2 cycle x lts__cycles_elapsed.avg.per_second), or None."""
+    path = os.path.join(ROOT, "profiles", "peaks_ncu.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if "l2_gbs" in f:
+            return float(f["l2_gbs"])
+    return None
 
 
 def run_ours(args):
@@ -533,7 +526,8 @@ def _time_episodes(fn, reps):
 
 def _per_step_roofline(bytes_per_launch, launch_s, n, bound, peak, peak_kind, traffic):
     ach = bytes_per_launch / launch_s / 1e9
-    return {"bound": bound, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+    return {"bound": bound, "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak if peak else None,
             "peak_kind": peak_kind, "bytes_per_env_step": bytes_per_launch // n,
             "launch_us": launch_s * 1e6, "traffic": traffic}
 
@@ -544,8 +538,8 @@ def bench_per_step(sim, acts_dev, args, peaks, peak_kind):
     and the persistent form as the scale configuration names it (static grid, 50 sub-steps per
     launch, one graph).  Its working set (state, parameters, one command: 20 MB) stays in the
     129 MB L2 from launch to launch (ncu, steady state: no DRAM reads, ~40 KB of DRAM writes
-    against 24.8 MB of L2 traffic per launch), so its roofline is the L2-resident copy measured
-    here, not HBM."""
+    against 25 MB of L2 traffic per launch), so its roofline is the L2's bandwidth (ncu's peak),
+    not HBM; it runs far below it (launch- and latency-bound)."""
     import torch
     n, horizon, hold = args.n_envs, args.horizon, args.hold
     stream = torch.cuda.current_stream()
@@ -586,12 +580,11 @@ def bench_per_step(sim, acts_dev, args, peaks, peak_kind):
     k50_ms = timed(graph_episode)
     launch_s = graph_ms / 1e3 / horizon
     bytes_per_launch = n * (2 * STATE_BYTES[6] + PARAM_BYTES + CMD_BYTES[6])
-    l2 = l2_copy_gbs()
+    l2 = l2_peak_gbs()
     return {"host": n * horizon / (host_ms / 1e3), "graph": n * horizon / (graph_ms / 1e3),
             "k50_graph": n * horizon / (k50_ms / 1e3),
             "roofline": _per_step_roofline(bytes_per_launch, launch_s, n, "l2", l2,
-                                           "measured here (L2-resident copy)",
-                                           profiled_traffic("k_fleet_step1", n, 1)),
+                                           "ncu L2 peak", profiled_traffic("k_fleet_step1", n, 1)),
             "host_ms": host_ms, "graph_ms": graph_ms, "k50_ms": k50_ms}
 
 

@@ -41,14 +41,19 @@ struct ServeBlock {
 namespace {
 
 constexpr int kServeThreads = 128;
+// Register cap of the tick kernel for ticks of many blocks: the diagonal-mass step coefficients
+// do not fit 128 registers beside the trajectory record without spilling; 144 (three blocks per
+// SM) served the 200 req/s job mix at p99 2.0 ms against 2.25 ms at 128, and the 10x stream at
+// 6.7 against 8.4 ms.
+constexpr int kRegsServe = 144;
 
-// WIDE (diagonal mass): 200 registers instead of 128, for ticks whose blocks all fit at two per
-// SM.  Few envs (a warp per scheduler or fewer) run latency-bound and gain from the extra
-// registers; a tick of more blocks keeps four per SM resident with 128.  Measured on the
-// 200 req/s job mix: p50 0.60 -> 0.56 ms with this choice per tick; the wide kernel for every
-// tick gave the same p50 but p99 2.0 -> 2.3 ms (the 65,536-env jobs).
+// WIDE (diagonal mass): 200 registers, for ticks whose blocks all fit at two per SM.  Few envs
+// (a warp per scheduler or fewer) run latency-bound and gain from the extra registers; a tick of
+// more blocks keeps more per SM resident with kRegsServe.  Measured on the 200 req/s job mix: p50
+// 0.60 -> 0.56 ms with this choice per tick; the wide kernel for every tick gave the same p50 but
+// p99 2.0 -> 2.3 ms (the 65,536-env jobs).
 template <bool DIAG, int NH, bool WIDE = false>
-__global__ void __maxnreg__(!DIAG ? kRegsGeneral : WIDE ? kRegsWide : kRegsDiag)
+__global__ void __maxnreg__(!DIAG ? kRegsGeneral : WIDE ? kRegsWide : kRegsServe)
     k_serve(const FleetView fv, const JobDesc *__restrict__ jobs,
             const ServeBlock *__restrict__ blocks) {
   constexpr int MT = MG_MAX_THR;

@@ -11,7 +11,7 @@ observation / error / auto-reset epilogue, static grid); ``--split`` runs the sp
 comparison kernel, ``--full`` the general path with off-diagonal hydrodynamics; ``--adjoint`` runs
 ``launches`` forward and backward passes of the differentiable rollout (``k`` sub-steps,
 checkpoints every ``--chunk``, MSE loss on the trajectory; ``--adjoint-mode`` picks the backward
-kernel); ``--serve JOBS`` runs ``launches`` serving ticks of ``k`` sub-steps over JOBS jobs in a
+kernel; with ``--full`` on the general path); ``--serve JOBS`` runs ``launches`` serving ticks of ``k`` sub-steps over JOBS jobs in a
 job pool.  Holds well under a GB of device
 memory at 65,536 envs.
 """
@@ -117,7 +117,11 @@ def adjoint_case(args):
     sim = Sim(n, np.full(n, args.vehicle, dtype=np.int32), vs)
     sim.set_launch(args.epb, 1000, True)
     sim.set_adjoint_mode(args.adjoint_mode)
-    sim.randomize(1234, 0.8, 1.2, 0.2, 0.3)
+    sim.randomize(1234, 0.8, 1.2, 0.2, 0.3, rg_halfwidth=0.02 if args.full else 0.0)
+    if args.full:  # the general path: off-centre gravity and the off-diagonal extension
+        p = sim.get_params().double().cpu().numpy()
+        sim.set_hydro_offdiag(torch.tensor(I.hydro_offdiag(9, p), dtype=torch.float32,
+                                           device="cuda"))
     coeffs = sim.get_params()[:, COEF_SLICE].clone().requires_grad_(True)
     acts = torch.tensor(I.commands(5678, math.ceil(T / 10), n, vs[args.vehicle].n_thr),
                         device="cuda", requires_grad=True)

@@ -343,7 +343,7 @@ mg_status build_blocks(mg_sim *s) {
 // call, and the last advances the cursor by k.
 mg_status launch_chunks(mg_sim *s, int32_t k, float *traj, cudaStream_t stream) {
   FleetView v = s->view();
-  if (s->queue && !traj && !s->has_xh) {
+  if (s->queue && !traj) {
     v.cursor_adv = k;
     MG_CK(launch_fleet_queue(v, s->slices_d, s->n_slices, s->ntv, s->diag, s->structured,
                              s->wide, s->queue_warps_per_sm, k, s->spl, s->sched, s->n_sm,
@@ -483,8 +483,6 @@ mg_status mg_step_noalloc(mg_sim *s, int32_t k) {
   MG_NONNULL(s);
   NvtxRange nvtx("mg_step_noalloc");
   if (k < 1) return fail(MG_EINVAL, "k must be >= 1");
-  if (s->has_xh)
-    return fail(MG_EINVAL, "the work-queue kernel has no off-diagonal hydrodynamics variant");
   if (s->n_slices > kNoAllocMaxSlices) {
     char buf[200];
     snprintf(buf, sizeof buf,
@@ -1430,7 +1428,8 @@ mg_status mg_kernel_info(mg_sim *s, int32_t *regs, int32_t *max_threads, int32_t
   cudaFuncAttributes a;
   int per_sm = 0;
   if (s->queue)
-    MG_CK(queue_kernel_attributes(s->ntv, s->diag, s->wide, s->structured, &a, &per_sm));
+    MG_CK(queue_kernel_attributes(s->ntv, s->diag, s->wide, s->structured, s->has_xh, &a,
+                                  &per_sm));
   else
     MG_CK(fleet_kernel_attributes(s->ntv, s->diag, s->structured, false, s->wide, &a));
   if (regs) *regs = a.numRegs;

@@ -133,8 +133,9 @@ cudaError_t launch_fleet_queue(const FleetView &fv, const BlockDesc *slices, int
                                NtVariant ntv, bool diag, bool structured, bool wide,
                                int warps_per_sm, int32_t k, int32_t chunk, uint32_t *sched,
                                int n_sm, cudaStream_t stream);
+// xh: the general path's off-diagonal-hydrodynamics variant.
 cudaError_t queue_kernel_attributes(NtVariant ntv, bool diag, bool wide, bool structured,
-                                    cudaFuncAttributes *attr, int *blocks_per_sm);
+                                    bool xh, cudaFuncAttributes *attr, int *blocks_per_sm);
 
 // True when thrusters [0, 4) of the geometry have d_z = 0 and the rest d_x = d_y = 0.
 bool vectored_layout(const Geo &g);

@@ -77,10 +77,15 @@ __global__ void __maxnreg__(XH ? kRegsXH : !DIAG ? kRegsGeneral : WIDE ? kRegsWi
   if (fv.cursor_adv) finish_envs(fv, &s_done, bd.count, fv.cursor_adv);
 }
 
-template <int NTV, bool DIAG, bool WIDE, int NH>
-__global__ void __maxnreg__(!DIAG ? kRegsGeneral : WIDE ? kRegsWide : kRegsDiag)
+// XH (general path): each warp stages the off-diagonal hydrodynamic coefficients of the slice it
+// claimed into its own rows of dynamic shared memory [kQueueWarps * 32][MG_NXPARAM] (every lane
+// writes and reads only its own row, so program order suffices).
+template <int NTV, bool DIAG, bool WIDE, int NH, bool XH = false>
+__global__ void __maxnreg__(XH ? kRegsXH : !DIAG ? kRegsGeneral : WIDE ? kRegsWide : kRegsDiag)
     k_fleet_queue(const FleetView fv, const BlockDesc *__restrict__ slices, const int32_t n_slices,
                   const int32_t k_total, const int32_t chunk, uint32_t *__restrict__ sched) {
+  static_assert(!(XH && DIAG), "the off-diagonal hydrodynamics use the general path");
+  extern __shared__ float sxh[];
   constexpr int MT = (NTV == NT_6) ? 6 : 8;
   constexpr bool MIXED = (NTV == NT_MIXED);
   // Thruster geometry of every vehicle type at fixed shared addresses (a per-warp copy at a
@@ -121,11 +126,14 @@ __global__ void __maxnreg__(!DIAG ? kRegsGeneral : WIDE ? kRegsWide : kRegsDiag)
     const float4 *gdir = sgeo[bd.type & (MG_MAX_TYPES - 1)], *garm = gdir + MG_MAX_THR;
     if (lane < bd.count) {
       const int64_t e = (int64_t)bd.env0 + lane;
+      float *row = sxh + threadIdx.x * MG_NXPARAM;
+      if constexpr (XH)
+        for (int j = 0; j < MG_NXPARAM; ++j) row[j] = __ldg(fv.xh + (int64_t)j * fv.n + e);
       St<MT> st;
-      advance_env<MT, DIAG, MIXED, false, true, NH>(fv, e, MIXED ? bd.n_thr : MT, gdir, garm,
-                                                    step0 + (int64_t)c * chunk,
-                                                    min(chunk, k_total - c * chunk), nullptr,
-                                                    st);
+      advance_env<MT, DIAG, MIXED, false, true, NH, XH>(fv, e, MIXED ? bd.n_thr : MT, gdir, garm,
+                                                        step0 + (int64_t)c * chunk,
+                                                        min(chunk, k_total - c * chunk),
+                                                        nullptr, st, XH ? row : nullptr);
       store_and_flag<MT, true>(fv, e, st);
     }
     __syncwarp();
@@ -203,8 +211,10 @@ const void *kernel_ptr(bool structured) {
 }
 
 template <int NTV, bool DIAG>
-const void *queue_ptr(bool wide, bool structured) {
+const void *queue_ptr(bool wide, bool structured, bool xh) {
   constexpr int S = DIAG ? 4 : 0;
+  if constexpr (!DIAG)
+    if (xh) return reinterpret_cast<const void *>(&k_fleet_queue<NTV, false, false, 0, true>);
   if (DIAG && structured)
     return wide ? reinterpret_cast<const void *>(&k_fleet_queue<NTV, DIAG, true, S>)
                 : reinterpret_cast<const void *>(&k_fleet_queue<NTV, DIAG, false, S>);
@@ -212,22 +222,33 @@ const void *queue_ptr(bool wide, bool structured) {
               : reinterpret_cast<const void *>(&k_fleet_queue<NTV, DIAG, false, 0>);
 }
 
-const void *queue_kernel(NtVariant ntv, bool diag, bool wide, bool structured) {
+const void *queue_kernel(NtVariant ntv, bool diag, bool wide, bool structured, bool xh) {
   switch (ntv) {
     case NT_6:
-      return diag ? queue_ptr<NT_6, true>(wide, structured) : queue_ptr<NT_6, false>(wide, false);
+      return diag ? queue_ptr<NT_6, true>(wide, structured, false)
+                  : queue_ptr<NT_6, false>(wide, false, xh);
     case NT_8:
-      return diag ? queue_ptr<NT_8, true>(wide, structured) : queue_ptr<NT_8, false>(wide, false);
+      return diag ? queue_ptr<NT_8, true>(wide, structured, false)
+                  : queue_ptr<NT_8, false>(wide, false, xh);
     default:
-      return diag ? queue_ptr<NT_MIXED, true>(wide, structured)
-                  : queue_ptr<NT_MIXED, false>(wide, false);
+      return diag ? queue_ptr<NT_MIXED, true>(wide, structured, false)
+                  : queue_ptr<NT_MIXED, false>(wide, false, xh);
   }
 }
+
+// Dynamic shared memory of the XH work-queue kernel (one coefficient row per thread).
+constexpr size_t kQueueXhBytes = sizeof(float) * kQueueWarps * 32 * MG_NXPARAM;
 
 template <int NTV, bool DIAG, int NH>
 void queue_launch_w(bool wide, int grid, const FleetView &fv, const BlockDesc *slices,
                     int32_t n_slices, int32_t k, int32_t chunk, uint32_t *sched,
                     cudaStream_t stream) {
+  if constexpr (!DIAG)
+    if (fv.xh) {
+      k_fleet_queue<NTV, false, false, 0, true><<<grid, kQueueWarps * 32, kQueueXhBytes, stream>>>(
+          fv, slices, n_slices, k, chunk, sched);
+      return;
+    }
   if (wide)
     k_fleet_queue<NTV, DIAG, true, NH><<<grid, kQueueWarps * 32, 0, stream>>>(
         fv, slices, n_slices, k, chunk, sched);
@@ -289,21 +310,25 @@ cudaError_t fleet_kernel_attributes(NtVariant ntv, bool diag, bool structured, b
 size_t queue_sched_bytes(int n_slices) { return 16 + 4 * (size_t)n_slices; }
 
 cudaError_t queue_kernel_attributes(NtVariant ntv, bool diag, bool wide, bool structured,
-                                    cudaFuncAttributes *attr, int *blocks_per_sm) {
-  const void *f = queue_kernel(ntv, diag, wide, structured);
+                                    bool xh, cudaFuncAttributes *attr, int *blocks_per_sm) {
+  xh = xh && !diag;
+  const void *f = queue_kernel(ntv, diag, wide, structured, xh);
   cudaError_t e = cudaFuncGetAttributes(attr, f);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kQueueWarps * 32, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kQueueWarps * 32,
+                                                       xh ? kQueueXhBytes : 0);
 }
 
 cudaError_t launch_fleet_queue(const FleetView &fv, const BlockDesc *slices, int n_slices,
                                NtVariant ntv, bool diag, bool structured, bool wide,
                                int warps_per_sm, int32_t k, int32_t chunk, uint32_t *sched,
                                int n_sm, cudaStream_t stream) {
-  if (n_slices < 1 || k < 1 || chunk < 1 || n_sm < 1 || fv.xh) return cudaErrorInvalidValue;
+  if (n_slices < 1 || k < 1 || chunk < 1 || n_sm < 1 || (fv.xh && diag))
+    return cudaErrorInvalidValue;
   cudaFuncAttributes attr;
   int per_sm = 0;
-  cudaError_t e = queue_kernel_attributes(ntv, diag, wide, structured, &attr, &per_sm);
+  cudaError_t e = queue_kernel_attributes(ntv, diag, wide, structured, fv.xh != nullptr, &attr,
+                                          &per_sm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   // Resident warps: at most what fits (and at most warps_per_sm per SM when that is > 0), and no

@@ -82,8 +82,8 @@ def test_full_hydro_500_substeps_matches_oracle(epb, spl):
 
 def test_extension_round_trip_clear_and_schedules():
     """get returns what was set; clearing gives the diagonal model bit for bit; the work-queue
-    schedule and graph replay fall back to the static grid with identical bits; the task step
-    carries the extension; mg_step_noalloc and the split step reject it."""
+    schedule (its off-diagonal variant), graph replay and mg_step_noalloc give the static grid's
+    bits; the task step carries the extension; the split step rejects it."""
     vs = vehicles()
     n = 1500
     types, params, xpar = _fleet(91, n, vs, rg=0.0)
@@ -103,8 +103,12 @@ def test_extension_round_trip_clear_and_schedules():
     for _ in range(12):
         sim.step(10)
     torch.testing.assert_close(sim.get_state().cpu(), a, rtol=0, atol=0)
-    with pytest.raises(MGError):
+    # the no-allocation entry point runs the same work-queue kernel
+    sim.set_state(torch.tensor(states, dtype=torch.float32, device="cuda"))
+    sim.set_procedural_actions(7, 10)
+    for _ in range(12):
         call("mg_step_noalloc", sim._h, 10)
+    torch.testing.assert_close(sim.get_state().cpu(), a, rtol=0, atol=0)
     with pytest.raises(MGError):
         sim.step_split(1, torch.zeros((6, n), device="cuda"))
     # cleared: the same as a sim that never had the extension

@@ -482,44 +482,22 @@ __device__ __forceinline__ void rhs(const St<MT> &s, const float (&cs)[MT], cons
   d.q[3] = fmaf(qw, w2, fmaf(qx, w1, -qy * w0));
 }
 
-// Packed FP32x2 FMAs for the RK4 stage updates: measured on GB300 without gain (the pairs cost
-// register moves), so off; kept selectable because the result is bit-identical either way.
-#ifndef MG_PACKED_FMA
-#define MG_PACKED_FMA 0
-#endif
-
-// Two correctly rounded FMAs in one instruction (sm_100+): bit-identical to two fmaf calls.
-__device__ __forceinline__ void fma2(float a0, float a1, float k0, float k1, float x0, float x1,
-                                     float &y0, float &y1) {
-#if MG_PACKED_FMA
-  const float2 r = __ffma2_rn(make_float2(a0, a1), make_float2(k0, k1), make_float2(x0, x1));
-  y0 = r.x;
-  y1 = r.y;
-#else
-  y0 = fmaf(a0, k0, x0);
-  y1 = fmaf(a1, k1, x1);
-#endif
-}
-
 // y = x + a k, with the quaternion taking a / 2 (its derivative is stored doubled).  WN = false
 // leaves the throttle states alone.
 template <int MT, bool WN = true>
 __device__ __forceinline__ void axpy(St<MT> &y, const St<MT> &x, float a, const St<MT> &k) {
   const float aq = 0.5f * a;
-  fma2(a, a, k.p[0], k.p[1], x.p[0], x.p[1], y.p[0], y.p[1]);
-  fma2(a, a, k.p[2], k.v[0], x.p[2], x.v[0], y.p[2], y.v[0]);
-  fma2(aq, aq, k.q[0], k.q[1], x.q[0], x.q[1], y.q[0], y.q[1]);
-  fma2(aq, aq, k.q[2], k.q[3], x.q[2], x.q[3], y.q[2], y.q[3]);
-  fma2(a, a, k.v[1], k.v[2], x.v[1], x.v[2], y.v[1], y.v[2]);
-  fma2(a, a, k.w[0], k.w[1], x.w[0], x.w[1], y.w[0], y.w[1]);
-  if constexpr (WN) {
-    fma2(a, a, k.w[2], k.n[0], x.w[2], x.n[0], y.w[2], y.n[0]);
 #pragma unroll
-    for (int i = 1; i + 1 < MT; i += 2)
-      fma2(a, a, k.n[i], k.n[i + 1], x.n[i], x.n[i + 1], y.n[i], y.n[i + 1]);
-    if constexpr (MT % 2 == 0) y.n[MT - 1] = fmaf(a, k.n[MT - 1], x.n[MT - 1]);
-  } else {
-    y.w[2] = fmaf(a, k.w[2], x.w[2]);
+  for (int i = 0; i < 3; ++i) {
+    y.p[i] = fmaf(a, k.p[i], x.p[i]);
+    y.v[i] = fmaf(a, k.v[i], x.v[i]);
+    y.w[i] = fmaf(a, k.w[i], x.w[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) y.q[i] = fmaf(aq, k.q[i], x.q[i]);
+  if constexpr (WN) {
+#pragma unroll
+    for (int i = 0; i < MT; ++i) y.n[i] = fmaf(a, k.n[i], x.n[i]);
   }
 }
 

@@ -145,14 +145,19 @@ KERNEL_SOURCES = {
 
 
 def kernel_sources_sha(files) -> str:
-    """Hash of the sources a kernel is compiled from, to tell whether a committed ncu capture
-    still describes the kernel being timed."""
+    """Hash of the code of the sources a kernel is compiled from (comments removed, whitespace
+    collapsed: an edit of the documentation alone keeps the kernel), to tell whether a committed
+    ncu capture still describes the kernel being timed."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for rel in files:
         h.update(rel.encode())
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, rel), encoding="utf-8") as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

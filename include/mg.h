@@ -451,6 +451,17 @@ mg_status mg_pool_set_stream(mg_pool *pool, void *cuda_stream);
  * enough; nothing changed). */
 mg_status mg_pool_admit(mg_pool *pool, const mg_job_spec *spec, float *traj, int32_t *job_id);
 
+/* mg_pool_admit for a job with the off-diagonal hydrodynamic extension (full M_A and D_l, the
+ * layout of MG_NXPARAM above): xh [n_envs][MG_NXPARAM], host or device, copied before the call
+ * returns (NULL: mg_pool_admit).  The job's M^-1 is derived with the off-diagonal added mass,
+ * and the ticks advance it on the general path in a second launch beside the other jobs (whose
+ * results do not change).  A job with the extension may randomise r_g in any pool.  The first
+ * such job allocates the pool's [MG_NXPARAM][capacity_envs] planes (MG_ENOMEM if that fails;
+ * nothing changed).  The native request loop (mg_server_*) admits jobs without the extension.
+ * Errors as mg_pool_admit. */
+mg_status mg_pool_admit_offdiag(mg_pool *pool, const mg_job_spec *spec, float *traj,
+                                const float *xh, int32_t *job_id);
+
 /* One launch: every admitted job with sub-steps left advances min(k, horizon - done) of them.
  * *n_running (may be NULL) receives how many jobs advanced.  Asynchronous. */
 mg_status mg_pool_tick(mg_pool *pool, int32_t k, int32_t *n_running);

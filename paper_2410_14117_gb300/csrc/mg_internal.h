@@ -149,7 +149,8 @@ struct SetupView {
   ParamPlanes pa;
   unsigned long long *n_not_spd;
   unsigned int *any_offdiag;
-  const float *xh;           // device [MG_NXPARAM][n] off-diagonal hydrodynamics, or null
+  const float *xh;           // device [MG_NXPARAM][xh_stride] off-diagonal hydrodynamics, or null
+  int64_t xh_stride;         // floats between xh's component planes (0: n)
 };
 
 // background_blocks > 0: at most that many 64-thread blocks striding over the fleet (leaves room
@@ -159,9 +160,10 @@ cudaError_t launch_randomize(const SetupView &v, const float *nominal /*dev [n_t
                              double rg_halfwidth, cudaStream_t stream, int background_blocks = 0);
 cudaError_t launch_import_params(const SetupView &v, const float *in /*dev [n][35]*/,
                                  cudaStream_t stream);
-// [n][MG_NXPARAM] records <-> [MG_NXPARAM][n] planes (to_planes: records -> planes).
+// [n][MG_NXPARAM] records <-> [MG_NXPARAM][stride] planes (to_planes: records -> planes); the
+// planes' first n floats of each component are read or written.  stride 0: n.
 cudaError_t launch_xh_transpose(const float *in, float *out, int64_t n, bool to_planes,
-                                cudaStream_t stream);
+                                cudaStream_t stream, int64_t stride = 0);
 cudaError_t launch_export_params(const SetupView &v, float *out /*dev [n][35]*/,
                                  cudaStream_t stream);
 cudaError_t launch_reset(const StatePlanes &st, int64_t n, int64_t gid0, const uint8_t *mask,

@@ -7,7 +7,9 @@
 // the job's seeds and job-local env ids, so a job's result does not depend on where it sits or
 // what else runs.  Each tick is one launch of k_serve over every running job: a job advances
 // min(k, horizon - done) sub-steps, recording its trajectory into a caller-owned device buffer.
-// Jobs that arrive while others run join at the next tick.
+// Jobs that arrive while others run join at the next tick.  Jobs admitted with the off-diagonal
+// hydrodynamic extension (full M_A and D_l) run in a second launch of the same tick, on the
+// general path with each block's coefficients staged in shared memory.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -52,18 +54,23 @@ constexpr int kRegsServe = 144;
 // more blocks keeps more per SM resident with kRegsServe.  Measured on the 200 req/s job mix: p50
 // 0.60 -> 0.56 ms with this choice per tick; the wide kernel for every tick gave the same p50 but
 // p99 2.0 -> 2.3 ms (the 65,536-env jobs).
-template <bool DIAG, int NH, bool WIDE = false>
-__global__ void __maxnreg__(!DIAG ? kRegsGeneral : WIDE ? kRegsWide : kRegsServe)
+// XH (general path): the off-diagonal hydrodynamic coefficients of the block's envs, read from
+// the pool's [MG_NXPARAM][capacity] planes into dynamic shared memory [kServeThreads][MG_NXPARAM].
+template <bool DIAG, int NH, bool WIDE = false, bool XH = false>
+__global__ void __maxnreg__(XH ? kRegsXH : !DIAG ? kRegsGeneral : WIDE ? kRegsWide : kRegsServe)
     k_serve(const FleetView fv, const JobDesc *__restrict__ jobs,
             const ServeBlock *__restrict__ blocks) {
+  static_assert(!XH || !DIAG, "the off-diagonal extension runs on the general path");
   constexpr int MT = MG_MAX_THR;
   __shared__ float4 sdir[MG_MAX_THR], sarm[MG_MAX_THR];
+  extern __shared__ float sxh[];
   const ServeBlock b = blocks[blockIdx.x];
   const JobDesc jd = jobs[b.job];
   if (threadIdx.x < MG_MAX_THR) {
     sdir[threadIdx.x] = fv.geo[jd.type].dir[threadIdx.x];
     sarm[threadIdx.x] = fv.geo[jd.type].arm[threadIdx.x];
   }
+  if constexpr (XH) stage_xh(fv.xh, fv.n, jd.env0 + b.first, b.count, sxh);
   __syncthreads();
   if ((int)threadIdx.x >= b.count || jd.steps <= 0) return;
   const int64_t el = (int64_t)b.first + threadIdx.x;  // job-local env
@@ -97,7 +104,8 @@ __global__ void __maxnreg__(!DIAG ? kRegsGeneral : WIDE ? kRegsWide : kRegsServe
       left = jd.hold;
       load(seg);
     }
-    rk4_step_lag<MT, DIAG, true, NH>(s, lb, L, P, sdir, sarm, nt, current_accel, fv.dt);
+    rk4_step_lag<MT, DIAG, true, NH, XH>(s, lb, L, P, sdir, sarm, nt, current_accel, fv.dt,
+                                         XH ? sxh + threadIdx.x * MG_NXPARAM : nullptr);
     --left;
     if (jd.traj) {
       float *t = jd.traj + ((int64_t)(jd.step0 + it) * MG_NTRAJ) * jd.n + el;
@@ -151,6 +159,7 @@ bool dev_ptr(const void *p) {
 
 struct Job {
   bool live = false;
+  bool xh = false;  // admitted with the off-diagonal hydrodynamic extension
   int64_t env0 = 0;
   int32_t n = 0, type = 0, hold = 1, horizon = 0, done = 0;
   uint64_t cmd_seed = 0;
@@ -183,6 +192,9 @@ struct mg_pool {
   uint32_t *flags = nullptr, *episode = nullptr;
   unsigned long long *counters = nullptr;
   unsigned int *offdiag = nullptr;
+  // off-diagonal hydrodynamics, [MG_NXPARAM][cap] planes (allocated at the first job that has
+  // them; rows of other jobs are stale and never read)
+  float *xh = nullptr;
   std::map<int64_t, int64_t> free_ranges;  // start -> length
   std::vector<Job> jobs;
   void *dev_table = nullptr;  // device copy of the tick's job table + block list
@@ -207,6 +219,7 @@ FleetView pool_view(const mg_pool *p) {
   v.counters = p->counters;
   v.hold = 1;
   v.spin_limit = MG_WAIT_POLLS_DEFAULT;
+  v.xh = p->xh;
   return v;
 }
 
@@ -381,6 +394,7 @@ mg_status mg_pool_destroy(mg_pool *p) {
     if (r.used) cudaEventDestroy(r.used);
   }
   cudaFree(p->dev_table);
+  cudaFree(p->xh);
   cudaFree(p->arena);
   delete p;
   return MG_OK;
@@ -399,8 +413,12 @@ mg_status mg_pool_set_stream(mg_pool *p, void *stream) {
   return MG_OK;
 }
 
-mg_status mg_pool_admit(mg_pool *p, const mg_job_spec *spec, float *traj, int32_t *job_id) {
-  NvtxRange nvtx("mg_pool_admit");
+}  // extern "C"
+
+namespace {
+
+mg_status admit_job(mg_pool *p, const mg_job_spec *spec, float *traj, const float *xh,
+                    int32_t *job_id) {
   if (!p || !spec || !job_id) return pfail(MG_EINVAL, "NULL argument");
   const mg_job_spec &s = *spec;
   const mg_ranges &r = s.ranges;
@@ -409,10 +427,19 @@ mg_status mg_pool_admit(mg_pool *p, const mg_job_spec *spec, float *traj, int32_
       !(r.lo <= r.hi) || !(r.current_sigma >= 0.f) || !(r.nu0_sigma >= 0.f) || r.flags != 0 ||
       !(r.rg_halfwidth >= 0.f))
     return pfail(MG_EINVAL, "bad job spec");
-  if (r.rg_halfwidth > 0.f && p->diag)
+  if (r.rg_halfwidth > 0.f && p->diag && !xh)
     return pfail(MG_EINVAL,
                  "randomised r_g needs a pool created with an off-centre-gravity vehicle type");
   if (traj && !dev_ptr(traj)) return pfail(MG_EINVAL, "traj must be device memory");
+  if (xh && !p->xh) {
+    const size_t bytes = (size_t)p->cap * MG_NXPARAM * 4;
+    if (cudaMalloc(reinterpret_cast<void **>(&p->xh), bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p->xh = nullptr;
+      return pfail(MG_ENOMEM, "cudaMalloc(pool off-diagonal hydrodynamics)");
+    }
+    PK(cudaMemsetAsync(p->xh, 0, bytes, p->stream));
+  }
   int64_t env0 = 0;
   if (!take_range(p, s.n_envs, &env0))
     return pfail(MG_ENOMEM, "no free range of the pool is large enough");
@@ -421,6 +448,7 @@ mg_status mg_pool_admit(mg_pool *p, const mg_job_spec *spec, float *traj, int32_
   if (id == (int32_t)p->jobs.size()) p->jobs.emplace_back();
   Job &j = p->jobs[id];
   j.live = true;
+  j.xh = (xh != nullptr);
   j.env0 = env0;
   j.n = (int32_t)s.n_envs;
   j.type = s.vehicle_type;
@@ -441,6 +469,22 @@ mg_status mg_pool_admit(mg_pool *p, const mg_job_spec *spec, float *traj, int32_
   v.pa = sub_params(p->pa, env0);
   v.n_not_spd = p->counters + 1;
   v.any_offdiag = p->offdiag;
+  if (xh) {
+    // the job's records -> its columns of the pool's planes (stride: the capacity)
+    const size_t bytes = (size_t)n * MG_NXPARAM * 4;
+    if (dev_ptr(xh)) {
+      PK(launch_xh_transpose(xh, p->xh + env0, n, true, p->stream, p->cap));
+    } else {
+      float *tmp = nullptr;
+      PK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), bytes, p->stream));
+      cudaError_t e = cudaMemcpyAsync(tmp, xh, bytes, cudaMemcpyHostToDevice, p->stream);
+      if (e == cudaSuccess) e = launch_xh_transpose(tmp, p->xh + env0, n, true, p->stream, p->cap);
+      cudaFreeAsync(tmp, p->stream);
+      if (e != cudaSuccess) return pfail_cuda(e, "off-diagonal hydrodynamics upload");
+    }
+    v.xh = p->xh + env0;
+    v.xh_stride = p->cap;
+  }
   PK(launch_randomize(v, p->nominal, s.param_seed, (double)r.lo, (double)r.hi,
                       (double)r.current_sigma, (double)r.rg_halfwidth, p->stream));
   PK(cudaMemsetAsync(p->episode + env0, 0, 4 * n, p->stream));
@@ -450,12 +494,27 @@ mg_status mg_pool_admit(mg_pool *p, const mg_job_spec *spec, float *traj, int32_
   return MG_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+mg_status mg_pool_admit(mg_pool *p, const mg_job_spec *spec, float *traj, int32_t *job_id) {
+  NvtxRange nvtx("mg_pool_admit");
+  return admit_job(p, spec, traj, nullptr, job_id);
+}
+
+mg_status mg_pool_admit_offdiag(mg_pool *p, const mg_job_spec *spec, float *traj,
+                                const float *xh, int32_t *job_id) {
+  NvtxRange nvtx("mg_pool_admit_offdiag");
+  return admit_job(p, spec, traj, xh, job_id);
+}
+
 mg_status mg_pool_tick(mg_pool *p, int32_t k, int32_t *n_running) {
   NvtxRange nvtx("mg_pool_tick");
   if (!p) return pfail(MG_EINVAL, "NULL pool");
   if (k < 1) return pfail(MG_EINVAL, "k must be >= 1");
   std::vector<JobDesc> table;
-  std::vector<ServeBlock> blocks;
+  std::vector<ServeBlock> blocks, xblocks;  // jobs without and with the off-diagonal extension
   for (size_t i = 0; i < p->jobs.size(); ++i) {
     Job &j = p->jobs[i];
     if (!j.live || j.done >= j.horizon) continue;
@@ -472,13 +531,14 @@ mg_status mg_pool_tick(mg_pool *p, int32_t k, int32_t *n_running) {
     const int32_t idx = (int32_t)table.size();
     table.push_back(d);
     for (int32_t f = 0; f < j.n; f += kServeThreads)
-      blocks.push_back(ServeBlock{idx, f, std::min(kServeThreads, j.n - f), 0});
+      (j.xh ? xblocks : blocks).push_back(ServeBlock{idx, f, std::min(kServeThreads, j.n - f), 0});
     j.done += d.steps;
   }
   if (n_running) *n_running = (int32_t)table.size();
   if (table.empty()) return MG_OK;
   const size_t tb = align_up(table.size() * sizeof(JobDesc), 256);
-  const size_t bytes = tb + blocks.size() * sizeof(ServeBlock);
+  const size_t nb = blocks.size(), nx = xblocks.size();
+  const size_t bytes = tb + (nb + nx) * sizeof(ServeBlock);
   Stage &sg = p->ring[p->ring_at];
   p->ring_at = (p->ring_at + 1) % 3;
   PK(cudaEventSynchronize(sg.used));  // the slot's previous copy has been consumed
@@ -499,26 +559,35 @@ mg_status mg_pool_tick(mg_pool *p, int32_t k, int32_t *n_running) {
   }
   char *h = static_cast<char *>(sg.host);
   memcpy(h, table.data(), table.size() * sizeof(JobDesc));
-  memcpy(h + tb, blocks.data(), blocks.size() * sizeof(ServeBlock));
+  memcpy(h + tb, blocks.data(), nb * sizeof(ServeBlock));
+  memcpy(h + tb + nb * sizeof(ServeBlock), xblocks.data(), nx * sizeof(ServeBlock));
   PK(cudaMemcpyAsync(p->dev_table, h, bytes, cudaMemcpyHostToDevice, p->stream));
   PK(cudaEventRecord(sg.used, p->stream));
   const JobDesc *jt = static_cast<const JobDesc *>(p->dev_table);
   const ServeBlock *bl =
       reinterpret_cast<const ServeBlock *>(static_cast<char *>(p->dev_table) + tb);
   const FleetView v = pool_view(p);
-  const int nb = (int)blocks.size();
-  const bool wide = nb <= 2 * p->n_sm;
-  if (p->diag && p->structured && wide)
-    k_serve<true, 4, true><<<nb, kServeThreads, 0, p->stream>>>(v, jt, bl);
+  const int g = (int)nb;
+  const bool wide = g <= 2 * p->n_sm;
+  if (g == 0)
+    ;
+  else if (p->diag && p->structured && wide)
+    k_serve<true, 4, true><<<g, kServeThreads, 0, p->stream>>>(v, jt, bl);
   else if (p->diag && p->structured)
-    k_serve<true, 4><<<nb, kServeThreads, 0, p->stream>>>(v, jt, bl);
+    k_serve<true, 4><<<g, kServeThreads, 0, p->stream>>>(v, jt, bl);
   else if (p->diag && wide)
-    k_serve<true, 0, true><<<nb, kServeThreads, 0, p->stream>>>(v, jt, bl);
+    k_serve<true, 0, true><<<g, kServeThreads, 0, p->stream>>>(v, jt, bl);
   else if (p->diag)
-    k_serve<true, 0><<<nb, kServeThreads, 0, p->stream>>>(v, jt, bl);
+    k_serve<true, 0><<<g, kServeThreads, 0, p->stream>>>(v, jt, bl);
   else
-    k_serve<false, 0><<<nb, kServeThreads, 0, p->stream>>>(v, jt, bl);
+    k_serve<false, 0><<<g, kServeThreads, 0, p->stream>>>(v, jt, bl);
   PK(cudaGetLastError());
+  if (nx > 0) {
+    constexpr size_t kXhBytes = sizeof(float) * kServeThreads * MG_NXPARAM;  // 23,040 B
+    k_serve<false, 0, false, true>
+        <<<(int)nx, kServeThreads, kXhBytes, p->stream>>>(v, jt, bl + nb);
+    PK(cudaGetLastError());
+  }
   return MG_OK;
 }
 

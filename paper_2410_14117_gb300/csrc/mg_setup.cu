@@ -86,10 +86,11 @@ __device__ void derive(const SetupView &v, int64_t e, const double *p) {
   const double rg[3] = {p[MG_P_RG], p[MG_P_RG + 1], p[MG_P_RG + 2]};
   const double *ma = p + MG_P_MA;
   const double r2 = rg[0] * rg[0] + rg[1] * rg[1] + rg[2] * rg[2];
+  const int64_t xs = v.xh_stride ? v.xh_stride : v.n;
   if (r2 == 0.0) {
     bool xh_zero = true;
     if (v.xh)
-      for (int t = 0; t < 15; ++t) xh_zero = xh_zero && v.xh[(int64_t)t * v.n + e] == 0.f;
+      for (int t = 0; t < 15; ++t) xh_zero = xh_zero && v.xh[(int64_t)t * xs + e] == 0.f;
     if (xh_zero) {
       derive_diag(v, e, p);
       return;
@@ -117,7 +118,7 @@ __device__ void derive(const SetupView &v, int64_t e, const double *p) {
     int t = 0;
     for (int i = 0; i < 6; ++i)
       for (int j = i + 1; j < 6; ++j, ++t) {
-        const double a = (double)v.xh[(int64_t)t * v.n + e];
+        const double a = (double)v.xh[(int64_t)t * xs + e];
         M[i][j] += a;
         M[j][i] += a;
         ma_off = ma_off || a != 0.0;
@@ -265,14 +266,14 @@ __global__ void k_import_params(const SetupView v, const float *__restrict__ in)
 // Off-diagonal hydrodynamics between the record layout [n][MG_NXPARAM] and the planes
 // [MG_NXPARAM][n] the step reads (to_planes), or back.
 __global__ void k_xh_transpose(const float *__restrict__ in, float *__restrict__ out, int64_t n,
-                               bool to_planes) {
+                               bool to_planes, int64_t stride) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
   for (int c = 0; c < MG_NXPARAM; ++c) {
     if (to_planes)
-      out[(int64_t)c * n + e] = in[e * MG_NXPARAM + c];
+      out[(int64_t)c * stride + e] = in[e * MG_NXPARAM + c];
     else
-      out[e * MG_NXPARAM + c] = in[(int64_t)c * n + e];
+      out[e * MG_NXPARAM + c] = in[(int64_t)c * stride + e];
   }
 }
 
@@ -390,8 +391,9 @@ cudaError_t launch_randomize(const SetupView &v, const float *nominal, uint64_t 
 }
 
 cudaError_t launch_xh_transpose(const float *in, float *out, int64_t n, bool to_planes,
-                                cudaStream_t stream) {
-  k_xh_transpose<<<blocks_for(n), kThreads, 0, stream>>>(in, out, n, to_planes);
+                                cudaStream_t stream, int64_t stride) {
+  if (stride < n) stride = n;
+  k_xh_transpose<<<blocks_for(n), kThreads, 0, stream>>>(in, out, n, to_planes, stride);
   return cudaGetLastError();
 }
 

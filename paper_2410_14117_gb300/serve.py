@@ -17,8 +17,8 @@ import time
 import numpy as np
 import torch
 
-from ._lib import (MG_NSTATE, MG_NTRAJ, JobSpec, MGError, Ranges, ServerConfig, VehicleParams,
-                   call)
+from ._lib import (MG_NSTATE, MG_NTRAJ, MG_NXPARAM, JobSpec, MGError, Ranges, ServerConfig,
+                   VehicleParams, call)
 from .sim import _ptr, vehicle_struct
 
 # Device bytes per env held by the pool arena (state planes, parameter planes and records,
@@ -39,13 +39,23 @@ class Pool:
         call("mg_pool_set_stream", self._h, ctypes.c_void_p(self.stream.cuda_stream))
 
     def admit(self, n_envs, vehicle_type, horizon, param_seed, cmd_seed, hold=10, traj=None,
-              lo=0.8, hi=1.2, current_sigma=0.2, nu0_sigma=0.3):
-        """Job id, or None when no free range is large enough."""
+              lo=0.8, hi=1.2, current_sigma=0.2, nu0_sigma=0.3, rg_halfwidth=0.0, xh=None):
+        """Job id, or None when no free range is large enough.  xh: the job's off-diagonal
+        added mass and linear damping, float32 [n_envs, MG_NXPARAM] (host or device), or None."""
         spec = JobSpec(int(n_envs), int(vehicle_type), int(hold), int(horizon), 0,
-                       int(param_seed), int(cmd_seed), Ranges(lo, hi, current_sigma, nu0_sigma, 0))
+                       int(param_seed), int(cmd_seed),
+                       Ranges(lo, hi, current_sigma, nu0_sigma, 0, rg_halfwidth))
         jid = ctypes.c_int32()
-        st = call("mg_pool_admit", self._h, ctypes.byref(spec),
-                  _ptr(traj) if traj is not None else None, ctypes.byref(jid), ok=(0, 2))
+        tp = _ptr(traj) if traj is not None else None
+        if xh is None:
+            st = call("mg_pool_admit", self._h, ctypes.byref(spec), tp, ctypes.byref(jid),
+                      ok=(0, 2))
+        else:
+            if tuple(xh.shape) != (int(n_envs), MG_NXPARAM) or xh.dtype not in (
+                    torch.float32, np.float32):
+                raise ValueError(f"xh must be float32 [{int(n_envs)}, {MG_NXPARAM}]")
+            st = call("mg_pool_admit_offdiag", self._h, ctypes.byref(spec), tp, _ptr(xh),
+                      ctypes.byref(jid), ok=(0, 2))
         return None if st == 2 else jid.value
 
     def tick(self, k: int) -> int:

@@ -252,3 +252,70 @@ def test_native_server_wait_times_out_and_stays_usable():
 def _ptr_of(t):
     import ctypes
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _serve_jobs(pool, jobs, k=50):
+    """Admit jobs (kwargs of Pool.admit plus n_envs / horizon), tick to completion, return
+    (final state, trajectory) per job."""
+    ids = []
+    for j in jobs:
+        traj = torch.empty((j["horizon"], 13, j["n_envs"]), device="cuda")
+        ids.append((pool.admit(traj=traj, **j), traj))
+    while pool.tick(k):
+        pass
+    pool.sync()
+    out = [(pool.job_state(i, j["n_envs"]), t) for (i, t), j in zip(ids, jobs)]
+    for i, _ in ids:
+        pool.release(i)
+    return out
+
+
+def test_offdiag_job_alone_equals_mix_and_matches_oracle():
+    """A job admitted with the off-diagonal extension (full M_A and D_l, randomised r_g) runs on
+    the general path in its own launch of each tick: served alone (extension from host memory)
+    or between two plain jobs (from device memory) it gives the same final state and trajectory
+    bit for bit, the plain jobs give what they give without it, and it matches the FP64 oracle."""
+    vs = vehicles()
+    n, T, rg = 600, 200, f32(0.02)
+    types = np.zeros(n, dtype=np.int32)
+    params = I.round_f32(O.randomize(91, oracle_nominal(vs), types, f32(0.8), f32(1.2),
+                                     f32(0.2), rg_halfwidth=rg))
+    xpar = I.hydro_offdiag(93, params)
+    xjob = dict(n_envs=n, vehicle_type=0, horizon=T, param_seed=91, cmd_seed=92, hold=10,
+                rg_halfwidth=rg)
+    plain = [dict(n_envs=1000, vehicle_type=1, horizon=150, param_seed=5, cmd_seed=6, hold=7),
+             dict(n_envs=300, vehicle_type=0, horizon=250, param_seed=8, cmd_seed=9, hold=3)]
+    pool = Pool(1 << 13, vs)
+    (alone,) = _serve_jobs(pool, [dict(xjob, xh=xpar.astype(np.float32))])
+    ref_plain = _serve_jobs(pool, plain)
+    mix = _serve_jobs(pool, [plain[0], dict(xjob, xh=torch.tensor(xpar, dtype=torch.float32,
+                                                                   device="cuda")), plain[1]])
+    pool.close()
+    assert torch.equal(mix[1][0], alone[0]) and torch.equal(mix[1][1], alone[1])
+    for (fs, tr), (rfs, rtr) in zip([mix[0], mix[2]], ref_plain):
+        assert torch.equal(fs, rfs) and torch.equal(tr, rtr)
+    s0 = np.stack([I.round_f32(O.reset_state(91, f32(0.3), e, 0)) for e in range(n)])
+    cmds = np.stack([np.stack([O.commands(92, e, sg, 6) for e in range(n)])
+                     for sg in range(T // 10)])
+    ref, traj = O.rollout(params, oracle_geo(vs), types, s0, cmds, 10, T, record=True, xpar=xpar)
+    got = alone[0].double().cpu().numpy()
+    assert rel_err(got, ref).max() <= TOL_ROLLOUT
+    g = alone[1].double().cpu().numpy()
+    np.testing.assert_allclose(g[100].T, traj[100, :, :13], rtol=0, atol=1e-4)
+    # the extension changes the rollout (it is not silently dropped)
+    ref0 = O.rollout(params, oracle_geo(vs), types, s0, cmds, 10, T)
+    assert rel_err(got, ref0).max() > 100 * TOL_ROLLOUT
+
+
+def test_offdiag_admission_checks():
+    vs = vehicles()
+    pool = Pool(1000, vs)
+    with pytest.raises(ValueError):
+        pool.admit(100, 0, 10, 1, 2, xh=np.zeros((100, 44), np.float32))
+    with pytest.raises(MGError) as ei:   # r_g randomisation needs the extension or an r_g pool
+        pool.admit(100, 0, 10, 1, 2, rg_halfwidth=0.01)
+    assert ei.value.code == "MG_EINVAL"
+    a = pool.admit(100, 0, 10, 1, 2, rg_halfwidth=0.01, xh=np.zeros((100, 45), np.float32))
+    assert a is not None
+    pool.release(a)
+    pool.close()

@@ -7,12 +7,13 @@
 
 namespace mg {
 
-// Register caps: the diagonal-mass step fits 128 registers (16 resident warps per SM); the
-// general step keeps 168.
+// Register caps: the narrow diagonal-mass step keeps 128 registers (16 resident warps per SM,
+// for the per-step form and large per-step grids; about 100 bytes of the step coefficients
+// spill to L1 at this cap); the general step keeps 168.
 constexpr int kRegsDiag = 128;
 constexpr int kRegsGeneral = 168;
 // The wide diagonal-mass variants (mg_set_schedule's wide): the work-queue kernel runs at 8
-// warps/SM, where 256 registers per thread would fit; a 200 cap measured best (ptxas uses 184;
+// warps/SM, where 256 registers per thread would fit; a 200 cap measured best (ptxas uses 181;
 // +1.7 % over 168, none at 255).  The static-grid kernel with the same cap runs small fleets
 // (one warp per scheduler or fewer, latency-bound) 6-7 % faster than at 128: the extra
 // registers let the compiler interleave more independent work.

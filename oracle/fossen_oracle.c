@@ -607,7 +607,9 @@ double orc_task_observe(int32_t task, const double *s, const double *c, double r
  *
  * g_RB is the weight part of the restoring vector (acting at r_g), g_A the buoyancy part (at
  * r_b); the current term M_A [w x v_c^b; 0] follows the coupled reading and shares its flag.
- * a = 0 at an episode start. */
+ * a = 0 at an episode start.  M_RB is the full rigid-body inertia of Eq. 1 (r_g may be off the
+ * origin, and the solve is the general one); x is the off-diagonal extension of M_A and D_l
+ * (NULL: the diagonal model), as in the coupled step. */
 static void restoring_parts(const double *par, const double q[4], double g_rb[6],
                             double g_a[6]) {
   double Rf[9], R[3][3];
@@ -631,8 +633,9 @@ static void restoring_parts(const double *par, const double q[4], double g_rb[6]
   }
 }
 
-int orc_split_step(const double *par, const double *geo, const double *s, const double *a,
-                   const double *c, double h, int flags, double *out, double *a_out) {
+int orc_split_step_x(const double *par, const double *x, const double *geo, const double *s,
+                     const double *a, const double *c, double h, int flags, double *out,
+                     double *a_out) {
   const double *p = s + S_P, *q = s + S_Q, *nu = s + S_NU, *n = s + S_N;
   int nthr = (int)geo[0];
   double Rf[9], R[3][3];
@@ -649,9 +652,9 @@ int orc_split_step(const double *par, const double *geo, const double *s, const 
 
   /* hydrodynamic module: an external generalised force */
   double Ma[36], Ca[36], D[36], g_rb[6], g_a[6];
-  orc_mass_a(par, Ma);
-  orc_coriolis_a(par, nu_r, Ca);
-  orc_damping(par, nu_r, D);
+  orc_mass_a_x(par, x, Ma);
+  orc_coriolis_a_x(par, x, nu_r, Ca);
+  orc_damping_x(par, x, nu_r, D);
   restoring_parts(par, q, g_rb, g_a);
   double acc[6];
   for (int i = 0; i < 6; ++i) acc[i] = a[i];
@@ -703,11 +706,17 @@ int orc_split_step(const double *par, const double *geo, const double *s, const 
   return 0;
 }
 
-/* Fleet rollout of the split scheme; as orc_rollout, with the acceleration memory acc [n][6]
+int orc_split_step(const double *par, const double *geo, const double *s, const double *a,
+                   const double *c, double h, int flags, double *out, double *a_out) {
+  return orc_split_step_x(par, NULL, geo, s, a, c, h, flags, out, a_out);
+}
+
+/* Fleet rollout of the split scheme; as orc_rollout_x, with the acceleration memory acc [n][6]
  * advanced in place alongside s. */
-int64_t orc_split_rollout(int64_t n, const double *par, const double *geo, const int32_t *types,
-                          double *s, double *acc, const double *cmd, int32_t n_seg, int32_t hold,
-                          int32_t n_steps, double h, int32_t flags, int32_t nthreads) {
+int64_t orc_split_rollout_x(int64_t n, const double *par, const double *xpar,
+                            const double *geo, const int32_t *types, double *s, double *acc,
+                            const double *cmd, int32_t n_seg, int32_t hold, int32_t n_steps,
+                            double h, int32_t flags, int32_t nthreads) {
   int64_t fails = 0;
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -715,6 +724,7 @@ int64_t orc_split_rollout(int64_t n, const double *par, const double *geo, const
 #endif
   for (int64_t e = 0; e < n; ++e) {
     const double *pe = par + e * ORC_NPARAM;
+    const double *xe = xpar ? xpar + e * ORC_NXPARAM : NULL;
     const double *ge = geo + (int64_t)types[e] * ORC_NGEO;
     double *se = s + e * ORC_NSTATE, *ae = acc + e * 6, next[ORC_NSTATE], an[6];
     int bad = 0;
@@ -722,7 +732,7 @@ int64_t orc_split_rollout(int64_t n, const double *par, const double *geo, const
       int32_t seg = j / hold;
       if (seg > n_seg - 1) seg = n_seg - 1;
       const double *c = cmd + ((int64_t)seg * n + e) * ORC_MAXTHR;
-      bad |= orc_split_step(pe, ge, se, ae, c, h, flags, next, an);
+      bad |= orc_split_step_x(pe, xe, ge, se, ae, c, h, flags, next, an);
       memcpy(se, next, sizeof next);
       memcpy(ae, an, sizeof an);
     }

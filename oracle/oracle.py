@@ -94,13 +94,13 @@ def lib():
                                            ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_int32, ctypes.c_double, ctypes.c_double, _D]
             L.orc_task_observe.restype = ctypes.c_double
-            L.orc_split_step.argtypes = [_D, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D,
-                                         _D]
-            L.orc_split_step.restype = ctypes.c_int
-            L.orc_split_rollout.argtypes = [ctypes.c_int64, _D, _D, _I32, _D, _D, _D,
-                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                                            ctypes.c_double, ctypes.c_int32, ctypes.c_int32]
-            L.orc_split_rollout.restype = ctypes.c_int64
+            L.orc_split_step_x.argtypes = [_D, _D, _D, _D, _D, _D, ctypes.c_double,
+                                           ctypes.c_int, _D, _D]
+            L.orc_split_step_x.restype = ctypes.c_int
+            L.orc_split_rollout_x.argtypes = [ctypes.c_int64, _D, _D, _D, _I32, _D, _D, _D,
+                                              ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_double, ctypes.c_int32, ctypes.c_int32]
+            L.orc_split_rollout_x.restype = ctypes.c_int64
             _lib = L
     return _lib
 
@@ -298,25 +298,26 @@ def task_observe(task: int, s, centre, radius, omega, vz, psi_r, m, dt_look, t):
 
 # ------------------------------------------------------------------ split integration (§METHOD)
 
-def split_step(par, geo, s, a, c, h: float, flags: int = 0):
+def split_step(par, geo, s, a, c, h: float, flags: int = 0, xpar=None):
     """One sub-step of the split scheme (rigid body by semi-implicit Euler, hydrodynamic term as
-    an external force with the previous acceleration ``a`` in its added-mass part).  Returns
-    (state, acceleration)."""
+    an external force with the previous acceleration ``a`` in its added-mass part); xpar: the
+    off-diagonal extension of M_A and D_l, or None.  Returns (state, acceleration)."""
     out = np.zeros(NSTATE)
     a_out = np.zeros(6)
     c8 = np.zeros(MAX_THR)
     c = np.asarray(c, dtype=np.float64)
     c8[:c.size] = c
-    rc = lib().orc_split_step(_p(_f64(par, (NPARAM,))), _p(_f64(geo, (NGEO,))),
-                              _p(_f64(s, (NSTATE,))), _p(_f64(a, (6,))), _p(c8), h, flags,
-                              _p(out), _p(a_out))
+    xp = None if xpar is None else _p(_f64(xpar, (NXPARAM,)))
+    rc = lib().orc_split_step_x(_p(_f64(par, (NPARAM,))), xp, _p(_f64(geo, (NGEO,))),
+                                _p(_f64(s, (NSTATE,))), _p(_f64(a, (6,))), _p(c8), h, flags,
+                                _p(out), _p(a_out))
     if rc != 0:
         raise FloatingPointError("singular rigid-body mass matrix")
     return out, a_out
 
 
 def split_rollout(par, geo, types, s0, a0, cmd, hold: int, n_steps: int, h: float = 0.01,
-                  flags: int = 0, nthreads: int = 0):
+                  flags: int = 0, nthreads: int = 0, xpar=None):
     """Fleet rollout of the split scheme; returns (state [n, NSTATE], acceleration [n, 6])."""
     par = _f64(par)
     n = par.shape[0]
@@ -325,8 +326,10 @@ def split_rollout(par, geo, types, s0, a0, cmd, hold: int, n_steps: int, h: floa
     s = _f64(s0).reshape(n, NSTATE).copy()
     a = _f64(a0).reshape(n, 6).copy()
     cmd = _f64(cmd).reshape(-1, n, MAX_THR)
-    fails = lib().orc_split_rollout(n, _p(par), _p(geo), _p(types, _I32), _p(s), _p(a), _p(cmd),
-                                    cmd.shape[0], hold, n_steps, h, flags, nthreads)
+    xp = None if xpar is None else _f64(xpar).reshape(n, NXPARAM)
+    fails = lib().orc_split_rollout_x(n, _p(par), _p(xp) if xp is not None else None, _p(geo),
+                                      _p(types, _I32), _p(s), _p(a), _p(cmd), cmd.shape[0], hold,
+                                      n_steps, h, flags, nthreads)
     if fails:
         raise FloatingPointError(f"{fails} envs had a singular rigid-body mass matrix")
     return s, a

@@ -89,11 +89,11 @@ def one_thruster_vehicle(r=(0, 0, 0), d=(1, 0, 0)):
     return geo
 
 
-def rollout1(par, geo, s0, c, n_steps, h=0.01, flags=0):
+def rollout1(par, geo, s0, c, n_steps, h=0.01, flags=0, xpar=None):
     cmd = np.zeros((1, 1, 8))
     cmd[0, 0, :len(c)] = c
     s, traj = O.rollout(par[None], geo[None], [0], s0[None], cmd, 1, n_steps, h=h, flags=flags,
-                        record=True)
+                        record=True, xpar=None if xpar is None else xpar[None])
     return s[0], traj[:, 0]
 
 
@@ -642,13 +642,13 @@ def test_task_observation_and_error():
 
 # ----------------------------------------------------------------------------- split scheme
 
-def split_run(par, geo, s0, c, n_steps, h=0.01, flags=0):
+def split_run(par, geo, s0, c, n_steps, h=0.01, flags=0, xpar=None):
     """Split-scheme sub-steps of one env from rest of the acceleration memory; returns the
     states and accelerations after every sub-step."""
     s, a = s0.copy(), np.zeros(6)
     ss, aa = [], []
     for _ in range(n_steps):
-        s, a = O.split_step(par, geo, s, a, c, h, flags)
+        s, a = O.split_step(par, geo, s, a, c, h, flags, xpar=xpar)
         ss.append(s)
         aa.append(a)
     return np.array(ss), np.array(aa)
@@ -755,6 +755,72 @@ def test_split_converges_to_the_coupled_solution_at_first_order():
         errs.append(np.abs(ss[-1][I.S_NU:I.S_NU + 6] - ref[I.S_NU:I.S_NU + 6]).max())
     for e1, e2 in zip(errs, errs[1:]):
         assert 1.7 < e1 / e2 < 2.3, errs
+
+
+def split_general_case(kind):
+    """Off-centre gravity and / or a full M_A and D_l, with every added mass small enough for the
+    lagged added-mass mode to decay (spectral radius of M_RB^-1 M_A below 0.6)."""
+    par = stable_added_mass(V.params, 0.35)
+    par[I.P_VC:I.P_VC + 3] = [0.1, -0.05, 0.02]
+    xpar = None
+    g = np.random.default_rng(17)
+    if kind in ("rg", "both"):
+        par[I.P_RG:I.P_RG + 3] = [0.012, -0.018, 0.02]
+    if kind in ("full", "both"):
+        ma, dl = par[I.P_MA:I.P_MA + 6], par[I.P_DL:I.P_DL + 6]
+        U = g.uniform(-1, 1, (6, 6))
+        MA = np.diag(ma) + 0.12 * (U + U.T) / 2 * np.sqrt(np.outer(ma, ma)) * (1 - np.eye(6))
+        DL = np.diag(dl) + 0.12 * g.uniform(-1, 1, (6, 6)) * np.sqrt(np.outer(dl, dl)) * (
+            1 - np.eye(6))
+        xpar = xpar_from_matrices(MA, DL)
+    rho = np.abs(np.linalg.eigvals(np.linalg.solve(O.mass_rb(par), O.mass_a(par, xpar)))).max()
+    assert rho < 0.6, rho
+    return par, xpar
+
+
+@pytest.mark.parametrize("kind", ["rg", "full", "both"])
+def test_split_general_model_converges_to_the_coupled_solution_at_first_order(kind):
+    """The split scheme with the full rigid-body inertia (r_g off the origin: M_RB couples
+    surge, sway and heave to the rotations, C_RB carries the m r_g terms and the weight a
+    moment) and the full M_A and D_l converges to the coupled equation with the same terms at
+    first order: any term dropped or mis-signed on one side changes the limit."""
+    par, xpar = split_general_case(kind)
+    c = np.array([0.5, -0.3, 0.2, 0.4, -0.6, 0.1])
+    s0 = state(q=quat_from_euler(0.2, -0.1, 0.5), nu=(0.2, -0.1, 0.05, 0.1, -0.2, 0.15))
+    T = 1.0
+    ref, _ = rollout1(par, GEO, s0, c, 4000, h=T / 4000, xpar=xpar)
+    errs = []
+    for h in (0.01, 0.005, 0.0025):
+        ss, _ = split_run(par, GEO, s0, c, int(round(T / h)), h, xpar=xpar)
+        errs.append(np.abs(ss[-1][I.S_NU:I.S_NU + 6] - ref[I.S_NU:I.S_NU + 6]).max())
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 1.7 < e1 / e2 < 2.3, errs
+    assert errs[-1] < 5e-3, errs
+
+
+def test_split_general_model_equilibrium_equals_the_coupled_one():
+    """Held throttles, off-centre gravity, full M_A and D_l: at rest of the acceleration memory
+    the split scheme's fixed point is the coupled equation's steady state."""
+    par, xpar = split_general_case("both")
+    par[I.P_VC:I.P_VC + 3] = 0.0
+    c = np.array([0.6, 0.6, -0.6, -0.6, 0.3, -0.3])
+    ss, aa = split_run(par, GEO, state(), c, 10000, xpar=xpar)
+    s_rk4, _ = rollout1(par, GEO, state(), c, 10000, xpar=xpar)
+    assert np.abs(aa[-1]).max() < 1e-8
+    np.testing.assert_allclose(ss[-1][I.S_NU:I.S_NU + 6], s_rk4[I.S_NU:I.S_NU + 6], rtol=1e-6,
+                               atol=1e-8)
+
+
+def test_split_step_defaults_to_the_diagonal_extension():
+    """xpar = None and an all-zero extension give the same split sub-step, bit for bit."""
+    par, _ = split_general_case("rg")
+    s0 = state(q=quat_from_euler(0.3, 0.1, -0.4), nu=(0.2, 0.1, -0.1, 0.2, 0.1, -0.3),
+               n=(0.2, -0.4, 0.1, 0.3, -0.2, 0.5))
+    a0 = np.array([0.1, -0.2, 0.05, 0.3, -0.1, 0.2])
+    c = np.array([0.5, -0.3, 0.2, 0.4, -0.6, 0.1])
+    s1, a1 = O.split_step(par, GEO, s0, a0, c, 0.01)
+    s2, a2 = O.split_step(par, GEO, s0, a0, c, 0.01, xpar=np.zeros(O.NXPARAM))
+    assert np.array_equal(s1, s2) and np.array_equal(a1, a2)
 
 
 # ----------------------------------------------------------------------------- full M_A and D

@@ -213,7 +213,7 @@ mg_status mg_get_params(mg_sim *sim, float *out);
  * x [n][MG_NXPARAM] (host or device; layout above), or clear it (x = NULL: the diagonal model).
  * The mass matrices are re-inverted in FP64 with the off-diagonal added mass; a fleet with a
  * non-zero extension steps on the general path (static grid or work queue, each block or warp
- * staging its envs' coefficients in shared memory; mg_step_split rejects it).  mg_randomize and
+ * staging its envs' coefficients in shared memory; mg_step_split runs its general form).  mg_randomize and
  * mg_set_params keep the extension.  Synchronous.  Errors: MG_EINVAL, MG_ENOMEM, MG_ENOTSPD
  * (stored, but some M_RB + M_A is not positive definite), MG_ECUDA. */
 mg_status mg_set_hydro_offdiag(mg_sim *sim, const float *x);
@@ -267,8 +267,11 @@ mg_status mg_step(mg_sim *sim, int32_t k);
  * exceeds the rigid-body mass.  accel: device [6][n_envs] (component-major), in: the previous
  * sub-step's acceleration (zeros at an episode start), out: the last sub-step's.  Uses and
  * advances the action cursor like mg_step, the static grid with the sim's envs_per_block and
- * steps_per_launch, no graph; non-finite states are flagged as by mg_step.  Errors: MG_EINVAL
- * (k < 1, accel NULL or not device memory, a fleet with off-centre gravity). */
+ * steps_per_launch, no graph; non-finite states are flagged as by mg_step.  A fleet with
+ * off-centre gravity or the off-diagonal extension takes the general form: the full M_RB (its
+ * inverse in closed form, w' = I_g^-1 (f_w - r_g x f_v), v' = f_v / m + r_g x w'), C_RB with the
+ * m r_g terms, the weight's moment, and the full M_A and D_l in the hydrodynamic force.  Errors:
+ * MG_EINVAL (k < 1, accel NULL or not device memory). */
 mg_status mg_step_split(mg_sim *sim, int32_t k, float *accel);
 
 /* As mg_step with the work-queue schedule, for callers that must not allocate device memory

@@ -1122,16 +1122,13 @@ mg_status mg_step_split(mg_sim *s, int32_t k, float *accel) {
   MG_NONNULL(accel);
   if (k < 1) return fail(MG_EINVAL, "k must be >= 1");
   if (!is_device_ptr(accel)) return fail(MG_EINVAL, "accel must be device memory");
-  if (!s->mass_diag)
-    return fail(MG_EINVAL, "the split step covers diagonal-mass fleets (r_g = 0, no "
-                           "off-diagonal hydrodynamics) only");
   FleetView v = s->view();
   for (int32_t done = 0; done < k;) {
     const int32_t kk = std::min(s->spl, k - done);
     v.cursor_off = done;
     v.cursor_adv = (done + kk == k) ? k : 0;
-    MG_CK(launch_split(v, s->blocks_d, s->n_blocks, s->threads, s->ntv, s->raw, accel, kk,
-                       s->stream));
+    MG_CK(launch_split(v, s->blocks_d, s->n_blocks, s->threads, s->ntv, !s->mass_diag, s->raw,
+                       accel, kk, s->stream));
     done += kk;
   }
   s->cursor += k;

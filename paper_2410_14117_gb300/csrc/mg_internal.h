@@ -208,8 +208,9 @@ struct TaskView {
 
 // Split-integration comparison step (mg_split.cu): k sub-steps of the engine-style scheme on the
 // static grid; raw [n][MG_NPARAM] parameter records, accel [6][n] acceleration memory (in/out).
+// general: the full M_RB (off-centre gravity) and fv.xh's off-diagonal M_A / D_l (or none).
 cudaError_t launch_split(const FleetView &fv, const BlockDesc *blocks, int n_blocks, int threads,
-                         NtVariant ntv, const float *raw, float *accel, int32_t k,
+                         NtVariant ntv, bool general, const float *raw, float *accel, int32_t k,
                          cudaStream_t stream);
 
 // Outputs and reset inputs of the fused task step.

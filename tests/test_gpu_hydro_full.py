@@ -83,7 +83,7 @@ def test_full_hydro_500_substeps_matches_oracle(epb, spl):
 def test_extension_round_trip_clear_and_schedules():
     """get returns what was set; clearing gives the diagonal model bit for bit; the work-queue
     schedule (its off-diagonal variant), graph replay and mg_step_noalloc give the static grid's
-    bits; the task step carries the extension; the split step rejects it."""
+    bits; the task step carries the extension."""
     vs = vehicles()
     n = 1500
     types, params, xpar = _fleet(91, n, vs, rg=0.0)
@@ -109,8 +109,6 @@ def test_extension_round_trip_clear_and_schedules():
     for _ in range(12):
         call("mg_step_noalloc", sim._h, 10)
     torch.testing.assert_close(sim.get_state().cpu(), a, rtol=0, atol=0)
-    with pytest.raises(MGError):
-        sim.step_split(1, torch.zeros((6, n), device="cuda"))
     # cleared: the same as a sim that never had the extension
     sim.set_hydro_offdiag(None)
     assert not sim.get_hydro_offdiag().any()

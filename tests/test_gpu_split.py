@@ -1,7 +1,8 @@
 """Split-integration comparison step (§METHOD's engine + hydrodynamics-module arrangement) on the
 GPU against the FP64 oracle's split scheme: one teacher-forced sub-step with a non-zero
 acceleration memory, stable rollouts, the unstable added-mass mode, and launch-shape
-invariance."""
+invariance, for diagonal-mass fleets and on the general model (off-centre gravity, full M_A and
+D_l)."""
 import numpy as np
 import pytest
 import torch
@@ -23,10 +24,24 @@ def _params(seed, types, vs, ma_scale):
     return p
 
 
-def _sim(types, vs, params, states, accel, epb=128, spl=50):
+def _general(seed, params, kind, coupling=0.15):
+    """Off-centre gravity (r_g ~ U[-2, 2] cm) and / or the off-diagonal extension."""
+    p = params.copy()
+    xpar = None
+    if kind in ("rg", "both"):
+        p[:, I.P_RG:I.P_RG + 3] = I.round_f32(
+            np.random.default_rng(seed).uniform(-0.02, 0.02, (len(p), 3)))
+    if kind in ("full", "both"):
+        xpar = I.hydro_offdiag(seed + 1, p, coupling)
+    return p, xpar
+
+
+def _sim(types, vs, params, states, accel, epb=128, spl=50, xpar=None):
     sim = Sim(len(types), types, vs)
     sim.set_launch(epb, spl, False)
     sim.set_params(torch.tensor(params, dtype=torch.float32, device="cuda"))
+    if xpar is not None:
+        sim.set_hydro_offdiag(torch.tensor(xpar, dtype=torch.float32, device="cuda"))
     sim.set_state(torch.tensor(states, dtype=torch.float32, device="cuda"))
     acc = torch.tensor(np.ascontiguousarray(accel.T), dtype=torch.float32, device="cuda")
     return sim, acc
@@ -60,6 +75,60 @@ def test_split_one_substep_matches_oracle(flags):
                                     cmds[0, e], H, flags)
         assert rel_err(got[e][None], s_ref[None]).max() <= TOL_STEP, e
         assert _acc_err(got_a[e][None], a_ref[None]).max() <= TOL_STEP, e
+
+
+@pytest.mark.parametrize("kind", ["rg", "full", "both"])
+def test_split_general_one_substep_matches_oracle(kind):
+    vs = vehicles()
+    n = 3000
+    types = I.mixed_fleet(131, n, max_group=400)
+    nt = np.array([vs[t].n_thr for t in types])
+    params, xpar = _general(136, _params(132, types, vs, 1.0), kind)
+    states = I.random_states(133, n, nt)
+    accel = I.round_f32(np.random.default_rng(134).normal(0.0, 0.5, (n, 6)))
+    cmds = I.commands(135, 1, n, nt)
+    sim, acc = _sim(types, vs, params, states, accel, xpar=xpar)
+    sim.set_actions(torch.tensor(cmds, device="cuda"), 1)
+    sim.step_split(1, acc)
+    got = sim.get_state().double().cpu().numpy()
+    got_a = acc.double().cpu().numpy().T
+    sim.close()
+    geo = oracle_geo(vs)
+    for e in range(n):
+        s_ref, a_ref = O.split_step(params[e], geo[types[e]], states[e], accel[e], cmds[0, e],
+                                    H, 0, xpar=None if xpar is None else xpar[e])
+        assert rel_err(got[e][None], s_ref[None]).max() <= TOL_STEP, e
+        assert _acc_err(got_a[e][None], a_ref[None]).max() <= TOL_STEP, e
+
+
+def test_split_general_stable_rollout_matches_oracle():
+    """Off-centre gravity with a 10 %-coupled M_A and D_l, added mass scaled by 0.4 (every env's
+    lagged added-mass mode decays: spectral radius of M_RB^-1 M_A below 1): 300 sub-steps."""
+    vs = vehicles()
+    n = 1024
+    types = I.mixed_fleet(141, n, max_group=300)
+    nt = np.array([vs[t].n_thr for t in types])
+    params, xpar = _general(146, _params(142, types, vs, 0.4), "both", coupling=0.1)
+    rho = max(np.abs(np.linalg.eigvals(np.linalg.solve(O.mass_rb(params[e]),
+                                                       O.mass_a(params[e], xpar[e])))).max()
+              for e in range(n))
+    assert rho < 0.95, rho
+    states = I.initial_states(143, n)
+    for e in range(n):
+        states[e, I.S_N + nt[e]:] = 0.0
+    cmds = I.commands(144, 30, n, nt)
+    sim, acc = _sim(types, vs, params, states, np.zeros((n, 6)), spl=64, xpar=xpar)
+    sim.set_actions(torch.tensor(cmds, device="cuda"), 10)
+    sim.step_split(300, acc)
+    assert sim.sync() == 0
+    got = sim.get_state().double().cpu().numpy()
+    got_a = acc.double().cpu().numpy().T
+    sim.close()
+    ref, ref_a = O.split_rollout(params, oracle_geo(vs), types, states, np.zeros((n, 6)),
+                                 cmds.astype(np.float64), 10, 300, h=H, xpar=xpar)
+    err = rel_err(got, ref)
+    assert err.max() <= TOL_ROLLOUT, err.max(axis=0)
+    assert _acc_err(got_a, ref_a).max() <= 10 * TOL_ROLLOUT
 
 
 def test_split_stable_rollout_matches_oracle():
@@ -131,21 +200,23 @@ def test_split_unstable_added_mass_mode_grows_as_predicted():
     assert np.abs(a30[:, [0, 1, 3, 4, 5]]).max() == 0.0
 
 
-def test_split_launch_shape_and_errors():
-    """Chunked launches (sub-steps per launch, block size) give the same bits; a fleet with
-    off-centre gravity and a host accel buffer are rejected on the host."""
+@pytest.mark.parametrize("kind", ["diag", "both"])
+def test_split_launch_shape_and_errors(kind):
+    """Chunked launches (sub-steps per launch, block size) give the same bits, for a diagonal-
+    mass fleet and on the general model; a host accel buffer is rejected on the host."""
     vs = vehicles()
     n = 1000
     types = I.mixed_fleet(61, n, max_group=200)
     nt = np.array([vs[t].n_thr for t in types])
-    params = _params(62, types, vs, 0.5)
+    params, xpar = _general(67, _params(62, types, vs, 0.5), kind, coupling=0.1)
     states = I.initial_states(63, n)
     for e in range(n):
         states[e, I.S_N + nt[e]:] = 0.0
     cmds = torch.tensor(I.commands(64, 12, n, nt), device="cuda")
     out = []
     for epb, spl, calls in ((128, 50, (120,)), (64, 7, (33, 80, 7)), (256, 1, (120,))):
-        sim, acc = _sim(types, vs, params, states, np.zeros((n, 6)), epb=epb, spl=spl)
+        sim, acc = _sim(types, vs, params, states, np.zeros((n, 6)), epb=epb, spl=spl,
+                        xpar=xpar)
         sim.set_actions(cmds, 10)
         for k in calls:
             sim.step_split(k, acc)
@@ -153,11 +224,6 @@ def test_split_launch_shape_and_errors():
         sim.close()
     for s, a in out[1:]:
         assert torch.equal(s, out[0][0]) and torch.equal(a, out[0][1])
-    params[:, I.P_RG] = 0.01
-    sim, acc = _sim(types, vs, params, states, np.zeros((n, 6)))
-    with pytest.raises(MGError):
-        sim.step_split(1, acc)
-    sim.close()
     sim, _ = _sim(np.zeros(8, np.int32), vs, _params(65, np.zeros(8, np.int32), vs, 0.5),
                   I.initial_states(66, 8), np.zeros((8, 6)))
     with pytest.raises((MGError, ValueError)):

@@ -460,7 +460,7 @@ mg_status mg_pool_admit(mg_pool *pool, const mg_job_spec *spec, float *traj, int
  * and the ticks advance it on the general path in a second launch beside the other jobs (whose
  * results do not change).  A job with the extension may randomise r_g in any pool.  The first
  * such job allocates the pool's [MG_NXPARAM][capacity_envs] planes (MG_ENOMEM if that fails;
- * nothing changed).  The native request loop (mg_server_*) admits jobs without the extension.
+ * nothing changed).  The native request loop takes such jobs through mg_server_submit_offdiag.
  * Errors as mg_pool_admit. */
 mg_status mg_pool_admit_offdiag(mg_pool *pool, const mg_job_spec *spec, float *traj,
                                 const float *xh, int32_t *job_id);
@@ -521,6 +521,13 @@ mg_status mg_server_destroy(mg_server *srv);
  * MG_EINVAL (n_envs outside [1, the pool's capacity], horizon or hold < 1, a record larger than
  * the whole budget). */
 mg_status mg_server_submit(mg_server *srv, const mg_job_spec *spec, int64_t *ticket);
+
+/* mg_server_submit for a job with the off-diagonal hydrodynamic extension: xh [n_envs]
+ * [MG_NXPARAM] (host or device) is copied into host memory before the call returns and handed
+ * to mg_pool_admit_offdiag at admission (the pool's extension planes are not part of the
+ * trajectory budget).  Errors as mg_server_submit, and MG_ECUDA if xh cannot be read. */
+mg_status mg_server_submit_offdiag(mg_server *srv, const mg_job_spec *spec, const float *xh,
+                                   int64_t *ticket);
 
 /* One round of the loop (above); the counts (any may be NULL) are those after it: jobs queued,
  * admitted and not yet handed back, ticks in flight.  Errors: MG_ETIMEOUT, MG_ECUDA, and those of

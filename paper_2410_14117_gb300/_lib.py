@@ -119,6 +119,7 @@ SIGNATURES = {
     "mg_pool_set_stream": [_P, _P],
     "mg_pool_admit": [_P, ctypes.POINTER(JobSpec), _P, ctypes.POINTER(_I32)],
     "mg_pool_admit_offdiag": [_P, ctypes.POINTER(JobSpec), _P, _P, ctypes.POINTER(_I32)],
+    "mg_server_submit_offdiag": [_P, ctypes.POINTER(JobSpec), _P, ctypes.POINTER(_I64)],
     "mg_pool_tick": [_P, _I32, ctypes.POINTER(_I32)],
     "mg_pool_job_progress": [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)],
     "mg_pool_get_job_state": [_P, _I32, _P],

@@ -29,6 +29,7 @@ enum JobState { QUEUED = 0, RUNNING = 1, DONE = 2, RELEASED = 3 };
 
 struct ServeJob {
   mg_job_spec spec;
+  std::vector<float> xh;     // off-diagonal extension records [n_envs][MG_NXPARAM], or empty
   double submit_s = 0.0, admit_s = -1.0, done_s = -1.0;
   int32_t job_id = -1;       // pool handle while admitted
   float *traj = nullptr;     // trajectory record (stream-ordered allocation) or null
@@ -138,7 +139,9 @@ mg_status admit_queued(mg_server *s) {
       if (e != cudaSuccess) return sfail_cuda(e, "cudaMallocFromPoolAsync(trajectory record)");
     }
     int32_t jid = -1;
-    const mg_status st = mg_pool_admit(s->pool, &j.spec, traj, &jid);
+    const mg_status st =
+        j.xh.empty() ? mg_pool_admit(s->pool, &j.spec, traj, &jid)
+                     : mg_pool_admit_offdiag(s->pool, &j.spec, traj, j.xh.data(), &jid);
     if (st == MG_ENOMEM) {  // no free arena range large enough yet
       if (traj) SK(cudaFreeAsync(traj, s->stream));
       break;
@@ -149,6 +152,7 @@ mg_status admit_queued(mg_server *s) {
     }
     j.job_id = jid;
     j.traj = traj;
+    std::vector<float>().swap(j.xh);  // uploaded by the admission
     j.traj_bytes = need;
     j.admit_s = s->now();
     j.state = RUNNING;
@@ -211,7 +215,11 @@ mg_status mg_server_destroy(mg_server *s) {
   return MG_OK;
 }
 
-mg_status mg_server_submit(mg_server *s, const mg_job_spec *spec, int64_t *ticket) {
+}  // extern "C"
+
+namespace {
+
+mg_status submit_job(mg_server *s, const mg_job_spec *spec, const float *xh, int64_t *ticket) {
   if (!s || !spec || !ticket) return sfail(MG_EINVAL, "NULL argument");
   if (spec->n_envs < 1 || spec->n_envs > s->capacity || spec->horizon < 1 ||
       spec->hold_steps < 1)
@@ -220,11 +228,28 @@ mg_status mg_server_submit(mg_server *s, const mg_job_spec *spec, int64_t *ticke
     return sfail(MG_EINVAL, "the job's trajectory record alone exceeds the budget");
   ServeJob j;
   j.spec = *spec;
+  if (xh) {  // a copy of the records, kept until the job is admitted
+    j.xh.resize((size_t)spec->n_envs * MG_NXPARAM);
+    SK(cudaMemcpy(j.xh.data(), xh, j.xh.size() * sizeof(float), cudaMemcpyDefault));
+  }
   j.submit_s = s->now();
   *ticket = (int64_t)s->jobs.size();
-  s->jobs.push_back(j);
+  s->jobs.push_back(std::move(j));
   s->queue.push_back(*ticket);
   return MG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mg_status mg_server_submit(mg_server *s, const mg_job_spec *spec, int64_t *ticket) {
+  return submit_job(s, spec, nullptr, ticket);
+}
+
+mg_status mg_server_submit_offdiag(mg_server *s, const mg_job_spec *spec, const float *xh,
+                                   int64_t *ticket) {
+  return submit_job(s, spec, xh, ticket);
 }
 
 mg_status mg_server_poll(mg_server *s, int32_t *n_queued, int32_t *n_running,

@@ -111,6 +111,7 @@ class Request:
     job_id: int = -1
     traj: object = None
     final_state: object = None
+    xh: object = None  # off-diagonal added mass and damping, float32 [n_envs, MG_NXPARAM], or None
 
     @property
     def latency_s(self):
@@ -216,7 +217,7 @@ class Server:
                     break
                 traj = (self._traj_buffer(r) if self.record else None)
                 jid = pool.admit(r.n_envs, r.vehicle, r.horizon, r.param_seed, r.cmd_seed,
-                                 r.hold, traj)
+                                 r.hold, traj, xh=r.xh)
                 if jid is None:
                     break
                 r.job_id, r.traj, r.admitted_s = jid, traj, now()
@@ -329,7 +330,11 @@ class NativeServer:
                                int(r.param_seed), int(r.cmd_seed),
                                Ranges(0.8, 1.2, 0.2, 0.3, 0))
                 tk = ctypes.c_int64()
-                call("mg_server_submit", h, ctypes.byref(spec), ctypes.byref(tk))
+                if r.xh is None:
+                    call("mg_server_submit", h, ctypes.byref(spec), ctypes.byref(tk))
+                else:
+                    call("mg_server_submit_offdiag", h, ctypes.byref(spec), _ptr(r.xh),
+                         ctypes.byref(tk))
                 tickets[tk.value] = r
                 nxt += 1
             call("mg_server_poll", h, *[ctypes.byref(c) for c in counts])

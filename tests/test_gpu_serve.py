@@ -319,3 +319,37 @@ def test_offdiag_admission_checks():
     assert a is not None
     pool.release(a)
     pool.close()
+
+
+def test_native_server_serves_offdiag_jobs():
+    """Jobs with the off-diagonal extension through the native request loop
+    (mg_server_submit_offdiag, records from host and from device memory): each job's final
+    state and trajectory are the same in the mix, one at a time and through the Python loop, bit
+    for bit, and the extension is applied (the same job without it ends elsewhere)."""
+    vs = vehicles()
+    reqs = _requests(seed=9, n_jobs=8)
+    for i in (1, 4, 6):
+        r = reqs[i]
+        nominal = np.repeat(oracle_nominal(vs)[r.vehicle][None], r.n_envs, axis=0)
+        x = I.hydro_offdiag(300 + i, nominal, 0.1).astype(np.float32)
+        r.xh = x if i != 4 else torch.tensor(x, device="cuda")
+    keys = ("arrival_s", "n_envs", "horizon", "vehicle", "param_seed", "cmd_seed", "hold", "xh")
+    out = {}
+    for name, cls, mode in [("mix", NativeServer, "batched"), ("alone", NativeServer, "serial"),
+                            ("python", Server, "batched")]:
+        srv = cls(vs, budget_bytes=8e9, capacity_envs=1 << 16, k=25, keep_results=True)
+        done, stats = srv.run([Request(**{k: getattr(r, k) for k in keys}) for r in reqs],
+                              mode=mode)
+        srv.close()
+        assert stats["jobs"] == len(reqs)
+        out[name] = _by_key(done)
+    for key, r in out["alone"].items():
+        for other in ("mix", "python"):
+            torch.testing.assert_close(out[other][key].final_state, r.final_state, rtol=0, atol=0)
+            torch.testing.assert_close(out[other][key].traj, r.traj, rtol=0, atol=0)
+    plain = reqs[1]
+    srv = NativeServer(vs, budget_bytes=8e9, capacity_envs=1 << 16, k=25, keep_results=True)
+    (res,), _ = srv.run([Request(**{k: getattr(plain, k) for k in keys[:-1]})], mode="batched")
+    srv.close()
+    key = (plain.param_seed, plain.cmd_seed)
+    assert (res.final_state - out["mix"][key].final_state).abs().max() > 1e-3

@@ -18,7 +18,7 @@ class FakePool:
         self.admitted = []
         self.max_live = 0
 
-    def admit(self, n_envs, vehicle, horizon, param_seed, cmd_seed, hold=10, traj=None):
+    def admit(self, n_envs, vehicle, horizon, param_seed, cmd_seed, hold=10, traj=None, xh=None):
         if n_envs > self.free:
             return None
         jid = len(self.admitted)

@@ -834,6 +834,21 @@ def bench_split(vs, n=65536, horizon=1000, n_acc=4096, reps=3):
     sim.close()
     out["split"] = n * horizon / (split_ms / 1e3)
     out["coupled"] = n * horizon / (coupled_ms / 1e3)
+    # the general form: off-centre gravity (r_g ~ U[-2, 2] cm), 10 %-coupled M_A and D_l
+    sim = Sim(n, np.zeros(n, np.int32), vs)
+    sim.randomize(1234, 0.8, 1.2, 0.2, 0.3, rg_halfwidth=0.02)
+    p = sim.get_params()
+    p[:, I.P_MA:I.P_MA + 6] *= 0.4
+    sim.set_params(p)
+    sim.set_hydro_offdiag(torch.tensor(I.hydro_offdiag(9, p.double().cpu().numpy(), 0.1),
+                                       dtype=torch.float32, device="cuda"))
+    sim.reset()
+    sim.set_launch(128, horizon, False)
+    sim.set_procedural_actions(5678, 10)
+    acc.zero_()
+    general_ms = _time_episodes(lambda: sim.step_split(horizon, acc), reps)
+    sim.close()
+    out["split_general"] = n * horizon / (general_ms / 1e3)
     # accuracy: the same commands in time (held 0.1 s) at h = 0.01 and the h = 0.001 reference
     res = {}
     for name, dt, hold, steps, split in (("ref", 0.001, 100, 1000, False),

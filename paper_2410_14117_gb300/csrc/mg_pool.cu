@@ -417,6 +417,50 @@ mg_status mg_pool_set_stream(mg_pool *p, void *stream) {
 
 namespace {
 
+// Device work of an admission: the job's type ids, its off-diagonal records (xh: host or device
+// [n_envs][MG_NXPARAM], or null) into its columns of the pool's planes, randomised parameters
+// and derived planes, episode counters and start states.
+cudaError_t init_job(mg_pool *p, const mg_job_spec &s, int64_t env0, const float *xh) {
+  const mg_ranges &r = s.ranges;
+  const int64_t n = s.n_envs;
+  const int grid = (int)((n + 255) / 256);
+  k_fill_i32<<<grid, 256, 0, p->stream>>>(p->types + env0, n, s.vehicle_type);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  SetupView v{};
+  v.n = n;
+  v.gid0 = 0;
+  v.types = p->types + env0;
+  v.raw = p->raw + env0 * MG_NPARAM;
+  v.pa = sub_params(p->pa, env0);
+  v.n_not_spd = p->counters + 1;
+  v.any_offdiag = p->offdiag;
+  if (xh) {
+    // stride of the planes: the capacity
+    const size_t bytes = (size_t)n * MG_NXPARAM * 4;
+    if (dev_ptr(xh)) {
+      e = launch_xh_transpose(xh, p->xh + env0, n, true, p->stream, p->cap);
+    } else {
+      float *tmp = nullptr;
+      e = cudaMallocAsync(reinterpret_cast<void **>(&tmp), bytes, p->stream);
+      if (e != cudaSuccess) return e;
+      e = cudaMemcpyAsync(tmp, xh, bytes, cudaMemcpyHostToDevice, p->stream);
+      if (e == cudaSuccess) e = launch_xh_transpose(tmp, p->xh + env0, n, true, p->stream, p->cap);
+      cudaFreeAsync(tmp, p->stream);
+    }
+    if (e != cudaSuccess) return e;
+    v.xh = p->xh + env0;
+    v.xh_stride = p->cap;
+  }
+  e = launch_randomize(v, p->nominal, s.param_seed, (double)r.lo, (double)r.hi,
+                       (double)r.current_sigma, (double)r.rg_halfwidth, p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->episode + env0, 0, 4 * n, p->stream);
+  if (e == cudaSuccess)
+    e = launch_reset(sub_state(p->st, env0), n, 0, nullptr, s.param_seed, (double)r.nu0_sigma,
+                     p->episode + env0, p->flags + env0, p->counters, p->stream);
+  return e;
+}
+
 mg_status admit_job(mg_pool *p, const mg_job_spec *spec, float *traj, const float *xh,
                     int32_t *job_id) {
   if (!p || !spec || !job_id) return pfail(MG_EINVAL, "NULL argument");
@@ -457,39 +501,15 @@ mg_status admit_job(mg_pool *p, const mg_job_spec *spec, float *traj, const floa
   j.done = 0;
   j.cmd_seed = s.cmd_seed;
   j.traj = traj;
-  // Parameters and start state of the job's envs, keyed by its own seed and local env ids.
-  const int64_t n = s.n_envs;
-  const int grid = (int)((n + 255) / 256);
-  k_fill_i32<<<grid, 256, 0, p->stream>>>(p->types + env0, n, s.vehicle_type);
-  SetupView v{};
-  v.n = n;
-  v.gid0 = 0;
-  v.types = p->types + env0;
-  v.raw = p->raw + env0 * MG_NPARAM;
-  v.pa = sub_params(p->pa, env0);
-  v.n_not_spd = p->counters + 1;
-  v.any_offdiag = p->offdiag;
-  if (xh) {
-    // the job's records -> its columns of the pool's planes (stride: the capacity)
-    const size_t bytes = (size_t)n * MG_NXPARAM * 4;
-    if (dev_ptr(xh)) {
-      PK(launch_xh_transpose(xh, p->xh + env0, n, true, p->stream, p->cap));
-    } else {
-      float *tmp = nullptr;
-      PK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), bytes, p->stream));
-      cudaError_t e = cudaMemcpyAsync(tmp, xh, bytes, cudaMemcpyHostToDevice, p->stream);
-      if (e == cudaSuccess) e = launch_xh_transpose(tmp, p->xh + env0, n, true, p->stream, p->cap);
-      cudaFreeAsync(tmp, p->stream);
-      if (e != cudaSuccess) return pfail_cuda(e, "off-diagonal hydrodynamics upload");
-    }
-    v.xh = p->xh + env0;
-    v.xh_stride = p->cap;
+  // Parameters and start state of the job's envs, keyed by its own seed and local env ids; on
+  // a failure the range and the slot are given back.
+  const cudaError_t e = init_job(p, s, env0, xh);
+  if (e != cudaSuccess) {
+    give_range(p, env0, s.n_envs);
+    j.live = false;
+    j.traj = nullptr;
+    return pfail_cuda(e, "job admission");
   }
-  PK(launch_randomize(v, p->nominal, s.param_seed, (double)r.lo, (double)r.hi,
-                      (double)r.current_sigma, (double)r.rg_halfwidth, p->stream));
-  PK(cudaMemsetAsync(p->episode + env0, 0, 4 * n, p->stream));
-  PK(launch_reset(sub_state(p->st, env0), n, 0, nullptr, s.param_seed, (double)r.nu0_sigma,
-                  p->episode + env0, p->flags + env0, p->counters, p->stream));
   *job_id = id;
   return MG_OK;
 }

@@ -77,8 +77,9 @@ def test_split_one_substep_matches_oracle(flags):
         assert _acc_err(got_a[e][None], a_ref[None]).max() <= TOL_STEP, e
 
 
+@pytest.mark.parametrize("flags", [0, 1])
 @pytest.mark.parametrize("kind", ["rg", "full", "both"])
-def test_split_general_one_substep_matches_oracle(kind):
+def test_split_general_one_substep_matches_oracle(kind, flags):
     vs = vehicles()
     n = 3000
     types = I.mixed_fleet(131, n, max_group=400)
@@ -88,6 +89,7 @@ def test_split_general_one_substep_matches_oracle(kind):
     accel = I.round_f32(np.random.default_rng(134).normal(0.0, 0.5, (n, 6)))
     cmds = I.commands(135, 1, n, nt)
     sim, acc = _sim(types, vs, params, states, accel, xpar=xpar)
+    sim.set_model_flags(flags)
     sim.set_actions(torch.tensor(cmds, device="cuda"), 1)
     sim.step_split(1, acc)
     got = sim.get_state().double().cpu().numpy()
@@ -96,7 +98,7 @@ def test_split_general_one_substep_matches_oracle(kind):
     geo = oracle_geo(vs)
     for e in range(n):
         s_ref, a_ref = O.split_step(params[e], geo[types[e]], states[e], accel[e], cmds[0, e],
-                                    H, 0, xpar=None if xpar is None else xpar[e])
+                                    H, flags, xpar=None if xpar is None else xpar[e])
         assert rel_err(got[e][None], s_ref[None]).max() <= TOL_STEP, e
         assert _acc_err(got_a[e][None], a_ref[None]).max() <= TOL_STEP, e
 

@@ -455,8 +455,9 @@ mg_status mg_pool_set_stream(mg_pool *pool, void *cuda_stream);
 mg_status mg_pool_admit(mg_pool *pool, const mg_job_spec *spec, float *traj, int32_t *job_id);
 
 /* mg_pool_admit for a job with the off-diagonal hydrodynamic extension (full M_A and D_l, the
- * layout of MG_NXPARAM above): xh [n_envs][MG_NXPARAM], host or device, copied before the call
- * returns (NULL: mg_pool_admit).  The job's M^-1 is derived with the off-diagonal added mass,
+ * layout of MG_NXPARAM above): xh [n_envs][MG_NXPARAM] (NULL: mg_pool_admit); host memory may
+ * be reused once the call returns, device memory is read in order on the pool's stream (keep it
+ * until that stream passes the call).  The job's M^-1 is derived with the off-diagonal added mass,
  * and the ticks advance it on the general path in a second launch beside the other jobs (whose
  * results do not change).  A job with the extension may randomise r_g in any pool.  The first
  * such job allocates the pool's [MG_NXPARAM][capacity_envs] planes (MG_ENOMEM if that fails;

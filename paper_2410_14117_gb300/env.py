@@ -1,0 +1,120 @@
+"""Gym-style vectorised environment over the fused task step.
+
+The paper's four tasks (§EXPERIMENTS: station keeping, circle, helix and lemniscate tracking)
+are offered in a Gym-style format: a policy sees the observation of Eq. 2, sets one throttle per
+thruster (the action space of Eq. 3) and is scored by the position error of Eq. 4.
+``MarineEnv`` keeps a whole fleet of such environments on the GPU.  ``step`` copies the actions
+into a resident device buffer that the step kernel reads in place, advances every env
+``sub_steps`` RK4 sub-steps (the paper's sub-simulation steps within one simulation step) with
+the observation, the error and the auto-reset of finished episodes fused into the last launch
+(mg_task_step), and returns device tensors.  The reward is the negative position error: the
+paper names the error the tasks are judged by, not its reward weights.
+
+Every env's reference path starts within ``spawn_radius`` of the origin, where a reset puts
+the vehicle; each env has its own phase on its path.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import inputs as I
+from .sim import Sim
+
+# mg.h MG_TASK_*
+TASKS = {"station": 0, "circle": 1, "helix": 2, "lemniscate": 3}
+
+
+def task_centres(task: str, n_envs: int, radius: float, seed: int,
+                 spawn_radius: float = 0.5) -> np.ndarray:
+    """Centres and phases [n_envs, 4] = (cx, cy, cz, phi0) that put every env's reference at
+    t = 0 within spawn_radius of the origin (uniform in the ball), at a uniform random phase."""
+    if task not in TASKS:
+        raise ValueError(f"unknown task {task!r}; one of {sorted(TASKS)}")
+    g = np.random.default_rng(seed)
+    phase = g.uniform(0.0, 2.0 * math.pi, n_envs)
+    c = np.zeros((n_envs, 4))
+    c[:, 3] = phase
+    if task in ("circle", "helix"):
+        c[:, 0] = -radius * np.cos(phase)
+        c[:, 1] = -radius * np.sin(phase)
+    elif task == "lemniscate":
+        den = 1.0 + np.sin(phase) ** 2
+        c[:, 0] = -radius * np.cos(phase) / den
+        c[:, 1] = -radius * np.sin(phase) * np.cos(phase) / den
+    # offsets uniform in the ball of radius spawn_radius
+    d = g.normal(size=(n_envs, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    c[:, :3] += d * (spawn_radius * g.uniform(0.0, 1.0, (n_envs, 1)) ** (1.0 / 3.0))
+    return c
+
+
+class MarineEnv:
+    """``n_envs`` environments of one vehicle type and one task.
+
+    reset() -> obs [n, obs_dim];  step(actions [n, n_thr]) -> (obs, reward [n], done [n] bool,
+    {"episode_error": [n]}).  obs, reward and the info tensor live on the GPU; obs and
+    episode_error are buffers the next call overwrites.  Throttles are clamped to [-1, 1].  An
+    episode ends when the position error exceeds ``max_error``, after ``episode_steps``
+    sub-steps, or on a non-finite state; the env is then reset inside the step and its returned
+    observation is the new episode's first.
+    """
+
+    def __init__(self, n_envs: int, task: str = "circle", vehicle: int = 1, sub_steps: int = 10,
+                 seed: int = 0, dt: float = 0.01, lo: float = 0.8, hi: float = 1.2,
+                 current_sigma: float = 0.2, nu0_sigma: float = 0.0, radius: float = 2.0,
+                 omega: float = 0.3, vz: float = 0.1, psi_r: float = 0.0, lookahead: int = 4,
+                 lookahead_dt: float = 0.5, max_error: float = 3.0, episode_steps: int = 1000,
+                 spawn_radius: float = 0.5, vehicles=None):
+        if task not in TASKS:
+            raise ValueError(f"unknown task {task!r}; one of {sorted(TASKS)}")
+        if sub_steps < 1:
+            raise ValueError("sub_steps must be >= 1")
+        self.vehicles = list(vehicles) if vehicles is not None else I.fleet_vehicles()
+        if not 0 <= vehicle < len(self.vehicles):
+            raise ValueError("vehicle out of range")
+        self.n, self.k, self.task = int(n_envs), int(sub_steps), task
+        self.n_thr = int(self.vehicles[vehicle].n_thr)
+        sim = Sim(self.n, np.full(self.n, vehicle, dtype=np.int32), self.vehicles)
+        self.sim = sim
+        sim.set_timestep(dt)
+        if self.n_thr == 6:
+            sim.set_action_width(6)  # unpadded throttle rows
+        sim.randomize(seed, lo, hi, current_sigma, nu0_sigma)
+        sim.reset()
+        self.centres = torch.tensor(task_centres(task, self.n, radius, seed, spawn_radius),
+                                    dtype=torch.float32, device=sim.device)
+        self._task_args = dict(radius=radius, omega=omega, vz=vz, psi_r=psi_r,
+                               lookahead=lookahead, lookahead_dt=lookahead_dt,
+                               max_error=max_error, episode_steps=episode_steps)
+        sim.set_task(TASKS[task], self.centres, **self._task_args)
+        self.obs_dim = sim.obs_dim
+        self.action_dim = self.n_thr
+        self._act = torch.zeros((1, self.n, sim.act_w), dtype=torch.float32, device=sim.device)
+        sim.set_actions_borrowed(self._act, self.k)
+
+    def reset(self):
+        """Start a new episode in every env (state reset, episode clocks and error sums back to
+        zero); returns the observation."""
+        self.sim.reset()
+        self.sim.set_task(TASKS[self.task], self.centres, **self._task_args)
+        self._act.zero_()
+        self.sim.set_actions_borrowed(self._act, self.k)
+        obs, _, _, _ = self.sim.task_step(0)
+        return obs
+
+    def step(self, actions):
+        a = torch.as_tensor(actions, dtype=torch.float32, device=self._act.device)
+        if tuple(a.shape) != (self.n, self.n_thr):
+            raise ValueError(f"actions must be [{self.n}, {self.n_thr}]")
+        self._act[0, :, :self.n_thr].copy_(a.clamp(-1.0, 1.0))
+        self.sim.set_actions_borrowed(self._act, self.k)  # the step reads them from sub-step 0
+        obs, err, done, ep = self.sim.task_step(self.k)
+        return obs, -err, done.bool(), {"episode_error": ep}
+
+    def close(self):
+        if self.sim is not None:
+            self.sim.close()
+            self.sim = None

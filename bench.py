@@ -501,6 +501,7 @@ def run_ours(args):
         line["mixed_fleet"] = bench_mixed_fleet(vs)
         line["adjoint"] = bench_adjoint(vs)
         line["task"] = bench_task(vs)
+        line["env"] = bench_env()
         line["split"] = bench_split(vs)
         line["full_hydro"] = bench_full_hydro(vs)
         line["serve"] = bench_serve(vs, args.serve_seconds)
@@ -792,6 +793,30 @@ def bench_task(vs, n=65536, k=10, steps=100, reps=3):
     return {"rate": n * k * steps / (task_ms / 1e3), "plain": n * k * steps / (plain_ms / 1e3),
             "step_us": task_ms / steps * 1e3, "observe_us": observe_ms / steps * 1e3,
             "resets": resets}
+
+
+def bench_env(sizes=(4096, 65536), k=10, steps=100, reps=3):
+    """The Gym-style environment (MarineEnv, §EXPERIMENTS' task format): BlueROV2 Heavy circle
+    tracking, one throttle vector per env and step held over k sub-steps, the actions copied
+    in by the step call; rows [envs, µs per env step, env-sub-steps/s]."""
+    import torch
+    from paper_2410_14117_gb300.env import MarineEnv
+
+    rows = []
+    for n in sizes:
+        env = MarineEnv(n, task="circle", vehicle=1, sub_steps=k, seed=3)
+        g = torch.Generator(device="cuda").manual_seed(5)
+        acts = torch.rand((steps, n, env.action_dim), generator=g, device="cuda") * 2 - 1
+        env.reset()
+
+        def loop():
+            for i in range(steps):
+                env.step(acts[i])
+
+        ms = _time_episodes(loop, reps)
+        env.close()
+        rows.append([n, ms / steps * 1e3, n * k * steps / (ms / 1e3)])
+    return rows
 
 
 def _count_resets(sim, k, steps):

@@ -3,8 +3,9 @@
 The paper's four tasks (§EXPERIMENTS: station keeping, circle, helix and lemniscate tracking)
 are offered in a Gym-style format: a policy sees the observation of Eq. 2, sets one throttle per
 thruster (the action space of Eq. 3) and is scored by the position error of Eq. 4.
-``MarineEnv`` keeps a whole fleet of such environments on the GPU.  ``step`` copies the actions
-into a resident device buffer that the step kernel reads in place, advances every env
+``MarineEnv`` keeps a whole fleet of such environments on the GPU.  ``step`` clamps the actions
+into a resident one-segment schedule that the step kernel reads in place (every sub-step past
+the schedule's end holds its last segment, so the buffer never needs rewinding), advances every env
 ``sub_steps`` RK4 sub-steps (the paper's sub-simulation steps within one simulation step) with
 the observation, the error and the auto-reset of finished episodes fused into the last launch
 (mg_task_step), and returns device tensors.  The reward is the negative position error: the
@@ -55,8 +56,8 @@ class MarineEnv:
     """``n_envs`` environments of one vehicle type and one task.
 
     reset() -> obs [n, obs_dim];  step(actions [n, n_thr]) -> (obs, reward [n], done [n] bool,
-    {"episode_error": [n]}).  obs, reward and the info tensor live on the GPU; obs and
-    episode_error are buffers the next call overwrites.  Throttles are clamped to [-1, 1].  An
+    {"episode_error": [n]}).  All four live on the GPU in buffers the next call overwrites
+    (done is a bool view of the step's flags).  Throttles are clamped to [-1, 1].  An
     episode ends when the position error exceeds ``max_error``, after ``episode_steps``
     sub-steps, or on a non-finite state; the env is then reset inside the step and its returned
     observation is the new episode's first.
@@ -93,6 +94,8 @@ class MarineEnv:
         self.obs_dim = sim.obs_dim
         self.action_dim = self.n_thr
         self._act = torch.zeros((1, self.n, sim.act_w), dtype=torch.float32, device=sim.device)
+        self._thr = self._act[0, :, :self.n_thr]
+        self._rew = torch.empty(self.n, dtype=torch.float32, device=sim.device)
         sim.set_actions_borrowed(self._act, self.k)
 
     def reset(self):
@@ -106,13 +109,15 @@ class MarineEnv:
         return obs
 
     def step(self, actions):
-        a = torch.as_tensor(actions, dtype=torch.float32, device=self._act.device)
+        a = actions if isinstance(actions, torch.Tensor) else torch.as_tensor(actions)
         if tuple(a.shape) != (self.n, self.n_thr):
             raise ValueError(f"actions must be [{self.n}, {self.n_thr}]")
-        self._act[0, :, :self.n_thr].copy_(a.clamp(-1.0, 1.0))
-        self.sim.set_actions_borrowed(self._act, self.k)  # the step reads them from sub-step 0
+        if a.device != self._act.device or a.dtype != torch.float32:
+            a = a.to(device=self._act.device, dtype=torch.float32)
+        torch.clamp(a, -1.0, 1.0, out=self._thr)  # ordered before the step on the same stream
         obs, err, done, ep = self.sim.task_step(self.k)
-        return obs, -err, done.bool(), {"episode_error": ep}
+        torch.neg(err, out=self._rew)
+        return obs, self._rew, done.view(torch.bool), {"episode_error": ep}
 
     def close(self):
         if self.sim is not None:

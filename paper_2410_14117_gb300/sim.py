@@ -244,13 +244,21 @@ class Sim:
                           torch.empty(self.n, dtype=torch.float32, device=dev),
                           torch.empty(self.n, dtype=torch.uint8, device=dev),
                           torch.empty(self.n, dtype=torch.float32, device=dev))
+        self._task_ptrs = None
 
     def task_step(self, k: int):
         """(obs [n, obs_dim], err [n], done [n], episode_err [n]) after k sub-steps (k = 0:
         observe only).  The tensors are reused by the next call."""
-        obs, err, done, ep = self._task_out
-        call("mg_task_step", self._h, int(k), _ptr(obs), _ptr(err), _ptr(done), _ptr(ep))
-        return obs, err, done, ep
+        out = self._task_out
+        if getattr(self, "_task_ptrs", None) is None or self._task_ptrs[0] is not out:
+            # a policy loop calls this every few microseconds of GPU time: marshal the output
+            # pointers once per set of buffers
+            self._task_ptrs = (out, _lib.load(), tuple(_ptr(t) for t in out))
+        _, lib, ptrs = self._task_ptrs
+        st = lib.mg_task_step(self._h, int(k), *ptrs)
+        if st != 0:
+            raise MGError(st, "mg_task_step", lib.mg_last_error().decode(errors="replace"))
+        return out
 
     # ------------------------------------------------------------------ state
     def get_state(self, out=None):

@@ -420,6 +420,19 @@ mg_status mg_task_obs_dim(mg_sim *sim, int32_t *obs_dim);
 mg_status mg_task_step(mg_sim *sim, int32_t k, float *obs, float *err, uint8_t *done,
                        float *episode_err);
 
+/* One step of a Gym-style environment (§EXPERIMENTS: the tasks in a Gym-style format; the
+ * action space of Eq. 3): the policy's throttles actions (device [n][w], w = the action width
+ * of mg_set_action_width) are clamped to [-1, 1] (NaN kept) into the library's own
+ * one-segment schedule, held over all k >= 1 sub-steps, and the task step of mg_task_step
+ * follows, writing reward = -(Eq. 4 position error) instead of err.  The schedule replaces the
+ * sim's actions on the first call (and after any other action call) and is rewritten in place
+ * by the later ones, so a policy loop pays one small copy kernel per step.  actions may be
+ * reused once the stream has passed the call.  obs, reward, done, episode_err: device, as
+ * mg_task_step.  Asynchronous.  Errors: MG_ESTATE (no task), MG_EINVAL (k < 1, NULL, host
+ * memory), MG_ENOMEM (the schedule's first allocation). */
+mg_status mg_env_step(mg_sim *sim, int32_t k, const float *actions, float *obs, float *reward,
+                      uint8_t *done, float *episode_err);
+
 /* ------------------------------------------------------------------------------------------
  * Serving: a job pool with continuous batching.  A pool holds an arena of capacity_envs envs; a
  * job (one vehicle type, its own parameter and command seeds, hold and horizon) is admitted into

@@ -114,6 +114,7 @@ SIGNATURES = {
     "mg_set_task": [_P, ctypes.POINTER(TaskSpec), _P],
     "mg_task_obs_dim": [_P, ctypes.POINTER(_I32)],
     "mg_task_step": [_P, _I32, _P, _P, _P, _P],
+    "mg_env_step": [_P, _I32, _P, _P, _P, _P, _P],
     "mg_pool_create": [_I64, ctypes.POINTER(VehicleParams), _I32, ctypes.POINTER(_P)],
     "mg_pool_destroy": [_P],
     "mg_pool_set_stream": [_P, _P],

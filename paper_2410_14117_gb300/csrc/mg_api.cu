@@ -189,7 +189,12 @@ struct mg_sim {
 
   // task layer
   bool has_task = false;
-  const void *task_out_ok[4] = {nullptr, nullptr, nullptr, nullptr};  // last validated outputs
+  const void *task_out_ok[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // last validated
+  // environment step (mg_env_step): the library's one-segment schedule of clamped throttles
+  // [n][act_w], and the last validated action input
+  float *env_act = nullptr;
+  size_t env_act_cap = 0;  // floats
+  const void *env_in_ok = nullptr;
   mg_task_spec task{};
   void *task_buf = nullptr;  // centre [n] float4, clock [n] int32, err_sum [n] float
   TaskView task_view() const {
@@ -705,6 +710,7 @@ mg_status mg_destroy(mg_sim *s) {
   cudaFree(s->act);
   cudaFree(s->stage);
   cudaFree(s->xh);
+  cudaFree(s->env_act);
   cudaFree(s->adj_ws);
   cudaFree(s->arena);
   delete s;
@@ -1246,24 +1252,22 @@ mg_status mg_task_obs_dim(mg_sim *s, int32_t *obs_dim) {
   return MG_OK;
 }
 
-mg_status mg_task_step(mg_sim *s, int32_t k, float *obs, float *err, uint8_t *done,
-                       float *episode_err) {
-  MG_NONNULL(s);
-  NvtxRange nvtx("mg_task_step");
-  MG_NONNULL(obs);
-  MG_NONNULL(err);
-  MG_NONNULL(done);
+}  // extern "C"
+
+namespace {
+
+// A task step (mg_task_step) with its outputs; err and reward may each be null.
+mg_status task_step_outputs(mg_sim *s, int32_t k, float *obs, float *err, float *reward,
+                            uint8_t *done, float *episode_err) {
   if (!s->has_task) return fail(MG_ESTATE, "no task set");
   if (k < 0) return fail(MG_EINVAL, "k must be >= 0");
   // a policy loop passes the same output buffers every call: check them once (a pointer query
   // costs microseconds, more than the host budget of a task step)
-  const void *outs[4] = {obs, err, done, episode_err};
-  if (!std::equal(outs, outs + 4, s->task_out_ok)) {
-    for (const void *p : {(const void *)obs, (const void *)err, (const void *)done})
-      if (!is_device_ptr(p)) return fail(MG_EINVAL, "task outputs must be device memory");
-    if (episode_err && !is_device_ptr(episode_err))
-      return fail(MG_EINVAL, "task outputs must be device memory");
-    std::copy(outs, outs + 4, s->task_out_ok);
+  const void *outs[5] = {obs, err, done, episode_err, reward};
+  if (!std::equal(outs, outs + 5, s->task_out_ok)) {
+    for (const void *p : outs)
+      if (p && !is_device_ptr(p)) return fail(MG_EINVAL, "task outputs must be device memory");
+    std::copy(outs, outs + 5, s->task_out_ok);
   }
   if (k == 0) {  // observe only
     MG_CK(launch_task(s->st, s->task_view(), s->n, s->gid0, 0, s->dt, obs, err, done,
@@ -1279,13 +1283,71 @@ mg_status mg_task_step(mg_sim *s, int32_t k, float *obs, float *err, uint8_t *do
   }
   int32_t obs_dim = 0;
   mg_task_obs_dim(s, &obs_dim);
-  TaskOut to{obs, err, done, episode_err, obs_dim, 0, s->reset_seed, s->nu0_sigma, s->episode};
+  TaskOut to{obs, err, done, episode_err, obs_dim, 0, s->reset_seed, s->nu0_sigma, s->episode,
+             reward};
   FleetView v = s->view();
   v.cursor_adv = k_last;
   MG_CK(launch_fleet_task(v, s->blocks_d, s->n_blocks, s->threads, s->ntv, s->diag,
                           s->structured, k_last, k, s->task_view(), to, s->stream));
   s->cursor += k_last;
   return MG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mg_status mg_task_step(mg_sim *s, int32_t k, float *obs, float *err, uint8_t *done,
+                       float *episode_err) {
+  MG_NONNULL(s);
+  NvtxRange nvtx("mg_task_step");
+  MG_NONNULL(obs);
+  MG_NONNULL(err);
+  MG_NONNULL(done);
+  return task_step_outputs(s, k, obs, err, nullptr, done, episode_err);
+}
+
+mg_status mg_env_step(mg_sim *s, int32_t k, const float *actions, float *obs, float *reward,
+                      uint8_t *done, float *episode_err) {
+  MG_NONNULL(s);
+  NvtxRange nvtx("mg_env_step");
+  MG_NONNULL(actions);
+  MG_NONNULL(obs);
+  MG_NONNULL(reward);
+  MG_NONNULL(done);
+  if (!s->has_task) return fail(MG_ESTATE, "no task set");
+  if (k < 1) return fail(MG_EINVAL, "k must be >= 1");
+  if (actions != s->env_in_ok) {
+    if (!is_device_ptr(actions)) return fail(MG_EINVAL, "actions must be device memory");
+    s->env_in_ok = actions;
+  }
+  const size_t floats = (size_t)s->n * s->act_w;
+  if (s->env_act_cap < floats) {
+    MG_CK(cudaStreamSynchronize(s->stream));
+    cudaFree(s->env_act);
+    s->env_act = nullptr;
+    s->env_act_cap = 0;
+    if (cudaMalloc(reinterpret_cast<void **>(&s->env_act), floats * sizeof(float)) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      s->env_act = nullptr;
+      return fail(MG_ENOMEM, "cudaMalloc(environment actions)");
+    }
+    s->env_act_cap = floats;
+  }
+  // The schedule is one segment held for good (every sub-step past a schedule's end holds its
+  // last segment), so it is set up once and then only rewritten.
+  if (s->act_src != s->env_act || s->n_seg != 1 || s->proc) {
+    mg_status st = release_async_actions(s);
+    if (st != MG_OK) return st;
+    s->act_src = s->env_act;
+    s->proc = 0;
+    s->n_seg = 1;
+    s->hold = 1 << 30;
+    if ((st = rewind_cursor(s)) != MG_OK) return st;
+  }
+  MG_CK(launch_clamp_actions(actions, s->env_act, (int64_t)floats, s->stream));
+  return task_step_outputs(s, k, obs, nullptr, reward, done, episode_err);
 }
 
 mg_status mg_get_state(mg_sim *s, float *out) {

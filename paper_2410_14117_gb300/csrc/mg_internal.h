@@ -216,7 +216,7 @@ cudaError_t launch_split(const FleetView &fv, const BlockDesc *blocks, int n_blo
 // Outputs and reset inputs of the fused task step.
 struct TaskOut {
   float *obs;        // [n][obs_dim]
-  float *err;        // [n]
+  float *err;        // [n] or null
   uint8_t *done;     // [n]
   float *ep_err;     // [n] or null
   int32_t obs_dim;
@@ -224,6 +224,7 @@ struct TaskOut {
   uint64_t seed;     // episode-start draws (as mg_reset)
   double sigma;
   uint32_t *episode;
+  float *reward;     // [n] or null: the negative error
 };
 
 // Final launch of a task step: k_launch sub-steps (static grid), then the task epilogue for a
@@ -232,6 +233,9 @@ cudaError_t launch_fleet_task(const FleetView &fv, const BlockDesc *blocks, int 
                               int threads, NtVariant ntv, bool diag, bool structured,
                               int32_t k_launch, int32_t k_task, const TaskView &tv, TaskOut to,
                               cudaStream_t stream);
+
+// Throttles clamped to [-1, 1] (NaN kept): out[i] = clamp(in[i]) for i < count.
+cudaError_t launch_clamp_actions(const float *in, float *out, int64_t count, cudaStream_t stream);
 
 cudaError_t launch_task(const StatePlanes &st, const TaskView &tv, int64_t n, int64_t gid0,
                         int32_t k, float dt, float *obs, float *err, uint8_t *done,

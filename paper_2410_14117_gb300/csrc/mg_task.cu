@@ -191,7 +191,8 @@ __device__ __forceinline__ void task_epilogue(const FleetView &fv, const TaskVie
   const bool over = (tv.max_err > 0.f && e0 > tv.max_err) ||
                     (tv.episode_steps > 0 && clock >= tv.episode_steps);
   const float sum = in.err_sum + e0;
-  to.err[e] = e0;
+  if (to.err) to.err[e] = e0;
+  if (to.reward) to.reward[e] = -e0;
   float nu[6] = {s.v[0], s.v[1], s.v[2], s.w[0], s.w[1], s.w[2]};
   if (bad || over) {
     // new episode (as reset_env)
@@ -265,7 +266,11 @@ __global__ void __maxnreg__(XH ? kRegsXH : DIAG ? kRegsDiag : kRegsGeneral)
     sdir[threadIdx.x] = fv.geo[bd.type].dir[threadIdx.x];
     sarm[threadIdx.x] = fv.geo[bd.type].arm[threadIdx.x];
   }
-  if (threadIdx.x == 0) {  // the cursor load overlaps the geometry loads
+  // Programmatic dependent launch: the block descriptors and the geometry above are written
+  // before any step; everything below waits for the previous kernel in the stream (the action
+  // copy of mg_env_step, or the task step's leading launches) to complete.
+  cudaGridDependencySynchronize();
+  if (threadIdx.x == 0) {
     s_done = 0u;
     s_cursor = launch_cursor(fv);
   }
@@ -301,9 +306,18 @@ cudaError_t fleet_task_t(const FleetView &fv, const BlockDesc *blocks, int n_blo
   const cudaError_t e = allow_dynamic_smem(
       reinterpret_cast<const void *>(&k_fleet_task<NTV, DIAG, NH, XH>), smem);
   if (e != cudaSuccess) return e;
-  k_fleet_task<NTV, DIAG, NH, XH><<<n_blocks, threads, smem, stream>>>(fv, blocks, k_launch,
-                                                                       k_task, tv, to);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)n_blocks);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_fleet_task<NTV, DIAG, NH, XH>, fv, blocks, k_launch, k_task,
+                            tv, to);
 }
 
 
@@ -325,7 +339,24 @@ cudaError_t fleet_task_d(const FleetView &fv, const BlockDesc *blocks, int n_blo
                                      smem, stream);
 }
 
+__global__ void k_clamp_actions(const float *__restrict__ in, float *__restrict__ out,
+                                int64_t count) {
+  // the task kernel that follows may launch now and wait for this copy at its dependency point
+  cudaTriggerProgrammaticLaunchCompletion();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const float x = in[i];
+  out[i] = x < -1.f ? -1.f : (x > 1.f ? 1.f : x);
+}
+
 }  // namespace
+
+cudaError_t launch_clamp_actions(const float *in, float *out, int64_t count, cudaStream_t stream) {
+  if (count < 1) return cudaSuccess;
+  const int64_t grid = (count + 255) / 256;
+  k_clamp_actions<<<(unsigned)grid, 256, 0, stream>>>(in, out, count);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_task(const StatePlanes &st, const TaskView &tv, int64_t n, int64_t gid0,
                         int32_t k, float dt, float *obs, float *err, uint8_t *done,

@@ -3,13 +3,12 @@
 The paper's four tasks (§EXPERIMENTS: station keeping, circle, helix and lemniscate tracking)
 are offered in a Gym-style format: a policy sees the observation of Eq. 2, sets one throttle per
 thruster (the action space of Eq. 3) and is scored by the position error of Eq. 4.
-``MarineEnv`` keeps a whole fleet of such environments on the GPU.  ``step`` clamps the actions
-into a resident one-segment schedule that the step kernel reads in place (every sub-step past
-the schedule's end holds its last segment, so the buffer never needs rewinding), advances every env
-``sub_steps`` RK4 sub-steps (the paper's sub-simulation steps within one simulation step) with
-the observation, the error and the auto-reset of finished episodes fused into the last launch
-(mg_task_step), and returns device tensors.  The reward is the negative position error: the
-paper names the error the tasks are judged by, not its reward weights.
+``MarineEnv`` keeps a whole fleet of such environments on the GPU.  ``step`` is one library call
+(mg_env_step): the actions are clamped into the library's resident one-segment schedule, every
+env advances ``sub_steps`` RK4 sub-steps (the paper's sub-simulation steps within one simulation
+step), and the observation, the reward and the auto-reset of finished episodes are fused into
+the last launch.  The reward is the negative position error: the paper names the error the tasks
+are judged by, not its reward weights.
 
 Every env's reference path starts within ``spawn_radius`` of the origin, where a reset puts
 the vehicle; each env has its own phase on its path.
@@ -21,7 +20,11 @@ import math
 import numpy as np
 import torch
 
+import ctypes
+
+from . import _lib
 from . import inputs as I
+from ._lib import MGError
 from .sim import Sim
 
 # mg.h MG_TASK_*
@@ -93,31 +96,40 @@ class MarineEnv:
         sim.set_task(TASKS[task], self.centres, **self._task_args)
         self.obs_dim = sim.obs_dim
         self.action_dim = self.n_thr
-        self._act = torch.zeros((1, self.n, sim.act_w), dtype=torch.float32, device=sim.device)
-        self._thr = self._act[0, :, :self.n_thr]
-        self._rew = torch.empty(self.n, dtype=torch.float32, device=sim.device)
-        sim.set_actions_borrowed(self._act, self.k)
+        dev = sim.device
+        self._obs = torch.empty((self.n, self.obs_dim), dtype=torch.float32, device=dev)
+        self._rew = torch.empty(self.n, dtype=torch.float32, device=dev)
+        self._err = torch.empty(self.n, dtype=torch.float32, device=dev)
+        self._done = torch.zeros(self.n, dtype=torch.uint8, device=dev)
+        self._ep = torch.zeros(self.n, dtype=torch.float32, device=dev)
+        self._lib = _lib.load()
+        p = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+        self._step_outs = (p(self._obs), p(self._rew), p(self._done), p(self._ep))
+        self._obs_outs = (p(self._obs), p(self._err), p(self._done), p(self._ep))
+        self._info = {"episode_error": self._ep}
+
+    def _check(self, st, where):
+        if st != 0:
+            raise MGError(st, where, self._lib.mg_last_error().decode(errors="replace"))
 
     def reset(self):
         """Start a new episode in every env (state reset, episode clocks and error sums back to
         zero); returns the observation."""
         self.sim.reset()
         self.sim.set_task(TASKS[self.task], self.centres, **self._task_args)
-        self._act.zero_()
-        self.sim.set_actions_borrowed(self._act, self.k)
-        obs, _, _, _ = self.sim.task_step(0)
-        return obs
+        self._check(self._lib.mg_task_step(self.sim._h, 0, *self._obs_outs), "mg_task_step")
+        return self._obs
 
     def step(self, actions):
-        a = actions if isinstance(actions, torch.Tensor) else torch.as_tensor(actions)
+        a = actions
+        if not (isinstance(a, torch.Tensor) and a.is_cuda and a.dtype == torch.float32
+                and a.is_contiguous()):
+            a = torch.as_tensor(a, dtype=torch.float32).to(self._obs.device).contiguous()
         if tuple(a.shape) != (self.n, self.n_thr):
             raise ValueError(f"actions must be [{self.n}, {self.n_thr}]")
-        if a.device != self._act.device or a.dtype != torch.float32:
-            a = a.to(device=self._act.device, dtype=torch.float32)
-        torch.clamp(a, -1.0, 1.0, out=self._thr)  # ordered before the step on the same stream
-        obs, err, done, ep = self.sim.task_step(self.k)
-        torch.neg(err, out=self._rew)
-        return obs, self._rew, done.view(torch.bool), {"episode_error": ep}
+        self._check(self._lib.mg_env_step(self.sim._h, self.k, ctypes.c_void_p(a.data_ptr()),
+                                          *self._step_outs), "mg_env_step")
+        return self._obs, self._rew, self._done.view(torch.bool), self._info
 
     def close(self):
         if self.sim is not None:

@@ -120,3 +120,46 @@ def test_env_shapes_and_arguments():
     with pytest.raises(ValueError):
         MarineEnv(8, sub_steps=0)
     assert math.isclose(float(TASKS["helix"]), 2.0)
+
+
+def test_env_step_entry_point_errors_and_switching_back():
+    """mg_env_step rejects what it cannot run on the host; after environment steps an ordinary
+    action schedule takes over again, with the bits of a sim that never used mg_env_step."""
+    import ctypes
+    from paper_2410_14117_gb300._lib import MGError, call
+    n, k = 128, 10
+    env = MarineEnv(n, task="circle", vehicle=1, sub_steps=k, seed=9)
+    sim = env.sim
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    obs, rew, ep = env._obs, env._rew, env._ep
+    done = env._done
+    host = torch.zeros((n, 8))
+    for bad_k, acts in ((0, torch.zeros((n, 8), device="cuda")), (k, host)):
+        with pytest.raises(MGError) as ei:
+            call("mg_env_step", sim._h, bad_k, ptr(acts), ptr(obs), ptr(rew), ptr(done), ptr(ep))
+        assert ei.value.code == "MG_EINVAL"
+    plain = Sim(n, np.full(n, 1, dtype=np.int32), I.fleet_vehicles())
+    with pytest.raises(MGError) as ei:
+        call("mg_env_step", plain._h, k, ptr(torch.zeros((n, 8), device="cuda")), ptr(obs),
+             ptr(rew), ptr(done), ptr(ep))
+    assert ei.value.code == "MG_ESTATE"
+    plain.close()
+    # two environment steps, then an ordinary schedule on both this sim and a twin
+    twin = Sim(n, np.full(n, 1, dtype=np.int32), I.fleet_vehicles())
+    twin.randomize(9, 0.8, 1.2, 0.2, 0.0)
+    twin.reset()
+    twin.set_task(TASKS["circle"], env.centres.clone(), **SPEC)
+    tact = torch.zeros((1, n, 8), device="cuda")
+    for step in range(2):
+        a = _actions(step, n, 8)
+        env.step(a)
+        tact[0] = a.clamp(-1, 1)
+        twin.set_actions_borrowed(tact, k)
+        twin.task_step(k)
+    cmds = torch.tensor(I.commands(4, 3, n, 8), device="cuda")
+    for s_ in (sim, twin):
+        s_.set_actions(cmds, 10)
+        s_.step(30)
+    assert torch.equal(sim.get_state(), twin.get_state())
+    env.close()
+    twin.close()

@@ -63,7 +63,9 @@ class MarineEnv:
     (done is a bool view of the step's flags).  Throttles are clamped to [-1, 1].  An
     episode ends when the position error exceeds ``max_error``, after ``episode_steps``
     sub-steps, or on a non-finite state; the env is then reset inside the step and its returned
-    observation is the new episode's first.
+    observation is the new episode's first.  tune: time the launch shapes for calls of
+    sub_steps sub-steps first (a few seconds; at 1,024-65,536 envs the default shape measured
+    within 4 % of the tuned one).  The fleet runs on torch's current stream at construction.
     """
 
     def __init__(self, n_envs: int, task: str = "circle", vehicle: int = 1, sub_steps: int = 10,
@@ -71,7 +73,7 @@ class MarineEnv:
                  current_sigma: float = 0.2, nu0_sigma: float = 0.0, radius: float = 2.0,
                  omega: float = 0.3, vz: float = 0.1, psi_r: float = 0.0, lookahead: int = 4,
                  lookahead_dt: float = 0.5, max_error: float = 3.0, episode_steps: int = 1000,
-                 spawn_radius: float = 0.5, vehicles=None):
+                 spawn_radius: float = 0.5, vehicles=None, tune: bool = False):
         if task not in TASKS:
             raise ValueError(f"unknown task {task!r}; one of {sorted(TASKS)}")
         if sub_steps < 1:
@@ -84,6 +86,9 @@ class MarineEnv:
         sim = Sim(self.n, np.full(self.n, vehicle, dtype=np.int32), self.vehicles)
         self.sim = sim
         sim.set_timestep(dt)
+        if tune:  # launch shape timed for calls of sub_steps sub-steps (on a scratch fleet)
+            from .autotune import Autotuner
+            Autotuner(horizon=10 * self.k, reps=2, k_per_call=self.k).tune(sim, self.vehicles)
         if self.n_thr == 6:
             sim.set_action_width(6)  # unpadded throttle rows
         sim.randomize(seed, lo, hi, current_sigma, nu0_sigma)

@@ -56,7 +56,9 @@ def task_centres(task: str, n_envs: int, radius: float, seed: int,
 
 
 class MarineEnv:
-    """``n_envs`` environments of one vehicle type and one task.
+    """``n_envs`` environments of one task; ``vehicle`` is a vehicle type for all of them or a
+    per-env sequence of types (a mixed fleet; actions then have the largest thruster count, and
+    entries past an env's own count are ignored).
 
     reset() -> obs [n, obs_dim];  step(actions [n, n_thr]) -> (obs, reward [n], done [n] bool,
     {"episode_error": [n]}).  All four live on the GPU in buffers the next call overwrites
@@ -68,7 +70,7 @@ class MarineEnv:
     within 8 % of the tuned one, either way).  The fleet runs on torch's current stream at construction.
     """
 
-    def __init__(self, n_envs: int, task: str = "circle", vehicle: int = 1, sub_steps: int = 10,
+    def __init__(self, n_envs: int, task: str = "circle", vehicle=1, sub_steps: int = 10,
                  seed: int = 0, dt: float = 0.01, lo: float = 0.8, hi: float = 1.2,
                  current_sigma: float = 0.2, nu0_sigma: float = 0.0, radius: float = 2.0,
                  omega: float = 0.3, vz: float = 0.1, psi_r: float = 0.0, lookahead: int = 4,
@@ -79,18 +81,21 @@ class MarineEnv:
         if sub_steps < 1:
             raise ValueError("sub_steps must be >= 1")
         self.vehicles = list(vehicles) if vehicles is not None else I.fleet_vehicles()
-        if not 0 <= vehicle < len(self.vehicles):
-            raise ValueError("vehicle out of range")
         self.n, self.k, self.task = int(n_envs), int(sub_steps), task
-        self.n_thr = int(self.vehicles[vehicle].n_thr)
-        sim = Sim(self.n, np.full(self.n, vehicle, dtype=np.int32), self.vehicles)
+        types = (np.full(self.n, vehicle, dtype=np.int32) if np.ndim(vehicle) == 0
+                 else np.asarray(vehicle, dtype=np.int32))
+        if types.shape != (self.n,) or types.min() < 0 or types.max() >= len(self.vehicles):
+            raise ValueError("vehicle: a type index, or one per env, in range")
+        self.types = types
+        self.n_thr = max(int(self.vehicles[t].n_thr) for t in np.unique(types))
+        sim = Sim(self.n, types, self.vehicles)
         self.sim = sim
         sim.set_timestep(dt)
         if tune:  # launch shape timed for calls of sub_steps sub-steps (on a scratch fleet)
             from .autotune import Autotuner
             Autotuner(horizon=10 * self.k, reps=2, k_per_call=self.k).tune(sim, self.vehicles)
-        if self.n_thr == 6:
-            sim.set_action_width(6)  # unpadded throttle rows
+        if self.n_thr == 6:  # every env has 6 thrusters: unpadded throttle rows
+            sim.set_action_width(6)
         sim.randomize(seed, lo, hi, current_sigma, nu0_sigma)
         sim.reset()
         self.centres = torch.tensor(task_centres(task, self.n, radius, seed, spawn_radius),

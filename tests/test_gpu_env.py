@@ -26,11 +26,14 @@ def _actions(step, n, nt, scale=1.3):
     return ((torch.rand((n, nt), generator=g) * 2 - 1) * scale).cuda()
 
 
-def test_env_step_equals_the_task_step_it_wraps():
+@pytest.mark.parametrize("mixed", [False, True])
+def test_env_step_equals_the_task_step_it_wraps(mixed):
     n, k, seed = 700, 10, 3
-    env = MarineEnv(n, task="helix", vehicle=1, sub_steps=k, seed=seed, nu0_sigma=0.2)
+    types = I.mixed_fleet(8, n, max_group=90) if mixed else np.full(n, 1, dtype=np.int32)
+    env = MarineEnv(n, task="helix", vehicle=types if mixed else 1, sub_steps=k, seed=seed,
+                    nu0_sigma=0.2)
     vs = I.fleet_vehicles()
-    sim = Sim(n, np.full(n, 1, dtype=np.int32), vs)
+    sim = Sim(n, types, vs)
     sim.randomize(seed, 0.8, 1.2, 0.2, 0.2)
     sim.reset()
     sim.set_task(TASKS["helix"], env.centres.clone(), **SPEC)
@@ -119,6 +122,8 @@ def test_env_shapes_and_arguments():
         MarineEnv(8, task="orbit")
     with pytest.raises(ValueError):
         MarineEnv(8, sub_steps=0)
+    with pytest.raises(ValueError):
+        MarineEnv(8, vehicle=[0, 1])
     assert math.isclose(float(TASKS["helix"]), 2.0)
 
 

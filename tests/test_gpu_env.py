@@ -26,9 +26,10 @@ def _actions(step, n, nt, scale=1.3):
     return ((torch.rand((n, nt), generator=g) * 2 - 1) * scale).cuda()
 
 
-@pytest.mark.parametrize("mixed", [False, True])
-def test_env_step_equals_the_task_step_it_wraps(mixed):
-    n, k, seed = 700, 10, 3
+# k = 60 runs its first 50 sub-steps as a graph-replayed mg_step on the library's schedule
+@pytest.mark.parametrize("mixed,k", [(False, 10), (True, 10), (False, 60)])
+def test_env_step_equals_the_task_step_it_wraps(mixed, k):
+    n, seed = 700, 3
     types = I.mixed_fleet(8, n, max_group=90) if mixed else np.full(n, 1, dtype=np.int32)
     env = MarineEnv(n, task="helix", vehicle=types if mixed else 1, sub_steps=k, seed=seed,
                     nu0_sigma=0.2)

@@ -868,11 +868,141 @@ cudaError_t launch_adjoint_t(const FleetView &fv, const int32_t *types, const fl
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- forward pass
+// The forward of the differentiable rollout in one launch: T sub-steps from the sim's state on
+// the static grid, the state written to ckpt [n_ck][MG_NSTATE][n] (record order, lag entries
+// past the vehicle's thrusters zero) before sub-steps 0, C, 2C, ... and the trajectory recorded
+// after every sub-step into traj [T][MG_NTRAJ][n].  Per env the arithmetic is advance_env's
+// (the same step code, commands and lag segments), so the result equals a chain of recording
+// launches of C sub-steps each, bit for bit, without the launches or the state's round trips.
+template <int MT>
+__device__ __forceinline__ void write_checkpoint(float *__restrict__ ck, int64_t n, int64_t e,
+                                                 const St<MT> &s) {
+  float *c = ck + e;
+  for (int i = 0; i < 3; ++i) c[(int64_t)i * n] = s.p[i];
+  for (int i = 0; i < 4; ++i) c[(int64_t)(3 + i) * n] = s.q[i];
+  for (int i = 0; i < 3; ++i) c[(int64_t)(7 + i) * n] = s.v[i];
+  for (int i = 0; i < 3; ++i) c[(int64_t)(10 + i) * n] = s.w[i];
+#pragma unroll
+  for (int i = 0; i < MG_MAX_THR; ++i) c[(int64_t)(13 + i) * n] = i < MT ? s.n[i] : 0.f;
+}
+
+template <int NTV, bool DIAG, int NH, bool XH>
+__global__ void __maxnreg__(XH ? kRegsXH : DIAG ? kRegsWide : kRegsGeneral)
+    k_rollout_fwd(const FleetView fv, const BlockDesc *__restrict__ blocks, const int32_t T,
+                  const int32_t C, float *__restrict__ traj, float *__restrict__ ckpt) {
+  constexpr int MT = (NTV == NT_6) ? 6 : 8;
+  constexpr bool MIXED = (NTV == NT_MIXED);
+  __shared__ float4 sdir[MG_MAX_THR], sarm[MG_MAX_THR];
+  __shared__ unsigned s_done;
+  __shared__ int64_t s_cursor;
+  extern __shared__ float sxh[];
+  const BlockDesc bd = blocks[blockIdx.x];
+  if (threadIdx.x < MG_MAX_THR) {
+    sdir[threadIdx.x] = fv.geo[bd.type].dir[threadIdx.x];
+    sarm[threadIdx.x] = fv.geo[bd.type].arm[threadIdx.x];
+  }
+  if (threadIdx.x == 0) {
+    s_done = 0u;
+    s_cursor = launch_cursor(fv);
+  }
+  if constexpr (XH) stage_xh(fv.xh, fv.n, bd.env0, bd.count, sxh);
+  __syncthreads();
+  if ((int)threadIdx.x >= bd.count) return;
+  const int64_t e = (int64_t)bd.env0 + threadIdx.x;
+  const int64_t n = fv.n;
+  const int nt = MIXED ? bd.n_thr : MT;
+  const bool current_accel = !(fv.model_flags & MG_MODEL_NO_CURRENT_ACCEL);
+  const float h = fv.dt;
+  const float *xh = XH ? sxh + threadIdx.x * MG_NXPARAM : nullptr;
+
+  St<MT> s;
+  load_state<MT>(fv.st, e, s);
+  Coef<DIAG> P;
+  {
+    Par<DIAG> raw;
+    load_par<DIAG>(fv.pa, e, raw);
+    P = make_coef<DIAG>(raw);
+  }
+  const int64_t step0 = s_cursor + fv.cursor_off;
+  int64_t seg = step0 / fv.hold;
+  int32_t left = fv.hold - (int32_t)(step0 - seg * fv.hold);
+  const LagEnv L = lag_env(P.itau, h);
+  float b[MT];
+  {
+    float c[MT];
+    load_commands<MT>(fv, e, seg, nt, P.itau, c);
+    lag_segment<MT>(c, L, b);
+  }
+  for (int32_t it = 0; it < T; ++it) {
+    if (it % C == 0) write_checkpoint<MT>(ckpt + (int64_t)(it / C) * MG_NSTATE * n, n, e, s);
+    if (left == 0) {
+      ++seg;
+      left = fv.hold;
+      float c[MT];
+      load_commands<MT>(fv, e, seg, nt, P.itau, c);
+      lag_segment<MT>(c, L, b);
+    }
+    rk4_step_lag<MT, DIAG, MIXED, NH, XH>(s, b, L, P, sdir, sarm, nt, current_accel, h, xh);
+    --left;
+    record<MT>(traj + (int64_t)it * MG_NTRAJ * n, n, e, s);
+  }
+  store_and_flag<MT, false>(fv, e, s);
+  if (fv.cursor_adv) finish_envs(fv, &s_done, bd.count, fv.cursor_adv);
+}
+
+template <int NTV, bool DIAG, int NH, bool XH>
+cudaError_t rollout_fwd_t(const FleetView &fv, const BlockDesc *blocks, int n_blocks,
+                          int threads, int32_t T, int32_t C, float *traj, float *ckpt,
+                          cudaStream_t stream) {
+  const size_t smem = XH ? sizeof(float) * threads * MG_NXPARAM : 0;  // <= 46,080 B
+  k_rollout_fwd<NTV, DIAG, NH, XH><<<n_blocks, threads, smem, stream>>>(fv, blocks, T, C, traj,
+                                                                         ckpt);
+  return cudaGetLastError();
+}
+
+template <int NTV>
+cudaError_t rollout_fwd_d(const FleetView &fv, const BlockDesc *blocks, int n_blocks,
+                          int threads, bool diag, bool structured, int32_t T, int32_t C,
+                          float *traj, float *ckpt, cudaStream_t stream) {
+  if (fv.xh)
+    return rollout_fwd_t<NTV, false, 0, true>(fv, blocks, n_blocks, threads, T, C, traj, ckpt,
+                                              stream);
+  if (diag && structured)
+    return rollout_fwd_t<NTV, true, 4, false>(fv, blocks, n_blocks, threads, T, C, traj, ckpt,
+                                              stream);
+  if (diag)
+    return rollout_fwd_t<NTV, true, 0, false>(fv, blocks, n_blocks, threads, T, C, traj, ckpt,
+                                              stream);
+  return rollout_fwd_t<NTV, false, 0, false>(fv, blocks, n_blocks, threads, T, C, traj, ckpt,
+                                             stream);
+}
+
 }  // namespace
 
 cudaError_t launch_checkpoint(const StatePlanes &st, int64_t n, float *ck, cudaStream_t stream) {
   k_checkpoint<<<(int)((n + 255) / 256), 256, 0, stream>>>(st, n, ck);
   return cudaGetLastError();
+}
+
+cudaError_t launch_rollout_forward(const FleetView &fv, const BlockDesc *blocks, int n_blocks,
+                                   int threads, NtVariant ntv, bool diag, bool structured,
+                                   int32_t T, int32_t C, float *traj, float *ckpt,
+                                   cudaStream_t stream) {
+  if (threads < 32 || threads > 256 || threads % 32 || n_blocks < 1 || T < 1 || C < 1 ||
+      (fv.xh && diag))
+    return cudaErrorInvalidValue;
+  switch (ntv) {
+    case NT_6:
+      return rollout_fwd_d<NT_6>(fv, blocks, n_blocks, threads, diag, structured, T, C, traj,
+                                 ckpt, stream);
+    case NT_8:
+      return rollout_fwd_d<NT_8>(fv, blocks, n_blocks, threads, diag, structured, T, C, traj,
+                                 ckpt, stream);
+    default:
+      return rollout_fwd_d<NT_MIXED>(fv, blocks, n_blocks, threads, diag, structured, T, C,
+                                     traj, ckpt, stream);
+  }
 }
 
 namespace {

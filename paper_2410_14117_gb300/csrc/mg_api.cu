@@ -1165,15 +1165,10 @@ mg_status mg_rollout_forward(mg_sim *s, int32_t T, int32_t C, float *traj, float
     return fail(MG_EINVAL, "traj and ckpt must be device memory");
   FleetView v = s->view();
   const int64_t step0 = s->cursor;
-  for (int32_t t0 = 0; t0 < T; t0 += C) {
-    const int32_t len = std::min(C, T - t0);
-    MG_CK(launch_checkpoint(s->st, s->n, ckpt + (int64_t)(t0 / C) * MG_NSTATE * s->n,
-                            s->stream));
-    v.cursor_off = t0;
-    v.cursor_adv = (t0 + len == T) ? T : 0;
-    MG_CK(launch_fleet(v, s->blocks_d, s->n_blocks, s->threads, s->ntv, s->diag, s->structured,
-                       false, len, traj + (int64_t)t0 * MG_NTRAJ * s->n, s->stream));
-  }
+  v.cursor_off = 0;
+  v.cursor_adv = T;
+  MG_CK(launch_rollout_forward(v, s->blocks_d, s->n_blocks, s->threads, s->ntv, s->diag,
+                               s->structured, T, C, traj, ckpt, s->stream));
   s->cursor += T;
   if (step0_out) *step0_out = step0;
   return MG_OK;

@@ -185,6 +185,12 @@ int64_t pool_capacity(const mg_pool *p);
 
 // ---------------------------------------------------------------- launchers (mg_adjoint.cu)
 cudaError_t launch_checkpoint(const StatePlanes &st, int64_t n, float *ck, cudaStream_t stream);
+// The rollout's forward in one launch on the static grid (mg_adjoint.cu): T sub-steps, ckpt
+// [ceil(T / C)][MG_NSTATE][n] before sub-steps 0, C, ..., traj [T][MG_NTRAJ][n] after each.
+cudaError_t launch_rollout_forward(const FleetView &fv, const BlockDesc *blocks, int n_blocks,
+                                   int threads, NtVariant ntv, bool diag, bool structured,
+                                   int32_t T, int32_t C, float *traj, float *ckpt,
+                                   cudaStream_t stream);
 // Backward kernel: mode 1 one warp per 32 envs, 2 the two-warp form (producer and consumer warps
 // per 32 envs, through a workspace of adjoint_workspace_bytes), 0 chosen by fleet size.
 cudaError_t adjoint_split(int64_t n, int mode, bool *split);

@@ -235,3 +235,44 @@ def test_backward_kernels_agree(n, mixed, T, C, general):
         sim.close()
     for name, a, b in zip(("coefficients", "actions", "initial state"), *outs):
         torch.testing.assert_close(b, a, rtol=0, atol=0, msg=name)
+
+
+@pytest.mark.parametrize("general", [False, True])
+def test_forward_equals_recorded_steps(general):
+    """The rollout's forward runs in one launch (checkpoints written from registers): its
+    trajectory, checkpoints and final state equal those of plain recording steps from the same
+    start, bit for bit (mixed fleet, ragged last segment; diagonal mass and the general path)."""
+    import ctypes
+    import math
+    from paper_2410_14117_gb300._lib import MG_NSTATE, call
+    from paper_2410_14117_gb300.sim import _ptr
+    vs = vehicles()
+    n, T, C, hold = 1000, 93, 7, 10
+    types = I.mixed_fleet(3, n, max_group=300)
+    nt = np.array([vs[t].n_thr for t in types])
+    acts = torch.tensor(I.commands(5, math.ceil(T / hold), n, nt), device="cuda")
+    s0 = torch.tensor(I.initial_states(21, n), dtype=torch.float32, device="cuda")
+    sims = []
+    for _ in range(2):
+        sim = Sim(n, types, vs)
+        sim.randomize(77, 0.8, 1.2, 0.2, 0.3, rg_halfwidth=0.02 if general else 0.0)
+        if general:
+            p = sim.get_params().double().cpu().numpy()
+            sim.set_hydro_offdiag(torch.tensor(I.hydro_offdiag(8, p), dtype=torch.float32,
+                                               device="cuda"))
+        sim.set_state(s0)
+        sim.set_actions(acts, hold)
+        sims.append(sim)
+    a, b = sims
+    traj = torch.empty((T, 13, n), device="cuda")
+    ckpt = torch.empty((math.ceil(T / C), MG_NSTATE, n), device="cuda")
+    step0 = ctypes.c_int64()
+    call("mg_rollout_forward", a._h, T, C, _ptr(traj), _ptr(ckpt), ctypes.byref(step0))
+    ref = []
+    for j in range(math.ceil(T / C)):
+        torch.testing.assert_close(ckpt[j].T.contiguous(), b.get_state(), rtol=0, atol=0)
+        ref.append(b.step_record(min(C, T - j * C)))
+    assert torch.equal(traj, torch.cat(ref))
+    assert torch.equal(a.get_state(), b.get_state())
+    a.close()
+    b.close()

@@ -297,7 +297,8 @@ mg_status mg_step_noalloc(mg_sim *sim, int32_t k);
 mg_status mg_step_record(mg_sim *sim, int32_t k, float *traj);
 
 /* Forward rollout for differentiation: T sub-steps from the current state and action cursor
- * (static grid, as mg_step_record), writing the state after every sub-step to traj, device
+ * in one launch on the static grid (results equal mg_step_record's bit for bit; the
+ * checkpoints are written from registers), writing the state after every sub-step to traj, device
  * [T][MG_NTRAJ][n], and the full state before sub-steps 0, C, 2C, ... to ckpt, device
  * [ceil(T / C)][MG_NSTATE][n] (component-major).  *step0_out (may be NULL) receives the action
  * cursor at the start; pass it to mg_rollout_backward.  Errors: MG_EINVAL (T < 1, C outside

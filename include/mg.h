@@ -213,8 +213,8 @@ mg_status mg_get_params(mg_sim *sim, float *out);
  * x [n][MG_NXPARAM] (host or device; layout above), or clear it (x = NULL: the diagonal model).
  * The mass matrices are re-inverted in FP64 with the off-diagonal added mass; a fleet with a
  * non-zero extension steps on the general path (static grid or work queue, each block or warp
- * staging its envs' coefficients in shared memory; mg_step_split runs its general form).  mg_randomize and
- * mg_set_params keep the extension.  Synchronous.  Errors: MG_EINVAL, MG_ENOMEM, MG_ENOTSPD
+ * staging its envs' coefficients in shared memory; mg_step_split runs its general form).
+ * mg_randomize and mg_set_params keep the extension.  Synchronous.  Errors: MG_EINVAL, MG_ENOMEM, MG_ENOTSPD
  * (stored, but some M_RB + M_A is not positive definite), MG_ECUDA. */
 mg_status mg_set_hydro_offdiag(mg_sim *sim, const float *x);
 

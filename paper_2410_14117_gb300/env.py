@@ -67,7 +67,8 @@ class MarineEnv:
     sub-steps, or on a non-finite state; the env is then reset inside the step and its returned
     observation is the new episode's first.  tune: time the launch shapes for calls of
     sub_steps sub-steps first (a few seconds; at 1,024-65,536 envs the default shape measured
-    within 8 % of the tuned one, either way).  The fleet runs on torch's current stream at construction.
+    within 8 % of the tuned one, either way).  The fleet runs on torch's current stream at
+    construction.
     """
 
     def __init__(self, n_envs: int, task: str = "circle", vehicle=1, sub_steps: int = 10,

@@ -169,3 +169,28 @@ def test_env_step_entry_point_errors_and_switching_back():
     assert torch.equal(sim.get_state(), twin.get_state())
     env.close()
     twin.close()
+
+
+def test_env_non_finite_throttles_end_the_episode():
+    """A NaN throttle (kept by the clamp) makes that env's state non-finite within the step; the
+    step ends its episode and resets it (done, a finite start state at the origin), and the
+    other envs carry on untouched."""
+    n, k = 256, 10
+    env = MarineEnv(n, task="station", vehicle=0, sub_steps=k, seed=4)
+    a = torch.zeros((n, 6), device="cuda")
+    env.step(a)
+    a[7, 2] = float("nan")
+    _, rew, done, _ = env.step(a)
+    assert bool(done[7]) and int(done.sum()) == 1
+    s = env.sim.get_state()
+    assert torch.isfinite(s).all() and not s[7, 0:3].any()
+    assert torch.isfinite(rew[torch.arange(n, device="cuda") != 7]).all()
+    assert env.sim.sync() == 0  # the reset cleared the env's non-finite flag
+    # the others advanced exactly as they would have with zero throttles everywhere
+    twin = MarineEnv(n, task="station", vehicle=0, sub_steps=k, seed=4)
+    twin.step(torch.zeros((n, 6), device="cuda"))
+    twin.step(torch.zeros((n, 6), device="cuda"))
+    keep = torch.arange(n, device="cuda") != 7
+    assert torch.equal(s[keep], twin.sim.get_state()[keep])
+    env.close()
+    twin.close()

@@ -458,7 +458,10 @@ typedef struct {
 /* Create a pool on the current device; params host [n_types].  Errors as mg_create. */
 mg_status mg_pool_create(int64_t capacity_envs, const mg_vehicle_params *params, int32_t n_types,
                          mg_pool **out);
+/* Wait for the device and free the pool's arena, planes and staging buffers (a job's traj
+ * buffer stays the caller's).  NULL is a no-op. */
 mg_status mg_pool_destroy(mg_pool *pool);
+/* Stream every later pool call runs on (a cudaStream_t; NULL = the legacy default stream). */
 mg_status mg_pool_set_stream(mg_pool *pool, void *cuda_stream);
 
 /* Admit a job: takes a free range of spec->n_envs envs, randomises and resets them (asynchronous
